@@ -1,0 +1,190 @@
+"""Pins of the oracle's solid part: phase-field advection (Eq. phase_advection, Sec. 3.3),
+MPF kinetics (Eq. sim_proc_phase_field_dynamics), rigid-body integrator (Sec. 3.1.1) and
+solid-solid repulsion (Eqs. soild_solid_potential, solid_solid_force)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _sphere(n=(24, 20, 22), center=(10.0, 9.0, 11.0), R=5.0, **kw):
+    o = oracle.Oracle(*n, **kw)
+    o.add_body("sphere", center, radius=R, mass_density=2.0, wetting_rho=1.0)
+    o.init_fluid(1.0, 1.0)
+    return o
+
+
+def test_initial_profile_and_body_properties():
+    # sin profile across the interface: 1 inside d <= -eta/2, 0 outside, 1/2 on the surface
+    o = _sphere(center=(10.0, 9.0, 11.0), R=5.0)
+    phi = o.phi(0)
+    assert phi[11, 9, 10] == 1.0 and phi[11, 9, 10 + 5] == 0.5 and phi[11, 9, 10 + 8] == 0.0
+    assert abs(phi[11, 9, 16] - (0.5 - 0.5 * math.sin(math.pi / 5))) < 1e-15
+    b = o.bodies()
+    assert np.abs(b["X"][0] - [10, 9, 11]).max() < 1e-12  # centroid of a symmetric field
+    M = b["M"][0]
+    assert abs(M - 2.0 * phi.sum()) < 1e-9
+    # a rasterised sphere has a nearly isotropic inertia; for the radial profile phi(r) the
+    # continuum values are M = 4 pi rho int phi r^2 dr and I = (8 pi / 3) rho int phi r^4 dr
+    I = b["I"][0]
+    assert np.abs(I - np.diag(np.diag(I))).max() < 1e-9 * I[0, 0]
+    from scipy.integrate import quad
+    prof = lambda r: 1.0 if r <= 2.5 else (0.0 if r >= 7.5 else 0.5 - 0.5 * math.sin(math.pi * (r - 5) / 5))
+    m2 = quad(lambda r: prof(r) * r * r, 0, 7.5, points=[2.5])[0]
+    m4 = quad(lambda r: prof(r) * r ** 4, 0, 7.5, points=[2.5])[0]
+    assert abs(M / (4 * math.pi * 2.0 * m2) - 1) < 0.01
+    assert abs(I[0, 0] / (8 * math.pi / 3 * 2.0 * m4) - 1) < 0.02
+
+
+def test_zero_velocity_is_identity():
+    o = _sphere()
+    p0 = o.phi(0).copy()
+    o.phase_only(kinetics=False)
+    assert np.array_equal(o.phi(0), p0)
+
+
+@pytest.mark.parametrize("V", [(1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.0, 0.0, 1.0)])
+def test_unit_courant_advection_is_exact_shift(V):
+    # |u| = 1: the MUSCL face value reduces to the upwind cell value and the conservative update
+    # moves the field by exactly one cell in the direction of u (checks the sign of the
+    # advection term and the flux indexing of each sweep).
+    o = _sphere()
+    p0 = o.phi(0).copy()
+    o.set_body_velocity(0, V=V)
+    o.phase_only(kinetics=False)
+    shift = (int(V[2]), int(V[1]), int(V[0]))
+    assert np.abs(o.phi(0) - np.roll(p0, shift, axis=(0, 1, 2))).max() < 1e-15
+
+
+def test_constant_velocity_conserves_volume_and_stays_bounded():
+    # conservative flux form: sum phi is conserved; MC limiter: no new extrema (no clamping
+    # needed: min >= 0 and max <= 1 before the clamp is checked through the sum).
+    o = _sphere()
+    v0 = o.phi(0).sum()
+    o.set_body_velocity(0, V=(0.31, -0.17, 0.44))
+    for _ in range(25):
+        o.phase_only(kinetics=False)
+    p = o.phi(0)
+    assert abs(p.sum() - v0) < 1e-11 * v0
+    assert p.min() >= 0.0 and p.max() <= 1.0
+    # the centroid moved by 25 u (periodic box, minimum image)
+    idx = np.indices(p.shape).astype(float)
+    exp = [11 + 25 * 0.44, 9 - 25 * 0.17, 10 + 25 * 0.31]
+    for a, n in enumerate(p.shape):
+        rel = (idx[a] - exp[a] + n / 2) % n - n / 2  # minimum image about the expected centre
+        assert abs((p * rel).sum() / p.sum()) < 0.05, a
+
+
+def test_rotation_keeps_sphere_volume():
+    o = _sphere()
+    v0 = o.phi(0).sum()
+    o.set_body_velocity(0, W=(0.0, 0.0, 0.05))
+    for _ in range(10):
+        o.phase_only(kinetics=False)
+    p = o.phi(0)
+    assert abs(p.sum() - v0) < 1e-11 * v0
+    # a rotating sphere stays put (divergence-free rigid rotation)
+    idx = np.indices(p.shape).astype(float)
+    assert abs((p * idx[2]).sum() / p.sum() - 10.0) < 0.02
+
+
+def _flat_plate(mobility):
+    # a slab that spans the periodic x-y plane: the interface is flat
+    o = oracle.Oracle(8, 8, 40, mpf_kinetics=1, mobility=mobility, sigma_sf=1.0)
+    o.add_body("box", (3.5, 3.5, 20.0), half=(50.0, 50.0, 8.0), wetting_rho=1.0, fixed=True)
+    o.init_fluid(1.0, 1.0)
+    return o
+
+
+def test_kinetics_flat_profile_is_nearly_stationary():
+    # the sin profile makes I_solid - I_fluid vanish in the continuum; the discrete 7-point
+    # Laplacian and the kinks where the profile meets 0 and 1 leave a residual an order of
+    # magnitude below the scale M sigma pi^2 / eta^2
+    M = 1e-2
+    o = _flat_plate(M)
+    p0 = o.phi(0).copy()
+    o.phase_only(kinetics=True)
+    assert np.abs(o.phi(0) - p0).max() < 0.1 * M * (math.pi / 5) ** 2
+    v0 = p0.sum()
+    for _ in range(50):
+        o.phase_only(kinetics=True)
+    assert abs(o.phi(0).sum() - v0) < 1e-3 * v0
+
+
+def test_kinetics_volume_restoration_saturates():
+    # A sphere's curvature makes Eq. sim_proc_phase_field_dynamics shrink it. The Delta g term
+    # (Sec. 3.3) returns (M/N) of the volume deficit per step, so the deficit saturates instead of
+    # growing until the sphere vanishes.
+    o = _sphere(mpf_kinetics=1, mobility=0.05, sigma_sf=0.05)
+    v0 = o.phi(0).sum()
+    d = []
+    for _ in range(4):
+        for _ in range(100):
+            o.phase_only(kinetics=True)
+        d.append((v0 - o.phi(0).sum()) / v0)
+    assert 0 < d[-1] < 0.05
+    assert d[3] - d[2] < 0.1 * d[3]
+    p = o.phi(0)
+    assert p.min() >= 0 and p.max() <= 1
+
+
+def test_kinetics_single_phase_region_unchanged():
+    # where only one phase is active (deep inside or far outside) nothing changes
+    o = _sphere(mpf_kinetics=1, mobility=0.05)
+    p0 = o.phi(0).copy()
+    o.phase_only(kinetics=True)
+    p1 = o.phi(0)
+    assert p1[11, 9, 10] == 1.0 and p1[0, 0, 0] == 0.0
+    inside = p0 == 1.0
+    # cells whose 6-neighbourhood is entirely solid phase keep phi = 1
+    core = inside & np.roll(inside, 1, 0) & np.roll(inside, -1, 0) & np.roll(inside, 1, 1) & \
+        np.roll(inside, -1, 1) & np.roll(inside, 1, 2) & np.roll(inside, -1, 2)
+    assert np.all(p1[core] == 1.0)
+
+
+def test_integrator_closed_form():
+    # P14: semi-implicit Euler with dt = 1 under a constant force:
+    # X_n = X_0 + n (n + 1) / 2 F / M; under a constant torque about a principal axis of an
+    # (isotropic) sphere the rotation angle is n (n + 1) / 2 T / I.
+    o = _sphere(n=(40, 40, 40), center=(20.0, 20.0, 20.0), R=6.0)
+    b = o.bodies()
+    M, I = b["M"][0], b["I"][0][2, 2]
+    F = np.array([0.3, -0.1, 0.2]) * M * 1e-3
+    T = np.array([0.0, 0.0, 1.0]) * I * 1e-4
+    n = 12
+    for _ in range(n):
+        o.integrate_body(0, F, T)
+    b = o.bodies()
+    assert np.allclose(b["X"][0], np.array([20.0, 20.0, 20.0]) + n * (n + 1) / 2 * F / M, rtol=0, atol=1e-12)
+    assert np.allclose(b["V"][0], n * F / M, rtol=1e-12)
+    # inertia of the rasterised sphere is isotropic to ~1e-12, so omega stays along z
+    ang = 2 * math.acos(min(1.0, b["Q"][0][0]))
+    assert abs(ang - n * (n + 1) / 2 * 1e-4 * I / b["I"][0][2, 2]) < 1e-9
+    assert abs(b["Q"][0][3]) > 0 and abs(b["Q"][0][1]) < 1e-9
+
+
+def _two_points(dvec):
+    # Two one-point bodies: a sphere of radius 1/2 centred on a cell has exactly that cell with
+    # phi >= 1/2 (phi = 0.65 there, 0.35 at the face neighbours) and no solid cells.
+    o = oracle.Oracle(16, 16, 16, e0=1e-3, rc=3.0, nrep=4)
+    o.add_body("sphere", (7.0, 7.0, 7.0), radius=0.5, mass_density=1.0, wetting_rho=1.0, fixed=True)
+    o.add_body("sphere", (7.0 + dvec[0], 7.0 + dvec[1], 7.0 + dvec[2]), radius=0.5, mass_density=1.0,
+               wetting_rho=1.0, fixed=True)
+    o.init_fluid(1.0, 1.0)
+    o.step(1)
+    return o.body_forces()[2]
+
+
+@pytest.mark.parametrize("d", [(1, 0, 0), (0, 2, 0), (1, 1, 1), (2, 2, 0), (0, 0, 3), (2, 2, 1)])
+def test_repulsion_single_pair_closed_form(d):
+    parts = _two_points(d)
+    r = math.sqrt(sum(x * x for x in d))
+    rc, n, e0 = 3.0, 4, 1e-3
+    mag = e0 * n / rc * abs((r - rc) / rc) ** (n - 1) if r < rc else 0.0
+    exp_A = -np.array(d, float) / r * mag  # pushes body 0 away from body 1
+    FA, FB = parts[0, 2, :3], parts[1, 2, :3]
+    assert np.allclose(FA, exp_A, rtol=1e-12, atol=1e-18)
+    assert np.allclose(FB, -exp_A, rtol=1e-12, atol=1e-18)
+    assert np.abs(parts[:, 2, 3:]).max() < 1e-18  # arm = 0 for a one-point body at its centre
