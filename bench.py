@@ -1,0 +1,288 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the capillary-bridge time step on GB300.
+
+Workload (default): two free spheres R = 20 joined by a liquid bridge in a 128 x 128 x 256 periodic
+box, D3Q19, FP32 populations, phase-field kinetics on (the two-sphere set-up of Sec. 4.3.1 at
+R = 20). One step = the whole hot path: pull streaming + bounce-back, density/psi, Shan-Chen force,
+Guo-BGK collision, FP64 body reductions, repulsion, rigid-body update, phase-field advection and
+kinetics, flags and refill.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--precision fp32]
+
+N > 1 runs under torchrun as independent replicas (one per GPU, no collective: the step does not
+shard across GPUs in this build); value = cells x steps summed over ranks / max time.
+--impl reference times the FP64 CPU oracle (the slow, plain implementation the CUDA path is
+checked against) on the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic bytes per cell update of the collision kernel: read 19 populations, write 19,
+# read the uint16 flag (the density pass and psi are implementation overhead)
+POP_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
+KERNELS_PER_STEP = 11  # density, collide, repulsion, bodies, 3 sweeps, kinetics, flags, refill, + diag memset
+
+
+def alg_bytes_per_cell(prec):
+    return 2 * 19 * POP_BYTES[prec] + 2
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(name, prec):
+    from paper_1902_10432_gb300 import workloads
+
+    if name == "spheres2":
+        return workloads.spheres2(seed=0, prec=prec)
+    if name == "plates48":
+        return workloads.plates48(prec=prec)
+    if name == "tetra4":
+        return workloads.tetra4(seed=0, prec=prec)
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        import statistics
+
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle_steps(w, steps, warmup, threads):
+    import oracle
+    from paper_1902_10432_gb300 import workloads
+
+    kw = {k: v for k, v in w.params.items() if k != "prec"}
+    o = oracle.Oracle(w.nx, w.ny, w.nz, nthreads=threads, **kw)
+    workloads.build(o, w)
+    if warmup:
+        o.step(warmup)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline(w, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample: the same lattice, a few steps."""
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    times = run_oracle_steps(w, 1, 0, threads)
+    per = times[0]
+    n = max(1, min(20, int((budget_s - (time.perf_counter() - t0)) / max(per, 1e-3))))
+    times += run_oracle_steps(w, n, 0, threads) if n > 1 else []
+    steps = len(times)
+    tot = sum(times)
+    return {"value": w.ncells * steps / tot / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": "%s %dx%dx%d, %d time steps of the FP64 oracle (set-up excluded)" % (w.name, w.nx, w.ny, w.nz,
+                                                                                         steps)}
+
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = workload(args.workload, args.precision)
+    threads = os.cpu_count() or 1
+    times = run_oracle_steps(w, args.steps, args.warmup, threads)
+    tot = sum(times)
+    value = w.ncells * len(times) / tot / 1e6
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "%s %dx%dx%d D3Q19, 2 free spheres R=20" % (w.name, w.nx, w.ny, w.nz),
+                       "cells": w.ncells, "inputs_vs_l2": "CPU run"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": "%d time steps after %d warm-up steps, full lattice" % (args.steps, args.warmup)},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_cuda(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+
+    if not os.path.exists(os.path.join(ROOT, "paper_1902_10432_gb300", "_lib", "libcbl.so")):
+        __graft_entry__.build()
+    from paper_1902_10432_gb300 import cbl, workloads
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    w = workload(args.workload, args.precision)
+    prec = args.precision
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sim = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
+    workloads.build(sim, w)
+    stream = sim.stream
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * w.ncells * args.steps / (ms_max * 1e-3) / 1e6
+
+    # per-kernel durations (CUDA events between the phases, same stream, kernel-by-kernel launch)
+    phases = sim.time_phases(max(3, min(args.steps, 20)))
+    mass = sim.total_mass()
+    err = sim.info()["device_error"]
+    sim.close()
+    del sim
+
+    # end-to-end through the C ABI with host buffers: set-up from the host mask, K steps, fields back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
+    workloads.build(s2, w)
+    s2.step(args.steps)
+    rho, vel, phf = s2.fields()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    h2d = w.ncells * (1 + 8)  # liquid mask -> initial density field uploaded by cbl_init_fluid
+    d2h = w.ncells * (8 + 24 + 8)
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        bpc = alg_bytes_per_cell(prec)
+        t_col = phases["collide"] * 1e-3
+        achieved = bpc * w.ncells / t_col / 1e9
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[prec], "data": "synthetic",
+            "config": {"workload": "%s %dx%dx%d D3Q19, 2 free spheres R=20, %s populations, MPF kinetics on"
+                                   % (w.name, w.nx, w.ny, w.nz, prec),
+                       "cells": w.ncells, "seed": w.meta.get("seed"), "theta_deg": w.meta.get("theta_deg"),
+                       "liquid_fraction_of_solid": round(w.meta.get("liquid_fraction_of_solid", 0), 4),
+                       "inputs_vs_l2": "populations 2 x %.0f MB > 129 MB L2 (no flush needed)"
+                                       % (w.ncells * 19 * POP_BYTES[prec] / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "alg_bytes_per_cell": bpc,
+                         "step_frac": bpc * w.ncells / (ms_max / args.steps * 1e-3) / 1e9 / peak},
+            "phases_ms": {k: round(v, 5) for k, v in phases.items()},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": clk.summary(),
+            "e2e": {"value": w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "what": "create + bodies + init from host mask + K steps + fields to host, wall clock"},
+            "fluid_mass": mass, "device_error": err,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
+    ap.add_argument("--workload", default="spheres2", choices=["spheres2", "plates48", "tetra4"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args, rank, world)
+    return bench_cuda(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

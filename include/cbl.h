@@ -1,0 +1,176 @@
+/*
+ * cbl.h -- C ABI of the GB300 (sm_103a) capillary-bridge library: one time step of the combined
+ * multi-phase-field / lattice-Boltzmann method of Schiedung, Tegeler, Medvedev and Varnik,
+ * "Simulation of Capillary-Driven Kinetics with Multi-Phase-Field and Lattice-Boltzmann Method"
+ * (arXiv:1902.10432).
+ *
+ * The calls follow the paper's statement of the problem: set up the lattice and the solid bodies
+ * given as phase fields (Sec. 3.1), initialise the fluid (Sec. 3.2), advance N time steps
+ * (Sec. 3.2.1-3.3), read the fluid fields, read the per-body force and torque
+ * (Sec. 3.2.2 Eq. solid_liquid_force, Sec. 3.2.3), read or move the bodies (Sec. 3.1.1).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a cbl_status; nothing is thrown across the boundary. On failure
+ *    cbl_last_error() describes the cause.
+ *  - Lattice cells are indexed n = x + nx * (y + ny * z), periodic in all three axes; arrays of
+ *    vectors are [cell][3].
+ *  - Device memory is obtained only through the caller's cbl_allocator (NULL = cudaMalloc) and is
+ *    released by cbl_destroy. Output buffers are owned by the caller.
+ *  - Work is enqueued on the stream given in cbl_params; NULL makes the library create a
+ *    non-blocking stream of its own (the legacy default stream cannot be captured into the CUDA
+ *    graph that cbl_step replays). cbl_step returns before the work finishes; every cbl_read_* /
+ *    cbl_get_* call synchronises that stream first. One context must not be used from two host
+ *    threads at once.
+ *  - Wrong call order (e.g. cbl_step before cbl_init_fluid) returns CBL_ERR_STATE.
+ *  - Solid cells read back zero density and velocity.
+ */
+#ifndef CBL_H
+#define CBL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cbl_ctx cbl_ctx; /* opaque, library-owned */
+
+typedef enum {
+  CBL_OK = 0,
+  CBL_ERR_ARG = 1,         /* invalid argument (size, pointer, parameter out of range) */
+  CBL_ERR_STATE = 2,       /* wrong call order, or a device-side consistency check failed */
+  CBL_ERR_OOM = 3,         /* the allocator returned NULL */
+  CBL_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  CBL_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+  CBL_ERR_UNSTABLE = 6,    /* NaN / Inf in the fluid mass */
+  CBL_ERR_UNSUPPORTED = 7  /* feature not built (e.g. a velocity set other than D3Q19) */
+} cbl_status;
+
+/* Storage precision of the lattice-Boltzmann populations. Arithmetic is FP64 for CBL_FP64 and FP32
+ * otherwise. CBL_FP16DEV stores h_i = f_i - w_i in binary16 (w_i rounded to binary16), halving
+ * the population bytes. Phase fields, body reductions and the rigid-body integrator are FP64 in
+ * every mode. */
+typedef enum { CBL_FP64 = 0, CBL_FP32 = 1, CBL_FP16DEV = 2 } cbl_prec;
+
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user); /* device memory, >= 256-byte aligned, NULL on failure */
+  void (*free)(void* ptr, void* user);
+  void* user;
+} cbl_allocator;
+
+typedef struct {
+  int nx, ny, nz;          /* lattice size, each >= 4 */
+  int q;                   /* velocity set: 19 (D3Q19) */
+  double tau;              /* BGK relaxation time (Eq. lb_collision), > 0.5 */
+  double G;                /* Shan-Chen coupling (Eq. benzi_force), paper: -5 */
+  double rho0;             /* reference density of psi (Eq. mean_field_potential), paper: 1 */
+  double ext_force[3];     /* uniform external force density on fluid cells (0 in the paper) */
+  cbl_prec prec;
+  int mpf_kinetics;        /* 1: Eq. sim_proc_phase_field_dynamics after advection (Sec. 3.3) */
+  double mobility;         /* M_alpha_beta, paper: 1e-5 */
+  double eta;              /* interface width, paper: 5 */
+  double sigma_sf;         /* solid-fluid interface energy (not given in the paper) */
+  double sigma_ss;         /* solid-solid interface energy (not given in the paper) */
+  double e0;               /* repulsion strength (Eq. soild_solid_potential; not given) */
+  double rc;               /* repulsion range, paper: 3 */
+  int nrep;                /* repulsion exponent n, paper: 4 */
+  double solid_threshold;  /* a cell is solid iff its fluid phase < this; paper: 0.05 */
+  double member_threshold; /* a cell is a repulsion point of body B iff phi_B >= this */
+  void* stream;            /* cudaStream_t (not the legacy default stream), or NULL */
+} cbl_params;
+
+/* Solid body. The shape gives the phi = 1/2 surface; the phase field is the profile
+ * 1/2 - 1/2 sin(pi d / eta) of the signed distance d across |d| < eta/2 (Sec. 3.1). */
+typedef struct {
+  int shape;             /* 0 sphere, 1 box */
+  double center[3];      /* lattice coordinates; cell centres sit on integers */
+  double radius;         /* sphere */
+  double half[3];        /* box half extents in the body frame */
+  double quat[4];        /* initial orientation (w, x, y, z); zero = identity */
+  double mass_density;   /* rho_alpha: M = rho_alpha * sum phi */
+  double wetting_rho;    /* varrho_B: solid cells act as fluid of this density (Sec. 3.2.3) */
+  int fixed;             /* 1: the body never moves (forces are still reported) */
+} cbl_body;
+
+/* Create a context. Validates the parameters (CBL_ERR_ARG) and allocates the lattice arrays through
+ * `alloc` (NULL = cudaMalloc; CBL_ERR_OOM if it fails). `out` receives the context, owned by the
+ * caller until cbl_destroy. */
+cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_ctx** out);
+
+/* Add a solid body (before cbl_init_fluid). Its phase-field tile is allocated here. `body_id`
+ * (may be NULL) receives the 0-based id. */
+cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id);
+
+/* Initialise the phase fields, obstacle flags (Sec. 3.2.2: solid iff fluid phase < threshold),
+ * body mass, centre of mass and inertia, and the fluid: f = f_eq(rho, 0) with rho = rho_liquid
+ * where liquid_mask_host[n] != 0 and rho_vapour elsewhere (mask may be NULL: all vapour).
+ * The mask is a host array of nx*ny*nz bytes. */
+cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour,
+                          const unsigned char* liquid_mask_host);
+
+/* Same, from per-cell density and velocity (host arrays of N and 3N doubles; u may be NULL). */
+cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const double* u_host);
+
+/* Advance nsteps time steps (asynchronous on the context's stream). One step: pull streaming with
+ * half-way moving-wall bounce-back and local mass correction (Sec. 3.2.2), moments and psi,
+ * Shan-Chen force with wetting (Sec. 3.2.3), Guo-forced BGK collision (Sec. 3.2.1), per-body
+ * momentum-exchange and adhesion force/torque in FP64, solid-solid repulsion (Sec. 3.1.2),
+ * rigid-body update (Sec. 3.1.1), phase-field advection and kinetics (Sec. 3.1.1, 3.3), obstacle
+ * flags with cover refill / uncover (Sec. 3.2.2). The density and velocity of the last step of
+ * each call are kept for cbl_read_fields. */
+cbl_status cbl_step(cbl_ctx* ctx, int nsteps);
+
+/* Fields of the last completed step: rho (N), vel (3N, [cell][3]) as computed in that step's
+ * collision, and the fluid phase 1 - sum_B phi_B (N). Any pointer may be NULL. on_device != 0:
+ * the pointers are device pointers; otherwise host pointers. */
+cbl_status cbl_read_fields(cbl_ctx* ctx, double* rho, double* vel, double* phi_fluid, int on_device);
+
+/* Obstacle flags: solid (N bytes, 0/1) and owner body id (N int32, -1 on fluid). Host pointers. */
+cbl_status cbl_read_flags(cbl_ctx* ctx, unsigned char* solid, int32_t* owner);
+
+/* Dense phase field of one body (N doubles, host). */
+cbl_status cbl_read_phi(cbl_ctx* ctx, int body, double* phi_host);
+
+/* Per-body total force F (nb*3) and torque T (nb*3) of the last completed step, FP64, and, if parts
+ * is not NULL, the parts (nb*18): momentum exchange F,T | Shan-Chen adhesion F,T | repulsion F,T.
+ * Host pointers; any may be NULL. */
+cbl_status cbl_read_body_forces(cbl_ctx* ctx, double* F, double* T, double* parts);
+
+/* Body state (host arrays, nb*3 / nb*4 / nb / nb*9; any may be NULL): centre of mass, velocity,
+ * angular velocity, orientation quaternion, mass, body-frame inertia. */
+cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double* Q, double* M,
+                          double* I);
+
+/* Set body velocities (host arrays nb*3, either may be NULL). */
+cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W);
+
+/* Fluid mass sum_x rho(x) over fluid cells in the last completed step, FP64. Returns
+ * CBL_ERR_UNSTABLE if it is not finite. */
+cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass);
+
+/* Number of bodies, cells; device error word (0 = none; bit 0 tile overflow, bit 1 neighbour
+ * list overflow, bit 2 lost refill). */
+cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_error);
+
+/* Phases of one step, in launch order, as reported by cbl_time_phases. */
+#define CBL_NPHASES 8
+/* 0 pull + density + psi, 1 pull + force + collision + body/mass reductions, 2 solid-solid
+ * repulsion, 3 rigid-body update, 4 phase-field advection (three sweeps), 5 phase-field kinetics,
+ * 6 obstacle flags, 7 cover refill. */
+
+/* Run nsteps time steps launched kernel by kernel (not through the graph) with CUDA events recorded
+ * on the context's stream between the phases, synchronise, and write the mean duration per step of
+ * each phase in milliseconds to ms[CBL_NPHASES] (host array). The state advances by nsteps. */
+cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
+
+/* Release every device allocation and the context. */
+cbl_status cbl_destroy(cbl_ctx* ctx);
+
+/* Human-readable description of the last failure on this context (never NULL). */
+const char* cbl_last_error(const cbl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBL_H */

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of the C ABI in include/cbl.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_lib/libcbl.so``; this module only converts
+arguments. Device memory comes from PyTorch's caching allocator through the ``cbl_allocator``
+callbacks, and work runs on a PyTorch stream. If the library has not been built the import of
+the library fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libcbl.so")
+
+CBL_FP64, CBL_FP32, CBL_FP16DEV = 0, 1, 2
+PRECISIONS = {"fp64": CBL_FP64, "fp32": CBL_FP32, "fp16dev": CBL_FP16DEV}
+STATUS = {0: "CBL_OK", 1: "CBL_ERR_ARG", 2: "CBL_ERR_STATE", 3: "CBL_ERR_OOM", 4: "CBL_ERR_CUDA",
+          5: "CBL_ERR_TIMEOUT", 6: "CBL_ERR_UNSTABLE", 7: "CBL_ERR_UNSUPPORTED"}
+
+
+class cbl_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("q", ctypes.c_int),
+        ("tau", ctypes.c_double), ("G", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("ext_force", ctypes.c_double * 3),
+        ("prec", ctypes.c_int),
+        ("mpf_kinetics", ctypes.c_int),
+        ("mobility", ctypes.c_double), ("eta", ctypes.c_double),
+        ("sigma_sf", ctypes.c_double), ("sigma_ss", ctypes.c_double),
+        ("e0", ctypes.c_double), ("rc", ctypes.c_double),
+        ("nrep", ctypes.c_int),
+        ("solid_threshold", ctypes.c_double), ("member_threshold", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class cbl_body(ctypes.Structure):
+    _fields_ = [
+        ("shape", ctypes.c_int),
+        ("center", ctypes.c_double * 3),
+        ("radius", ctypes.c_double),
+        ("half", ctypes.c_double * 3),
+        ("quat", ctypes.c_double * 4),
+        ("mass_density", ctypes.c_double),
+        ("wetting_rho", ctypes.c_double),
+        ("fixed", ctypes.c_int),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cbl_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes); the names are those of include/cbl.h
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "cbl_create": (ctypes.c_int, [ctypes.POINTER(cbl_params), ctypes.POINTER(cbl_allocator), ctypes.POINTER(_P)]),
+    "cbl_add_body": (ctypes.c_int, [_P, ctypes.POINTER(cbl_body), ctypes.POINTER(ctypes.c_int)]),
+    "cbl_init_fluid": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P]),
+    "cbl_init_fluid_fields": (ctypes.c_int, [_P, _P, _P]),
+    "cbl_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cbl_read_fields": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "cbl_read_flags": (ctypes.c_int, [_P, _P, _P]),
+    "cbl_read_phi": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "cbl_read_body_forces": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cbl_get_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "cbl_set_body_velocities": (ctypes.c_int, [_P, _P, _P]),
+    "cbl_total_mass": (ctypes.c_int, [_P, _D]),
+    "cbl_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int)]),
+    "cbl_time_phases": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "cbl_destroy": (ctypes.c_int, [_P]),
+    "cbl_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class CblError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _vp(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def torch_allocator(device=None, stream=None):
+    """cbl_allocator backed by PyTorch's caching allocator. Keep the returned object alive."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=stream)
+        except Exception:  # OOM -> NULL, reported by the library as CBL_ERR_OOM
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = cbl_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    a._keep = (_alloc, _free)
+    return a
+
+
+class Sim:
+    """One simulation on the GPU through the C ABI. Arrays are numpy; cell index x + nx*(y + ny*z)."""
+
+    DEFAULTS = dict(q=19, tau=1.0, G=-5.0, rho0=1.0, ext_force=(0.0, 0.0, 0.0), prec="fp32",
+                    mpf_kinetics=0, mobility=1e-5, eta=5.0, sigma_sf=3.583e-2, sigma_ss=0.5 * 3.583e-2,
+                    e0=1e-3, rc=3.0, nrep=4, solid_threshold=0.05, member_threshold=0.5)
+
+    def __init__(self, nx, ny, nz, use_torch=True, **kw):
+        self._lib = load()
+        cfg = dict(self.DEFAULTS)
+        unknown = set(kw) - set(cfg)
+        if unknown:
+            raise TypeError("unknown parameters: %s" % sorted(unknown))
+        cfg.update(kw)
+        p = cbl_params()
+        p.nx, p.ny, p.nz = nx, ny, nz
+        for k, v in cfg.items():
+            if k == "ext_force":
+                p.ext_force[:] = list(v)
+            elif k == "prec":
+                p.prec = PRECISIONS[v] if isinstance(v, str) else int(v)
+            else:
+                setattr(p, k, v)
+        self._alloc = None
+        self._stream = None
+        if use_torch:
+            import torch
+
+            # a stream of its own: the legacy default stream cannot be captured into a graph
+            self._stream = torch.cuda.Stream()
+            p.stream = ctypes.c_void_p(self._stream.cuda_stream)
+            self._alloc = torch_allocator(stream=self._stream)
+        self.params = cfg
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        h = ctypes.c_void_p()
+        st = self._lib.cbl_create(ctypes.byref(p), ctypes.byref(self._alloc) if self._alloc else None,
+                                  ctypes.byref(h))
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(None).decode())
+        self._h = h
+        self.nb = 0
+
+    def _ck(self, st):
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cbl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_body(self, shape, center, radius=0.0, half=(0.0, 0.0, 0.0), quat=(1.0, 0.0, 0.0, 0.0),
+                 mass_density=4.0, wetting_rho=2.0, fixed=False):
+        b = cbl_body()
+        b.shape = {"sphere": 0, "box": 1}[shape] if isinstance(shape, str) else int(shape)
+        b.center[:] = [float(v) for v in center]
+        b.radius = float(radius)
+        b.half[:] = [float(v) for v in half]
+        b.quat[:] = [float(v) for v in quat]
+        b.mass_density = float(mass_density)
+        b.wetting_rho = float(wetting_rho)
+        b.fixed = int(bool(fixed))
+        bid = ctypes.c_int()
+        self._ck(self._lib.cbl_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)))
+        self.nb += 1
+        return bid.value
+
+    def init_fluid(self, rho_l, rho_v, mask=None):
+        m = None if mask is None else np.ascontiguousarray(mask, np.uint8).reshape(-1)
+        self._ck(self._lib.cbl_init_fluid(self._h, float(rho_l), float(rho_v), _vp(m)))
+
+    def init_fluid_fields(self, rho, u=None):
+        r = np.ascontiguousarray(rho, np.float64).reshape(-1)
+        uu = None if u is None else np.ascontiguousarray(u, np.float64).reshape(-1)
+        self._ck(self._lib.cbl_init_fluid_fields(self._h, _vp(r), _vp(uu)))
+
+    def step(self, n=1):
+        self._ck(self._lib.cbl_step(self._h, int(n)))
+
+    def fields(self):
+        rho = np.empty(self.N)
+        vel = np.empty(3 * self.N)
+        phf = np.empty(self.N)
+        self._ck(self._lib.cbl_read_fields(self._h, _vp(rho), _vp(vel), _vp(phf), 0))
+        return rho.reshape(self.shape), vel.reshape(self.shape + (3,)), phf.reshape(self.shape)
+
+    def fields_device(self, rho, vel=None, phi_fluid=None):
+        """Read into device tensors (torch, float64, contiguous)."""
+        ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        self._ck(self._lib.cbl_read_fields(self._h, ptr(rho), ptr(vel), ptr(phi_fluid), 1))
+
+    def flags(self):
+        s = np.empty(self.N, np.uint8)
+        o = np.empty(self.N, np.int32)
+        self._ck(self._lib.cbl_read_flags(self._h, _vp(s), _vp(o)))
+        return s.reshape(self.shape), o.reshape(self.shape)
+
+    def phi(self, body):
+        out = np.empty(self.N)
+        self._ck(self._lib.cbl_read_phi(self._h, int(body), _vp(out)))
+        return out.reshape(self.shape)
+
+    def body_forces(self):
+        nb = self.nb
+        F = np.empty(3 * nb)
+        T = np.empty(3 * nb)
+        parts = np.empty(18 * nb)
+        self._ck(self._lib.cbl_read_body_forces(self._h, _vp(F), _vp(T), _vp(parts)))
+        return F.reshape(nb, 3), T.reshape(nb, 3), parts.reshape(nb, 3, 6)
+
+    def bodies(self):
+        nb = self.nb
+        X, V, W = (np.empty(3 * nb) for _ in range(3))
+        Q = np.empty(4 * nb)
+        M = np.empty(nb)
+        I = np.empty(9 * nb)
+        self._ck(self._lib.cbl_get_bodies(self._h, _vp(X), _vp(V), _vp(W), _vp(Q), _vp(M), _vp(I)))
+        return dict(X=X.reshape(nb, 3), V=V.reshape(nb, 3), W=W.reshape(nb, 3), Q=Q.reshape(nb, 4), M=M,
+                    I=I.reshape(nb, 3, 3))
+
+    def set_body_velocities(self, V=None, W=None):
+        v = None if V is None else np.ascontiguousarray(V, np.float64).reshape(-1)
+        w = None if W is None else np.ascontiguousarray(W, np.float64).reshape(-1)
+        self._ck(self._lib.cbl_set_body_velocities(self._h, _vp(v), _vp(w)))
+
+    def total_mass(self):
+        m = ctypes.c_double()
+        self._ck(self._lib.cbl_total_mass(self._h, ctypes.byref(m)))
+        return m.value
+
+    PHASES = ("density", "collide", "repulsion", "bodies", "advect", "kinetics", "flags", "refill")
+
+    def time_phases(self, n):
+        """Mean per-step duration (ms) of each kernel phase over n steps, CUDA events on the stream."""
+        ms = (ctypes.c_double * len(self.PHASES))()
+        self._ck(self._lib.cbl_time_phases(self._h, int(n), ms))
+        return dict(zip(self.PHASES, list(ms)))
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def info(self):
+        nb = ctypes.c_int()
+        nc = ctypes.c_int64()
+        err = ctypes.c_int()
+        self._ck(self._lib.cbl_info(self._h, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(err)))
+        return dict(nbodies=nb.value, ncells=nc.value, device_error=err.value)

@@ -1,0 +1,514 @@
+// C ABI of the capillary-bridge library: context life cycle, set-up, stepping under a captured
+// CUDA graph, read-out. Declared in include/cbl.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cbl.h"
+#include "cbl_dev.cuh"
+
+using namespace cbl;
+
+struct cbl_ctx {
+  cbl_params p;
+  cbl_allocator alloc;
+  bool user_alloc = false;
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  Lat lat;
+  int prec = 1;
+  size_t elem = 4;
+  PhysParams pp;
+  void *fa = nullptr, *fb = nullptr, *psi = nullptr;
+  uint16_t* flags = nullptr;
+  double *diag_rho = nullptr, *diag_vel = nullptr, *dense = nullptr;
+  std::vector<BodyDev> hb;
+  BodyDev* db = nullptr;
+  double* arena = nullptr;
+  long long arena_n = 0;
+  int max_tile = 0;
+  double *acc = nullptr, *last = nullptr, *volacc = nullptr, *scratch = nullptr;
+  double* mass_part = nullptr;
+  unsigned n_mass_part = 0;
+  StepState* st = nullptr;
+  bool ready = false;
+  long long t = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+static thread_local std::string g_err;
+
+static cbl_status fail(cbl_ctx* c, cbl_status s, const std::string& m) {
+  if (c) c->err = m;
+  else g_err = m;
+  return s;
+}
+
+static cbl_status cuda_check(cbl_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CBL_OK;
+  return fail(c, CBL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                            \
+  do {                                                      \
+    cbl_status _s = cuda_check(ctx, (call), #call);         \
+    if (_s != CBL_OK) return _s;                            \
+  } while (0)
+
+static void* dalloc(cbl_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (c->user_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+static void dfree_all(cbl_ctx* c) {
+  for (void* p : c->allocs) {
+    if (c->user_alloc) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
+  }
+  c->allocs.clear();
+}
+
+extern "C" {
+
+const char* cbl_last_error(const cbl_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_ctx** out) {
+  if (!params || !out) return fail(nullptr, CBL_ERR_ARG, "params and out must not be NULL");
+  const cbl_params& p = *params;
+  if (p.nx < 4 || p.ny < 4 || p.nz < 4) return fail(nullptr, CBL_ERR_ARG, "lattice sides must be >= 4");
+  if (p.q != 19) return fail(nullptr, CBL_ERR_UNSUPPORTED, "only D3Q19 is built");
+  if (!(p.tau > 0.5)) return fail(nullptr, CBL_ERR_ARG, "tau must be > 0.5");
+  if (!(p.rho0 > 0)) return fail(nullptr, CBL_ERR_ARG, "rho0 must be > 0");
+  if (p.prec < CBL_FP64 || p.prec > CBL_FP16DEV) return fail(nullptr, CBL_ERR_ARG, "unknown precision");
+  if (!(p.eta > 0) || !(p.rc > 0) || p.nrep < 1 || p.rc > 6.0)
+    return fail(nullptr, CBL_ERR_ARG, "eta, rc (<= 6) and nrep must be positive");
+  if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, CBL_ERR_ARG, "allocator callbacks missing");
+  cbl_ctx* ctx = new cbl_ctx();
+  ctx->p = p;
+  if (alloc) {
+    ctx->alloc = *alloc;
+    ctx->user_alloc = true;
+  }
+  if (p.stream) {
+    ctx->s = (cudaStream_t)p.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return fail(nullptr, CBL_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    ctx->own_stream = true;
+  }
+  ctx->lat.nx = p.nx;
+  ctx->lat.ny = p.ny;
+  ctx->lat.nz = p.nz;
+  ctx->lat.N = (long long)p.nx * p.ny * p.nz;
+  ctx->prec = (int)p.prec;
+  ctx->elem = p.prec == CBL_FP64 ? 8 : (p.prec == CBL_FP32 ? 4 : 2);
+  PhysParams& pp = ctx->pp;
+  pp.tau = p.tau;
+  pp.G = p.G;
+  pp.rho0 = p.rho0;
+  for (int a = 0; a < 3; ++a) pp.ext[a] = p.ext_force[a];
+  pp.eta = p.eta;
+  pp.mobility = p.mobility;
+  pp.sigma_sf = p.sigma_sf;
+  pp.sigma_ss = p.sigma_ss;
+  pp.e0 = p.e0;
+  pp.rc = p.rc;
+  pp.nrep = p.nrep;
+  pp.solid_threshold = p.solid_threshold;
+  pp.member_threshold = p.member_threshold;
+  pp.mpf = p.mpf_kinetics;
+
+  const size_t N = (size_t)ctx->lat.N;
+  ctx->fa = dalloc(ctx, N * Q * ctx->elem);
+  ctx->fb = dalloc(ctx, N * Q * ctx->elem);
+  ctx->psi = dalloc(ctx, N * (ctx->prec == 0 ? 8 : 4));
+  ctx->flags = (uint16_t*)dalloc(ctx, N * 2);
+  ctx->diag_rho = (double*)dalloc(ctx, N * 8);
+  ctx->diag_vel = (double*)dalloc(ctx, N * 24);
+  ctx->n_mass_part = lbm_blocks(ctx->lat);
+  ctx->mass_part = (double*)dalloc(ctx, (size_t)ctx->n_mass_part * 8);
+  ctx->st = (StepState*)dalloc(ctx, sizeof(StepState));
+  if (!ctx->fa || !ctx->fb || !ctx->psi || !ctx->flags || !ctx->diag_rho || !ctx->diag_vel || !ctx->mass_part ||
+      !ctx->st) {
+    dfree_all(ctx);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+    delete ctx;
+    return fail(nullptr, CBL_ERR_OOM, "device allocation failed");
+  }
+  cudaMemsetAsync(ctx->flags, 0, N * 2, ctx->s);
+  cudaMemsetAsync(ctx->st, 0, sizeof(StepState), ctx->s);
+  set_fp16_weights(ctx->s);
+  set_repulsion_offsets(p.rc, ctx->s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    dfree_all(ctx);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+    delete ctx;
+    return fail(nullptr, CBL_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return CBL_OK;
+}
+
+cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
+  if (!ctx || !body) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "bodies must be added before cbl_init_fluid");
+  if ((int)ctx->hb.size() >= MAX_BODIES) return fail(ctx, CBL_ERR_ARG, "too many bodies");
+  if (body->shape != 0 && body->shape != 1) return fail(ctx, CBL_ERR_ARG, "shape must be 0 (sphere) or 1 (box)");
+  if (!(body->mass_density > 0)) return fail(ctx, CBL_ERR_ARG, "mass_density must be > 0");
+  BodyDev b;
+  std::memset(&b, 0, sizeof(b));
+  b.shape = body->shape;
+  b.radius = body->radius;
+  for (int a = 0; a < 3; ++a) {
+    b.c0[a] = body->center[a];
+    b.half[a] = body->half[a];
+    b.X[a] = b.Xprev[a] = body->center[a];
+  }
+  double qn = std::sqrt(body->quat[0] * body->quat[0] + body->quat[1] * body->quat[1] + body->quat[2] * body->quat[2] +
+                        body->quat[3] * body->quat[3]);
+  for (int a = 0; a < 4; ++a) b.q0[a] = qn > 0 ? body->quat[a] / qn : (a == 0 ? 1.0 : 0.0);
+  for (int a = 0; a < 4; ++a) b.Q[a] = b.q0[a];
+  b.rho_s = body->mass_density;
+  b.wet = body->wetting_rho;
+  b.psi_wet = 1.0 - std::exp(-body->wetting_rho / ctx->p.rho0);
+  b.fixed = body->fixed;
+  // tile: support half-extent + 2 halo layers + 1 cell of motion before recentring
+  double h[3];
+  if (b.shape == 0) {
+    if (!(b.radius > 0)) return fail(ctx, CBL_ERR_ARG, "sphere radius must be > 0");
+    for (int a = 0; a < 3; ++a) h[a] = b.radius;
+  } else {
+    double w = b.q0[0], x = b.q0[1], y = b.q0[2], z = b.q0[3];
+    double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                   2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                   2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+    for (int a = 0; a < 3; ++a) h[a] = std::fabs(R[3 * a]) * b.half[0] + std::fabs(R[3 * a + 1]) * b.half[1] +
+                                       std::fabs(R[3 * a + 2]) * b.half[2];
+  }
+  const int n[3] = {ctx->p.nx, ctx->p.ny, ctx->p.nz};
+  long long sz = 1;
+  for (int a = 0; a < 3; ++a) {
+    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 3.0);
+    int L = 2 * half + 1;
+    if (L >= n[a]) {
+      L = n[a];
+      b.o[a] = 0;
+    } else {
+      b.o[a] = (int)std::floor(b.c0[a] + 0.5) - L / 2;
+    }
+    b.o_prev[a] = b.o[a];
+    b.L[a] = L;
+    sz *= L;
+  }
+  b.sz = sz;
+  b.off = ctx->arena_n;
+  ctx->arena_n += 3 * sz;
+  if (sz > ctx->max_tile) ctx->max_tile = (int)sz;
+  ctx->hb.push_back(b);
+  if (body_id) *body_id = (int)ctx->hb.size() - 1;
+  return CBL_OK;
+}
+
+static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double* u_host) {
+  const size_t N = (size_t)ctx->lat.N;
+  const int nb = (int)ctx->hb.size();
+  if (nb) {
+    ctx->db = (BodyDev*)dalloc(ctx, sizeof(BodyDev) * nb);
+    ctx->arena = (double*)dalloc(ctx, sizeof(double) * (size_t)ctx->arena_n);
+    ctx->acc = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
+    ctx->last = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
+    ctx->volacc = (double*)dalloc(ctx, sizeof(double) * 2 * nb);
+    ctx->scratch = (double*)dalloc(ctx, sizeof(double) * 9 * nb);
+    if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch)
+      return fail(ctx, CBL_ERR_OOM, "device allocation failed (bodies)");
+    CK(cudaMemcpyAsync(ctx->db, ctx->hb.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * ACC_N * nb, ctx->s));
+    CK(cudaMemsetAsync(ctx->last, 0, sizeof(double) * ACC_N * nb, ctx->s));
+    CK(cudaMemsetAsync(ctx->volacc, 0, sizeof(double) * 2 * nb, ctx->s));
+    launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
+    launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 1, ctx->s);
+    launch_body_props(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->scratch, ctx->s);
+  }
+  double* drho = (double*)dalloc(ctx, N * 8);
+  double* du = u_host ? (double*)dalloc(ctx, N * 24) : nullptr;
+  if (!drho || (u_host && !du)) return fail(ctx, CBL_ERR_OOM, "device allocation failed (initial fields)");
+  CK(cudaMemcpyAsync(drho, rho_host, N * 8, cudaMemcpyHostToDevice, ctx->s));
+  if (du) CK(cudaMemcpyAsync(du, u_host, N * 24, cudaMemcpyHostToDevice, ctx->s));
+  launch_init_fluid(ctx->prec, ctx->lat, ctx->fa, ctx->flags, drho, du, ctx->s);
+  CK(cudaMemsetAsync(ctx->diag_rho, 0, N * 8, ctx->s));
+  CK(cudaMemsetAsync(ctx->diag_vel, 0, N * 24, ctx->s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->s));
+  // the initial-field buffers are released right away
+  for (void* q : {(void*)drho, (void*)du}) {
+    if (!q) continue;
+    for (size_t k = 0; k < ctx->allocs.size(); ++k)
+      if (ctx->allocs[k] == q) {
+        if (ctx->user_alloc) ctx->alloc.free(q, ctx->alloc.user);
+        else cudaFree(q);
+        ctx->allocs.erase(ctx->allocs.begin() + k);
+        break;
+      }
+  }
+  ctx->ready = true;
+  ctx->t = 0;
+  return CBL_OK;
+}
+
+cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour, const unsigned char* mask) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "already initialised");
+  if (!(rho_liquid >= 0) || !(rho_vapour >= 0)) return fail(ctx, CBL_ERR_ARG, "densities must be >= 0");
+  std::vector<double> rho((size_t)ctx->lat.N);
+  for (size_t n = 0; n < rho.size(); ++n) rho[n] = (mask && mask[n]) ? rho_liquid : rho_vapour;
+  return init_common(ctx, rho.data(), nullptr);
+}
+
+cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const double* u_host) {
+  if (!ctx || !rho_host) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "already initialised");
+  return init_common(ctx, rho_host, u_host);
+}
+
+static void enqueue_step(cbl_ctx* ctx) {
+  const int nb = (int)ctx->hb.size();
+  launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
+                  ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s);
+  if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
+  launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
+                ctx->s);
+  if (nb) {
+    launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
+    if (ctx->pp.mpf) launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->s);
+    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->s);
+  }
+}
+
+cbl_status cbl_step(cbl_ctx* ctx, int nsteps) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "cbl_step before cbl_init_fluid");
+  if (nsteps < 0) return fail(ctx, CBL_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return CBL_OK;
+  if (!ctx->gexec) {
+    CK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(ctx);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(ctx->s, &ctx->graph);
+    CK(e1);
+    CK(e2);
+    CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+  }
+  // the diag word is tested for non-zero: byte-wise memsets keep the whole call asynchronous
+  CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
+  for (int k = 0; k < nsteps - 1; ++k) CK(cudaGraphLaunch(ctx->gexec, ctx->s));
+  CK(cudaMemsetAsync(&ctx->st->diag, 1, sizeof(int), ctx->s));
+  CK(cudaGraphLaunch(ctx->gexec, ctx->s));
+  ctx->t += nsteps;
+  return CBL_OK;
+}
+
+cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
+  if (!ctx || !ms) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "cbl_time_phases before cbl_init_fluid");
+  if (nsteps <= 0) return fail(ctx, CBL_ERR_ARG, "nsteps must be > 0");
+  const int nb = (int)ctx->hb.size();
+  cudaEvent_t ev[CBL_NPHASES + 1];
+  for (int k = 0; k <= CBL_NPHASES; ++k) CK(cudaEventCreate(&ev[k]));
+  double acc[CBL_NPHASES] = {0};
+  CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
+  for (int it = 0; it < nsteps; ++it) {
+    CK(cudaEventRecord(ev[0], ctx->s));
+    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
+                    ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 1);
+    CK(cudaEventRecord(ev[1], ctx->s));
+    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
+                    ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 2);
+    CK(cudaEventRecord(ev[2], ctx->s));
+    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
+    CK(cudaEventRecord(ev[3], ctx->s));
+    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part,
+                  ctx->st, ctx->s);
+    CK(cudaEventRecord(ev[4], ctx->s));
+    if (nb) launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
+    CK(cudaEventRecord(ev[5], ctx->s));
+    if (nb && ctx->pp.mpf)
+      launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
+    CK(cudaEventRecord(ev[6], ctx->s));
+    if (nb) launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->s);
+    CK(cudaEventRecord(ev[7], ctx->s));
+    if (nb) launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->s);
+    CK(cudaEventRecord(ev[8], ctx->s));
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(ev[8]));
+    for (int k = 0; k < CBL_NPHASES; ++k) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      acc[k] += t;
+    }
+  }
+  for (int k = 0; k <= CBL_NPHASES; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < CBL_NPHASES; ++k) ms[k] = acc[k] / nsteps;
+  ctx->t += nsteps;
+  return CBL_OK;
+}
+
+cbl_status cbl_read_fields(cbl_ctx* ctx, double* rho, double* vel, double* phi_fluid, int on_device) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const size_t N = (size_t)ctx->lat.N;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaStreamSynchronize(ctx->s));
+  if (rho) CK(cudaMemcpyAsync(rho, ctx->diag_rho, N * 8, k, ctx->s));
+  if (vel) CK(cudaMemcpyAsync(vel, ctx->diag_vel, N * 24, k, ctx->s));
+  if (phi_fluid) {
+    if (!ctx->dense && !(ctx->dense = (double*)dalloc(ctx, N * 8))) return fail(ctx, CBL_ERR_OOM, "dense buffer");
+    launch_phi_dense(ctx->lat, ctx->db, (int)ctx->hb.size(), ctx->max_tile, ctx->arena, -1, ctx->dense, ctx->s);
+    CK(cudaMemcpyAsync(phi_fluid, ctx->dense, N * 8, k, ctx->s));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
+cbl_status cbl_read_flags(cbl_ctx* ctx, unsigned char* solid, int32_t* owner) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  std::vector<uint16_t> f((size_t)ctx->lat.N);
+  CK(cudaMemcpyAsync(f.data(), ctx->flags, f.size() * 2, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (size_t n = 0; n < f.size(); ++n) {
+    bool s = f[n] & F_SOLID;
+    if (solid) solid[n] = s ? 1 : 0;
+    if (owner) owner[n] = s ? (int32_t)(f[n] & F_OWNER) : -1;
+  }
+  return CBL_OK;
+}
+
+cbl_status cbl_read_phi(cbl_ctx* ctx, int body, double* phi_host) {
+  if (!ctx || !phi_host) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  if (body < 0 || body >= (int)ctx->hb.size()) return fail(ctx, CBL_ERR_ARG, "body id out of range");
+  const size_t N = (size_t)ctx->lat.N;
+  if (!ctx->dense && !(ctx->dense = (double*)dalloc(ctx, N * 8))) return fail(ctx, CBL_ERR_OOM, "dense buffer");
+  launch_phi_dense(ctx->lat, ctx->db, (int)ctx->hb.size(), ctx->max_tile, ctx->arena, body, ctx->dense, ctx->s);
+  CK(cudaMemcpyAsync(phi_host, ctx->dense, N * 8, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
+cbl_status cbl_read_body_forces(cbl_ctx* ctx, double* F, double* T, double* parts) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const int nb = (int)ctx->hb.size();
+  if (!nb) return CBL_OK;
+  std::vector<double> h((size_t)nb * ACC_N);
+  CK(cudaMemcpyAsync(h.data(), ctx->last, h.size() * 8, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (int b = 0; b < nb; ++b) {
+    const double* a = &h[(size_t)b * ACC_N];
+    for (int k = 0; k < 3; ++k) {
+      if (F) F[3 * b + k] = a[ACC_MOM_F + k] + a[ACC_ADH_F + k] + a[ACC_REP_F + k];
+      if (T) T[3 * b + k] = a[ACC_MOM_T + k] + a[ACC_ADH_T + k] + a[ACC_REP_T + k];
+    }
+    if (parts)
+      for (int k = 0; k < ACC_N; ++k) parts[(size_t)b * ACC_N + k] = a[k];
+  }
+  return CBL_OK;
+}
+
+cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double* Qo, double* M, double* I) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const int nb = (int)ctx->hb.size();
+  if (!nb) return CBL_OK;
+  std::vector<BodyDev> h(nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (int b = 0; b < nb; ++b) {
+    for (int a = 0; a < 3; ++a) {
+      if (X) X[3 * b + a] = h[b].X[a];
+      if (V) V[3 * b + a] = h[b].V[a];
+      if (W) W[3 * b + a] = h[b].W[a];
+    }
+    if (Qo)
+      for (int a = 0; a < 4; ++a) Qo[4 * b + a] = h[b].Q[a];
+    if (M) M[b] = h[b].M;
+    if (I)
+      for (int a = 0; a < 9; ++a) I[9 * b + a] = h[b].Ib[a];
+  }
+  return CBL_OK;
+}
+
+cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const int nb = (int)ctx->hb.size();
+  if (!nb) return CBL_OK;
+  std::vector<BodyDev> h(nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (int b = 0; b < nb; ++b)
+    for (int a = 0; a < 3; ++a) {
+      if (V) h[b].V[a] = V[3 * b + a];
+      if (W) h[b].W[a] = W[3 * b + a];
+    }
+  CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
+cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass) {
+  if (!ctx || !mass) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  StepState h;
+  CK(cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  *mass = h.last_mass;
+  if (!std::isfinite(h.last_mass)) return fail(ctx, CBL_ERR_UNSTABLE, "fluid mass is not finite");
+  return CBL_OK;
+}
+
+cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_error) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (nbodies) *nbodies = (int)ctx->hb.size();
+  if (ncells) *ncells = ctx->lat.N;
+  if (device_error) {
+    StepState h;
+    CK(cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    *device_error = h.err;
+  }
+  return CBL_OK;
+}
+
+cbl_status cbl_destroy(cbl_ctx* ctx) {
+  if (!ctx) return CBL_OK;
+  cudaStreamSynchronize(ctx->s);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  dfree_all(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+  delete ctx;
+  return CBL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal device-side definitions of the capillary-bridge library (not part of the C ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace cbl {
+
+// ------------------------------------------------------------------------------------------
+// D3Q19 velocity set (Sec. 3.2.1 gives D3Q27; D3Q19 is the textbook |c|^2 <= 2 subset with
+// weights 1/3, 1/18, 1/36). Order: rest, +-x, +-y, +-z, then the 12 edge directions; each odd
+// index i is followed by its opposite, so opp(i) = i + 1 for odd i and i - 1 for even i > 0.
+constexpr int Q = 19;
+__host__ __device__ constexpr int cx_of(int i) {
+  constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  return v[i];
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  return v[i];
+}
+__host__ __device__ constexpr int cz_of(int i) {
+  constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+  return v[i];
+}
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double w_of(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Cell flags (uint16): bit 15 solid, bit 14 "became solid in the last flag update" (cover
+// event, consumed by the refill), bits 0..13 owner body id of a solid cell.
+constexpr uint16_t F_SOLID = 0x8000;
+constexpr uint16_t F_COVER = 0x4000;
+constexpr uint16_t F_OWNER = 0x3FFF;
+constexpr int MAX_BODIES = 0x3FFF;
+constexpr int MAXNB = 24;  // neighbour-list capacity per body (tiles that overlap)
+
+// Device error word bits.
+constexpr int E_TILE = 1, E_NBLIST = 2, E_REFILL = 4;
+
+struct Lat {
+  int nx, ny, nz;
+  long long N;
+};
+
+// One solid body: rigid state (FP64), shape for the initial profile, and its phase-field tile.
+// The tile is a box of L cells per axis whose cell (i,j,k) holds the global cell
+// ((o + (i,j,k)) mod n); cells outside the tile have phi = 0. Three buffers of `sz` doubles start
+// at `off` in the arena: buffer 0 is the current field.
+struct BodyDev {
+  double X[3], Xprev[3], V[3], W[3], Q[4];
+  double M, Ib[9];
+  double wet, psi_wet, vol_ref, rho_s;
+  double c0[3], radius, half[3], q0[4];
+  int fixed, shape;
+  int o[3], o_prev[3], L[3];
+  long long off, sz;
+  int nnb;
+  int nbl[MAXNB];
+};
+
+// Per-step accumulator layout per body (18 doubles).
+constexpr int ACC_MOM_F = 0, ACC_MOM_T = 3, ACC_ADH_F = 6, ACC_ADH_T = 9, ACC_REP_F = 12,
+              ACC_REP_T = 15, ACC_N = 18;
+
+struct StepState {
+  int parity;   // which population buffer is the source this step
+  int diag;     // 1: the collision writes rho and v
+  int err;      // error word
+  int pad;
+  double mass;       // fluid mass of the current step (accumulating)
+  double last_mass;  // fluid mass of the last completed step
+  unsigned long long lost_refills;
+};
+
+struct PhysParams {
+  double tau, G, rho0;
+  double ext[3];
+  double eta, mobility, sigma_sf, sigma_ss;
+  double e0, rc;
+  int nrep;
+  double solid_threshold, member_threshold;
+  int mpf;
+};
+
+__host__ __device__ inline int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+// minimum image, same rule as a plain "while (d >= n/2) d -= n; while (d < -n/2) d += n"
+__host__ __device__ inline double mimg(double d, int n) {
+  double h = 0.5 * n;
+  while (d >= h) d -= n;
+  while (d < -h) d += n;
+  return d;
+}
+
+// ---- kernel launchers (defined in lbm.cu / phase.cu) --------------------------------------
+void set_fp16_weights(cudaStream_t s);
+// Populations live in two buffers fa, fb; StepState::parity selects the current state
+// (0: fa, 1: fb). The step reads the current buffer, writes the other, and the body kernel flips
+// the parity, so one captured graph serves every step.
+unsigned lbm_blocks(const Lat& lat);
+// phases: bit 0 launches the density kernel, bit 1 the collision kernel
+void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
+                     const BodyDev* bodies, double* acc, double* mass_part, StepState* st,
+                     double* diag_rho, double* diag_vel, const PhysParams& pp, cudaStream_t s,
+                     int phases = 3);
+void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
+                       const double* u, cudaStream_t s);
+void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,
+                   const BodyDev* bodies, int nb, int max_tile, StepState* st, cudaStream_t s);
+
+void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
+                      double eta, cudaStream_t s);
+void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st, cudaStream_t s);
+void launch_flags(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, uint16_t* flags,
+                  double threshold, int init, cudaStream_t s);
+void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
+                       double* scratch, cudaStream_t s);
+void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena,
+                      double* acc, const PhysParams& pp, cudaStream_t s);
+void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
+                   const double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
+void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf,
+                   double* volacc, StepState* st, cudaStream_t s);
+void set_repulsion_offsets(double rc, cudaStream_t s);
+void launch_kinetics(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena,
+                     const double* volacc, const PhysParams& pp, cudaStream_t s);
+void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena,
+                      int body, double* out, cudaStream_t s);
+
+}  // namespace cbl

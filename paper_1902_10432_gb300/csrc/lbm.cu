@@ -1,0 +1,499 @@
+// Lattice-Boltzmann kernels of the capillary-bridge step (Sec. 3.2 of arXiv:1902.10432).
+//
+//  k_density  : pull streaming with half-way bounce-back, density, psi = 1 - exp(-rho/rho0)
+//               (Eq. lb_streaming, Eq. lb_bounce_back, Eq. mean_field_potential); solid cells
+//               carry psi of their owner's wetting density (Sec. 3.2.3).
+//  k_collide  : pull again, moving-wall term g and local mass correction
+//               (Eqs. lb_bounce_back_us, lb_bounce_back_mass), momentum exchange on the bodies
+//               (Eq. solid_liquid_force), Shan-Chen force (Eq. benzi_force) and its reaction on
+//               the bodies, Guo-forced BGK collision (Eqs. lb_collision, distribution_eq,
+//               guo_forcing, fluid_velocity), FP64 per-body and mass reductions.
+//  k_refill   : cover refill of nodes that became solid (Sec. 3.2.2), as a gather over each
+//               fluid node's 26 neighbours so that no two threads write the same populations.
+//
+// Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights.
+#include "cbl_dev.cuh"
+
+namespace cbl {
+
+__constant__ float c_wh[Q];  // binary16-rounded weights: base of the FP16-deviation storage
+
+void set_fp16_weights(cudaStream_t s) {
+  float wh[Q];
+  for (int i = 0; i < Q; ++i) wh[i] = __half2float(__float2half_rn((float)w_of(i)));
+  cudaMemcpyToSymbolAsync(c_wh, wh, sizeof(wh), 0, cudaMemcpyHostToDevice, s);
+}
+
+template <typename S>
+struct St;
+template <>
+struct St<double> {
+  using R = double;
+  __device__ static R ld(const double* p, size_t k, int) { return __ldg(p + k); }
+  __device__ static void st(double* p, size_t k, int, R v) { p[k] = v; }
+};
+template <>
+struct St<float> {
+  using R = float;
+  __device__ static R ld(const float* p, size_t k, int) { return __ldg(p + k); }
+  __device__ static void st(float* p, size_t k, int, R v) { p[k] = v; }
+};
+template <>
+struct St<__half> {
+  using R = float;
+  // f = h + w_hat: zero populations (solid cells) are stored exactly as h = -w_hat.
+  __device__ static R ld(const __half* p, size_t k, int i) { return __half2float(p[k]) + c_wh[i]; }
+  __device__ static void st(__half* p, size_t k, int i, R v) { p[k] = __float2half_rn(v - c_wh[i]); }
+};
+
+struct Cell {
+  int x, y, z;
+  int xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Cell cell_of(long long n, const Lat& lat) {
+  Cell c;
+  c.x = (int)(n % lat.nx);
+  long long r = n / lat.nx;
+  c.y = (int)(r % lat.ny);
+  c.z = (int)(r / lat.ny);
+  c.xm = c.x ? c.x - 1 : lat.nx - 1;
+  c.xp = c.x + 1 < lat.nx ? c.x + 1 : 0;
+  c.ym = c.y ? c.y - 1 : lat.ny - 1;
+  c.yp = c.y + 1 < lat.ny ? c.y + 1 : 0;
+  c.zm = c.z ? c.z - 1 : lat.nz - 1;
+  c.zp = c.z + 1 < lat.nz ? c.z + 1 : 0;
+  return c;
+}
+
+// neighbour x + s * c_i (s = +1 downstream, -1 upstream)
+__device__ __forceinline__ long long nbr(const Cell& c, const Lat& lat, int i, int s) {
+  int dx = s * cx_of(i), dy = s * cy_of(i), dz = s * cz_of(i);
+  int X = dx > 0 ? c.xp : (dx < 0 ? c.xm : c.x);
+  int Y = dy > 0 ? c.yp : (dy < 0 ? c.ym : c.y);
+  int Z = dz > 0 ? c.zp : (dz < 0 ? c.zm : c.z);
+  return (long long)X + (long long)lat.nx * ((long long)Y + (long long)lat.ny * Z);
+}
+
+// Pull: f_i(x) = f*_i(x - c_i) from a fluid source, else f*_opp(i)(x) (half-way bounce-back).
+template <typename S>
+__device__ __forceinline__ void pull(const S* __restrict__ f, const uint16_t* __restrict__ flags,
+                                     const Lat& lat, const Cell& c, long long n,
+                                     typename St<S>::R fi[Q], unsigned& solid_links) {
+  const size_t N = (size_t)lat.N;
+  solid_links = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (i == 0) {
+      fi[0] = St<S>::ld(f, (size_t)n, 0);
+      continue;
+    }
+    long long s = nbr(c, lat, i, -1);
+    if (__ldg(flags + s) & F_SOLID) {
+      solid_links |= 1u << i;
+      fi[i] = St<S>::ld(f, (size_t)opp_of(i) * N + n, opp_of(i));
+    } else {
+      fi[i] = St<S>::ld(f, (size_t)i * N + s, i);
+    }
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_density(const S* __restrict__ fa, const S* __restrict__ fb,
+                                                 const StepState* __restrict__ st,
+                                                 const uint16_t* __restrict__ flags,
+                                                 const BodyDev* __restrict__ bodies,
+                                                 typename St<S>::R* __restrict__ psi, Lat lat, double rho0) {
+  using R = typename St<S>::R;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= lat.N) return;
+  const S* __restrict__ f = st->parity ? fb : fa;
+  uint16_t fl = flags[n];
+  R ps;
+  if (fl & F_SOLID) {
+    ps = (R)bodies[fl & F_OWNER].psi_wet;
+  } else {
+    Cell c = cell_of(n, lat);
+    R fi[Q];
+    unsigned sl;
+    pull<S>(f, flags, lat, c, n, fi, sl);
+    R rho = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += fi[i];
+    ps = (R)1 - exp(-rho / (R)rho0);
+  }
+  psi[n] = ps;
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restrict__ fb,
+                                                 const uint16_t* __restrict__ flags,
+                                                 const typename St<S>::R* __restrict__ psi,
+                                                 const BodyDev* __restrict__ bodies, double* __restrict__ acc,
+                                                 double* __restrict__ mass_part, const StepState* __restrict__ st,
+                                                 double* __restrict__ diag_rho, double* __restrict__ diag_vel,
+                                                 Lat lat, PhysParams pp) {
+  using R = typename St<S>::R;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = n < lat.N;
+  const size_t N = (size_t)lat.N;
+  const int diag = st->diag;
+  const S* __restrict__ src = st->parity ? fb : fa;
+  S* __restrict__ dst = st->parity ? fa : fb;
+  double a12[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a12[k] = 0.0;
+  int cur = -1;
+  double my_mass = 0.0;
+
+  auto flush = [&](int B) {
+    if (B < 0) return;
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (a12[k] != 0.0) atomicAdd(acc + (size_t)B * ACC_N + k, a12[k]);
+  };
+  auto select = [&](int B) {
+    if (B != cur) {
+      flush(cur);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) a12[k] = 0.0;
+      cur = B;
+    }
+  };
+
+  uint16_t fl = valid ? flags[n] : F_SOLID;
+  if (valid && (fl & F_SOLID)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
+    if (diag) {
+      diag_rho[n] = 0.0;
+      diag_vel[3 * n] = 0.0;
+      diag_vel[3 * n + 1] = 0.0;
+      diag_vel[3 * n + 2] = 0.0;
+    }
+  } else if (valid) {
+    Cell c = cell_of(n, lat);
+    R fi[Q];
+    unsigned sl;
+    pull<S>(src, flags, lat, c, n, fi, sl);
+    R rho = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += fi[i];
+    my_mass = (double)rho;
+    if (sl) {
+      // moving-wall term g_i = 2 rho w_i c_i.u_B(x - c_i/2) / c_s^2 on each solid link, the mass
+      // correction delta rho = -sum g_i on the rest population, and the momentum handed to the
+      // body: -c_i (2 f*_opp(x) + g_i) with the arm at the link midpoint.
+      R drho = 0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!(sl & (1u << i))) continue;
+        long long s = nbr(c, lat, i, -1);
+        int B = __ldg(flags + s) & F_OWNER;
+        const BodyDev& b = bodies[B];
+        double mid[3] = {c.x - 0.5 * cx_of(i), c.y - 0.5 * cy_of(i), c.z - 0.5 * cz_of(i)};
+        double arm[3] = {mimg(mid[0] - b.X[0], lat.nx), mimg(mid[1] - b.X[1], lat.ny),
+                         mimg(mid[2] - b.X[2], lat.nz)};
+        double wr[3];
+        cross3(b.W, arm, wr);
+        double cu = cx_of(i) * (b.V[0] + wr[0]) + cy_of(i) * (b.V[1] + wr[1]) + cz_of(i) * (b.V[2] + wr[2]);
+        R g = (R)2 * rho * (R)w_of(i) * (R)cu * (R)3;
+        R fbar = fi[i];  // = f*_opp(i)(x) on a solid link
+        fi[i] += g;
+        drho -= g;
+        double m2 = (double)((R)2 * fbar + g);
+        double dP[3] = {-cx_of(i) * m2, -cy_of(i) * m2, -cz_of(i) * m2};
+        double dL[3];
+        cross3(arm, dP, dL);
+        select(B);
+        a12[0] += dP[0]; a12[1] += dP[1]; a12[2] += dP[2];
+        a12[3] += dL[0]; a12[4] += dL[1]; a12[5] += dL[2];
+      }
+      fi[0] += drho;
+    }
+    // Shan-Chen force with wetting; reaction on the owner of each solid neighbour
+    const R ps = psi[n];
+    R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      long long m = nbr(c, lat, i, +1);
+      R wp = (R)w_of(i) * psi[m];
+      sx += wp * (R)cx_of(i);
+      sy += wp * (R)cy_of(i);
+      sz += wp * (R)cz_of(i);
+      uint16_t fm = __ldg(flags + m);
+      if (fm & F_SOLID) {
+        int B = fm & F_OWNER;
+        const BodyDev& b = bodies[B];
+        R gpw = (R)pp.G * ps * wp;
+        double fr[3] = {(double)(gpw * (R)cx_of(i)), (double)(gpw * (R)cy_of(i)), (double)(gpw * (R)cz_of(i))};
+        double pos[3] = {(double)c.x + cx_of(i), (double)c.y + cy_of(i), (double)c.z + cz_of(i)};
+        double arm[3] = {mimg(pos[0] - b.X[0], lat.nx), mimg(pos[1] - b.X[1], lat.ny),
+                         mimg(pos[2] - b.X[2], lat.nz)};
+        double tq[3];
+        cross3(arm, fr, tq);
+        select(B);
+        a12[6] += fr[0]; a12[7] += fr[1]; a12[8] += fr[2];
+        a12[9] += tq[0]; a12[10] += tq[1]; a12[11] += tq[2];
+      }
+    }
+    const R mG = -(R)pp.G * ps;
+    const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
+    // velocity with the half-force shift, Eq. fluid_velocity
+    R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (cx_of(i)) mx += (R)cx_of(i) * fi[i];
+      if (cy_of(i)) my += (R)cy_of(i) * fi[i];
+      if (cz_of(i)) mz += (R)cz_of(i) * fi[i];
+    }
+    R vx = 0, vy = 0, vz = 0;
+    if (rho > (R)0) {
+      vx = mx / rho;
+      vy = my / rho;
+      vz = mz / rho;
+    }
+    const R itau = (R)1 / (R)pp.tau;
+    const R pref = (R)1 - (R)0.5 * itau;
+    const R uu = vx * vx + vy * vy + vz * vz;
+    const R vF = vx * Fx + vy * Fy + vz * Fz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
+      const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
+      const R w = (R)w_of(i);
+      const R feq = rho * w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+      const R Fi = pref * w * ((R)3 * (cF - vF) + (R)9 * cu * cF);
+      St<S>::st(dst, (size_t)i * N + n, i, fi[i] - (fi[i] - feq) * itau + Fi);
+    }
+    if (diag) {
+      diag_rho[n] = (double)rho;
+      diag_vel[3 * n] = (double)vx;
+      diag_vel[3 * n + 1] = (double)vy;
+      diag_vel[3 * n + 2] = (double)vz;
+    }
+  }
+
+  // ---- per-body reduction: warp-uniform body -> shuffle sum, else per-lane atomics ----------
+  const unsigned any = __ballot_sync(0xffffffffu, cur >= 0);
+  if (any) {
+    const int lead = __ffs(any) - 1;
+    const int b0 = __shfl_sync(0xffffffffu, cur, lead);
+    const bool uniform = __all_sync(0xffffffffu, cur < 0 || cur == b0);
+    if (uniform) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        double v = warp_sum(cur >= 0 ? a12[k] : 0.0);
+        if ((threadIdx.x & 31) == lead && v != 0.0) atomicAdd(acc + (size_t)b0 * ACC_N + k, v);
+      }
+    } else {
+      flush(cur);
+    }
+  }
+  // ---- fluid mass: block partial sums (summed in a fixed order by the body kernel) ----------
+  __shared__ double wsum[8];
+  double m = warp_sum(my_mass);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    mass_part[blockIdx.x] = t;
+  }
+}
+
+template <typename S>
+__global__ void k_init_fluid(S* __restrict__ f, const uint16_t* __restrict__ flags, const double* __restrict__ rho,
+                             const double* __restrict__ u, Lat lat) {
+  using R = typename St<S>::R;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= lat.N) return;
+  const size_t N = (size_t)lat.N;
+  if (flags[n] & F_SOLID) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St<S>::st(f, (size_t)i * N + n, i, (R)0);
+    return;
+  }
+  double r = rho[n];
+  double ux = u ? u[3 * n] : 0.0, uy = u ? u[3 * n + 1] : 0.0, uz = u ? u[3 * n + 2] : 0.0;
+  double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    double cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+    St<S>::st(f, (size_t)i * N + n, i, (R)(r * w_of(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
+  }
+}
+
+// ---- cover refill ----------------------------------------------------------------------------
+__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
+                                                 int gz, const Lat& lat) {
+  for (int k = 0; k < b.nnb; ++k) {
+    int o = b.nbl[k];
+    if (o >= self) break;
+    const BodyDev& ob = bodies[o];
+    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
+        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
+      return true;
+  }
+  return false;
+}
+
+template <typename S>
+__global__ void k_refill(S* __restrict__ fa, S* __restrict__ fb, const uint16_t* __restrict__ flags,
+                         const BodyDev* __restrict__ bodies, StepState* st, Lat lat) {
+  using R = typename St<S>::R;
+  S* __restrict__ f = st->parity ? fb : fa;  // the state buffer written by this step's collision
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  int i0 = (int)(t % b.L[0]);
+  long long r = t / b.L[0];
+  int i1 = (int)(r % b.L[1]), i2 = (int)(r / b.L[1]);
+  int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
+  if (b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat)) return;
+  const long long m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
+  const uint16_t fm = flags[m];
+  const size_t N = (size_t)lat.N;
+  auto at = [&](int x, int y, int z) {
+    return (long long)wrapi(x, lat.nx) + (long long)lat.nx * (wrapi(y, lat.ny) + (long long)lat.ny * wrapi(z, lat.nz));
+  };
+  auto fluid_count = [&](int x, int y, int z, bool faces_only) {
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 == 0 || (faces_only && d2 > 1)) continue;
+          if (!(flags[at(x + dx, y + dy, z + dz)] & F_SOLID)) cnt++;
+        }
+    return cnt;
+  };
+  if (fm & F_SOLID) {
+    // a covered node with no fluid node within sqrt(3) loses its mass: count it
+    if ((fm & F_COVER) && fluid_count(gx, gy, gz, false) == 0) {
+      atomicAdd(&st->lost_refills, 1ull);
+      atomicOr(&st->err, E_REFILL);
+    }
+    return;
+  }
+  // quick reject: no covered neighbour
+  bool any = false;
+  for (int dz = -1; dz <= 1 && !any; ++dz)
+    for (int dy = -1; dy <= 1 && !any; ++dy)
+      for (int dx = -1; dx <= 1 && !any; ++dx)
+        if ((dx | dy | dz) && (flags[at(gx + dx, gy + dy, gz + dz)] & F_COVER)) any = true;
+  if (!any) return;
+  R add[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) add[i] = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 == 0) continue;
+        int nxp = gx + dx, nyp = gy + dy, nzp = gz + dz;
+        long long nn = at(nxp, nyp, nzp);
+        if (!(flags[nn] & F_COVER)) continue;
+        int c6 = fluid_count(nxp, nyp, nzp, true);
+        int cnt;
+        if (c6 > 0) {
+          if (d2 != 1) continue;  // only face neighbours share this node's populations
+          cnt = c6;
+        } else {
+          cnt = fluid_count(nxp, nyp, nzp, false);
+        }
+        // moments of the covered node's populations
+        R fi[Q];
+        R rho = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          fi[i] = St<S>::ld(f, (size_t)i * N + nn, i);
+          rho += fi[i];
+          mx += (R)cx_of(i) * fi[i];
+          my += (R)cy_of(i) * fi[i];
+          mz += (R)cz_of(i) * fi[i];
+        }
+        R ux = 0, uy = 0, uz = 0;
+        if (rho > (R)0) {
+          ux = mx / rho;
+          uy = my / rho;
+          uz = mz / rho;
+        }
+        R uu = ux * ux + uy * uy + uz * uz;
+        R inv = (R)1 / (R)cnt;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          R cu = (R)cx_of(i) * ux + (R)cy_of(i) * uy + (R)cz_of(i) * uz;
+          add[i] += rho * (R)w_of(i) * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu) * inv;
+        }
+      }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    size_t k = (size_t)i * N + m;
+    St<S>::st(f, k, i, St<S>::ld(f, k, i) + add[i]);
+  }
+}
+
+// ---- launchers -------------------------------------------------------------------------------
+template <typename S>
+static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
+                       double* acc, double* mass_part, StepState* st, double* diag_rho, double* diag_vel,
+                       const PhysParams& pp, cudaStream_t s, int phases) {
+  using R = typename St<S>::R;
+  const int T = 256;
+  const unsigned blocks = (unsigned)((lat.N + T - 1) / T);
+  if (phases & 1) k_density<S><<<blocks, T, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
+  if (phases & 2)
+    k_collide<S><<<blocks, T, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, acc, mass_part, st, diag_rho,
+                                      diag_vel, lat, pp);
+}
+
+unsigned lbm_blocks(const Lat& lat) { return (unsigned)((lat.N + 255) / 256); }
+
+void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
+                     const BodyDev* bodies, double* acc, double* mass_part, StepState* st, double* diag_rho,
+                     double* diag_vel, const PhysParams& pp, cudaStream_t s, int phases) {
+  if (prec == 0)
+    lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, bodies, acc, mass_part, st, diag_rho, diag_vel, pp,
+                       s, phases);
+  else if (prec == 1)
+    lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, bodies, acc, mass_part, st, diag_rho, diag_vel, pp,
+                      s, phases);
+  else
+    lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, bodies, acc, mass_part, st, diag_rho, diag_vel, pp,
+                       s, phases);
+}
+
+void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags, const double* rho, const double* u,
+                       cudaStream_t s) {
+  const int T = 256;
+  const unsigned blocks = (unsigned)((lat.N + T - 1) / T);
+  if (prec == 0) k_init_fluid<double><<<blocks, T, 0, s>>>((double*)f, flags, rho, u, lat);
+  else if (prec == 1) k_init_fluid<float><<<blocks, T, 0, s>>>((float*)f, flags, rho, u, lat);
+  else k_init_fluid<__half><<<blocks, T, 0, s>>>((__half*)f, flags, rho, u, lat);
+}
+
+void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
+                   int nb, int max_tile, StepState* st, cudaStream_t s) {
+  if (nb == 0) return;
+  const int T = 256;
+  dim3 grid((unsigned)((max_tile + T - 1) / T), (unsigned)nb);
+  if (prec == 0) k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, lat);
+  else if (prec == 1) k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, lat);
+  else k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, lat);
+}
+
+}  // namespace cbl

@@ -1,0 +1,691 @@
+// Solid-body kernels of the capillary-bridge step (Sec. 3.1 and 3.3 of arXiv:1902.10432).
+//
+// Each body's phase field lives in a tile (a box of the periodic lattice that follows the body);
+// phi is zero outside it. All phase-field arithmetic, reductions and the rigid-body update are FP64.
+//  k_rasterize    : initial profile 1/2 - 1/2 sin(pi d / eta) of the signed distance d (Sec. 3.1).
+//  k_flags        : clamp to [0,1], renormalise the solid sum, obstacle flag (fluid phase below the
+//                   threshold, Sec. 3.2.2), owner = argmax, cover events.
+//  k_body_props   : mass, centre of mass and inertia from phi.
+//  k_repulsion    : solid-solid repulsion between body points (Eqs. soild_solid_potential and
+//                   solid_solid_force, Sec. 3.1.2).
+//  k_bodies       : force/torque totals and the rigid-body update (Sec. 3.1.1), tile recentring,
+//                   overlap lists, fluid-mass total.
+//  k_sweep        : one conservative MUSCL sweep with the monotonized-central limiter of
+//                   d(phi)/dt = -u_B . grad(phi) (Eq. phase_advection, Sec. 3.3), x, y, z in turn.
+//  k_kinetics     : Eq. sim_proc_phase_field_dynamics with the volume-restoring Delta g (Sec. 3.3).
+#include "cbl_dev.cuh"
+
+namespace cbl {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr int MAXOFF = 512;
+__constant__ int c_off[3 * MAXOFF];
+__constant__ int c_noff;
+
+void set_repulsion_offsets(double rc, cudaStream_t s) {
+  int off[3 * MAXOFF];
+  int n = 0;
+  int R = (int)ceil(rc);
+  for (int dz = -R; dz <= R; ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        int d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > 0 && (double)d2 < rc * rc && n < MAXOFF) {
+          off[3 * n] = dx;
+          off[3 * n + 1] = dy;
+          off[3 * n + 2] = dz;
+          n++;
+        }
+      }
+  cudaMemcpyToSymbolAsync(c_off, off, sizeof(int) * 3 * n, 0, cudaMemcpyHostToDevice, s);
+  cudaMemcpyToSymbolAsync(c_noff, &n, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+}
+
+// ---- tile helpers ------------------------------------------------------------------------------
+struct TileCell {
+  int i0, i1, i2;  // tile-local
+  int gx, gy, gz;  // global (wrapped)
+};
+
+__device__ __forceinline__ TileCell tile_cell(const BodyDev& b, long long t, const Lat& lat) {
+  TileCell c;
+  c.i0 = (int)(t % b.L[0]);
+  long long r = t / b.L[0];
+  c.i1 = (int)(r % b.L[1]);
+  c.i2 = (int)(r / b.L[1]);
+  c.gx = wrapi(b.o[0] + c.i0, lat.nx);
+  c.gy = wrapi(b.o[1] + c.i1, lat.ny);
+  c.gz = wrapi(b.o[2] + c.i2, lat.nz);
+  return c;
+}
+
+// local index of global cell g in a tile with origin o, or -1 if outside
+__device__ __forceinline__ long long tile_index(const int o[3], const int L[3], int gx, int gy, int gz, const Lat& lat) {
+  int a = wrapi(gx - o[0], lat.nx), b = wrapi(gy - o[1], lat.ny), c = wrapi(gz - o[2], lat.nz);
+  if (a >= L[0] || b >= L[1] || c >= L[2]) return -1;
+  return (long long)a + (long long)L[0] * ((long long)b + (long long)L[1] * c);
+}
+
+__device__ __forceinline__ double phi_at(const double* buf, const BodyDev& b, int gx, int gy, int gz, const Lat& lat) {
+  long long k = tile_index(b.o, b.L, gx, gy, gz, lat);
+  return k < 0 ? 0.0 : buf[k];
+}
+
+__device__ __forceinline__ bool covered_by_lower_body(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
+                                                      int gz, const Lat& lat) {
+  for (int k = 0; k < b.nnb; ++k) {
+    int o = b.nbl[k];
+    if (o >= self) break;
+    if (tile_index(bodies[o].o, bodies[o].L, gx, gy, gz, lat) >= 0) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void quat_R(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+__device__ __forceinline__ void xcross(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ double dwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- initial profile ---------------------------------------------------------------------------
+__device__ double body_sdf(const BodyDev& b, const double r[3]) {
+  if (b.shape == 0) return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) - b.radius;
+  double R[9];
+  quat_R(b.q0, R);
+  double o = 0, m = -1e300;
+  for (int a = 0; a < 3; ++a) {
+    double l = R[0 + a] * r[0] + R[3 + a] * r[1] + R[6 + a] * r[2];
+    double q = fabs(l) - b.half[a];
+    double v = q > 0 ? q : 0;
+    o += v * v;
+    m = q > m ? q : m;
+  }
+  return sqrt(o) + (m < 0 ? m : 0.0);
+}
+
+__global__ void k_rasterize(BodyDev* bodies, double* arena, Lat lat, double eta) {
+  const BodyDev& b = bodies[blockIdx.y];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  TileCell c = tile_cell(b, t, lat);
+  double r[3] = {mimg(c.gx - b.c0[0], lat.nx), mimg(c.gy - b.c0[1], lat.ny), mimg(c.gz - b.c0[2], lat.nz)};
+  double d = body_sdf(b, r);
+  double v = d <= -0.5 * eta ? 1.0 : (d >= 0.5 * eta ? 0.0 : 0.5 - 0.5 * sin(PI * d / eta));
+  double* buf = arena + b.off;
+  buf[t] = v;
+  buf[b.sz + t] = 0.0;
+  buf[2 * b.sz + t] = 0.0;
+}
+
+// ---- overlap lists -----------------------------------------------------------------------------
+__device__ bool tiles_overlap(const BodyDev& a, const BodyDev& b, const Lat& lat) {
+  const int n[3] = {lat.nx, lat.ny, lat.nz};
+  for (int d = 0; d < 3; ++d) {
+    bool ov = wrapi(b.o[d] - a.o[d], n[d]) < a.L[d] || wrapi(a.o[d] - b.o[d], n[d]) < b.L[d];
+    if (!ov) return false;
+  }
+  return true;
+}
+
+__device__ void build_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st) {
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+    int cnt = 0;
+    for (int b = 0; b < nb; ++b) {
+      if (b == a || !tiles_overlap(bodies[a], bodies[b], lat)) continue;
+      if (cnt < MAXNB) bodies[a].nbl[cnt++] = b;
+      else atomicOr(&st->err, E_NBLIST);
+    }
+    bodies[a].nnb = cnt;
+  }
+}
+
+__global__ void k_neighbour_lists(BodyDev* bodies, int nb, Lat lat, StepState* st) {
+  build_lists(bodies, nb, lat, st);
+}
+
+// ---- flags --------------------------------------------------------------------------------------
+__global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat, double thr, int init) {
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  TileCell c = tile_cell(b, t, lat);
+  if (b.nnb && covered_by_lower_body(bodies, b, self, c.gx, c.gy, c.gz, lat)) return;
+  // bodies covering this cell, ascending id (self is the lowest)
+  double* ptr[MAXNB + 1];
+  int ids[MAXNB + 1];
+  int m = 0;
+  ptr[m] = arena + b.off + t;
+  ids[m++] = self;
+  for (int k = 0; k < b.nnb; ++k) {
+    const BodyDev& o = bodies[b.nbl[k]];
+    long long j = tile_index(o.o, o.L, c.gx, c.gy, c.gz, lat);
+    if (j >= 0) {
+      ptr[m] = arena + o.off + j;
+      ids[m++] = b.nbl[k];
+    }
+  }
+  double S = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double v = *ptr[k];
+    v = fmin(1.0, fmax(0.0, v));
+    *ptr[k] = v;
+    S += v;
+  }
+  if (S > 1.0) {
+    double S2 = 0.0;
+    for (int k = 0; k < m; ++k) {
+      double v = *ptr[k] / S;
+      *ptr[k] = v;
+      S2 += v;
+    }
+    S = S2;
+  }
+  const long long n = c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz);
+  uint16_t old = flags[n];
+  uint16_t nf = 0;
+  if (1.0 - S < thr) {
+    int best = ids[0];
+    double bv = *ptr[0];
+    for (int k = 1; k < m; ++k)
+      if (*ptr[k] > bv) {
+        bv = *ptr[k];
+        best = ids[k];
+      }
+    nf = F_SOLID | (uint16_t)best;
+    if (!init && !(old & F_SOLID)) nf |= F_COVER;
+  }
+  flags[n] = nf;
+}
+
+// ---- body properties (initialisation) ---------------------------------------------------------
+// pass 0: sum phi and sum r phi about the nominal centre; pass 1: inertia about X
+__global__ void k_body_props(const BodyDev* bodies, const double* arena, double* scratch, Lat lat, int pass) {
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  TileCell c;
+  if (t < b.sz) {
+    c = tile_cell(b, t, lat);
+    v = arena[b.off + t];
+  }
+  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (v != 0.0) {
+    if (pass == 0) {
+      a[0] = v;
+      a[1] = v * mimg(c.gx - b.c0[0], lat.nx);
+      a[2] = v * mimg(c.gy - b.c0[1], lat.ny);
+      a[3] = v * mimg(c.gz - b.c0[2], lat.nz);
+    } else {
+      double r[3] = {mimg(c.gx - b.X[0], lat.nx), mimg(c.gy - b.X[1], lat.ny), mimg(c.gz - b.X[2], lat.nz)};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) a[3 * p + q] = v * ((p == q ? rr : 0.0) - r[p] * r[q]);
+    }
+  }
+  for (int k = 0; k < 9; ++k) {
+    double s = dwarp_sum(a[k]);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(scratch + self * 9 + k, s);
+  }
+}
+
+__global__ void k_body_props_finish(BodyDev* bodies, int nb, const double* scratch, Lat lat, int pass) {
+  int self = blockIdx.x * blockDim.x + threadIdx.x;
+  if (self >= nb) return;
+  BodyDev& b = bodies[self];
+  const double* s = scratch + self * 9;
+  const int n[3] = {lat.nx, lat.ny, lat.nz};
+  if (pass == 0) {
+    for (int a = 0; a < 3; ++a) {
+      double X = b.c0[a] + s[1 + a] / s[0];
+      X = fmod(X, (double)n[a]);
+      if (X < 0) X += n[a];
+      b.X[a] = X;
+      b.Xprev[a] = X;
+    }
+    b.M = b.rho_s * s[0];
+    b.vol_ref = s[0];
+  } else {
+    double R[9];
+    quat_R(b.Q, R);
+    const double rho_s = b.rho_s;
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0;
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) acc += R[3 * k + a] * (rho_s * s[3 * k + l]) * R[3 * l + c];
+        b.Ib[3 * a + c] = acc;
+      }
+  }
+}
+
+// ---- solid-solid repulsion ---------------------------------------------------------------------
+__global__ void k_repulsion(const BodyDev* bodies, const double* arena, double* acc, Lat lat, double e0, double rc,
+                            int nrep, double thr) {
+  const int self = blockIdx.y;
+  const BodyDev& a = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+  if (t < a.sz && a.nnb > 0 && arena[a.off + t] >= thr) {
+    TileCell c = tile_cell(a, t, lat);
+    double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
+    for (int k = 0; k < a.nnb; ++k) {
+      const BodyDev& b = bodies[a.nbl[k]];
+      const double* bb = arena + b.off;
+      for (int j = 0; j < c_noff; ++j) {
+        int dx = c_off[3 * j], dy = c_off[3 * j + 1], dz = c_off[3 * j + 2];
+        long long q = tile_index(b.o, b.L, c.gx + dx, c.gy + dy, c.gz + dz, lat);
+        if (q < 0 || bb[q] < thr) continue;
+        double d = sqrt((double)(dx * dx + dy * dy + dz * dz));
+        double mag = e0 * nrep / rc * pow(fabs((d - rc) / rc), (double)(nrep - 1));
+        double fv[3] = {-dx / d * mag, -dy / d * mag, -dz / d * mag};
+        double tq[3];
+        xcross(arm, fv, tq);
+        for (int p = 0; p < 3; ++p) {
+          F[p] += fv[p];
+          T[p] += tq[p];
+        }
+      }
+    }
+  }
+  for (int p = 0; p < 3; ++p) {
+    double sf = dwarp_sum(F[p]), st = dwarp_sum(T[p]);
+    if ((threadIdx.x & 31) == 0) {
+      if (sf != 0.0) atomicAdd(acc + (size_t)self * ACC_N + ACC_REP_F + p, sf);
+      if (st != 0.0) atomicAdd(acc + (size_t)self * ACC_N + ACC_REP_T + p, st);
+    }
+  }
+}
+
+// ---- rigid bodies ------------------------------------------------------------------------------
+// Semi-implicit Euler with dt = 1: V += F/M, X += V, omega += I_w^-1 T with I_w = R I_body R^T,
+// q <- normalize(exp(omega/2) q); fixed bodies keep V = omega = 0.
+__device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
+  double F[3], T[3];
+  for (int a = 0; a < 3; ++a) {
+    F[a] = parts[ACC_MOM_F + a] + parts[ACC_ADH_F + a] + parts[ACC_REP_F + a];
+    T[a] = parts[ACC_MOM_T + a] + parts[ACC_ADH_T + a] + parts[ACC_REP_T + a];
+    b.Xprev[a] = b.X[a];
+  }
+  if (b.fixed) {
+    for (int a = 0; a < 3; ++a) {
+      b.V[a] = 0;
+      b.W[a] = 0;
+    }
+    return;
+  }
+  const int n[3] = {lat.nx, lat.ny, lat.nz};
+  for (int a = 0; a < 3; ++a) {
+    b.V[a] += F[a] / b.M;
+    double x = b.X[a] + b.V[a];
+    x = fmod(x, (double)n[a]);
+    if (x < 0) x += n[a];
+    b.X[a] = x;
+  }
+  double R[9], Iw[9];
+  quat_R(b.Q, R);
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) acc += R[3 * a + k] * b.Ib[3 * k + l] * R[3 * c + l];
+      Iw[3 * a + c] = acc;
+    }
+  double det = Iw[0] * (Iw[4] * Iw[8] - Iw[5] * Iw[7]) - Iw[1] * (Iw[3] * Iw[8] - Iw[5] * Iw[6]) +
+               Iw[2] * (Iw[3] * Iw[7] - Iw[4] * Iw[6]);
+  double inv[9];
+  inv[0] = (Iw[4] * Iw[8] - Iw[5] * Iw[7]) / det;
+  inv[1] = (Iw[2] * Iw[7] - Iw[1] * Iw[8]) / det;
+  inv[2] = (Iw[1] * Iw[5] - Iw[2] * Iw[4]) / det;
+  inv[3] = (Iw[5] * Iw[6] - Iw[3] * Iw[8]) / det;
+  inv[4] = (Iw[0] * Iw[8] - Iw[2] * Iw[6]) / det;
+  inv[5] = (Iw[2] * Iw[3] - Iw[0] * Iw[5]) / det;
+  inv[6] = (Iw[3] * Iw[7] - Iw[4] * Iw[6]) / det;
+  inv[7] = (Iw[1] * Iw[6] - Iw[0] * Iw[7]) / det;
+  inv[8] = (Iw[0] * Iw[4] - Iw[1] * Iw[3]) / det;
+  for (int a = 0; a < 3; ++a) b.W[a] += inv[3 * a] * T[0] + inv[3 * a + 1] * T[1] + inv[3 * a + 2] * T[2];
+  double wn = sqrt(b.W[0] * b.W[0] + b.W[1] * b.W[1] + b.W[2] * b.W[2]);
+  if (wn > 0) {
+    double h = 0.5 * wn, s = sin(h) / wn;
+    double dq[4] = {cos(h), b.W[0] * s, b.W[1] * s, b.W[2] * s};
+    const double* q = b.Q;
+    double nq[4] = {dq[0] * q[0] - dq[1] * q[1] - dq[2] * q[2] - dq[3] * q[3],
+                    dq[0] * q[1] + dq[1] * q[0] + dq[2] * q[3] - dq[3] * q[2],
+                    dq[0] * q[2] - dq[1] * q[3] + dq[2] * q[0] + dq[3] * q[1],
+                    dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0]};
+    double qn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+    for (int a = 0; a < 4; ++a) b.Q[a] = nq[a] / qn;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
+                                                const double* mass_part, unsigned n_mass_part, StepState* st,
+                                                Lat lat) {
+  const int n[3] = {lat.nx, lat.ny, lat.nz};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    BodyDev& b = bodies[i];
+    double* a = acc + (size_t)i * ACC_N;
+    integrate(b, a, lat);
+    for (int k = 0; k < ACC_N; ++k) {
+      last[(size_t)i * ACC_N + k] = a[k];
+      a[k] = 0.0;
+    }
+    volacc[2 * i] = 0.0;
+    volacc[2 * i + 1] = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      b.o_prev[d] = b.o[d];
+      if (b.L[d] < n[d]) b.o[d] = (int)floor(b.X[d] + 0.5) - b.L[d] / 2;
+    }
+  }
+  // fluid mass of this step: fixed-order sum of the per-block partials
+  __shared__ double red[256];
+  double s = 0.0;
+  for (unsigned k = threadIdx.x; k < n_mass_part; k += blockDim.x) s += mass_part[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  build_lists(bodies, nb, lat, st);
+  if (threadIdx.x == 0) {
+    st->last_mass = red[0];
+    st->parity ^= 1;
+  }
+}
+
+// ---- advection ---------------------------------------------------------------------------------
+__device__ __forceinline__ double mc_slope(double dm, double dp) {
+  if (dm * dp <= 0.0) return 0.0;
+  double s = fmin(fmin(2.0 * fabs(dm), 0.5 * fabs(dm + dp)), 2.0 * fabs(dp));
+  return dm > 0 ? s : -s;
+}
+
+// one sweep along axis d: out (origin b.o) <- in (origin o_in); x-sweep reads with the previous
+// origin, so the recentring shift is folded into it.
+__global__ void k_sweep(const BodyDev* bodies, double* arena, Lat lat, int d, int in_buf, int out_buf, int use_prev,
+                        int last, double* volacc, StepState* st) {
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  bool inside = t < b.sz;
+  if (inside) {
+    TileCell c = tile_cell(b, t, lat);
+    const int* oin = use_prev ? b.o_prev : b.o;
+    const double* in = arena + b.off + (long long)in_buf * b.sz;
+    const int e[3] = {d == 0, d == 1, d == 2};
+    double p[5];
+    for (int k = 0; k < 5; ++k) {
+      long long q = tile_index(oin, b.L, c.gx + (k - 2) * e[0], c.gy + (k - 2) * e[1], c.gz + (k - 2) * e[2], lat);
+      p[k] = q < 0 ? 0.0 : in[q];
+    }
+    // face velocities u_d at the face centres (the d-component of V + omega x r, r about X_prev)
+    const int g[3] = {c.gx, c.gy, c.gz};
+    const int nn[3] = {lat.nx, lat.ny, lat.nz};
+    double uf[2];
+    for (int s = 0; s < 2; ++s) {
+      // face between (g - e) and g for s = 0, between g and (g + e) for s = 1; the left cell is
+      // wrapped like a lattice coordinate
+      double pos[3];
+      for (int a = 0; a < 3; ++a) {
+        int left = a == d ? wrapi(g[a] - 1 + s, nn[a]) : g[a];
+        pos[a] = left + 0.5 * e[a];
+      }
+      double r[3] = {mimg(pos[0] - b.Xprev[0], lat.nx), mimg(pos[1] - b.Xprev[1], lat.ny),
+                     mimg(pos[2] - b.Xprev[2], lat.nz)};
+      double wr[3];
+      xcross(b.W, r, wr);
+      uf[s] = b.V[d] + wr[d];
+    }
+    // flux through the face between cells (k, k+1) of the 5-point stencil: k = 1 (left), 2 (right)
+    double Fl, Fr;
+    {
+      double u = uf[0];
+      double face = u >= 0.0 ? p[1] + 0.5 * (1.0 - u) * mc_slope(p[1] - p[0], p[2] - p[1])
+                             : p[2] - 0.5 * (1.0 + u) * mc_slope(p[2] - p[1], p[3] - p[2]);
+      Fl = u * face;
+    }
+    {
+      double u = uf[1];
+      double face = u >= 0.0 ? p[2] + 0.5 * (1.0 - u) * mc_slope(p[2] - p[1], p[3] - p[2])
+                             : p[3] - 0.5 * (1.0 + u) * mc_slope(p[3] - p[2], p[4] - p[3]);
+      Fr = u * face;
+    }
+    v = p[2] - (Fr - Fl);
+    arena[b.off + (long long)out_buf * b.sz + t] = v;
+    if (last) {
+      // the outer two layers must stay empty (they are the stencil halo)
+      const int ii[3] = {c.i0, c.i1, c.i2};
+      bool edge = false;
+      for (int a = 0; a < 3; ++a)
+        if (b.L[a] < nn[a] && (ii[a] < 2 || ii[a] >= b.L[a] - 2)) edge = true;
+      if (edge && v != 0.0) atomicOr(&st->err, E_TILE);
+    }
+  }
+  if (last) {
+    double sv = dwarp_sum(inside ? v : 0.0);
+    double sc = dwarp_sum((inside && v > 0.0 && v < 1.0) ? 1.0 : 0.0);
+    if ((threadIdx.x & 31) == 0) {
+      if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
+      if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
+    }
+  }
+}
+
+__global__ void k_volume(const BodyDev* bodies, const double* arena, double* volacc) {
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = t < b.sz ? arena[b.off + t] : 0.0;
+  double sv = dwarp_sum(v);
+  double sc = dwarp_sum((v > 0.0 && v < 1.0) ? 1.0 : 0.0);
+  if ((threadIdx.x & 31) == 0) {
+    if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
+    if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
+  }
+}
+
+// ---- MPF kinetics ------------------------------------------------------------------------------
+// For body a at cell g: active phases = solids with phi > 0 at g or a face neighbour, plus the fluid
+// if 1 - sum phi > 0 there; N = their number; explicit Euler step of
+// phi_a += sum_b (M/N) [ s_ab (I_a - I_b) + sum_c (s_bc - s_ac) I_c + (D_a - D_b if 0<phi_a<1) ]
+// with I = lap(phi) + (pi/eta)^2 phi, D_B = (V_B(0) - sum phi_B) / #{0 < phi_B < 1}, D_fluid = 0.
+constexpr int MAXACT = 8;
+__global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* volacc, Lat lat, double eta,
+                           double mob, double s_sf, double s_ss) {
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  const double* in = arena + b.off + b.sz;  // buffer 1: advected field
+  double* out = arena + b.off;              // buffer 0: new field
+  TileCell c = tile_cell(b, t, lat);
+  const int nxv[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  double pa[7];
+  bool act_a = false;
+  for (int k = 0; k < 7; ++k) {
+    pa[k] = phi_at(in, b, c.gx + nxv[k][0], c.gy + nxv[k][1], c.gz + nxv[k][2], lat);
+    act_a |= pa[k] > 0.0;
+  }
+  if (!act_a) {
+    out[t] = pa[0];
+    return;
+  }
+  // active solids in ascending id order, with their 7-point values
+  double vals[MAXACT][7];
+  int ids[MAXACT];
+  int na = 0;
+  int pos_self = -1;
+  double S[7] = {0, 0, 0, 0, 0, 0, 0};
+  // merge self into the ascending neighbour list
+  int k_nb = 0;
+  for (int step = 0; step <= b.nnb; ++step) {
+    int id;
+    if (pos_self < 0 && (k_nb >= b.nnb || b.nbl[k_nb] > self)) id = self;
+    else id = b.nbl[k_nb++];
+    if (id == self) {
+      pos_self = na;
+      for (int k = 0; k < 7; ++k) vals[na][k] = pa[k];
+      ids[na++] = self;
+      for (int k = 0; k < 7; ++k) S[k] += pa[k];
+      continue;
+    }
+    const BodyDev& o = bodies[id];
+    const double* ob = arena + o.off + o.sz;
+    double v7[7];
+    bool on = false;
+    for (int k = 0; k < 7; ++k) {
+      v7[k] = phi_at(ob, o, c.gx + nxv[k][0], c.gy + nxv[k][1], c.gz + nxv[k][2], lat);
+      on |= v7[k] > 0.0;
+    }
+    if (!on) continue;
+    if (na < MAXACT - (pos_self < 0 ? 1 : 0)) {  // always keep a slot for self
+      for (int k = 0; k < 7; ++k) {
+        vals[na][k] = v7[k];
+        S[k] += v7[k];
+      }
+      ids[na++] = id;
+    }
+  }
+  bool fl = false;
+  for (int k = 0; k < 7; ++k) fl |= S[k] < 1.0;
+  const int N = na + (fl ? 1 : 0);
+  if (N <= 1) {
+    out[t] = pa[0];
+    return;
+  }
+  const double k2 = PI * PI / (eta * eta);
+  double I[MAXACT + 1], D[MAXACT + 1];
+  for (int j = 0; j < na; ++j) {
+    double lap = 0.0;
+    for (int k = 1; k < 7; ++k) lap += vals[j][k];
+    lap -= 6.0 * vals[j][0];
+    I[j] = lap + k2 * vals[j][0];
+    const double cnt = volacc[2 * ids[j] + 1];
+    D[j] = cnt > 0.0 ? (bodies[ids[j]].vol_ref - volacc[2 * ids[j]]) / cnt : 0.0;
+  }
+  if (fl) {
+    double lap = 0.0;
+    for (int k = 1; k < 7; ++k) lap += 1.0 - S[k];
+    lap -= 6.0 * (1.0 - S[0]);
+    I[na] = lap + k2 * (1.0 - S[0]);
+    D[na] = 0.0;
+  }
+  auto sig = [&](int p, int q) { return (p == na || q == na) ? s_sf : s_ss; };
+  const int a = pos_self;
+  const bool in_if = pa[0] > 0.0 && pa[0] < 1.0;
+  double rate = 0.0;
+  for (int bq = 0; bq < N; ++bq) {
+    if (bq == a) continue;
+    double term = sig(a, bq) * (I[a] - I[bq]);
+    for (int g = 0; g < N; ++g) {
+      if (g == a || g == bq) continue;
+      term += (sig(bq, g) - sig(a, g)) * I[g];
+    }
+    if (in_if) term += D[a] - D[bq];
+    rate += mob / N * term;
+  }
+  out[t] = pa[0] + rate;
+}
+
+// ---- dense read-out ----------------------------------------------------------------------------
+__global__ void k_fill(double* out, long long N, double v) {
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) out[n] = v;
+}
+
+// body >= 0: scatter that body's field; body < 0: 1 - sum of all bodies (fluid phase)
+__global__ void k_phi_scatter(const BodyDev* bodies, const double* arena, double* out, Lat lat, int body) {
+  const int self = body >= 0 ? body : blockIdx.y;
+  const BodyDev& b = bodies[self];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  TileCell c = tile_cell(b, t, lat);
+  const long long n = c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz);
+  if (body >= 0) {
+    out[n] = arena[b.off + t];
+    return;
+  }
+  if (b.nnb && covered_by_lower_body(bodies, b, self, c.gx, c.gy, c.gz, lat)) return;
+  double S = arena[b.off + t];
+  for (int k = 0; k < b.nnb; ++k) {
+    const BodyDev& o = bodies[b.nbl[k]];
+    if (b.nbl[k] < self) continue;
+    long long j = tile_index(o.o, o.L, c.gx, c.gy, c.gz, lat);
+    if (j >= 0) S += arena[o.off + j];
+  }
+  out[n] = 1.0 - S;
+}
+
+// ---- launchers ---------------------------------------------------------------------------------
+static dim3 tile_grid(int max_tile, int nb) { return dim3((unsigned)((max_tile + 255) / 256), (unsigned)nb); }
+
+void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, double eta,
+                      cudaStream_t s) {
+  if (nb) k_rasterize<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, lat, eta);
+}
+void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st, cudaStream_t s) {
+  if (nb) k_neighbour_lists<<<1, 256, 0, s>>>(bodies, nb, lat, st);
+}
+void launch_flags(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, uint16_t* flags,
+                  double threshold, int init, cudaStream_t s) {
+  if (nb) k_flags<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, flags, lat, threshold, init);
+}
+void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, double* scratch,
+                       cudaStream_t s) {
+  if (!nb) return;
+  cudaMemsetAsync(scratch, 0, sizeof(double) * 9 * nb, s);
+  k_body_props<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, scratch, lat, 0);
+  k_body_props_finish<<<(nb + 127) / 128, 128, 0, s>>>(bodies, nb, scratch, lat, 0);
+  cudaMemsetAsync(scratch, 0, sizeof(double) * 9 * nb, s);
+  k_body_props<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, scratch, lat, 1);
+  k_body_props_finish<<<(nb + 127) / 128, 128, 0, s>>>(bodies, nb, scratch, lat, 1);
+}
+void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
+                      const PhysParams& pp, cudaStream_t s) {
+  if (nb > 1 && pp.e0 != 0.0)
+    k_repulsion<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, acc, lat, pp.e0, pp.rc, pp.nrep,
+                                                       pp.member_threshold);
+}
+void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
+                   const double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {
+  k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, mass_part, n_mass_part, st, lat);
+}
+void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
+                   StepState* st, cudaStream_t s) {
+  if (!nb) return;
+  dim3 g = tile_grid(max_tile, nb);
+  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 0, 0, 1, 1, 0, volacc, st);
+  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 1, 1, 2, 0, 0, volacc, st);
+  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 2, 2, mpf ? 1 : 0, 0, 1, volacc, st);
+}
+void launch_kinetics(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, const double* volacc,
+                     const PhysParams& pp, cudaStream_t s) {
+  if (nb)
+    k_kinetics<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, volacc, lat, pp.eta, pp.mobility, pp.sigma_sf,
+                                                      pp.sigma_ss);
+}
+void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, int body,
+                      double* out, cudaStream_t s) {
+  k_fill<<<(unsigned)((lat.N + 255) / 256), 256, 0, s>>>(out, lat.N, body >= 0 ? 0.0 : 1.0);
+  if (!nb) return;
+  dim3 g = tile_grid(max_tile, body >= 0 ? 1 : nb);
+  k_phi_scatter<<<g, 256, 0, s>>>(bodies, arena, out, lat, body);
+}
+
+}  // namespace cbl

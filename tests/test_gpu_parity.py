@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 path against the FP64 oracle at round-off (sums in another order, fused
+multiply-adds); FP32 path: relative L-infinity 1e-4 on density and velocity after 500 steps and
+1e-3 on the per-body force; FP16-deviation storage: error reported with a loose bound.
+"""
+import numpy as np
+import pytest
+
+from paper_1902_10432_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+from _pair import compare, make_pair  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    import torch
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def test_plates48_fp64_500_steps():
+    w = workloads.plates48(prec="fp64")
+    g, o = make_pair(w)
+    g.step(w.steps)
+    o.step(w.steps)
+    e = compare(g, o)
+    print(e)
+    assert e["flag_mismatch"] == 0
+    assert e["rho"] < 1e-10 and e["vel"] < 1e-8
+    assert e["force"] < 1e-9 and e["parts"] < 1e-9
+    # mirror symmetry of the fixed plates on the GPU as well
+    F, _, _ = g.body_forces()
+    assert abs(F[0, 2] + F[1, 2]) < 1e-9 * abs(F[0, 2])
+    assert abs(g.total_mass() - o.total_mass()) < 1e-10 * o.total_mass()
+
+
+def test_plates48_fp32_500_steps():
+    w = workloads.plates48(prec="fp32")
+    g, o = make_pair(w)
+    g.step(w.steps)
+    o.step(w.steps)
+    e = compare(g, o)
+    print(e)
+    assert e["flag_mismatch"] == 0
+    assert e["rho"] < 1e-4 and e["vel"] < 1e-4
+    assert e["force"] < 1e-3
+
+
+def test_plates48_fp16dev_error_reported():
+    w = workloads.plates48(prec="fp16dev")
+    g, o = make_pair(w)
+    g.step(w.steps)
+    o.step(w.steps)
+    e = compare(g, o)
+    print("FP16-deviation storage vs FP64 oracle after 500 steps:", e)
+    assert e["flag_mismatch"] == 0
+    assert e["rho"] < 2e-2 and e["force"] < 0.2
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_moving_spheres(prec, tol):
+    # light spheres: they move, cells are covered and uncovered, tiles recentre, kinetics on
+    w = workloads.small_spheres(prec=prec, mobility=2e-3)
+    g, o = make_pair(w)
+    s0, _ = o.flags()
+    for k in range(3):
+        g.step(100)
+        o.step(100)
+        e = compare(g, o)
+        print(prec, o.t, e)
+        if prec == "fp64":
+            assert e["flag_mismatch"] == 0
+        assert e["flag_mismatch"] <= 4
+        assert e["rho"] < tol and e["vel"] < 10 * tol
+        assert e["force"] < 10 * tol and e["X"] < 1e-3
+        assert e["phi_fluid"] < (1e-9 if prec == "fp64" else 1e-3)
+    s1, _ = o.flags()
+    assert (s0 != s1).sum() > 10  # bodies actually moved
+    assert g.info()["device_error"] == 0
+
+
+def test_mass_conservation_moving_fp64():
+    w = workloads.small_spheres(prec="fp64", mobility=2e-3)
+    g, o = make_pair(w)
+    g.step(1)
+    m0 = g.total_mass()
+    g.step(299)
+    assert abs(g.total_mass() - m0) < 1e-12 * m0
+
+
+def test_ragged_lattice_no_bodies_fp64():
+    rng = np.random.default_rng(5)
+    nx, ny, nz = 37, 29, 23
+    rho = 0.12 + 1.77 * (rng.random((nz, ny, nx)) > 0.6)
+    u = 0.01 * rng.standard_normal((nz, ny, nx, 3))
+    from _pair import rel_linf
+
+    import oracle
+    from paper_1902_10432_gb300 import cbl
+
+    g = cbl.Sim(nx, ny, nz, prec="fp64")
+    g.init_fluid_fields(rho, u)
+    o = oracle.Oracle(nx, ny, nz)
+    o.init_fluid_fields(rho, u)
+    g.step(60)
+    o.step(60)
+    rg, vg, _ = g.fields()
+    ro, vo, _ = o.fields()
+    assert rel_linf(rg, ro) < 1e-11 and rel_linf(vg, vo) < 1e-9
+
+
+def test_minimal_lattice_and_body_across_periodic_edge():
+    # 4^3 lattice; a sphere centred on the periodic corner (its tile wraps in all three axes)
+    import oracle
+    from _pair import rel_linf
+    from paper_1902_10432_gb300 import cbl
+
+    g = cbl.Sim(4, 4, 4, prec="fp64")
+    g.init_fluid(1.2, 1.2)
+    g.step(5)
+    r, _, _ = g.fields()
+    assert np.allclose(r, 1.2, rtol=1e-14)
+    n = 24
+    g = cbl.Sim(n, n, n, prec="fp64", mpf_kinetics=1, mobility=1e-3)
+    o = oracle.Oracle(n, n, n, mpf_kinetics=1, mobility=1e-3)
+    z, y, x = np.mgrid[0:n, 0:n, 0:n]
+    mask = ((x - 12) ** 2 + (y - 12) ** 2 + (z - 12) ** 2) < 36
+    for s in (g, o):
+        s.add_body("sphere", (0.5, 23.0, 0.0), radius=5.0, wetting_rho=1.1, mass_density=0.05)
+        s.init_fluid(workloads.RHO_L, workloads.RHO_V, mask)
+    g.step(80)
+    o.step(80)
+    e = compare(g, o)
+    assert e["flag_mismatch"] == 0 and e["rho"] < 1e-10 and e["force"] < 1e-8
+    assert rel_linf(g.phi(0), o.phi(0)) < 1e-10
+
+
+@pytest.mark.slow
+def test_spheres2_full_size_fp32_500_steps():
+    # the benchmark workload at full size (128 x 128 x 256, two free spheres), 500 steps
+    w = workloads.spheres2(seed=0, prec="fp32")
+    g, o = make_pair(w)
+    g.step(w.steps)
+    o.step(w.steps)
+    e = compare(g, o)
+    print("spheres2 full size:", w.meta, e)
+    assert e["flag_mismatch"] <= 8
+    assert e["rho"] < 1e-4 and e["vel"] < 1e-3
+    assert e["force"] < 1e-3
