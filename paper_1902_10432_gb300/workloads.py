@@ -148,9 +148,10 @@ def tetra4(seed=0, prec="fp32", n=256, R=24.0, f=0.05, theta=60.0, surface_gap=8
                     meta=dict(seed=seed, liquid_fraction_of_solid=f, theta_deg=theta, varrho=varrho))
 
 
-def small_spheres(seed=0, prec="fp64", nx=40, ny=36, nz=64, R=8.0, gap=3.0, mpf=1, rho_s=0.05,
+def small_spheres(seed=0, prec="fp64", nx=40, ny=36, nz=64, R=8.0, gap=3.0, mpf=1, rho_s=4.0,
                   theta=45.0, f=0.3, mobility=1e-5):
-    """A reduced two-sphere bridge (light spheres so that they move within a few hundred steps)."""
+    """A reduced two-sphere bridge (the paper's mass density 4; the spheres move by cells within a
+    few hundred steps)."""
     w = spheres2(seed=seed, prec=prec, nx=nx, ny=ny, nz=nz, R=R, gap=gap, mpf=mpf, rho_s=rho_s)
     varrho = varrho_for_angle(theta)
     for b in w.bodies:

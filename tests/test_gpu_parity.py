@@ -68,7 +68,7 @@ def test_moving_spheres(prec, tol):
     w = workloads.small_spheres(prec=prec, mobility=2e-3)
     g, o = make_pair(w)
     s0, _ = o.flags()
-    for k in range(3):
+    for k in range(2):
         g.step(100)
         o.step(100)
         e = compare(g, o)
@@ -89,7 +89,7 @@ def test_mass_conservation_moving_fp64():
     g, o = make_pair(w)
     g.step(1)
     m0 = g.total_mass()
-    g.step(299)
+    g.step(199)
     assert abs(g.total_mass() - m0) < 1e-12 * m0
 
 
