@@ -155,7 +155,8 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
 
 /* Phases of one step, in launch order, as reported by cbl_time_phases. */
 #define CBL_NPHASES 8
-/* 0 pull + density + psi, 1 pull + force + collision + body/mass reductions, 2 solid-solid
+/* 0 pull + density + psi, 1 pull + force + collision + mass partials, then the solid-fluid
+ * force on the bodies (momentum exchange and adhesion, FP64 sums), 2 solid-solid
  * repulsion, 3 rigid-body update, 4 phase-field advection (three sweeps), 5 phase-field kinetics,
  * 6 obstacle flags, 7 cover refill. */
 

@@ -96,6 +96,10 @@ Lattice make_lattice(int Q) {
 }
 
 const double PI = 3.14159265358979323846;
+// Numerical presence tolerance of a phase (READING): phi below it counts as absent and is set to 0
+// at the clamp, phi above 1 - it is set to 1. Without it the limiter leaves ever smaller but
+// non-zero values ahead of a moving front, and "phase present" (phi > 0) would hinge on rounding.
+const double PHI_EPS = 1e-12;
 
 struct Body {
   int shape;            // 0 sphere, 1 box
@@ -218,6 +222,8 @@ void clamp_and_flag(Oracle& o, std::vector<uint8_t>& new_solid, std::vector<int>
     for (int b = 0; b < nb; ++b) {
       double v = o.bodies[b].phi[n];
       v = std::min(1.0, std::max(0.0, v));
+      if (v < PHI_EPS) v = 0.0;
+      if (v > 1.0 - PHI_EPS) v = 1.0;
       o.bodies[b].phi[n] = v;
       S += v;
     }
@@ -594,11 +600,12 @@ void advect(Oracle& o) {
 }
 
 // Step part 7b: Eq. sim_proc_phase_field_dynamics, one explicit Euler step (dt = 1).
-// READINGS: N = number of phases active at the cell (phi > 0 at the cell or one of its 6
+// READINGS: N = number of phases active at the cell (phi > PHI_EPS at the cell or one of its 6
 // face neighbours; the fluid phase is 1 - sum of solid phases); sigma between a solid and the
 // fluid is sigma_sf, between two solids sigma_ss; the volume term (pi^2/(4 eta)) Delta g_ab
 // equals D_a - D_b with D_B = (V_B(0) - sum phi_B) / #{0 < phi_B < 1} for a solid and D = 0 for
-// the fluid, and is applied only where 0 < phi_a < 1; 7-point Laplacian.
+// the fluid, and is applied only where 0 < phi_a < 1 (both "0 <" and "< 1" with the PHI_EPS
+// tolerance); 7-point Laplacian.
 void kinetics(Oracle& o) {
   const int nb = (int)o.bodies.size();
   if (nb == 0) return;
@@ -612,7 +619,7 @@ void kinetics(Oracle& o) {
     for (long n = 0; n < N; ++n) {
       double v = o.bodies[b].phi[n];
       s += v;
-      if (v > 0.0 && v < 1.0) cnt++;
+      if (v > PHI_EPS && v < 1.0 - PHI_EPS) cnt++;
     }
     D[b] = cnt ? (o.bodies[b].vol_ref - s) / (double)cnt : 0.0;
   }
@@ -635,12 +642,12 @@ void kinetics(Oracle& o) {
         int na = 0;
         for (int b = 0; b < nb && na < 63; ++b) {
           const std::vector<double>& ph = o.bodies[b].phi;
-          bool on = ph[n] > 0.0;
-          for (int k = 0; k < 6 && !on; ++k) on = ph[nbr[k]] > 0.0;
+          bool on = ph[n] > PHI_EPS;
+          for (int k = 0; k < 6 && !on; ++k) on = ph[nbr[k]] > PHI_EPS;
           if (on) act[na++] = b;
         }
-        bool fl = S[n] < 1.0;
-        for (int k = 0; k < 6 && !fl; ++k) fl = S[nbr[k]] < 1.0;
+        bool fl = S[n] < 1.0 - PHI_EPS;
+        for (int k = 0; k < 6 && !fl; ++k) fl = S[nbr[k]] < 1.0 - PHI_EPS;
         if (fl) act[na++] = nb;
         if (na <= 1) continue;
         double I[64];
@@ -665,7 +672,7 @@ void kinetics(Oracle& o) {
           int a = act[ka];
           if (a == nb) continue;  // the fluid phase is implicit
           double pa = o.bodies[a].phi[n];
-          bool in_if = pa > 0.0 && pa < 1.0;
+          bool in_if = pa > PHI_EPS && pa < 1.0 - PHI_EPS;
           double rate = 0.0;
           for (int kb = 0; kb < na; ++kb) {
             if (kb == ka) continue;

@@ -291,6 +291,8 @@ static void enqueue_step(cbl_ctx* ctx) {
   const int nb = (int)ctx->hb.size();
   launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
                   ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s);
+  launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->max_tile, ctx->acc,
+                  ctx->st, ctx->pp.G, ctx->s);
   if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
   launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
                 ctx->s);
@@ -341,6 +343,8 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     CK(cudaEventRecord(ev[1], ctx->s));
     launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
                     ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 2);
+    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->max_tile,
+                    ctx->acc, ctx->st, ctx->pp.G, ctx->s);
     CK(cudaEventRecord(ev[2], ctx->s));
     if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
     CK(cudaEventRecord(ev[3], ctx->s));

@@ -109,6 +109,9 @@ void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_
                      const BodyDev* bodies, double* acc, double* mass_part, StepState* st,
                      double* diag_rho, double* diag_vel, const PhysParams& pp, cudaStream_t s,
                      int phases = 3);
+void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
+                     const void* psi, const BodyDev* bodies, int nb, int max_tile, double* acc,
+                     const StepState* st, double G, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,

@@ -137,11 +137,35 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// minimum image of a coordinate difference in (-1.5 n, 1.5 n): one wrap, the same result as
+// repeated wrapping
+template <typename R>
+__device__ __forceinline__ R mimg1(R d, int n) {
+  const R h = (R)0.5 * (R)n;
+  if (d >= h) d -= (R)n;
+  else if (d < -h) d += (R)n;
+  return d;
+}
+
+// moving-wall term of solid link i at fluid cell c: g_i = 2 rho w_i c_i.u_B(x - c_i/2) / c_s^2
+template <typename R>
+__device__ __forceinline__ R wall_term(const BodyDev& b, const Cell& c, const Lat& lat, int i, R rho) {
+  const R mx = (R)c.x - (R)0.5 * (R)cx_of(i), my = (R)c.y - (R)0.5 * (R)cy_of(i), mz = (R)c.z - (R)0.5 * (R)cz_of(i);
+  const R ax = mimg1<R>(mx - (R)b.X[0], lat.nx), ay = mimg1<R>(my - (R)b.X[1], lat.ny),
+          az = mimg1<R>(mz - (R)b.X[2], lat.nz);
+  const R wx = (R)b.W[0], wy = (R)b.W[1], wz = (R)b.W[2];
+  const R ux = (R)b.V[0] + (wy * az - wz * ay);
+  const R uy = (R)b.V[1] + (wz * ax - wx * az);
+  const R uz = (R)b.V[2] + (wx * ay - wy * ax);
+  const R cu = (R)cx_of(i) * ux + (R)cy_of(i) * uy + (R)cz_of(i) * uz;
+  return (R)2 * rho * (R)w_of(i) * cu * (R)3;
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restrict__ fb,
                                                  const uint16_t* __restrict__ flags,
                                                  const typename St<S>::R* __restrict__ psi,
-                                                 const BodyDev* __restrict__ bodies, double* __restrict__ acc,
+                                                 const BodyDev* __restrict__ bodies,
                                                  double* __restrict__ mass_part, const StepState* __restrict__ st,
                                                  double* __restrict__ diag_rho, double* __restrict__ diag_vel,
                                                  Lat lat, PhysParams pp) {
@@ -152,26 +176,7 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
-  double a12[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) a12[k] = 0.0;
-  int cur = -1;
-  double my_mass = 0.0;
-
-  auto flush = [&](int B) {
-    if (B < 0) return;
-#pragma unroll
-    for (int k = 0; k < 12; ++k)
-      if (a12[k] != 0.0) atomicAdd(acc + (size_t)B * ACC_N + k, a12[k]);
-  };
-  auto select = [&](int B) {
-    if (B != cur) {
-      flush(cur);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) a12[k] = 0.0;
-      cur = B;
-    }
-  };
+  R my_mass = 0;
 
   uint16_t fl = valid ? flags[n] : F_SOLID;
   if (valid && (fl & F_SOLID)) {
@@ -185,72 +190,40 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
     }
   } else if (valid) {
     Cell c = cell_of(n, lat);
+    // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
+    // it needs only psi, so the populations are not yet live
+    const R ps = psi[n];
+    R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const R wp = (R)w_of(i) * psi[nbr(c, lat, i, +1)];
+      if (cx_of(i)) sx += wp * (R)cx_of(i);
+      if (cy_of(i)) sy += wp * (R)cy_of(i);
+      if (cz_of(i)) sz += wp * (R)cz_of(i);
+    }
+    const R mG = -(R)pp.G * ps;
+    const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
     R fi[Q];
     unsigned sl;
     pull<S>(src, flags, lat, c, n, fi, sl);
     R rho = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) rho += fi[i];
-    my_mass = (double)rho;
+    my_mass = rho;
     if (sl) {
-      // moving-wall term g_i = 2 rho w_i c_i.u_B(x - c_i/2) / c_s^2 on each solid link, the mass
-      // correction delta rho = -sum g_i on the rest population, and the momentum handed to the
-      // body: -c_i (2 f*_opp(x) + g_i) with the arm at the link midpoint.
+      // moving-wall term on each solid link and the mass correction delta rho = -sum g_i on the
+      // rest population (Eqs. lb_bounce_back_us, lb_bounce_back_mass)
       R drho = 0;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         if (!(sl & (1u << i))) continue;
-        long long s = nbr(c, lat, i, -1);
-        int B = __ldg(flags + s) & F_OWNER;
-        const BodyDev& b = bodies[B];
-        double mid[3] = {c.x - 0.5 * cx_of(i), c.y - 0.5 * cy_of(i), c.z - 0.5 * cz_of(i)};
-        double arm[3] = {mimg(mid[0] - b.X[0], lat.nx), mimg(mid[1] - b.X[1], lat.ny),
-                         mimg(mid[2] - b.X[2], lat.nz)};
-        double wr[3];
-        cross3(b.W, arm, wr);
-        double cu = cx_of(i) * (b.V[0] + wr[0]) + cy_of(i) * (b.V[1] + wr[1]) + cz_of(i) * (b.V[2] + wr[2]);
-        R g = (R)2 * rho * (R)w_of(i) * (R)cu * (R)3;
-        R fbar = fi[i];  // = f*_opp(i)(x) on a solid link
+        const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
+        const R g = wall_term<R>(bodies[B], c, lat, i, rho);
         fi[i] += g;
         drho -= g;
-        double m2 = (double)((R)2 * fbar + g);
-        double dP[3] = {-cx_of(i) * m2, -cy_of(i) * m2, -cz_of(i) * m2};
-        double dL[3];
-        cross3(arm, dP, dL);
-        select(B);
-        a12[0] += dP[0]; a12[1] += dP[1]; a12[2] += dP[2];
-        a12[3] += dL[0]; a12[4] += dL[1]; a12[5] += dL[2];
       }
       fi[0] += drho;
     }
-    // Shan-Chen force with wetting; reaction on the owner of each solid neighbour
-    const R ps = psi[n];
-    R sx = 0, sy = 0, sz = 0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      long long m = nbr(c, lat, i, +1);
-      R wp = (R)w_of(i) * psi[m];
-      sx += wp * (R)cx_of(i);
-      sy += wp * (R)cy_of(i);
-      sz += wp * (R)cz_of(i);
-      uint16_t fm = __ldg(flags + m);
-      if (fm & F_SOLID) {
-        int B = fm & F_OWNER;
-        const BodyDev& b = bodies[B];
-        R gpw = (R)pp.G * ps * wp;
-        double fr[3] = {(double)(gpw * (R)cx_of(i)), (double)(gpw * (R)cy_of(i)), (double)(gpw * (R)cz_of(i))};
-        double pos[3] = {(double)c.x + cx_of(i), (double)c.y + cy_of(i), (double)c.z + cz_of(i)};
-        double arm[3] = {mimg(pos[0] - b.X[0], lat.nx), mimg(pos[1] - b.X[1], lat.ny),
-                         mimg(pos[2] - b.X[2], lat.nz)};
-        double tq[3];
-        cross3(arm, fr, tq);
-        select(B);
-        a12[6] += fr[0]; a12[7] += fr[1]; a12[8] += fr[2];
-        a12[9] += tq[0]; a12[10] += tq[1]; a12[11] += tq[2];
-      }
-    }
-    const R mG = -(R)pp.G * ps;
-    const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
     // velocity with the half-force shift, Eq. fluid_velocity
     R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
 #pragma unroll
@@ -261,9 +234,10 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
     }
     R vx = 0, vy = 0, vz = 0;
     if (rho > (R)0) {
-      vx = mx / rho;
-      vy = my / rho;
-      vz = mz / rho;
+      const R ir = (R)1 / rho;
+      vx = mx * ir;
+      vy = my * ir;
+      vz = mz * ir;
     }
     const R itau = (R)1 / (R)pp.tau;
     const R pref = (R)1 - (R)0.5 * itau;
@@ -285,8 +259,137 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
       diag_vel[3 * n + 2] = (double)vz;
     }
   }
+  // fluid mass: warp sums in the working precision, block partial sums in FP64, summed in a fixed
+  // order by the body kernel
+  __shared__ double wsum[8];
+  R m = my_mass;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (double)m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    mass_part[blockIdx.x] = t;
+  }
+}
 
-  // ---- per-body reduction: warp-uniform body -> shuffle sum, else per-lane atomics ----------
+// ---- solid-fluid force on the bodies ---------------------------------------------------------
+// Over the body tiles (each cell once: the lowest-id tile that covers it). For a fluid cell x with
+// a solid upstream neighbour s = x - c_i (owner B): momentum exchange -c_i (2 f*_opp(i)(x) + g_i)
+// with the arm at the link midpoint (Eq. solid_liquid_force). For a solid downstream neighbour
+// x + c_i (owner B): the reaction of the Shan-Chen force, +G psi(x) w_i psi(x + c_i) c_i, arm
+// x + c_i - X_B (Sec. 3.2.3). Reads the same source populations and psi as the collision, so g_i
+// and rho are bit-identical to the ones it used.
+__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
+                                                 int gz, const Lat& lat) {
+  for (int k = 0; k < b.nnb; ++k) {
+    int o = b.nbl[k];
+    if (o >= self) break;
+    const BodyDev& ob = bodies[o];
+    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
+        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
+      return true;
+  }
+  return false;
+}
+
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
+                                                  const uint16_t* __restrict__ flags,
+                                                  const typename St<S>::R* __restrict__ psi,
+                                                  const BodyDev* __restrict__ bodies, double* __restrict__ acc,
+                                                  const StepState* __restrict__ st, Lat lat, double G) {
+  using R = typename St<S>::R;
+  const int self = blockIdx.y;
+  const BodyDev& tb = bodies[self];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double a12[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a12[k] = 0.0;
+  int cur = -1;
+  auto flush = [&](int B) {
+    if (B < 0) return;
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (a12[k] != 0.0) atomicAdd(acc + (size_t)B * ACC_N + k, a12[k]);
+  };
+  auto select = [&](int B) {
+    if (B != cur) {
+      flush(cur);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) a12[k] = 0.0;
+      cur = B;
+    }
+  };
+  bool work = false;
+  long long n = 0;
+  Cell c;
+  if (t < tb.sz) {
+    const int i0 = (int)(t % tb.L[0]);
+    const long long r = t / tb.L[0];
+    const int i1 = (int)(r % tb.L[1]), i2 = (int)(r / tb.L[1]);
+    const int gx = wrapi(tb.o[0] + i0, lat.nx), gy = wrapi(tb.o[1] + i1, lat.ny), gz = wrapi(tb.o[2] + i2, lat.nz);
+    n = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
+    if (!(flags[n] & F_SOLID) && !(tb.nnb && covered_by_lower(bodies, tb, self, gx, gy, gz, lat))) {
+      c = cell_of(n, lat);
+      bool near = false;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) near |= (__ldg(flags + nbr(c, lat, i, +1)) & F_SOLID) != 0;
+      work = near;
+    }
+  }
+  if (work) {
+    const S* __restrict__ src = st->parity ? fb : fa;
+    const size_t N = (size_t)lat.N;
+    R fi[Q];
+    unsigned sl;
+    pull<S>(src, flags, lat, c, n, fi, sl);
+    R rho = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += fi[i];
+    for (int i = 1; i < Q; ++i) {
+      if (!(sl & (1u << i))) continue;
+      const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
+      const BodyDev& b = bodies[B];
+      const R g = wall_term<R>(b, c, lat, i, rho);
+      const R fbar = fi[i];  // f*_opp(i)(x)
+      const double m2 = (double)((R)2 * fbar + g);
+      const double dP[3] = {-cx_of(i) * m2, -cy_of(i) * m2, -cz_of(i) * m2};
+      const double mid[3] = {c.x - 0.5 * cx_of(i), c.y - 0.5 * cy_of(i), c.z - 0.5 * cz_of(i)};
+      const double arm[3] = {mimg(mid[0] - b.X[0], lat.nx), mimg(mid[1] - b.X[1], lat.ny),
+                             mimg(mid[2] - b.X[2], lat.nz)};
+      select(B);
+      a12[0] += dP[0];
+      a12[1] += dP[1];
+      a12[2] += dP[2];
+      a12[3] += arm[1] * dP[2] - arm[2] * dP[1];
+      a12[4] += arm[2] * dP[0] - arm[0] * dP[2];
+      a12[5] += arm[0] * dP[1] - arm[1] * dP[0];
+    }
+    const R ps = psi[n];
+    for (int i = 1; i < Q; ++i) {
+      const long long m = nbr(c, lat, i, +1);
+      const uint16_t fm = __ldg(flags + m);
+      if (!(fm & F_SOLID)) continue;
+      const int B = fm & F_OWNER;
+      const BodyDev& b = bodies[B];
+      const R gpw = (R)G * ps * ((R)w_of(i) * psi[m]);
+      const double fr[3] = {(double)(gpw * (R)cx_of(i)), (double)(gpw * (R)cy_of(i)), (double)(gpw * (R)cz_of(i))};
+      const double arm[3] = {mimg((double)c.x + cx_of(i) - b.X[0], lat.nx), mimg((double)c.y + cy_of(i) - b.X[1], lat.ny),
+                             mimg((double)c.z + cz_of(i) - b.X[2], lat.nz)};
+      select(B);
+      a12[6] += fr[0];
+      a12[7] += fr[1];
+      a12[8] += fr[2];
+      a12[9] += arm[1] * fr[2] - arm[2] * fr[1];
+      a12[10] += arm[2] * fr[0] - arm[0] * fr[2];
+      a12[11] += arm[0] * fr[1] - arm[1] * fr[0];
+    }
+    (void)N;
+  }
+  // warp-uniform body -> shuffle sum, else per-lane atomics
   const unsigned any = __ballot_sync(0xffffffffu, cur >= 0);
   if (any) {
     const int lead = __ffs(any) - 1;
@@ -301,16 +404,6 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
     } else {
       flush(cur);
     }
-  }
-  // ---- fluid mass: block partial sums (summed in a fixed order by the body kernel) ----------
-  __shared__ double wsum[8];
-  double m = warp_sum(my_mass);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-    mass_part[blockIdx.x] = t;
   }
 }
 
@@ -337,19 +430,6 @@ __global__ void k_init_fluid(S* __restrict__ f, const uint16_t* __restrict__ fla
 }
 
 // ---- cover refill ----------------------------------------------------------------------------
-__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
-                                                 int gz, const Lat& lat) {
-  for (int k = 0; k < b.nnb; ++k) {
-    int o = b.nbl[k];
-    if (o >= self) break;
-    const BodyDev& ob = bodies[o];
-    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
-        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
-      return true;
-  }
-  return false;
-}
-
 template <typename S>
 __global__ void k_refill(S* __restrict__ fa, S* __restrict__ fb, const uint16_t* __restrict__ flags,
                          const BodyDev* __restrict__ bodies, StepState* st, Lat lat) {
@@ -457,8 +537,29 @@ static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void
   const unsigned blocks = (unsigned)((lat.N + T - 1) / T);
   if (phases & 1) k_density<S><<<blocks, T, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
   if (phases & 2)
-    k_collide<S><<<blocks, T, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, acc, mass_part, st, diag_rho,
-                                      diag_vel, lat, pp);
+    k_collide<S><<<blocks, T, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel,
+                                      lat, pp);
+}
+
+template <typename S>
+static void boundary_t(const Lat& lat, const S* fa, const S* fb, const uint16_t* flags, const void* psi,
+                       const BodyDev* bodies, int nb, int max_tile, double* acc, const StepState* st, double G,
+                       cudaStream_t s) {
+  using R = typename St<S>::R;
+  dim3 grid((unsigned)((max_tile + 255) / 256), (unsigned)nb);
+  k_boundary<S><<<grid, 256, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, acc, st, lat, G);
+}
+
+void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags, const void* psi,
+                     const BodyDev* bodies, int nb, int max_tile, double* acc, const StepState* st, double G,
+                     cudaStream_t s) {
+  if (nb == 0) return;
+  if (prec == 0)
+    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, psi, bodies, nb, max_tile, acc, st, G, s);
+  else if (prec == 1)
+    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, psi, bodies, nb, max_tile, acc, st, G, s);
+  else
+    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, psi, bodies, nb, max_tile, acc, st, G, s);
 }
 
 unsigned lbm_blocks(const Lat& lat) { return (unsigned)((lat.N + 255) / 256); }

@@ -18,6 +18,10 @@
 namespace cbl {
 
 constexpr double PI = 3.14159265358979323846;
+// A phase counts as present where phi > PHI_EPS; the clamp sets phi < PHI_EPS to 0 and
+// phi > 1 - PHI_EPS to 1. This keeps "present" (which sets N in the kinetics) from hinging on the
+// last bit of a rounding, and keeps the support of a moving field compact.
+constexpr double PHI_EPS = 1e-12;
 constexpr int MAXOFF = 512;
 __constant__ int c_off[3 * MAXOFF];
 __constant__ int c_noff;
@@ -182,6 +186,8 @@ __global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat
   for (int k = 0; k < m; ++k) {
     double v = *ptr[k];
     v = fmin(1.0, fmax(0.0, v));
+    if (v < PHI_EPS) v = 0.0;
+    if (v > 1.0 - PHI_EPS) v = 1.0;
     *ptr[k] = v;
     S += v;
   }
@@ -283,8 +289,19 @@ __global__ void k_repulsion(const BodyDev* bodies, const double* arena, double* 
   if (t < a.sz && a.nnb > 0 && arena[a.off + t] >= thr) {
     TileCell c = tile_cell(a, t, lat);
     double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
+    const int R = (int)ceil(rc);
+    const int g[3] = {c.gx, c.gy, c.gz};
+    const int nn[3] = {lat.nx, lat.ny, lat.nz};
     for (int k = 0; k < a.nnb; ++k) {
       const BodyDev& b = bodies[a.nbl[k]];
+      // skip unless this point lies within rc of the other body's tile
+      bool near = true;
+      for (int d = 0; d < 3; ++d) {
+        if (b.L[d] >= nn[d]) continue;
+        const int l = wrapi(g[d] - b.o[d], nn[d]);
+        if (l >= b.L[d] + R && l < nn[d] - R) near = false;
+      }
+      if (!near) continue;
       const double* bb = arena + b.off;
       for (int j = 0; j < c_noff; ++j) {
         int dx = c_off[3 * j], dy = c_off[3 * j + 1], dz = c_off[3 * j + 2];
@@ -393,9 +410,14 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
   }
   // fluid mass of this step: fixed-order sum of the per-block partials
   __shared__ double red[256];
-  double s = 0.0;
-  for (unsigned k = threadIdx.x; k < n_mass_part; k += blockDim.x) s += mass_part[k];
-  red[threadIdx.x] = s;
+  double s4[4] = {0.0, 0.0, 0.0, 0.0};  // independent partial sums keep several loads in flight
+  unsigned k = threadIdx.x;
+  for (; k + 3 * blockDim.x < n_mass_part; k += 4 * blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s4[u] += __ldg(mass_part + k + u * blockDim.x);
+  }
+  for (; k < n_mass_part; k += blockDim.x) s4[0] += __ldg(mass_part + k);
+  red[threadIdx.x] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -479,7 +501,7 @@ __global__ void k_sweep(const BodyDev* bodies, double* arena, Lat lat, int d, in
   }
   if (last) {
     double sv = dwarp_sum(inside ? v : 0.0);
-    double sc = dwarp_sum((inside && v > 0.0 && v < 1.0) ? 1.0 : 0.0);
+    double sc = dwarp_sum((inside && v > PHI_EPS && v < 1.0 - PHI_EPS) ? 1.0 : 0.0);
     if ((threadIdx.x & 31) == 0) {
       if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
       if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
@@ -493,7 +515,7 @@ __global__ void k_volume(const BodyDev* bodies, const double* arena, double* vol
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double v = t < b.sz ? arena[b.off + t] : 0.0;
   double sv = dwarp_sum(v);
-  double sc = dwarp_sum((v > 0.0 && v < 1.0) ? 1.0 : 0.0);
+  double sc = dwarp_sum((v > PHI_EPS && v < 1.0 - PHI_EPS) ? 1.0 : 0.0);
   if ((threadIdx.x & 31) == 0) {
     if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
     if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
@@ -501,8 +523,8 @@ __global__ void k_volume(const BodyDev* bodies, const double* arena, double* vol
 }
 
 // ---- MPF kinetics ------------------------------------------------------------------------------
-// For body a at cell g: active phases = solids with phi > 0 at g or a face neighbour, plus the fluid
-// if 1 - sum phi > 0 there; N = their number; explicit Euler step of
+// For body a at cell g: active phases = solids with phi > PHI_EPS at g or a face neighbour, plus the
+// fluid if 1 - sum phi > PHI_EPS there; N = their number; explicit Euler step of
 // phi_a += sum_b (M/N) [ s_ab (I_a - I_b) + sum_c (s_bc - s_ac) I_c + (D_a - D_b if 0<phi_a<1) ]
 // with I = lap(phi) + (pi/eta)^2 phi, D_B = (V_B(0) - sum phi_B) / #{0 < phi_B < 1}, D_fluid = 0.
 constexpr int MAXACT = 8;
@@ -520,7 +542,7 @@ __global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* v
   bool act_a = false;
   for (int k = 0; k < 7; ++k) {
     pa[k] = phi_at(in, b, c.gx + nxv[k][0], c.gy + nxv[k][1], c.gz + nxv[k][2], lat);
-    act_a |= pa[k] > 0.0;
+    act_a |= pa[k] > PHI_EPS;
   }
   if (!act_a) {
     out[t] = pa[0];
@@ -551,7 +573,7 @@ __global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* v
     bool on = false;
     for (int k = 0; k < 7; ++k) {
       v7[k] = phi_at(ob, o, c.gx + nxv[k][0], c.gy + nxv[k][1], c.gz + nxv[k][2], lat);
-      on |= v7[k] > 0.0;
+      on |= v7[k] > PHI_EPS;
     }
     if (!on) continue;
     if (na < MAXACT - (pos_self < 0 ? 1 : 0)) {  // always keep a slot for self
@@ -563,7 +585,7 @@ __global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* v
     }
   }
   bool fl = false;
-  for (int k = 0; k < 7; ++k) fl |= S[k] < 1.0;
+  for (int k = 0; k < 7; ++k) fl |= S[k] < 1.0 - PHI_EPS;
   const int N = na + (fl ? 1 : 0);
   if (N <= 1) {
     out[t] = pa[0];
@@ -588,7 +610,7 @@ __global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* v
   }
   auto sig = [&](int p, int q) { return (p == na || q == na) ? s_sf : s_ss; };
   const int a = pos_self;
-  const bool in_if = pa[0] > 0.0 && pa[0] < 1.0;
+  const bool in_if = pa[0] > PHI_EPS && pa[0] < 1.0 - PHI_EPS;
   double rate = 0.0;
   for (int bq = 0; bq < N; ++bq) {
     if (bq == a) continue;
