@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 # algorithmic bytes per cell update of the collision kernel: read 19 populations, write 19,
 # read the uint16 flag (the density pass and psi are implementation overhead)
 POP_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
-KERNELS_PER_STEP = 11  # density, collide, repulsion, bodies, 3 sweeps, kinetics, flags, refill, + diag memset
+KERNELS_PER_STEP = 11  # density, collide, boundary, repulsion, bodies, 3 sweeps, kinetics, flags, refill
 
 
 def alg_bytes_per_cell(prec):

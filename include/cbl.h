@@ -154,11 +154,11 @@ cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass);
 cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_error);
 
 /* Phases of one step, in launch order, as reported by cbl_time_phases. */
-#define CBL_NPHASES 8
-/* 0 pull + density + psi, 1 pull + force + collision + mass partials, then the solid-fluid
- * force on the bodies (momentum exchange and adhesion, FP64 sums), 2 solid-solid
- * repulsion, 3 rigid-body update, 4 phase-field advection (three sweeps), 5 phase-field kinetics,
- * 6 obstacle flags, 7 cover refill. */
+#define CBL_NPHASES 9
+/* 0 pull + density + psi, 1 pull + force + collision + mass partials, 2 solid-fluid force on the
+ * bodies (momentum exchange and adhesion, FP64 sums), 3 solid-solid repulsion, 4 rigid-body update,
+ * 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle flags, 8 cover refill
+ * and boundary-cell list. */
 
 /* Run nsteps time steps launched kernel by kernel (not through the graph) with CUDA events recorded
  * on the context's stream between the phases, synchronise, and write the mean duration per step of

@@ -266,7 +266,7 @@ class Sim:
         self._ck(self._lib.cbl_total_mass(self._h, ctypes.byref(m)))
         return m.value
 
-    PHASES = ("density", "collide", "repulsion", "bodies", "advect", "kinetics", "flags", "refill")
+    PHASES = ("density", "collide", "boundary", "repulsion", "bodies", "advect", "kinetics", "flags", "refill")
 
     def time_phases(self, n):
         """Mean per-step duration (ms) of each kernel phase over n steps, CUDA events on the stream."""

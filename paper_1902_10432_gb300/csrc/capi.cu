@@ -34,6 +34,7 @@ struct cbl_ctx {
   double *acc = nullptr, *last = nullptr, *volacc = nullptr, *scratch = nullptr;
   double* mass_part = nullptr;
   unsigned n_mass_part = 0;
+  int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -140,7 +141,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   ctx->flags = (uint16_t*)dalloc(ctx, N * 2);
   ctx->diag_rho = (double*)dalloc(ctx, N * 8);
   ctx->diag_vel = (double*)dalloc(ctx, N * 24);
-  ctx->n_mass_part = lbm_blocks(ctx->lat);
+  ctx->n_mass_part = MASS_SLOTS;
   ctx->mass_part = (double*)dalloc(ctx, (size_t)ctx->n_mass_part * 8);
   ctx->st = (StepState*)dalloc(ctx, sizeof(StepState));
   if (!ctx->fa || !ctx->fb || !ctx->psi || !ctx->flags || !ctx->diag_rho || !ctx->diag_vel || !ctx->mass_part ||
@@ -152,6 +153,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   }
   cudaMemsetAsync(ctx->flags, 0, N * 2, ctx->s);
   cudaMemsetAsync(ctx->st, 0, sizeof(StepState), ctx->s);
+  cudaMemsetAsync(ctx->mass_part, 0, (size_t)ctx->n_mass_part * 8, ctx->s);
   set_fp16_weights(ctx->s);
   set_repulsion_offsets(p.rc, ctx->s);
   cudaError_t e = cudaGetLastError();
@@ -235,7 +237,8 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
     ctx->last = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
     ctx->volacc = (double*)dalloc(ctx, sizeof(double) * 2 * nb);
     ctx->scratch = (double*)dalloc(ctx, sizeof(double) * 9 * nb);
-    if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch)
+    ctx->blist = (int*)dalloc(ctx, sizeof(int) * (size_t)(ctx->arena_n / 3));
+    if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch || !ctx->blist)
       return fail(ctx, CBL_ERR_OOM, "device allocation failed (bodies)");
     CK(cudaMemcpyAsync(ctx->db, ctx->hb.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
     CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * ACC_N * nb, ctx->s));
@@ -243,7 +246,8 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
     CK(cudaMemsetAsync(ctx->volacc, 0, sizeof(double) * 2 * nb, ctx->s));
     launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
     launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
-    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 1, ctx->s);
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 1, ctx->st,
+                 ctx->s);
     launch_body_props(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->scratch, ctx->s);
   }
   double* drho = (double*)dalloc(ctx, N * 8);
@@ -252,6 +256,9 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
   CK(cudaMemcpyAsync(drho, rho_host, N * 8, cudaMemcpyHostToDevice, ctx->s));
   if (du) CK(cudaMemcpyAsync(du, u_host, N * 24, cudaMemcpyHostToDevice, ctx->s));
   launch_init_fluid(ctx->prec, ctx->lat, ctx->fa, ctx->flags, drho, du, ctx->s);
+  // first boundary-cell list (no cover events yet, so the pass only scans)
+  launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                ctx->s);
   CK(cudaMemsetAsync(ctx->diag_rho, 0, N * 8, ctx->s));
   CK(cudaMemsetAsync(ctx->diag_vel, 0, N * 24, ctx->s));
   CK(cudaGetLastError());
@@ -289,9 +296,9 @@ cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const dou
 
 static void enqueue_step(cbl_ctx* ctx) {
   const int nb = (int)ctx->hb.size();
-  launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
-                  ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s);
-  launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->max_tile, ctx->acc,
+  launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+                  lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s);
+  launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->acc, ctx->blist,
                   ctx->st, ctx->pp.G, ctx->s);
   if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
   launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
@@ -299,8 +306,10 @@ static void enqueue_step(cbl_ctx* ctx) {
   if (nb) {
     launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
     if (ctx->pp.mpf) launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
-    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->s);
-    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->s);
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
+                 ctx->s);
+    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                  ctx->s);
   }
 }
 
@@ -338,30 +347,35 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
   CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
   for (int it = 0; it < nsteps; ++it) {
     CK(cudaEventRecord(ev[0], ctx->s));
-    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
-                    ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 1);
+    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+                    lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 1);
     CK(cudaEventRecord(ev[1], ctx->s));
-    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->acc, ctx->mass_part,
-                    ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 2);
-    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->max_tile,
-                    ctx->acc, ctx->st, ctx->pp.G, ctx->s);
+    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+                    lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 2);
     CK(cudaEventRecord(ev[2], ctx->s));
-    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
+    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->acc, ctx->blist,
+                    ctx->st, ctx->pp.G, ctx->s);
     CK(cudaEventRecord(ev[3], ctx->s));
+    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
+    CK(cudaEventRecord(ev[4], ctx->s));
     launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part,
                   ctx->st, ctx->s);
-    CK(cudaEventRecord(ev[4], ctx->s));
-    if (nb) launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
     CK(cudaEventRecord(ev[5], ctx->s));
+    if (nb) launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
+    CK(cudaEventRecord(ev[6], ctx->s));
     if (nb && ctx->pp.mpf)
       launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
-    CK(cudaEventRecord(ev[6], ctx->s));
-    if (nb) launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->s);
     CK(cudaEventRecord(ev[7], ctx->s));
-    if (nb) launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->s);
+    if (nb)
+      launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
+                   ctx->s);
     CK(cudaEventRecord(ev[8], ctx->s));
+    if (nb)
+      launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                    ctx->s);
+    CK(cudaEventRecord(ev[9], ctx->s));
     CK(cudaGetLastError());
-    CK(cudaEventSynchronize(ev[8]));
+    CK(cudaEventSynchronize(ev[9]));
     for (int k = 0; k < CBL_NPHASES; ++k) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));

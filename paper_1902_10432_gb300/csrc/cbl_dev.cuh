@@ -38,6 +38,9 @@ constexpr uint16_t F_OWNER = 0x3FFF;
 constexpr int MAX_BODIES = 0x3FFF;
 constexpr int MAXNB = 24;  // neighbour-list capacity per body (tiles that overlap)
 
+// Fluid-mass accumulation slots written by the collision kernel and summed by the body kernel.
+constexpr int MASS_SLOTS = 256;
+
 // Device error word bits.
 constexpr int E_TILE = 1, E_NBLIST = 2, E_REFILL = 4;
 
@@ -74,6 +77,8 @@ struct StepState {
   double mass;       // fluid mass of the current step (accumulating)
   double last_mass;  // fluid mass of the last completed step
   unsigned long long lost_refills;
+  unsigned nbnd;     // entries of the boundary-cell list (fluid cells next to a solid)
+  unsigned ncover;   // nodes covered in this step's flag update
 };
 
 struct PhysParams {
@@ -106,28 +111,28 @@ void set_fp16_weights(cudaStream_t s);
 unsigned lbm_blocks(const Lat& lat);
 // phases: bit 0 launches the density kernel, bit 1 the collision kernel
 void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
-                     const BodyDev* bodies, double* acc, double* mass_part, StepState* st,
+                     const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st,
                      double* diag_rho, double* diag_vel, const PhysParams& pp, cudaStream_t s,
                      int phases = 3);
 void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
-                     const void* psi, const BodyDev* bodies, int nb, int max_tile, double* acc,
+                     const void* psi, const BodyDev* bodies, int nb, double* acc, const int* blist,
                      const StepState* st, double G, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,
-                   const BodyDev* bodies, int nb, int max_tile, StepState* st, cudaStream_t s);
+                   const BodyDev* bodies, int nb, int max_tile, StepState* st, int* blist, cudaStream_t s);
 
 void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
                       double eta, cudaStream_t s);
 void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st, cudaStream_t s);
 void launch_flags(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, uint16_t* flags,
-                  double threshold, int init, cudaStream_t s);
+                  double threshold, int init, StepState* st, cudaStream_t s);
 void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
                        double* scratch, cudaStream_t s);
 void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena,
                       double* acc, const PhysParams& pp, cudaStream_t s);
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   const double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
+                   double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf,
                    double* volacc, StepState* st, cudaStream_t s);
 void set_repulsion_offsets(double rc, cudaStream_t s);

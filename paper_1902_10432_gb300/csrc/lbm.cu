@@ -3,15 +3,19 @@
 //  k_density  : pull streaming with half-way bounce-back, density, psi = 1 - exp(-rho/rho0)
 //               (Eq. lb_streaming, Eq. lb_bounce_back, Eq. mean_field_potential); solid cells
 //               carry psi of their owner's wetting density (Sec. 3.2.3).
-//  k_collide  : pull again, moving-wall term g and local mass correction
-//               (Eqs. lb_bounce_back_us, lb_bounce_back_mass), momentum exchange on the bodies
-//               (Eq. solid_liquid_force), Shan-Chen force (Eq. benzi_force) and its reaction on
-//               the bodies, Guo-forced BGK collision (Eqs. lb_collision, distribution_eq,
-//               guo_forcing, fluid_velocity), FP64 per-body and mass reductions.
+//  k_collide  : Shan-Chen force (Eq. benzi_force), pull again, moving-wall term g and local mass
+//               correction (Eqs. lb_bounce_back_us, lb_bounce_back_mass), Guo-forced BGK
+//               collision (Eqs. lb_collision, distribution_eq, guo_forcing, fluid_velocity),
+//               FP64 fluid-mass partial sums.
+//  k_boundary : over the list of fluid cells next to a solid: momentum exchange on the bodies
+//               (Eq. solid_liquid_force) and the reaction of the Shan-Chen force (Sec. 3.2.3),
+//               summed in FP64.
 //  k_refill   : cover refill of nodes that became solid (Sec. 3.2.2), as a gather over each
-//               fluid node's 26 neighbours so that no two threads write the same populations.
+//               fluid node's 26 neighbours so that no two threads write the same populations; the
+//               same scan rebuilds the boundary-cell list for the next step.
 //
-// Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights.
+// Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights. The
+// two lattice-wide kernels use a grid-stride loop over a grid of a few blocks per SM.
 #include "cbl_dev.cuh"
 
 namespace cbl {
@@ -105,30 +109,26 @@ __global__ void __launch_bounds__(256) k_density(const S* __restrict__ fa, const
                                                  const BodyDev* __restrict__ bodies,
                                                  typename St<S>::R* __restrict__ psi, Lat lat, double rho0) {
   using R = typename St<S>::R;
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= lat.N) return;
   const S* __restrict__ f = st->parity ? fb : fa;
-  uint16_t fl = flags[n];
-  R ps;
-  if (fl & F_SOLID) {
-    ps = (R)bodies[fl & F_OWNER].psi_wet;
-  } else {
-    Cell c = cell_of(n, lat);
-    R fi[Q];
-    unsigned sl;
-    pull<S>(f, flags, lat, c, n, fi, sl);
-    R rho = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+#pragma unroll 1
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < lat.N; n += stride) {
+    uint16_t fl = flags[n];
+    R ps;
+    if (fl & F_SOLID) {
+      ps = (R)bodies[fl & F_OWNER].psi_wet;
+    } else {
+      Cell c = cell_of(n, lat);
+      R fi[Q];
+      unsigned sl;
+      pull<S>(f, flags, lat, c, n, fi, sl);
+      R rho = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) rho += fi[i];
-    ps = (R)1 - exp(-rho / (R)rho0);
+      for (int i = 0; i < Q; ++i) rho += fi[i];
+      ps = (R)1 - exp(-rho / (R)rho0);
+    }
+    psi[n] = ps;
   }
-  psi[n] = ps;
-}
-
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double r[3]) {
-  r[0] = a[1] * b[2] - a[2] * b[1];
-  r[1] = a[2] * b[0] - a[0] * b[2];
-  r[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -137,7 +137,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// minimum image of a coordinate difference in (-1.5 n, 1.5 n): one wrap, the same result as
+// minimum image of a coordinate difference in (-1.5 n, 1.5 n): one wrap gives the same result as
 // repeated wrapping
 template <typename R>
 __device__ __forceinline__ R mimg1(R d, int n) {
@@ -170,16 +170,14 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
                                                  double* __restrict__ diag_rho, double* __restrict__ diag_vel,
                                                  Lat lat, PhysParams pp) {
   using R = typename St<S>::R;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = n < lat.N;
   const size_t N = (size_t)lat.N;
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   R my_mass = 0;
-
-  uint16_t fl = valid ? flags[n] : F_SOLID;
-  if (valid && (fl & F_SOLID)) {
+  const uint16_t fl = n < lat.N ? flags[n] : (uint16_t)0;
+  if (n < lat.N && (fl & F_SOLID)) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
     if (diag) {
@@ -188,7 +186,7 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
       diag_vel[3 * n + 1] = 0.0;
       diag_vel[3 * n + 2] = 0.0;
     }
-  } else if (valid) {
+  } else if (n < lat.N) {
     Cell c = cell_of(n, lat);
     // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
     // it needs only psi, so the populations are not yet live
@@ -259,150 +257,120 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
       diag_vel[3 * n + 2] = (double)vz;
     }
   }
-  // fluid mass: warp sums in the working precision, block partial sums in FP64, summed in a fixed
-  // order by the body kernel
+  // fluid mass in FP64: block sums added into one of MASS_SLOTS slots (spreads the atomics); the
+  // body kernel adds the slots in a fixed order and clears them
   __shared__ double wsum[8];
-  R m = my_mass;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (double)m;
+  double m = warp_sum((double)my_mass);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-    mass_part[blockIdx.x] = t;
+    if (t != 0.0) atomicAdd(mass_part + (blockIdx.x & (MASS_SLOTS - 1)), t);
   }
 }
 
 // ---- solid-fluid force on the bodies ---------------------------------------------------------
-// Over the body tiles (each cell once: the lowest-id tile that covers it). For a fluid cell x with
-// a solid upstream neighbour s = x - c_i (owner B): momentum exchange -c_i (2 f*_opp(i)(x) + g_i)
-// with the arm at the link midpoint (Eq. solid_liquid_force). For a solid downstream neighbour
-// x + c_i (owner B): the reaction of the Shan-Chen force, +G psi(x) w_i psi(x + c_i) c_i, arm
-// x + c_i - X_B (Sec. 3.2.3). Reads the same source populations and psi as the collision, so g_i
-// and rho are bit-identical to the ones it used.
-__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
-                                                 int gz, const Lat& lat) {
-  for (int k = 0; k < b.nnb; ++k) {
-    int o = b.nbl[k];
-    if (o >= self) break;
-    const BodyDev& ob = bodies[o];
-    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
-        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
-      return true;
-  }
-  return false;
-}
-
-
+// For each listed fluid cell x: for a solid upstream neighbour s = x - c_i (owner B), momentum
+// exchange -c_i (2 f*_opp(i)(x) + g_i) with the arm at the link midpoint (Eq. solid_liquid_force);
+// for a solid downstream neighbour x + c_i (owner B), the reaction of the Shan-Chen force,
+// +G psi(x) w_i psi(x + c_i) c_i, arm x + c_i - X_B (Sec. 3.2.3). It reads the same source
+// populations and psi as the collision, so g_i and rho are bit-identical to the ones it used.
 template <typename S>
-__global__ void __launch_bounds__(256) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
+__global__ void __launch_bounds__(128) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
                                                   const uint16_t* __restrict__ flags,
                                                   const typename St<S>::R* __restrict__ psi,
                                                   const BodyDev* __restrict__ bodies, double* __restrict__ acc,
-                                                  const StepState* __restrict__ st, Lat lat, double G) {
+                                                  const int* __restrict__ blist, const StepState* __restrict__ st,
+                                                  Lat lat, double G) {
   using R = typename St<S>::R;
-  const int self = blockIdx.y;
-  const BodyDev& tb = bodies[self];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double a12[12];
+  const unsigned count = st->nbnd;
+  const S* __restrict__ src = st->parity ? fb : fa;
+  const unsigned stride = gridDim.x * blockDim.x;
+  // whole-block rounds so that every lane reaches the shuffles below
+  for (unsigned base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const unsigned k = base + threadIdx.x;
+    double a12[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) a12[k] = 0.0;
-  int cur = -1;
-  auto flush = [&](int B) {
-    if (B < 0) return;
+    for (int q = 0; q < 12; ++q) a12[q] = 0.0;
+    int cur = -1;
+    auto flush = [&](int B) {
+      if (B < 0) return;
 #pragma unroll
-    for (int k = 0; k < 12; ++k)
-      if (a12[k] != 0.0) atomicAdd(acc + (size_t)B * ACC_N + k, a12[k]);
-  };
-  auto select = [&](int B) {
-    if (B != cur) {
-      flush(cur);
+      for (int q = 0; q < 12; ++q)
+        if (a12[q] != 0.0) atomicAdd(acc + (size_t)B * ACC_N + q, a12[q]);
+    };
+    auto select = [&](int B) {
+      if (B != cur) {
+        flush(cur);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) a12[k] = 0.0;
-      cur = B;
-    }
-  };
-  bool work = false;
-  long long n = 0;
-  Cell c;
-  if (t < tb.sz) {
-    const int i0 = (int)(t % tb.L[0]);
-    const long long r = t / tb.L[0];
-    const int i1 = (int)(r % tb.L[1]), i2 = (int)(r / tb.L[1]);
-    const int gx = wrapi(tb.o[0] + i0, lat.nx), gy = wrapi(tb.o[1] + i1, lat.ny), gz = wrapi(tb.o[2] + i2, lat.nz);
-    n = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
-    if (!(flags[n] & F_SOLID) && !(tb.nnb && covered_by_lower(bodies, tb, self, gx, gy, gz, lat))) {
-      c = cell_of(n, lat);
-      bool near = false;
-#pragma unroll
-      for (int i = 1; i < Q; ++i) near |= (__ldg(flags + nbr(c, lat, i, +1)) & F_SOLID) != 0;
-      work = near;
-    }
-  }
-  if (work) {
-    const S* __restrict__ src = st->parity ? fb : fa;
-    const size_t N = (size_t)lat.N;
-    R fi[Q];
-    unsigned sl;
-    pull<S>(src, flags, lat, c, n, fi, sl);
-    R rho = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) rho += fi[i];
-    for (int i = 1; i < Q; ++i) {
-      if (!(sl & (1u << i))) continue;
-      const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
-      const BodyDev& b = bodies[B];
-      const R g = wall_term<R>(b, c, lat, i, rho);
-      const R fbar = fi[i];  // f*_opp(i)(x)
-      const double m2 = (double)((R)2 * fbar + g);
-      const double dP[3] = {-cx_of(i) * m2, -cy_of(i) * m2, -cz_of(i) * m2};
-      const double mid[3] = {c.x - 0.5 * cx_of(i), c.y - 0.5 * cy_of(i), c.z - 0.5 * cz_of(i)};
-      const double arm[3] = {mimg(mid[0] - b.X[0], lat.nx), mimg(mid[1] - b.X[1], lat.ny),
-                             mimg(mid[2] - b.X[2], lat.nz)};
-      select(B);
-      a12[0] += dP[0];
-      a12[1] += dP[1];
-      a12[2] += dP[2];
-      a12[3] += arm[1] * dP[2] - arm[2] * dP[1];
-      a12[4] += arm[2] * dP[0] - arm[0] * dP[2];
-      a12[5] += arm[0] * dP[1] - arm[1] * dP[0];
-    }
-    const R ps = psi[n];
-    for (int i = 1; i < Q; ++i) {
-      const long long m = nbr(c, lat, i, +1);
-      const uint16_t fm = __ldg(flags + m);
-      if (!(fm & F_SOLID)) continue;
-      const int B = fm & F_OWNER;
-      const BodyDev& b = bodies[B];
-      const R gpw = (R)G * ps * ((R)w_of(i) * psi[m]);
-      const double fr[3] = {(double)(gpw * (R)cx_of(i)), (double)(gpw * (R)cy_of(i)), (double)(gpw * (R)cz_of(i))};
-      const double arm[3] = {mimg((double)c.x + cx_of(i) - b.X[0], lat.nx), mimg((double)c.y + cy_of(i) - b.X[1], lat.ny),
-                             mimg((double)c.z + cz_of(i) - b.X[2], lat.nz)};
-      select(B);
-      a12[6] += fr[0];
-      a12[7] += fr[1];
-      a12[8] += fr[2];
-      a12[9] += arm[1] * fr[2] - arm[2] * fr[1];
-      a12[10] += arm[2] * fr[0] - arm[0] * fr[2];
-      a12[11] += arm[0] * fr[1] - arm[1] * fr[0];
-    }
-    (void)N;
-  }
-  // warp-uniform body -> shuffle sum, else per-lane atomics
-  const unsigned any = __ballot_sync(0xffffffffu, cur >= 0);
-  if (any) {
-    const int lead = __ffs(any) - 1;
-    const int b0 = __shfl_sync(0xffffffffu, cur, lead);
-    const bool uniform = __all_sync(0xffffffffu, cur < 0 || cur == b0);
-    if (uniform) {
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        double v = warp_sum(cur >= 0 ? a12[k] : 0.0);
-        if ((threadIdx.x & 31) == lead && v != 0.0) atomicAdd(acc + (size_t)b0 * ACC_N + k, v);
+        for (int q = 0; q < 12; ++q) a12[q] = 0.0;
+        cur = B;
       }
-    } else {
-      flush(cur);
+    };
+    if (k < count) {
+      const long long n = blist[k];
+      const Cell c = cell_of(n, lat);
+      R fi[Q];
+      unsigned sl;
+      pull<S>(src, flags, lat, c, n, fi, sl);
+      R rho = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) rho += fi[i];
+      for (int i = 1; i < Q; ++i) {
+        if (!(sl & (1u << i))) continue;
+        const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
+        const BodyDev& b = bodies[B];
+        const R g = wall_term<R>(b, c, lat, i, rho);
+        const double m2 = (double)((R)2 * fi[i] + g);  // fi[i] = f*_opp(i)(x) on a solid link
+        const double dP[3] = {-cx_of(i) * m2, -cy_of(i) * m2, -cz_of(i) * m2};
+        const double arm[3] = {mimg1<double>(c.x - 0.5 * cx_of(i) - b.X[0], lat.nx),
+                               mimg1<double>(c.y - 0.5 * cy_of(i) - b.X[1], lat.ny),
+                               mimg1<double>(c.z - 0.5 * cz_of(i) - b.X[2], lat.nz)};
+        select(B);
+        a12[0] += dP[0];
+        a12[1] += dP[1];
+        a12[2] += dP[2];
+        a12[3] += arm[1] * dP[2] - arm[2] * dP[1];
+        a12[4] += arm[2] * dP[0] - arm[0] * dP[2];
+        a12[5] += arm[0] * dP[1] - arm[1] * dP[0];
+      }
+      const R ps = psi[n];
+      for (int i = 1; i < Q; ++i) {
+        const long long m = nbr(c, lat, i, +1);
+        const uint16_t fm = __ldg(flags + m);
+        if (!(fm & F_SOLID)) continue;
+        const int B = fm & F_OWNER;
+        const BodyDev& b = bodies[B];
+        const R gpw = (R)G * ps * ((R)w_of(i) * psi[m]);
+        const double fr[3] = {(double)(gpw * (R)cx_of(i)), (double)(gpw * (R)cy_of(i)), (double)(gpw * (R)cz_of(i))};
+        const double arm[3] = {mimg1<double>((double)c.x + cx_of(i) - b.X[0], lat.nx),
+                               mimg1<double>((double)c.y + cy_of(i) - b.X[1], lat.ny),
+                               mimg1<double>((double)c.z + cz_of(i) - b.X[2], lat.nz)};
+        select(B);
+        a12[6] += fr[0];
+        a12[7] += fr[1];
+        a12[8] += fr[2];
+        a12[9] += arm[1] * fr[2] - arm[2] * fr[1];
+        a12[10] += arm[2] * fr[0] - arm[0] * fr[2];
+        a12[11] += arm[0] * fr[1] - arm[1] * fr[0];
+      }
+    }
+    // warp-uniform body -> shuffle sum, else per-lane atomics
+    const unsigned any = __ballot_sync(0xffffffffu, cur >= 0);
+    if (any) {
+      const int lead = __ffs(any) - 1;
+      const int b0 = __shfl_sync(0xffffffffu, cur, lead);
+      const bool uniform = __all_sync(0xffffffffu, cur < 0 || cur == b0);
+      if (uniform) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          double v = warp_sum(cur >= 0 ? a12[q] : 0.0);
+          if ((int)(threadIdx.x & 31) == lead && v != 0.0) atomicAdd(acc + (size_t)b0 * ACC_N + q, v);
+        }
+      } else {
+        flush(cur);
+      }
     }
   }
 }
@@ -429,153 +397,199 @@ __global__ void k_init_fluid(S* __restrict__ f, const uint16_t* __restrict__ fla
   }
 }
 
-// ---- cover refill ----------------------------------------------------------------------------
+__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
+                                                 int gz, const Lat& lat) {
+  for (int k = 0; k < b.nnb; ++k) {
+    int o = b.nbl[k];
+    if (o >= self) break;
+    const BodyDev& ob = bodies[o];
+    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
+        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
+      return true;
+  }
+  return false;
+}
+
+// ---- cover refill and boundary list ------------------------------------------------------------
+// Over the body tiles (each cell once: the lowest-id tile that covers it), after the new flags.
+// A fluid cell with a solid neighbour along a lattice direction goes into the boundary list of the
+// next step. If any node was covered in this step, a fluid cell next to a covered node n receives
+// f_eq(rho_n, u_n) / |N_F(n)| (face neighbours; all 26 if n has no fluid face neighbour).
 template <typename S>
-__global__ void k_refill(S* __restrict__ fa, S* __restrict__ fb, const uint16_t* __restrict__ flags,
-                         const BodyDev* __restrict__ bodies, StepState* st, Lat lat) {
+__global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restrict__ fb,
+                                                const uint16_t* __restrict__ flags,
+                                                const BodyDev* __restrict__ bodies, StepState* st, int* blist,
+                                                Lat lat) {
   using R = typename St<S>::R;
   S* __restrict__ f = st->parity ? fb : fa;  // the state buffer written by this step's collision
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= b.sz) return;
-  int i0 = (int)(t % b.L[0]);
-  long long r = t / b.L[0];
-  int i1 = (int)(r % b.L[1]), i2 = (int)(r / b.L[1]);
-  int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
-  if (b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat)) return;
-  const long long m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
-  const uint16_t fm = flags[m];
-  const size_t N = (size_t)lat.N;
-  auto at = [&](int x, int y, int z) {
-    return (long long)wrapi(x, lat.nx) + (long long)lat.nx * (wrapi(y, lat.ny) + (long long)lat.ny * wrapi(z, lat.nz));
-  };
-  auto fluid_count = [&](int x, int y, int z, bool faces_only) {
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          int d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 == 0 || (faces_only && d2 > 1)) continue;
-          if (!(flags[at(x + dx, y + dy, z + dz)] & F_SOLID)) cnt++;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool boundary = false;
+  long long m = 0;
+  if (t < b.sz) {
+    const int i0 = (int)(t % b.L[0]);
+    const long long r = t / b.L[0];
+    const int i1 = (int)(r % b.L[1]), i2 = (int)(r / b.L[1]);
+    const int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
+    m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
+    if (!(b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat))) {
+      const Cell c = cell_of(m, lat);
+      const uint16_t fm = flags[m];
+      const bool events = st->ncover != 0;
+      const size_t N = (size_t)lat.N;
+      auto at = [&](int x, int y, int z) {
+        return (long long)wrapi(x, lat.nx) + (long long)lat.nx * (wrapi(y, lat.ny) + (long long)lat.ny * wrapi(z, lat.nz));
+      };
+      auto fluid_count = [&](int x, int y, int z, bool faces_only) {
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int d2 = dx * dx + dy * dy + dz * dz;
+              if (d2 == 0 || (faces_only && d2 > 1)) continue;
+              if (!(flags[at(x + dx, y + dy, z + dz)] & F_SOLID)) cnt++;
+            }
+        return cnt;
+      };
+      if (fm & F_SOLID) {
+        // a covered node with no fluid node within sqrt(3) loses its mass: count it
+        if ((fm & F_COVER) && fluid_count(gx, gy, gz, false) == 0) {
+          atomicAdd(&st->lost_refills, 1ull);
+          atomicOr(&st->err, E_REFILL);
         }
-    return cnt;
-  };
-  if (fm & F_SOLID) {
-    // a covered node with no fluid node within sqrt(3) loses its mass: count it
-    if ((fm & F_COVER) && fluid_count(gx, gy, gz, false) == 0) {
-      atomicAdd(&st->lost_refills, 1ull);
-      atomicOr(&st->err, E_REFILL);
-    }
-    return;
-  }
-  // quick reject: no covered neighbour
-  bool any = false;
-  for (int dz = -1; dz <= 1 && !any; ++dz)
-    for (int dy = -1; dy <= 1 && !any; ++dy)
-      for (int dx = -1; dx <= 1 && !any; ++dx)
-        if ((dx | dy | dz) && (flags[at(gx + dx, gy + dy, gz + dz)] & F_COVER)) any = true;
-  if (!any) return;
-  R add[Q];
+      } else {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) add[i] = 0;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        int d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 == 0) continue;
-        int nxp = gx + dx, nyp = gy + dy, nzp = gz + dz;
-        long long nn = at(nxp, nyp, nzp);
-        if (!(flags[nn] & F_COVER)) continue;
-        int c6 = fluid_count(nxp, nyp, nzp, true);
-        int cnt;
-        if (c6 > 0) {
-          if (d2 != 1) continue;  // only face neighbours share this node's populations
-          cnt = c6;
-        } else {
-          cnt = fluid_count(nxp, nyp, nzp, false);
-        }
-        // moments of the covered node's populations
-        R fi[Q];
-        R rho = 0, mx = 0, my = 0, mz = 0;
+        for (int i = 1; i < Q; ++i) boundary |= (__ldg(flags + nbr(c, lat, i, +1)) & F_SOLID) != 0;
+        if (events) {
+          bool any = false;
+          for (int dz = -1; dz <= 1 && !any; ++dz)
+            for (int dy = -1; dy <= 1 && !any; ++dy)
+              for (int dx = -1; dx <= 1 && !any; ++dx)
+                if ((dx | dy | dz) && (flags[at(gx + dx, gy + dy, gz + dz)] & F_COVER)) any = true;
+          if (any) {
+            R add[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          fi[i] = St<S>::ld(f, (size_t)i * N + nn, i);
-          rho += fi[i];
-          mx += (R)cx_of(i) * fi[i];
-          my += (R)cy_of(i) * fi[i];
-          mz += (R)cz_of(i) * fi[i];
-        }
-        R ux = 0, uy = 0, uz = 0;
-        if (rho > (R)0) {
-          ux = mx / rho;
-          uy = my / rho;
-          uz = mz / rho;
-        }
-        R uu = ux * ux + uy * uy + uz * uz;
-        R inv = (R)1 / (R)cnt;
+            for (int i = 0; i < Q; ++i) add[i] = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                  const int d2 = dx * dx + dy * dy + dz * dz;
+                  if (d2 == 0) continue;
+                  const int nxp = gx + dx, nyp = gy + dy, nzp = gz + dz;
+                  const long long nn = at(nxp, nyp, nzp);
+                  if (!(flags[nn] & F_COVER)) continue;
+                  const int c6 = fluid_count(nxp, nyp, nzp, true);
+                  int cnt;
+                  if (c6 > 0) {
+                    if (d2 != 1) continue;  // only face neighbours share this node's populations
+                    cnt = c6;
+                  } else {
+                    cnt = fluid_count(nxp, nyp, nzp, false);
+                  }
+                  R fi[Q];
+                  R rho = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          R cu = (R)cx_of(i) * ux + (R)cy_of(i) * uy + (R)cz_of(i) * uz;
-          add[i] += rho * (R)w_of(i) * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu) * inv;
+                  for (int i = 0; i < Q; ++i) {
+                    fi[i] = St<S>::ld(f, (size_t)i * N + nn, i);
+                    rho += fi[i];
+                    mx += (R)cx_of(i) * fi[i];
+                    my += (R)cy_of(i) * fi[i];
+                    mz += (R)cz_of(i) * fi[i];
+                  }
+                  R ux = 0, uy = 0, uz = 0;
+                  if (rho > (R)0) {
+                    ux = mx / rho;
+                    uy = my / rho;
+                    uz = mz / rho;
+                  }
+                  const R uu = ux * ux + uy * uy + uz * uz;
+                  const R inv = (R)1 / (R)cnt;
+#pragma unroll
+                  for (int i = 0; i < Q; ++i) {
+                    const R cu = (R)cx_of(i) * ux + (R)cy_of(i) * uy + (R)cz_of(i) * uz;
+                    add[i] += rho * (R)w_of(i) * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu) * inv;
+                  }
+                }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              const size_t k = (size_t)i * N + m;
+              St<S>::st(f, k, i, St<S>::ld(f, k, i) + add[i]);
+            }
+          }
         }
       }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    size_t k = (size_t)i * N + m;
-    St<S>::st(f, k, i, St<S>::ld(f, k, i) + add[i]);
+    }
+  }
+  // warp-aggregated append to the boundary list
+  const unsigned mask = __ballot_sync(0xffffffffu, boundary);
+  if (mask) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&st->nbnd, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (boundary) blist[base + __popc(mask & ((1u << lane) - 1))] = (int)m;
   }
 }
 
 // ---- launchers -------------------------------------------------------------------------------
+static int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+unsigned lbm_blocks(const Lat& lat) {
+  const long long need = (lat.N + 255) / 256;
+  const long long cap = 4LL * sm_count();  // a few resident blocks per SM, grid-stride beyond
+  return (unsigned)(need < cap ? need : cap);
+}
+
 template <typename S>
 static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
-                       double* acc, double* mass_part, StepState* st, double* diag_rho, double* diag_vel,
+                       double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
                        const PhysParams& pp, cudaStream_t s, int phases) {
   using R = typename St<S>::R;
-  const int T = 256;
-  const unsigned blocks = (unsigned)((lat.N + T - 1) / T);
-  if (phases & 1) k_density<S><<<blocks, T, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
+  if (phases & 1) k_density<S><<<blocks, 256, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
   if (phases & 2)
-    k_collide<S><<<blocks, T, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel,
-                                      lat, pp);
+    k_collide<S><<<(unsigned)((lat.N + 255) / 256), 256, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st,
+                                                                  diag_rho, diag_vel, lat, pp);
+}
+
+void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
+                     const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
+                     double* diag_vel, const PhysParams& pp, cudaStream_t s, int phases) {
+  if (prec == 0)
+    lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
+                       pp, s, phases);
+  else if (prec == 1)
+    lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
+                      pp, s, phases);
+  else
+    lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
+                       pp, s, phases);
 }
 
 template <typename S>
 static void boundary_t(const Lat& lat, const S* fa, const S* fb, const uint16_t* flags, const void* psi,
-                       const BodyDev* bodies, int nb, int max_tile, double* acc, const StepState* st, double G,
+                       const BodyDev* bodies, double* acc, const int* blist, const StepState* st, double G,
                        cudaStream_t s) {
   using R = typename St<S>::R;
-  dim3 grid((unsigned)((max_tile + 255) / 256), (unsigned)nb);
-  k_boundary<S><<<grid, 256, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, acc, st, lat, G);
+  k_boundary<S><<<2 * sm_count(), 128, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, acc, blist, st, lat, G);
 }
 
 void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags, const void* psi,
-                     const BodyDev* bodies, int nb, int max_tile, double* acc, const StepState* st, double G,
+                     const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st, double G,
                      cudaStream_t s) {
   if (nb == 0) return;
   if (prec == 0)
-    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, psi, bodies, nb, max_tile, acc, st, G, s);
+    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, psi, bodies, acc, blist, st, G, s);
   else if (prec == 1)
-    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, psi, bodies, nb, max_tile, acc, st, G, s);
+    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, psi, bodies, acc, blist, st, G, s);
   else
-    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, psi, bodies, nb, max_tile, acc, st, G, s);
-}
-
-unsigned lbm_blocks(const Lat& lat) { return (unsigned)((lat.N + 255) / 256); }
-
-void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
-                     const BodyDev* bodies, double* acc, double* mass_part, StepState* st, double* diag_rho,
-                     double* diag_vel, const PhysParams& pp, cudaStream_t s, int phases) {
-  if (prec == 0)
-    lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, bodies, acc, mass_part, st, diag_rho, diag_vel, pp,
-                       s, phases);
-  else if (prec == 1)
-    lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, bodies, acc, mass_part, st, diag_rho, diag_vel, pp,
-                      s, phases);
-  else
-    lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, bodies, acc, mass_part, st, diag_rho, diag_vel, pp,
-                       s, phases);
+    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, psi, bodies, acc, blist, st, G, s);
 }
 
 void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags, const double* rho, const double* u,
@@ -587,14 +601,14 @@ void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags,
   else k_init_fluid<__half><<<blocks, T, 0, s>>>((__half*)f, flags, rho, u, lat);
 }
 
-void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
-                   int nb, int max_tile, StepState* st, cudaStream_t s) {
+void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies, int nb,
+                   int max_tile, StepState* st, int* blist, cudaStream_t s) {
   if (nb == 0) return;
   const int T = 256;
   dim3 grid((unsigned)((max_tile + T - 1) / T), (unsigned)nb);
-  if (prec == 0) k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, lat);
-  else if (prec == 1) k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, lat);
-  else k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, lat);
+  if (prec == 0) k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, blist, lat);
+  else if (prec == 1) k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, blist, lat);
+  else k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, blist, lat);
 }
 
 }  // namespace cbl

@@ -161,7 +161,8 @@ __global__ void k_neighbour_lists(BodyDev* bodies, int nb, Lat lat, StepState* s
 }
 
 // ---- flags --------------------------------------------------------------------------------------
-__global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat, double thr, int init) {
+__global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat, double thr, int init,
+                        StepState* st) {
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,7 +213,10 @@ __global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat
         best = ids[k];
       }
     nf = F_SOLID | (uint16_t)best;
-    if (!init && !(old & F_SOLID)) nf |= F_COVER;
+    if (!init && !(old & F_SOLID)) {
+      nf |= F_COVER;
+      atomicAdd(&st->ncover, 1u);
+    }
   }
   flags[n] = nf;
 }
@@ -286,7 +290,8 @@ __global__ void k_repulsion(const BodyDev* bodies, const double* arena, double* 
   const BodyDev& a = bodies[self];
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  if (t < a.sz && a.nnb > 0 && arena[a.off + t] >= thr) {
+  if (a.nnb == 0) return;  // block-uniform
+  if (t < a.sz && arena[a.off + t] >= thr) {
     TileCell c = tile_cell(a, t, lat);
     double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
     const int R = (int)ceil(rc);
@@ -319,6 +324,8 @@ __global__ void k_repulsion(const BodyDev* bodies, const double* arena, double* 
       }
     }
   }
+  const bool has = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0;
+  if (__ballot_sync(0xffffffffu, has) == 0) return;
   for (int p = 0; p < 3; ++p) {
     double sf = dwarp_sum(F[p]), st = dwarp_sum(T[p]);
     if ((threadIdx.x & 31) == 0) {
@@ -390,7 +397,7 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
 }
 
 __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                                                const double* mass_part, unsigned n_mass_part, StepState* st,
+                                                double* mass_part, unsigned n_mass_part, StepState* st,
                                                 Lat lat) {
   const int n[3] = {lat.nx, lat.ny, lat.nz};
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -410,14 +417,12 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
   }
   // fluid mass of this step: fixed-order sum of the per-block partials
   __shared__ double red[256];
-  double s4[4] = {0.0, 0.0, 0.0, 0.0};  // independent partial sums keep several loads in flight
-  unsigned k = threadIdx.x;
-  for (; k + 3 * blockDim.x < n_mass_part; k += 4 * blockDim.x) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s4[u] += __ldg(mass_part + k + u * blockDim.x);
+  double sm = 0.0;
+  for (unsigned k = threadIdx.x; k < n_mass_part; k += blockDim.x) {
+    sm += mass_part[k];
+    mass_part[k] = 0.0;
   }
-  for (; k < n_mass_part; k += blockDim.x) s4[0] += __ldg(mass_part + k);
-  red[threadIdx.x] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+  red[threadIdx.x] = sm;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -427,6 +432,8 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
   if (threadIdx.x == 0) {
     st->last_mass = red[0];
     st->parity ^= 1;
+    st->nbnd = 0;    // the boundary list is rebuilt by the refill pass after the new flags
+    st->ncover = 0;  // counted by the flag pass
   }
 }
 
@@ -437,74 +444,89 @@ __device__ __forceinline__ double mc_slope(double dm, double dp) {
   return dm > 0 ? s : -s;
 }
 
-// one sweep along axis d: out (origin b.o) <- in (origin o_in); x-sweep reads with the previous
-// origin, so the recentring shift is folded into it.
-__global__ void k_sweep(const BodyDev* bodies, double* arena, Lat lat, int d, int in_buf, int out_buf, int use_prev,
-                        int last, double* volacc, StepState* st) {
+// one sweep along axis d: out (origin b.o) <- in (origin o_in). The x-sweep reads with the previous
+// origin, so the recentring shift (at most one cell per axis and step) is folded into it. Stencil
+// values are addressed in tile-local coordinates; a periodic axis (tile as long as the lattice)
+// wraps, any other axis reads zero outside the tile.
+__device__ __forceinline__ int in_local(int i, int shift, int L, int n) {
+  int l = i + shift;
+  if (L == n) l = l < 0 ? l + n : (l >= n ? l - n : l);
+  return l;
+}
+
+__global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* arena, Lat lat, int d, int in_buf,
+                                               int out_buf, int use_prev, int last, double* volacc, StepState* st) {
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
-  bool inside = t < b.sz;
+  const bool inside = t < b.sz;
   if (inside) {
-    TileCell c = tile_cell(b, t, lat);
-    const int* oin = use_prev ? b.o_prev : b.o;
-    const double* in = arena + b.off + (long long)in_buf * b.sz;
-    const int e[3] = {d == 0, d == 1, d == 2};
-    double p[5];
-    for (int k = 0; k < 5; ++k) {
-      long long q = tile_index(oin, b.L, c.gx + (k - 2) * e[0], c.gy + (k - 2) * e[1], c.gz + (k - 2) * e[2], lat);
-      p[k] = q < 0 ? 0.0 : in[q];
-    }
-    // face velocities u_d at the face centres (the d-component of V + omega x r, r about X_prev)
-    const int g[3] = {c.gx, c.gy, c.gz};
     const int nn[3] = {lat.nx, lat.ny, lat.nz};
-    double uf[2];
-    for (int s = 0; s < 2; ++s) {
-      // face between (g - e) and g for s = 0, between g and (g + e) for s = 1; the left cell is
-      // wrapped like a lattice coordinate
-      double pos[3];
-      for (int a = 0; a < 3; ++a) {
-        int left = a == d ? wrapi(g[a] - 1 + s, nn[a]) : g[a];
-        pos[a] = left + 0.5 * e[a];
+    int ii[3];
+    ii[0] = (int)(t % b.L[0]);
+    const long long r = t / b.L[0];
+    ii[1] = (int)(r % b.L[1]);
+    ii[2] = (int)(r / b.L[1]);
+    // input-local coordinates of this output cell
+    int li[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      const int shift = use_prev ? (b.L[a] == nn[a] ? 0 : b.o[a] - b.o_prev[a]) : 0;
+      li[a] = in_local(ii[a], shift, b.L[a], nn[a]);
+      if (a != d && (li[a] < 0 || li[a] >= b.L[a])) ok = false;
+    }
+    const double* in = arena + b.off + (long long)in_buf * b.sz;
+    const long long sd = d == 0 ? 1 : (d == 1 ? (long long)b.L[0] : (long long)b.L[0] * b.L[1]);
+    const long long base = li[0] + (long long)b.L[0] * (li[1] + (long long)b.L[1] * li[2]) - (long long)li[d] * sd;
+    double p[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int l = in_local(li[d], k - 2, b.L[d], b.L[d] == nn[d] ? nn[d] : -1);
+      p[k] = (ok && l >= 0 && l < b.L[d]) ? in[base + l * sd] : 0.0;
+    }
+    if (p[0] == p[2] && p[1] == p[2] && p[3] == p[2] && p[4] == p[2]) {
+      // flat stencil: both face fluxes are u * p with the same u, so the update is exactly zero
+      v = p[2];
+    } else {
+      // face velocity u_d (the d-component of V + omega x r, r about X_prev): it depends only on the
+      // two other coordinates, so both faces of the cell share it
+      const int g[3] = {wrapi(b.o[0] + ii[0], nn[0]), wrapi(b.o[1] + ii[1], nn[1]), wrapi(b.o[2] + ii[2], nn[2])};
+      const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+      const double r1 = mimg(g[d1] - b.Xprev[d1], nn[d1]);
+      const double r2 = mimg(g[d2] - b.Xprev[d2], nn[d2]);
+      const double u = b.V[d] + (b.W[d1] * r2 - b.W[d2] * r1);
+      double Fl, Fr;
+      {
+        const double face = u >= 0.0 ? p[1] + 0.5 * (1.0 - u) * mc_slope(p[1] - p[0], p[2] - p[1])
+                                     : p[2] - 0.5 * (1.0 + u) * mc_slope(p[2] - p[1], p[3] - p[2]);
+        Fl = u * face;
       }
-      double r[3] = {mimg(pos[0] - b.Xprev[0], lat.nx), mimg(pos[1] - b.Xprev[1], lat.ny),
-                     mimg(pos[2] - b.Xprev[2], lat.nz)};
-      double wr[3];
-      xcross(b.W, r, wr);
-      uf[s] = b.V[d] + wr[d];
+      {
+        const double face = u >= 0.0 ? p[2] + 0.5 * (1.0 - u) * mc_slope(p[2] - p[1], p[3] - p[2])
+                                     : p[3] - 0.5 * (1.0 + u) * mc_slope(p[3] - p[2], p[4] - p[3]);
+        Fr = u * face;
+      }
+      v = p[2] - (Fr - Fl);
     }
-    // flux through the face between cells (k, k+1) of the 5-point stencil: k = 1 (left), 2 (right)
-    double Fl, Fr;
-    {
-      double u = uf[0];
-      double face = u >= 0.0 ? p[1] + 0.5 * (1.0 - u) * mc_slope(p[1] - p[0], p[2] - p[1])
-                             : p[2] - 0.5 * (1.0 + u) * mc_slope(p[2] - p[1], p[3] - p[2]);
-      Fl = u * face;
-    }
-    {
-      double u = uf[1];
-      double face = u >= 0.0 ? p[2] + 0.5 * (1.0 - u) * mc_slope(p[2] - p[1], p[3] - p[2])
-                             : p[3] - 0.5 * (1.0 + u) * mc_slope(p[3] - p[2], p[4] - p[3]);
-      Fr = u * face;
-    }
-    v = p[2] - (Fr - Fl);
     arena[b.off + (long long)out_buf * b.sz + t] = v;
-    if (last) {
+    if (last && v != 0.0) {
       // the outer two layers must stay empty (they are the stencil halo)
-      const int ii[3] = {c.i0, c.i1, c.i2};
       bool edge = false;
       for (int a = 0; a < 3; ++a)
         if (b.L[a] < nn[a] && (ii[a] < 2 || ii[a] >= b.L[a] - 2)) edge = true;
-      if (edge && v != 0.0) atomicOr(&st->err, E_TILE);
+      if (edge) atomicOr(&st->err, E_TILE);
     }
   }
   if (last) {
-    double sv = dwarp_sum(inside ? v : 0.0);
-    double sc = dwarp_sum((inside && v > PHI_EPS && v < 1.0 - PHI_EPS) ? 1.0 : 0.0);
-    if ((threadIdx.x & 31) == 0) {
-      if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
-      if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
+    const bool live = inside && v != 0.0;
+    if (__ballot_sync(0xffffffffu, live)) {
+      double sv = dwarp_sum(live ? v : 0.0);
+      double sc = dwarp_sum((live && v > PHI_EPS && v < 1.0 - PHI_EPS) ? 1.0 : 0.0);
+      if ((threadIdx.x & 31) == 0) {
+        if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
+        if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
+      }
     }
   }
 }
@@ -528,33 +550,61 @@ __global__ void k_volume(const BodyDev* bodies, const double* arena, double* vol
 // phi_a += sum_b (M/N) [ s_ab (I_a - I_b) + sum_c (s_bc - s_ac) I_c + (D_a - D_b if 0<phi_a<1) ]
 // with I = lap(phi) + (pi/eta)^2 phi, D_B = (V_B(0) - sum phi_B) / #{0 < phi_B < 1}, D_fluid = 0.
 constexpr int MAXACT = 8;
-__global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* volacc, Lat lat, double eta,
-                           double mob, double s_sf, double s_ss) {
+
+// phi at a cell of a tile given in tile-local coordinates l and its 6 face neighbours (order: self,
+// +x, -x, +y, -y, +z, -z); periodic tile axes wrap, other axes read zero outside the tile
+__device__ __forceinline__ void tile_val7(const double* buf, const int L[3], const int l[3], const int nn[3],
+                                          double out[7]) {
+  const long long s1 = L[0], s2 = (long long)L[0] * L[1];
+  const bool in0 = l[0] >= 0 && l[0] < L[0] && l[1] >= 0 && l[1] < L[1] && l[2] >= 0 && l[2] < L[2];
+  const long long c = l[0] + s1 * l[1] + s2 * l[2];
+  out[0] = in0 ? buf[c] : 0.0;
+  const long long st[3] = {1, s1, s2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const int dlt = sg == 0 ? 1 : -1;
+      int q[3] = {l[0], l[1], l[2]};
+      q[a] += dlt;
+      if (L[a] == nn[a]) q[a] = q[a] < 0 ? q[a] + nn[a] : (q[a] >= nn[a] ? q[a] - nn[a] : q[a]);
+      const bool ok = q[0] >= 0 && q[0] < L[0] && q[1] >= 0 && q[1] < L[1] && q[2] >= 0 && q[2] < L[2];
+      out[1 + 2 * a + sg] = ok ? buf[q[0] + s1 * q[1] + s2 * q[2]] : 0.0;
+      (void)st;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double* arena, const double* volacc, Lat lat,
+                                                  double eta, double mob, double s_sf, double s_ss) {
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= b.sz) return;
   const double* in = arena + b.off + b.sz;  // buffer 1: advected field
   double* out = arena + b.off;              // buffer 0: new field
-  TileCell c = tile_cell(b, t, lat);
-  const int nxv[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  const int nn[3] = {lat.nx, lat.ny, lat.nz};
+  int ii[3];
+  ii[0] = (int)(t % b.L[0]);
+  const long long rr = t / b.L[0];
+  ii[1] = (int)(rr % b.L[1]);
+  ii[2] = (int)(rr / b.L[1]);
   double pa[7];
+  tile_val7(in, b.L, ii, nn, pa);
   bool act_a = false;
-  for (int k = 0; k < 7; ++k) {
-    pa[k] = phi_at(in, b, c.gx + nxv[k][0], c.gy + nxv[k][1], c.gz + nxv[k][2], lat);
-    act_a |= pa[k] > PHI_EPS;
-  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) act_a |= pa[k] > PHI_EPS;
   if (!act_a) {
     out[t] = pa[0];
     return;
   }
+  const int g[3] = {wrapi(b.o[0] + ii[0], nn[0]), wrapi(b.o[1] + ii[1], nn[1]), wrapi(b.o[2] + ii[2], nn[2])};
   // active solids in ascending id order, with their 7-point values
   double vals[MAXACT][7];
   int ids[MAXACT];
   int na = 0;
   int pos_self = -1;
   double S[7] = {0, 0, 0, 0, 0, 0, 0};
-  // merge self into the ascending neighbour list
   int k_nb = 0;
   for (int step = 0; step <= b.nnb; ++step) {
     int id;
@@ -562,19 +612,28 @@ __global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* v
     else id = b.nbl[k_nb++];
     if (id == self) {
       pos_self = na;
-      for (int k = 0; k < 7; ++k) vals[na][k] = pa[k];
+      for (int k = 0; k < 7; ++k) {
+        vals[na][k] = pa[k];
+        S[k] += pa[k];
+      }
       ids[na++] = self;
-      for (int k = 0; k < 7; ++k) S[k] += pa[k];
       continue;
     }
     const BodyDev& o = bodies[id];
-    const double* ob = arena + o.off + o.sz;
-    double v7[7];
-    bool on = false;
-    for (int k = 0; k < 7; ++k) {
-      v7[k] = phi_at(ob, o, c.gx + nxv[k][0], c.gy + nxv[k][1], c.gz + nxv[k][2], lat);
-      on |= v7[k] > PHI_EPS;
+    int lo[3];
+    bool near = true;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = wrapi(g[a] - o.o[a], nn[a]);
+      if (o.L[a] < nn[a]) {
+        if (lo[a] > nn[a] - 2) lo[a] -= nn[a];  // just below the tile: keep the +1 neighbour reachable
+        if (lo[a] < -1 || lo[a] > o.L[a]) near = false;
+      }
     }
+    if (!near) continue;
+    double v7[7];
+    tile_val7(arena + o.off + o.sz, o.L, lo, nn, v7);
+    bool on = false;
+    for (int k = 0; k < 7; ++k) on |= v7[k] > PHI_EPS;
     if (!on) continue;
     if (na < MAXACT - (pos_self < 0 ? 1 : 0)) {  // always keep a slot for self
       for (int k = 0; k < 7; ++k) {
@@ -615,9 +674,9 @@ __global__ void k_kinetics(const BodyDev* bodies, double* arena, const double* v
   for (int bq = 0; bq < N; ++bq) {
     if (bq == a) continue;
     double term = sig(a, bq) * (I[a] - I[bq]);
-    for (int g = 0; g < N; ++g) {
-      if (g == a || g == bq) continue;
-      term += (sig(bq, g) - sig(a, g)) * I[g];
+    for (int gg = 0; gg < N; ++gg) {
+      if (gg == a || gg == bq) continue;
+      term += (sig(bq, gg) - sig(a, gg)) * I[gg];
     }
     if (in_if) term += D[a] - D[bq];
     rate += mob / N * term;
@@ -665,8 +724,8 @@ void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* 
   if (nb) k_neighbour_lists<<<1, 256, 0, s>>>(bodies, nb, lat, st);
 }
 void launch_flags(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, uint16_t* flags,
-                  double threshold, int init, cudaStream_t s) {
-  if (nb) k_flags<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, flags, lat, threshold, init);
+                  double threshold, int init, StepState* st, cudaStream_t s) {
+  if (nb) k_flags<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, flags, lat, threshold, init, st);
 }
 void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena, double* scratch,
                        cudaStream_t s) {
@@ -685,7 +744,7 @@ void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_til
                                                        pp.member_threshold);
 }
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   const double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {
+                   double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {
   k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, mass_part, n_mass_part, st, lat);
 }
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
