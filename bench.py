@@ -28,7 +28,8 @@ sys.path.insert(0, ROOT)
 # algorithmic bytes per cell update of the collision kernel: read 19 populations, write 19,
 # read the uint16 flag (the density pass and psi are implementation overhead)
 POP_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
-KERNELS_PER_STEP = 11  # density, collide, boundary, repulsion, bodies, 3 sweeps, kinetics, flags, refill
+KERNELS = {"fp64": 11, "fp32": 10, "fp16dev": 10}  # [density,] collide/fused, boundary, repulsion, bodies,
+# 3 sweeps, kinetics, flags, refill
 
 
 def alg_bytes_per_cell(prec):
@@ -244,12 +245,12 @@ def bench_cuda(args, rank, world, local_rank):
                        "inputs_vs_l2": "populations 2 x %.0f MB > 129 MB L2 (no flush needed)"
                                        % (w.ncells * 19 * POP_BYTES[prec] / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": "k_collide" if prec == "fp64" else "k_lbm_fused", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "alg_bytes_per_cell": bpc,
                          "step_frac": bpc * w.ncells / (ms_max / args.steps * 1e-3) / 1e9 / peak},
             "phases_ms": {k: round(v, 5) for k, v in phases.items()},
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "gpu_launches": KERNELS[prec] * args.steps,
             "clocks": clk.summary(),
             "e2e": {"value": w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,

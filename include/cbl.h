@@ -155,7 +155,9 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
 
 /* Phases of one step, in launch order, as reported by cbl_time_phases. */
 #define CBL_NPHASES 9
-/* 0 pull + density + psi, 1 pull + force + collision + mass partials, 2 solid-fluid force on the
+/* 0 pull + density + psi (FP64 storage only), 1 pull + force + collision + mass partials (for FP32
+ * and FP16-deviation storage this is the single fused pass that also computes psi), 2 solid-fluid
+ * force on the
  * bodies (momentum exchange and adhesion, FP64 sums), 3 solid-solid repulsion, 4 rigid-body update,
  * 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle flags, 8 cover refill
  * and boundary-cell list. */

@@ -35,6 +35,7 @@ struct cbl_ctx {
   double* mass_part = nullptr;
   unsigned n_mass_part = 0;
   int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
+  int fused_tz = 0;      // > 0: FP32 / FP16 storage steps with the fused single-pass kernel
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -137,7 +138,8 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   const size_t N = (size_t)ctx->lat.N;
   ctx->fa = dalloc(ctx, N * Q * ctx->elem);
   ctx->fb = dalloc(ctx, N * Q * ctx->elem);
-  ctx->psi = dalloc(ctx, N * (ctx->prec == 0 ? 8 : 4));
+  if (ctx->prec != 0) ctx->fused_tz = fused_tz(ctx->lat, 2);
+  ctx->psi = dalloc(ctx, ctx->fused_tz ? 256 : N * (ctx->prec == 0 ? 8 : 4));
   ctx->flags = (uint16_t*)dalloc(ctx, N * 2);
   ctx->diag_rho = (double*)dalloc(ctx, N * 8);
   ctx->diag_vel = (double*)dalloc(ctx, N * 24);
@@ -294,12 +296,22 @@ cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const dou
   return init_common(ctx, rho_host, u_host);
 }
 
+static void enqueue_lbm(cbl_ctx* ctx, int phases) {
+  if (ctx->fused_tz) {
+    if (phases & 2)
+      launch_lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
+                       ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->s);
+  } else {
+    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+                    lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, phases);
+  }
+}
+
 static void enqueue_step(cbl_ctx* ctx) {
   const int nb = (int)ctx->hb.size();
-  launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                  lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s);
-  launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->acc, ctx->blist,
-                  ctx->st, ctx->pp.G, ctx->s);
+  enqueue_lbm(ctx, 3);
+  launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+                  ctx->pp.G, ctx->pp.rho0, ctx->s);
   if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
   launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
                 ctx->s);
@@ -347,14 +359,12 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
   CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
   for (int it = 0; it < nsteps; ++it) {
     CK(cudaEventRecord(ev[0], ctx->s));
-    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                    lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 1);
+    enqueue_lbm(ctx, 1);
     CK(cudaEventRecord(ev[1], ctx->s));
-    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                    lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, 2);
+    enqueue_lbm(ctx, 2);
     CK(cudaEventRecord(ev[2], ctx->s));
-    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, nb, ctx->acc, ctx->blist,
-                    ctx->st, ctx->pp.G, ctx->s);
+    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+                    ctx->pp.G, ctx->pp.rho0, ctx->s);
     CK(cudaEventRecord(ev[3], ctx->s));
     if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
     CK(cudaEventRecord(ev[4], ctx->s));

@@ -114,9 +114,15 @@ void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_
                      const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st,
                      double* diag_rho, double* diag_vel, const PhysParams& pp, cudaStream_t s,
                      int phases = 3);
+// fused single-pass LBM step for FP32 and FP16-deviation storage (prec 1, 2); tz = z extent of a
+// block (see fused_tz)
+int fused_tz(const Lat& lat, int blocks_per_sm);
+void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
+                      double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
+                      int tz, cudaStream_t s);
 void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
-                     const void* psi, const BodyDev* bodies, int nb, double* acc, const int* blist,
-                     const StepState* st, double G, cudaStream_t s);
+                     const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st,
+                     double G, double rho0, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,

@@ -270,6 +270,185 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
   }
 }
 
+// ---- fused step: pull + density + psi + Shan-Chen force + collision in one pass ----------------
+// A block owns a TX x TY column of cells and marches along z over [z0, z0 + tz). For every plane it
+// pulls the populations of the plane's cells plus a one-cell ring around them (periodic
+// coordinates), stores psi of that extended plane in a three-plane ring in shared memory and the
+// interior populations in a double buffer; once psi of plane z + 1 exists it collides plane z.
+// Every interior population is read from global memory once; the ring cells are re-reads of cells
+// that neighbouring blocks own (served from L2). Storage float or binary16, arithmetic FP32.
+template <typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __restrict__ fb,
+                                                      const uint16_t* __restrict__ flags,
+                                                      const BodyDev* __restrict__ bodies,
+                                                      double* __restrict__ mass_part,
+                                                      const StepState* __restrict__ st,
+                                                      double* __restrict__ diag_rho, double* __restrict__ diag_vel,
+                                                      Lat lat, PhysParams pp, int tz) {
+  using R = typename St<S>::R;
+  constexpr int NT = TX * TY, EX = TX + 2, EY = TY + 2, EP = EX * EY;
+  __shared__ R s_psi[3][EP];
+  __shared__ R s_f[2][Q][NT];
+  __shared__ unsigned s_sl[2][NT];
+  __shared__ double s_red[NT / 32];
+
+  const size_t N = (size_t)lat.N;
+  const int diag = st->diag;
+  const S* __restrict__ src = st->parity ? fb : fa;
+  S* __restrict__ dst = st->parity ? fa : fb;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
+  const int zend = min(z0 + tz, lat.nz);
+  const R rho0 = (R)pp.rho0;
+  R my_mass = 0;
+
+  // psi (and, for interior cells of the tile, the pulled populations) of plane z into ring slot
+  // and population buffer `buf` (buf < 0: psi only)
+  auto pull_plane = [&](int z, int buf) {
+    const int zz = z < 0 ? z + lat.nz : (z >= lat.nz ? z - lat.nz : z);
+    const int slot = (z - z0 + 3) % 3;
+    for (int p = tid; p < EP; p += NT) {
+      const int ex = p % EX, ey = p / EX;
+      int x = x0 - 1 + ex, y = y0 - 1 + ey;
+      x = x < 0 ? x + lat.nx : (x >= lat.nx ? x - lat.nx : x);
+      y = y < 0 ? y + lat.ny : (y >= lat.ny ? y - lat.ny : y);
+      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * zz);
+      const uint16_t fl = __ldg(flags + n);
+      const bool interior = buf >= 0 && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
+      const int ii = (ey - 1) * TX + (ex - 1);
+      if (fl & F_SOLID) {
+        s_psi[slot][p] = (R)bodies[fl & F_OWNER].psi_wet;
+        if (interior) s_sl[buf][ii] = 0xFFFFFFFFu;  // marks a solid cell
+        continue;
+      }
+      const Cell c = cell_of(n, lat);
+      R fi[Q];
+      unsigned sl;
+      pull<S>(src, flags, lat, c, n, fi, sl);
+      R rho = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) rho += fi[i];
+      s_psi[slot][p] = (R)1 - exp(-rho / rho0);
+      if (interior) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s_f[buf][i][ii] = fi[i];
+        s_sl[buf][ii] = sl;
+      }
+    }
+  };
+
+  pull_plane(z0 - 1, -1);
+  pull_plane(z0, 0);
+  const int tx = tid % TX, ty = tid / TX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool mine = x < lat.nx && y < lat.ny;
+  for (int z = z0; z < zend; ++z) {
+    const int buf = (z - z0) & 1;
+    pull_plane(z + 1, z + 1 < zend ? buf ^ 1 : -1);
+    __syncthreads();
+    const unsigned sl = s_sl[buf][tid];
+    if (mine && sl != 0xFFFFFFFFu) {
+      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * z);
+      const int sm = (z - 1 - z0 + 3) % 3, s0 = (z - z0 + 3) % 3, sp = (z + 1 - z0 + 3) % 3;
+      const int pc = (ty + 1) * EX + (tx + 1);
+      const R ps = s_psi[s0][pc];
+      R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int slot = cz_of(i) > 0 ? sp : (cz_of(i) < 0 ? sm : s0);
+        const R wp = (R)w_of(i) * s_psi[slot][pc + cy_of(i) * EX + cx_of(i)];
+        if (cx_of(i)) sx += wp * (R)cx_of(i);
+        if (cy_of(i)) sy += wp * (R)cy_of(i);
+        if (cz_of(i)) sz += wp * (R)cz_of(i);
+      }
+      const R mG = -(R)pp.G * ps;
+      const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
+      R fi[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fi[i] = s_f[buf][i][tid];
+      R rho = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) rho += fi[i];
+      my_mass += rho;
+      if (sl) {
+        Cell c;
+        c.x = x;
+        c.y = y;
+        c.z = z;
+        c.xm = x ? x - 1 : lat.nx - 1;
+        c.xp = x + 1 < lat.nx ? x + 1 : 0;
+        c.ym = y ? y - 1 : lat.ny - 1;
+        c.yp = y + 1 < lat.ny ? y + 1 : 0;
+        c.zm = z ? z - 1 : lat.nz - 1;
+        c.zp = z + 1 < lat.nz ? z + 1 : 0;
+        R drho = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (!(sl & (1u << i))) continue;
+          const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
+          const R g = wall_term<R>(bodies[B], c, lat, i, rho);
+          fi[i] += g;
+          drho -= g;
+        }
+        fi[0] += drho;
+      }
+      R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (cx_of(i)) mx += (R)cx_of(i) * fi[i];
+        if (cy_of(i)) my += (R)cy_of(i) * fi[i];
+        if (cz_of(i)) mz += (R)cz_of(i) * fi[i];
+      }
+      R vx = 0, vy = 0, vz = 0;
+      if (rho > (R)0) {
+        const R ir = (R)1 / rho;
+        vx = mx * ir;
+        vy = my * ir;
+        vz = mz * ir;
+      }
+      const R itau = (R)1 / (R)pp.tau;
+      const R pref = (R)1 - (R)0.5 * itau;
+      const R uu = vx * vx + vy * vy + vz * vz;
+      const R vF = vx * Fx + vy * Fy + vz * Fz;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
+        const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
+        const R w = (R)w_of(i);
+        const R feq = rho * w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+        const R Fi = pref * w * ((R)3 * (cF - vF) + (R)9 * cu * cF);
+        St<S>::st(dst, (size_t)i * N + n, i, fi[i] - (fi[i] - feq) * itau + Fi);
+      }
+      if (diag) {
+        diag_rho[n] = (double)rho;
+        diag_vel[3 * n] = (double)vx;
+        diag_vel[3 * n + 1] = (double)vy;
+        diag_vel[3 * n + 2] = (double)vz;
+      }
+    } else if (mine) {
+      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * z);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
+      if (diag) {
+        diag_rho[n] = 0.0;
+        diag_vel[3 * n] = 0.0;
+        diag_vel[3 * n + 1] = 0.0;
+        diag_vel[3 * n + 2] = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  double m = warp_sum((double)my_mass);
+  if ((tid & 31) == 0) s_red[tid >> 5] = m;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (t != 0.0) atomicAdd(mass_part + (b & (MASS_SLOTS - 1)), t);
+  }
+}
+
 // ---- solid-fluid force on the bodies ---------------------------------------------------------
 // For each listed fluid cell x: for a solid upstream neighbour s = x - c_i (owner B), momentum
 // exchange -c_i (2 f*_opp(i)(x) + g_i) with the arm at the link midpoint (Eq. solid_liquid_force);
@@ -277,12 +456,11 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
 // +G psi(x) w_i psi(x + c_i) c_i, arm x + c_i - X_B (Sec. 3.2.3). It reads the same source
 // populations and psi as the collision, so g_i and rho are bit-identical to the ones it used.
 template <typename S>
-__global__ void __launch_bounds__(128) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
-                                                  const uint16_t* __restrict__ flags,
-                                                  const typename St<S>::R* __restrict__ psi,
-                                                  const BodyDev* __restrict__ bodies, double* __restrict__ acc,
-                                                  const int* __restrict__ blist, const StepState* __restrict__ st,
-                                                  Lat lat, double G) {
+__global__ void __launch_bounds__(64) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
+                                                 const uint16_t* __restrict__ flags,
+                                                 const BodyDev* __restrict__ bodies, double* __restrict__ acc,
+                                                 const int* __restrict__ blist, const StepState* __restrict__ st,
+                                                 Lat lat, double G, double rho0) {
   using R = typename St<S>::R;
   const unsigned count = st->nbnd;
   const S* __restrict__ src = st->parity ? fb : fa;
@@ -290,21 +468,23 @@ __global__ void __launch_bounds__(128) k_boundary(const S* __restrict__ fa, cons
   // whole-block rounds so that every lane reaches the shuffles below
   for (unsigned base = blockIdx.x * blockDim.x; base < count; base += stride) {
     const unsigned k = base + threadIdx.x;
-    double a12[12];
+    // per-thread sums in the working precision (a cell has at most 18 links); FP64 from the
+    // warp reduction on
+    R a12[12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) a12[q] = 0.0;
+    for (int q = 0; q < 12; ++q) a12[q] = 0;
     int cur = -1;
     auto flush = [&](int B) {
       if (B < 0) return;
 #pragma unroll
       for (int q = 0; q < 12; ++q)
-        if (a12[q] != 0.0) atomicAdd(acc + (size_t)B * ACC_N + q, a12[q]);
+        if (a12[q] != (R)0) atomicAdd(acc + (size_t)B * ACC_N + q, (double)a12[q]);
     };
     auto select = [&](int B) {
       if (B != cur) {
         flush(cur);
 #pragma unroll
-        for (int q = 0; q < 12; ++q) a12[q] = 0.0;
+        for (int q = 0; q < 12; ++q) a12[q] = 0;
         cur = B;
       }
     };
@@ -317,46 +497,48 @@ __global__ void __launch_bounds__(128) k_boundary(const S* __restrict__ fa, cons
       R rho = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) rho += fi[i];
+      // psi from the same pulled density as the step's own psi pass (bit-identical)
+      const R ps = (R)1 - exp(-rho / (R)rho0);
+#pragma unroll
       for (int i = 1; i < Q; ++i) {
-        if (!(sl & (1u << i))) continue;
-        const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
-        const BodyDev& b = bodies[B];
-        const R g = wall_term<R>(b, c, lat, i, rho);
-        const double m2 = (double)((R)2 * fi[i] + g);  // fi[i] = f*_opp(i)(x) on a solid link
-        const double dP[3] = {-cx_of(i) * m2, -cy_of(i) * m2, -cz_of(i) * m2};
-        const double arm[3] = {mimg1<double>(c.x - 0.5 * cx_of(i) - b.X[0], lat.nx),
-                               mimg1<double>(c.y - 0.5 * cy_of(i) - b.X[1], lat.ny),
-                               mimg1<double>(c.z - 0.5 * cz_of(i) - b.X[2], lat.nz)};
-        select(B);
-        a12[0] += dP[0];
-        a12[1] += dP[1];
-        a12[2] += dP[2];
-        a12[3] += arm[1] * dP[2] - arm[2] * dP[1];
-        a12[4] += arm[2] * dP[0] - arm[0] * dP[2];
-        a12[5] += arm[0] * dP[1] - arm[1] * dP[0];
-      }
-      const R ps = psi[n];
-      for (int i = 1; i < Q; ++i) {
+        if (sl & (1u << i)) {
+          const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
+          const BodyDev& b = bodies[B];
+          const R g = wall_term<R>(b, c, lat, i, rho);
+          const R m2 = (R)2 * fi[i] + g;  // fi[i] = f*_opp(i)(x) on a solid link
+          const R dPx = -(R)cx_of(i) * m2, dPy = -(R)cy_of(i) * m2, dPz = -(R)cz_of(i) * m2;
+          const R ax = mimg1<R>((R)c.x - (R)0.5 * (R)cx_of(i) - (R)b.X[0], lat.nx);
+          const R ay = mimg1<R>((R)c.y - (R)0.5 * (R)cy_of(i) - (R)b.X[1], lat.ny);
+          const R az = mimg1<R>((R)c.z - (R)0.5 * (R)cz_of(i) - (R)b.X[2], lat.nz);
+          select(B);
+          a12[0] += dPx;
+          a12[1] += dPy;
+          a12[2] += dPz;
+          a12[3] += ay * dPz - az * dPy;
+          a12[4] += az * dPx - ax * dPz;
+          a12[5] += ax * dPy - ay * dPx;
+        }
         const long long m = nbr(c, lat, i, +1);
         const uint16_t fm = __ldg(flags + m);
-        if (!(fm & F_SOLID)) continue;
-        const int B = fm & F_OWNER;
-        const BodyDev& b = bodies[B];
-        const R gpw = (R)G * ps * ((R)w_of(i) * psi[m]);
-        const double fr[3] = {(double)(gpw * (R)cx_of(i)), (double)(gpw * (R)cy_of(i)), (double)(gpw * (R)cz_of(i))};
-        const double arm[3] = {mimg1<double>((double)c.x + cx_of(i) - b.X[0], lat.nx),
-                               mimg1<double>((double)c.y + cy_of(i) - b.X[1], lat.ny),
-                               mimg1<double>((double)c.z + cz_of(i) - b.X[2], lat.nz)};
-        select(B);
-        a12[6] += fr[0];
-        a12[7] += fr[1];
-        a12[8] += fr[2];
-        a12[9] += arm[1] * fr[2] - arm[2] * fr[1];
-        a12[10] += arm[2] * fr[0] - arm[0] * fr[2];
-        a12[11] += arm[0] * fr[1] - arm[1] * fr[0];
+        if (fm & F_SOLID) {
+          const int B = fm & F_OWNER;
+          const BodyDev& b = bodies[B];
+          const R gpw = (R)G * ps * ((R)w_of(i) * (R)b.psi_wet);
+          const R fx = gpw * (R)cx_of(i), fy = gpw * (R)cy_of(i), fz = gpw * (R)cz_of(i);
+          const R ax = mimg1<R>((R)c.x + (R)cx_of(i) - (R)b.X[0], lat.nx);
+          const R ay = mimg1<R>((R)c.y + (R)cy_of(i) - (R)b.X[1], lat.ny);
+          const R az = mimg1<R>((R)c.z + (R)cz_of(i) - (R)b.X[2], lat.nz);
+          select(B);
+          a12[6] += fx;
+          a12[7] += fy;
+          a12[8] += fz;
+          a12[9] += ay * fz - az * fy;
+          a12[10] += az * fx - ax * fz;
+          a12[11] += ax * fy - ay * fx;
+        }
       }
     }
-    // warp-uniform body -> shuffle sum, else per-lane atomics
+    // warp-uniform body -> shuffle sum in FP64, else per-lane atomics
     const unsigned any = __ballot_sync(0xffffffffu, cur >= 0);
     if (any) {
       const int lead = __ffs(any) - 1;
@@ -365,7 +547,7 @@ __global__ void __launch_bounds__(128) k_boundary(const S* __restrict__ fa, cons
       if (uniform) {
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
-          double v = warp_sum(cur >= 0 ? a12[q] : 0.0);
+          double v = warp_sum(cur >= 0 ? (double)a12[q] : 0.0);
           if ((int)(threadIdx.x & 31) == lead && v != 0.0) atomicAdd(acc + (size_t)b0 * ACC_N + q, v);
         }
       } else {
@@ -428,9 +610,9 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
   bool boundary = false;
   long long m = 0;
   if (t < b.sz) {
-    const int i0 = (int)(t % b.L[0]);
-    const long long r = t / b.L[0];
-    const int i1 = (int)(r % b.L[1]), i2 = (int)(r / b.L[1]);
+    const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];  // tiles hold < 2^31 cells
+    const unsigned r = u / L0;
+    const int i0 = (int)(u - r * L0), i1 = (int)(r % L1), i2 = (int)(r / L1);
     const int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
     m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
     if (!(b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat))) {
@@ -547,6 +729,36 @@ unsigned lbm_blocks(const Lat& lat) {
   return (unsigned)(need < cap ? need : cap);
 }
 
+constexpr int FTX = 32, FTY = 8;
+
+// z extent of a fused block: as long as possible while the grid still fills the GPU
+// (blocks_per_sm resident blocks per SM)
+int fused_tz(const Lat& lat, int blocks_per_sm) {
+  const long long cols = (long long)((lat.nx + FTX - 1) / FTX) * ((lat.ny + FTY - 1) / FTY);
+  const long long slots = (long long)blocks_per_sm * sm_count();
+  long long nzc = slots / cols;
+  if (nzc < 1) nzc = 1;
+  if (nzc > lat.nz) nzc = lat.nz;
+  return (int)((lat.nz + nzc - 1) / nzc);
+}
+
+template <typename S>
+static void fused_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, const BodyDev* bodies, double* mass_part,
+                    StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp, int tz, cudaStream_t s) {
+  dim3 grid((lat.nx + FTX - 1) / FTX, (lat.ny + FTY - 1) / FTY, (lat.nz + tz - 1) / tz);
+  k_lbm_fused<S, FTX, FTY><<<grid, FTX * FTY, 0, s>>>(fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, lat,
+                                                      pp, tz);
+}
+
+void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
+                      double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
+                      int tz, cudaStream_t s) {
+  if (prec == 1)
+    fused_t<float>(lat, (float*)fa, (float*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+  else if (prec == 2)
+    fused_t<__half>(lat, (__half*)fa, (__half*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+}
+
 template <typename S>
 static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
                        double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
@@ -573,23 +785,21 @@ void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_
 }
 
 template <typename S>
-static void boundary_t(const Lat& lat, const S* fa, const S* fb, const uint16_t* flags, const void* psi,
-                       const BodyDev* bodies, double* acc, const int* blist, const StepState* st, double G,
-                       cudaStream_t s) {
-  using R = typename St<S>::R;
-  k_boundary<S><<<2 * sm_count(), 128, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, acc, blist, st, lat, G);
+static void boundary_t(const Lat& lat, const S* fa, const S* fb, const uint16_t* flags, const BodyDev* bodies,
+                       double* acc, const int* blist, const StepState* st, double G, double rho0, cudaStream_t s) {
+  k_boundary<S><<<4 * sm_count(), 64, 0, s>>>(fa, fb, flags, bodies, acc, blist, st, lat, G, rho0);
 }
 
-void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags, const void* psi,
+void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
                      const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st, double G,
-                     cudaStream_t s) {
+                     double rho0, cudaStream_t s) {
   if (nb == 0) return;
   if (prec == 0)
-    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, psi, bodies, acc, blist, st, G, s);
+    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, bodies, acc, blist, st, G, rho0, s);
   else if (prec == 1)
-    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, psi, bodies, acc, blist, st, G, s);
+    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, bodies, acc, blist, st, G, rho0, s);
   else
-    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, psi, bodies, acc, blist, st, G, s);
+    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, bodies, acc, blist, st, G, rho0, s);
 }
 
 void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags, const double* rho, const double* u,

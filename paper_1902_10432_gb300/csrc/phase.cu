@@ -53,10 +53,11 @@ struct TileCell {
 
 __device__ __forceinline__ TileCell tile_cell(const BodyDev& b, long long t, const Lat& lat) {
   TileCell c;
-  c.i0 = (int)(t % b.L[0]);
-  long long r = t / b.L[0];
-  c.i1 = (int)(r % b.L[1]);
-  c.i2 = (int)(r / b.L[1]);
+  const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];  // tiles hold < 2^31 cells
+  const unsigned r = u / L0;
+  c.i0 = (int)(u - r * L0);
+  c.i1 = (int)(r % L1);
+  c.i2 = (int)(r / L1);
   c.gx = wrapi(b.o[0] + c.i0, lat.nx);
   c.gy = wrapi(b.o[1] + c.i1, lat.ny);
   c.gz = wrapi(b.o[2] + c.i2, lat.nz);
@@ -464,15 +465,23 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
   if (inside) {
     const int nn[3] = {lat.nx, lat.ny, lat.nz};
     int ii[3];
-    ii[0] = (int)(t % b.L[0]);
-    const long long r = t / b.L[0];
-    ii[1] = (int)(r % b.L[1]);
-    ii[2] = (int)(r / b.L[1]);
+    {
+      const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];
+      const unsigned r = u / L0;
+      ii[0] = (int)(u - r * L0);
+      ii[1] = (int)(r % L1);
+      ii[2] = (int)(r / L1);
+    }
     // input-local coordinates of this output cell
     int li[3];
     bool ok = true;
     for (int a = 0; a < 3; ++a) {
-      const int shift = use_prev ? (b.L[a] == nn[a] ? 0 : b.o[a] - b.o_prev[a]) : 0;
+      // origins are unwrapped integers: take the shift as the minimum image of their difference
+      int shift = 0;
+      if (use_prev && b.L[a] < nn[a]) {
+        shift = wrapi(b.o[a] - b.o_prev[a], nn[a]);
+        if (shift > nn[a] / 2) shift -= nn[a];
+      }
       li[a] = in_local(ii[a], shift, b.L[a], nn[a]);
       if (a != d && (li[a] < 0 || li[a] >= b.L[a])) ok = false;
     }
@@ -585,10 +594,13 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
   double* out = arena + b.off;              // buffer 0: new field
   const int nn[3] = {lat.nx, lat.ny, lat.nz};
   int ii[3];
-  ii[0] = (int)(t % b.L[0]);
-  const long long rr = t / b.L[0];
-  ii[1] = (int)(rr % b.L[1]);
-  ii[2] = (int)(rr / b.L[1]);
+  {
+    const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];
+    const unsigned r = u / L0;
+    ii[0] = (int)(u - r * L0);
+    ii[1] = (int)(r % L1);
+    ii[2] = (int)(r / L1);
+  }
   double pa[7];
   tile_val7(in, b.L, ii, nn, pa);
   bool act_a = false;
