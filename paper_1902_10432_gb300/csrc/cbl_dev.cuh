@@ -31,11 +31,13 @@ __host__ __device__ constexpr double w_of(int i) {
 }
 
 // Cell flags (uint16): bit 15 solid, bit 14 "became solid in the last flag update" (cover
-// event, consumed by the refill), bits 0..13 owner body id of a solid cell.
+// event, consumed by the refill), bit 13 "fluid cell with a solid neighbour along a lattice
+// direction" (set by the refill pass), bits 0..12 owner body id of a solid cell.
 constexpr uint16_t F_SOLID = 0x8000;
 constexpr uint16_t F_COVER = 0x4000;
-constexpr uint16_t F_OWNER = 0x3FFF;
-constexpr int MAX_BODIES = 0x3FFF;
+constexpr uint16_t F_NEAR = 0x2000;
+constexpr uint16_t F_OWNER = 0x1FFF;
+constexpr int MAX_BODIES = 0x1FFF;
 constexpr int MAXNB = 24;  // neighbour-list capacity per body (tiles that overlap)
 
 // Fluid-mass accumulation slots written by the collision kernel and summed by the body kernel.
@@ -125,7 +127,7 @@ void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, c
                      double G, double rho0, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
-void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,
+void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags,
                    const BodyDev* bodies, int nb, int max_tile, StepState* st, int* blist, cudaStream_t s);
 
 void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,

@@ -449,6 +449,244 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
   }
 }
 
+// ---- fused step with asynchronous plane prefetch (FP32 storage) -------------------------------
+// Same decomposition as k_lbm_fused, but the populations that the pull of a plane needs are copied
+// into shared memory with cp.async two planes ahead of their use (a three-stage ring), so the
+// global-memory latency of plane z + 2 overlaps the psi pass of plane z + 1 and the collision of
+// plane z. Sources that are solid (bounce-back) are substituted when the plane is consumed, only in
+// cells flagged as next to a solid.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int TX, int TY>
+struct AsyncSmem {
+  static constexpr int EX = TX + 2, EY = TY + 2, EP = EX * EY, NT = TX * TY;
+  float pull[3][Q][EP];
+  float psi[3][EP];
+  unsigned sl[3][NT];
+  double red[NT / 32];
+};
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__ fa, float* __restrict__ fb,
+                                                            const uint16_t* __restrict__ flags,
+                                                            const BodyDev* __restrict__ bodies,
+                                                            double* __restrict__ mass_part,
+                                                            const StepState* __restrict__ st,
+                                                            double* __restrict__ diag_rho,
+                                                            double* __restrict__ diag_vel, Lat lat, PhysParams pp,
+                                                            int tz) {
+  using R = float;
+  using SM = AsyncSmem<TX, TY>;
+  constexpr int NT = SM::NT, EX = SM::EX, EP = SM::EP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM& sm = *reinterpret_cast<SM*>(smem_raw);
+
+  const size_t N = (size_t)lat.N;
+  const int diag = st->diag;
+  const float* __restrict__ src = st->parity ? fb : fa;
+  float* __restrict__ dst = st->parity ? fa : fb;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
+  const int zend = min(z0 + tz, lat.nz);
+  const R rho0 = (R)pp.rho0;
+  R my_mass = 0;
+  auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
+  auto stage = [&](int z) { return (z - z0 + 1) % 3; };
+
+  // copy the pull sources of plane z (all 19 directions, the extended plane) into its stage
+  auto issue = [&](int z) {
+    const int sg = stage(z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int zs = wrap(wrap(z, lat.nz) - cz_of(i), lat.nz);
+      for (int p = tid; p < EP; p += NT) {
+        const int ex = p % EX, ey = p / EX;
+        const int xs = wrap(wrap(x0 - 1 + ex, lat.nx) - cx_of(i), lat.nx);
+        const int ys = wrap(wrap(y0 - 1 + ey, lat.ny) - cy_of(i), lat.ny);
+        const size_t n = (size_t)xs + (size_t)lat.nx * ((size_t)ys + (size_t)lat.ny * zs);
+        cp_async4(&sm.pull[sg][i][p], src + (size_t)i * N + n);
+      }
+    }
+  };
+  // psi of plane z (and, for interior cells, the bounce-back substitution kept in the stage)
+  auto consume = [&](int z, bool keep) {
+    const int sg = stage(z), slot = (z - z0 + 3) % 3;
+    const int zz = wrap(z, lat.nz);
+    for (int p = tid; p < EP; p += NT) {
+      const int ex = p % EX, ey = p / EX;
+      const int x = wrap(x0 - 1 + ex, lat.nx), y = wrap(y0 - 1 + ey, lat.ny);
+      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * zz);
+      const uint16_t fl = __ldg(flags + n);
+      const bool interior = keep && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
+      const int ii = (ey - 1) * TX + (ex - 1);
+      if (fl & F_SOLID) {
+        sm.psi[slot][p] = (R)bodies[fl & F_OWNER].psi_wet;
+        if (interior) sm.sl[sg][ii] = 0xFFFFFFFFu;
+        continue;
+      }
+      unsigned sl = 0;
+      R rho = 0;
+      if (fl & F_NEAR) {
+        const Cell c = cell_of(n, lat);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          R v = sm.pull[sg][i][p];
+          if (i && (__ldg(flags + nbr(c, lat, i, -1)) & F_SOLID)) {
+            sl |= 1u << i;
+            v = __ldg(src + (size_t)opp_of(i) * N + n);
+            sm.pull[sg][i][p] = v;
+          }
+          rho += v;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += sm.pull[sg][i][p];
+      }
+      sm.psi[slot][p] = (R)1 - exp(-rho / rho0);
+      if (interior) sm.sl[sg][ii] = sl;
+    }
+  };
+
+  issue(z0 - 1);
+  cp_async_commit();
+  issue(z0);
+  cp_async_commit();
+  if (z0 + 1 <= zend) issue(z0 + 1);
+  cp_async_commit();
+  cp_async_wait<2>();
+  __syncthreads();
+  consume(z0 - 1, false);
+  __syncthreads();
+  if (z0 + 2 <= zend) issue(z0 + 2);
+  cp_async_commit();
+  cp_async_wait<2>();
+  __syncthreads();
+  consume(z0, true);
+
+  const int tx = tid % TX, ty = tid / TX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool mine = x < lat.nx && y < lat.ny;
+  const int pc = (ty + 1) * EX + (tx + 1);
+  for (int z = z0; z < zend; ++z) {
+    cp_async_wait<1>();
+    __syncthreads();
+    consume(z + 1, z + 1 < zend);
+    __syncthreads();
+    const int sg = stage(z);
+    const unsigned sl = sm.sl[sg][tid];
+    if (mine) {
+      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * z);
+      if (sl == 0xFFFFFFFFu) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = 0.f;
+        if (diag) {
+          diag_rho[n] = 0.0;
+          diag_vel[3 * n] = 0.0;
+          diag_vel[3 * n + 1] = 0.0;
+          diag_vel[3 * n + 2] = 0.0;
+        }
+      } else {
+        const int sm_ = (z - 1 - z0 + 3) % 3, s0 = (z - z0 + 3) % 3, sp = (z + 1 - z0 + 3) % 3;
+        const R ps = sm.psi[s0][pc];
+        R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int slot = cz_of(i) > 0 ? sp : (cz_of(i) < 0 ? sm_ : s0);
+          const R wp = (R)w_of(i) * sm.psi[slot][pc + cy_of(i) * EX + cx_of(i)];
+          if (cx_of(i)) sx += wp * (R)cx_of(i);
+          if (cy_of(i)) sy += wp * (R)cy_of(i);
+          if (cz_of(i)) sz += wp * (R)cz_of(i);
+        }
+        const R mG = -(R)pp.G * ps;
+        const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
+        R fi[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fi[i] = sm.pull[sg][i][pc];
+        R rho = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += fi[i];
+        my_mass += rho;
+        if (sl) {
+          Cell c;
+          c.x = x;
+          c.y = y;
+          c.z = z;
+          c.xm = x ? x - 1 : lat.nx - 1;
+          c.xp = x + 1 < lat.nx ? x + 1 : 0;
+          c.ym = y ? y - 1 : lat.ny - 1;
+          c.yp = y + 1 < lat.ny ? y + 1 : 0;
+          c.zm = z ? z - 1 : lat.nz - 1;
+          c.zp = z + 1 < lat.nz ? z + 1 : 0;
+          R drho = 0;
+#pragma unroll
+          for (int i = 1; i < Q; ++i) {
+            if (!(sl & (1u << i))) continue;
+            const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
+            const R g = wall_term<R>(bodies[B], c, lat, i, rho);
+            fi[i] += g;
+            drho -= g;
+          }
+          fi[0] += drho;
+        }
+        R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (cx_of(i)) mx += (R)cx_of(i) * fi[i];
+          if (cy_of(i)) my += (R)cy_of(i) * fi[i];
+          if (cz_of(i)) mz += (R)cz_of(i) * fi[i];
+        }
+        R vx = 0, vy = 0, vz = 0;
+        if (rho > (R)0) {
+          const R ir = (R)1 / rho;
+          vx = mx * ir;
+          vy = my * ir;
+          vz = mz * ir;
+        }
+        const R itau = (R)1 / (R)pp.tau;
+        const R pref = (R)1 - (R)0.5 * itau;
+        const R uu = vx * vx + vy * vy + vz * vz;
+        const R vF = vx * Fx + vy * Fy + vz * Fz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
+          const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
+          const R w = (R)w_of(i);
+          const R feq = rho * w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+          const R Fi = pref * w * ((R)3 * (cF - vF) + (R)9 * cu * cF);
+          dst[(size_t)i * N + n] = fi[i] - (fi[i] - feq) * itau + Fi;
+        }
+        if (diag) {
+          diag_rho[n] = (double)rho;
+          diag_vel[3 * n] = (double)vx;
+          diag_vel[3 * n + 1] = (double)vy;
+          diag_vel[3 * n + 2] = (double)vz;
+        }
+      }
+    }
+    __syncthreads();
+    if (z + 3 <= zend) issue(z + 3);
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+  double m = warp_sum((double)my_mass);
+  if ((tid & 31) == 0) sm.red[tid >> 5] = m;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sm.red[w];
+    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (t != 0.0) atomicAdd(mass_part + (b & (MASS_SLOTS - 1)), t);
+  }
+}
+
 // ---- solid-fluid force on the bodies ---------------------------------------------------------
 // For each listed fluid cell x: for a solid upstream neighbour s = x - c_i (owner B), momentum
 // exchange -c_i (2 f*_opp(i)(x) + g_i) with the arm at the link midpoint (Eq. solid_liquid_force);
@@ -599,7 +837,7 @@ __device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const Bo
 // f_eq(rho_n, u_n) / |N_F(n)| (face neighbours; all 26 if n has no fluid face neighbour).
 template <typename S>
 __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restrict__ fb,
-                                                const uint16_t* __restrict__ flags,
+                                                uint16_t* __restrict__ flags,
                                                 const BodyDev* __restrict__ bodies, StepState* st, int* blist,
                                                 Lat lat) {
   using R = typename St<S>::R;
@@ -643,6 +881,9 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
       } else {
 #pragma unroll
         for (int i = 1; i < Q; ++i) boundary |= (__ldg(flags + nbr(c, lat, i, +1)) & F_SOLID) != 0;
+        // this thread is the only writer of the cell's flag word in this pass; concurrent readers
+        // only test the solid bit, which this store does not change
+        if (boundary != ((fm & F_NEAR) != 0)) flags[m] = boundary ? (uint16_t)(fm | F_NEAR) : (uint16_t)(fm & ~F_NEAR);
         if (events) {
           bool any = false;
           for (int dz = -1; dz <= 1 && !any; ++dz)
@@ -750,12 +991,22 @@ static void fused_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, const B
                                                       pp, tz);
 }
 
+size_t fused_async_smem() { return sizeof(AsyncSmem<FTX, FTY>); }
+
 void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
                       double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
                       int tz, cudaStream_t s) {
-  if (prec == 1)
-    fused_t<float>(lat, (float*)fa, (float*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
-  else if (prec == 2)
+  if (prec == 1) {
+    static bool attr = false;
+    const size_t bytes = fused_async_smem();
+    if (!attr) {
+      cudaFuncSetAttribute(k_lbm_fused_async<FTX, FTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      attr = true;
+    }
+    dim3 grid((lat.nx + FTX - 1) / FTX, (lat.ny + FTY - 1) / FTY, (lat.nz + tz - 1) / tz);
+    k_lbm_fused_async<FTX, FTY><<<grid, FTX * FTY, bytes, s>>>((float*)fa, (float*)fb, flags, bodies, mass_part, st,
+                                                               diag_rho, diag_vel, lat, pp, tz);
+  } else if (prec == 2)
     fused_t<__half>(lat, (__half*)fa, (__half*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
 }
 
@@ -811,7 +1062,7 @@ void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags,
   else k_init_fluid<__half><<<blocks, T, 0, s>>>((__half*)f, flags, rho, u, lat);
 }
 
-void launch_refill(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies, int nb,
+void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, int nb,
                    int max_tile, StepState* st, int* blist, cudaStream_t s) {
   if (nb == 0) return;
   const int T = 256;
