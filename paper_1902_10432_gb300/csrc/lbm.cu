@@ -500,30 +500,56 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
   R my_mass = 0;
   auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
   auto stage = [&](int z) { return (z - z0 + 1) % 3; };
+  const int nx = lat.nx, ny = lat.ny, nz = lat.nz;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
 
-  // copy the pull sources of plane z (all 19 directions, the extended plane) into its stage
+  // this thread's extended cells (at most two) and their wrapped x / y offsets for the source
+  // shifts -1, 0, +1 (the y offsets pre-multiplied by nx), computed once per block
+  constexpr int NP = (EP + NT - 1) / NT;
+  static_assert(NP <= 2, "at most two extended cells per thread");
+  int pp_[NP];
+  unsigned xo[NP][3], yo[NP][3];
+  int np = 0;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const int p = tid + j * NT;
+    pp_[j] = p;
+    if (p < EP) np = j + 1;
+    const int ex = p % EX, ey = p / EX;
+    const int xe = wrap(x0 - 1 + ex, nx), ye = wrap(y0 - 1 + ey, ny);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      xo[j][k] = (unsigned)wrap(xe + k - 1, nx);
+      yo[j][k] = (unsigned)wrap(ye + k - 1, ny) * (unsigned)nx;
+    }
+  }
+
+  // copy the pull sources of plane z (all 19 directions, the extended plane) into its stage:
+  // source of direction i at cell (x, y, z) is (x - cx, y - cy, z - cz), i.e. shift k = 1 - c
   auto issue = [&](int z) {
     const int sg = stage(z);
+    const int zz = wrap(z, nz);
+    size_t zo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) zo[k] = (size_t)wrap(zz + k - 1, nz) * nxy;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int zs = wrap(wrap(z, lat.nz) - cz_of(i), lat.nz);
-      for (int p = tid; p < EP; p += NT) {
-        const int ex = p % EX, ey = p / EX;
-        const int xs = wrap(wrap(x0 - 1 + ex, lat.nx) - cx_of(i), lat.nx);
-        const int ys = wrap(wrap(y0 - 1 + ey, lat.ny) - cy_of(i), lat.ny);
-        const size_t n = (size_t)xs + (size_t)lat.nx * ((size_t)ys + (size_t)lat.ny * zs);
-        cp_async4(&sm.pull[sg][i][p], src + (size_t)i * N + n);
-      }
+      const float* base = src + (size_t)i * N + zo[1 - cz_of(i)];
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        if (j < np) cp_async4(&sm.pull[sg][i][pp_[j]], base + xo[j][1 - cx_of(i)] + yo[j][1 - cy_of(i)]);
     }
   };
   // psi of plane z (and, for interior cells, the bounce-back substitution kept in the stage)
   auto consume = [&](int z, bool keep) {
     const int sg = stage(z), slot = (z - z0 + 3) % 3;
-    const int zz = wrap(z, lat.nz);
-    for (int p = tid; p < EP; p += NT) {
+    const size_t zoff = (size_t)wrap(z, nz) * nxy;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      if (j >= np) break;
+      const int p = pp_[j];
       const int ex = p % EX, ey = p / EX;
-      const int x = wrap(x0 - 1 + ex, lat.nx), y = wrap(y0 - 1 + ey, lat.ny);
-      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * zz);
+      const long long n = (long long)(zoff + xo[j][1] + yo[j][1]);
       const uint16_t fl = __ldg(flags + n);
       const bool interior = keep && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
       const int ii = (ey - 1) * TX + (ex - 1);
