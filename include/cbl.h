@@ -167,6 +167,14 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
  * each phase in milliseconds to ms[CBL_NPHASES] (host array). The state advances by nsteps. */
 cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
 
+/* Execution options (no effect on the results beyond rounding order):
+ *   "lbm_variant"  0 = split density and collision kernels (default), 1 = single fused pass that
+ *                  marches along z with prefetch into shared memory (FP32 and FP16-deviation storage
+ *                  only; CBL_ERR_UNSUPPORTED for FP64);
+ *   "fused_tz"     z extent of a fused block (0 = derived from the SM count).
+ * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
+cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
+
 /* Release every device allocation and the context. */
 cbl_status cbl_destroy(cbl_ctx* ctx);
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "cbl_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int)]),
     "cbl_time_phases": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "cbl_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
     "cbl_destroy": (ctypes.c_int, [_P]),
     "cbl_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -273,6 +274,9 @@ class Sim:
         ms = (ctypes.c_double * len(self.PHASES))()
         self._ck(self._lib.cbl_time_phases(self._h, int(n), ms))
         return dict(zip(self.PHASES, list(ms)))
+
+    def set_option(self, key, value):
+        self._ck(self._lib.cbl_set_option(self._h, key.encode(), float(value)))
 
     @property
     def stream(self):

@@ -36,6 +36,7 @@ struct cbl_ctx {
   unsigned n_mass_part = 0;
   int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
   int fused_tz = 0;      // > 0: FP32 / FP16 storage steps with the fused single-pass kernel
+  int fused_tz_req = 0;  // requested z extent of a fused block (0 = derived)
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -117,6 +118,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   ctx->lat.ny = p.ny;
   ctx->lat.nz = p.nz;
   ctx->lat.N = (long long)p.nx * p.ny * p.nz;
+  ctx->lat.Ns = pop_stride(ctx->lat.N);
   ctx->prec = (int)p.prec;
   ctx->elem = p.prec == CBL_FP64 ? 8 : (p.prec == CBL_FP32 ? 4 : 2);
   PhysParams& pp = ctx->pp;
@@ -136,10 +138,11 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   pp.mpf = p.mpf_kinetics;
 
   const size_t N = (size_t)ctx->lat.N;
-  ctx->fa = dalloc(ctx, N * Q * ctx->elem);
-  ctx->fb = dalloc(ctx, N * Q * ctx->elem);
-  if (ctx->prec != 0) ctx->fused_tz = fused_tz(ctx->lat, 2);
-  ctx->psi = dalloc(ctx, ctx->fused_tz ? 256 : N * (ctx->prec == 0 ? 8 : 4));
+  ctx->fa = dalloc(ctx, (size_t)ctx->lat.Ns * Q * ctx->elem);
+  ctx->fb = dalloc(ctx, (size_t)ctx->lat.Ns * Q * ctx->elem);
+  // the split density + collision pair is the default; the fused single-pass variant is chosen
+  // per lattice by cbl_tune (it needs no psi array but holds fewer threads per SM)
+  ctx->psi = dalloc(ctx, N * (ctx->prec == 0 ? 8 : 4));
   ctx->flags = (uint16_t*)dalloc(ctx, N * 2);
   ctx->diag_rho = (double*)dalloc(ctx, N * 8);
   ctx->diag_vel = (double*)dalloc(ctx, N * 24);
@@ -524,6 +527,32 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
     CK(cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     *device_error = h.err;
+  }
+  return CBL_OK;
+}
+
+cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
+  if (!ctx || !key) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  const std::string k(key);
+  if (k == "lbm_variant") {
+    const int v = (int)value;
+    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "lbm_variant must be 0 or 1");
+    if (v == 1 && ctx->prec == 0) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass stores FP32 or FP16");
+    ctx->fused_tz = v ? (ctx->fused_tz_req > 0 ? ctx->fused_tz_req : fused_tz(ctx->lat, 2)) : 0;
+  } else if (k == "fused_tz") {
+    const int v = (int)value;
+    if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
+    ctx->fused_tz_req = v;
+    if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : fused_tz(ctx->lat, 2);
+  } else {
+    return fail(ctx, CBL_ERR_ARG, "unknown option " + k);
+  }
+  if (ctx->gexec) {
+    cudaStreamSynchronize(ctx->s);
+    cudaGraphExecDestroy(ctx->gexec);
+    cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
   }
   return CBL_OK;
 }

@@ -48,8 +48,16 @@ constexpr int E_TILE = 1, E_NBLIST = 2, E_REFILL = 4;
 
 struct Lat {
   int nx, ny, nz;
-  long long N;
+  long long N;   // cells
+  long long Ns;  // distance between the population arrays of two directions, >= N (padded)
 };
+
+// Padding of the population stride: with N a large power of two the 19 direction arrays would all
+// start at the same DRAM channel offset; an odd multiple of 128 elements spreads them.
+#ifndef CBL_POP_PAD
+#define CBL_POP_PAD 1152
+#endif
+inline long long pop_stride(long long N) { return ((N + 127) / 128) * 128 + CBL_POP_PAD; }
 
 // One solid body: rigid state (FP64), shape for the initial profile, and its phase-field tile.
 // The tile is a box of L cells per axis whose cell (i,j,k) holds the global cell

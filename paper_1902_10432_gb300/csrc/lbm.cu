@@ -80,25 +80,59 @@ __device__ __forceinline__ long long nbr(const Cell& c, const Lat& lat, int i, i
 }
 
 // Pull: f_i(x) = f*_i(x - c_i) from a fluid source, else f*_opp(i)(x) (half-way bounce-back).
+// A cell without the near-solid flag has no solid neighbour, so its sources need no test.
 template <typename S>
 __device__ __forceinline__ void pull(const S* __restrict__ f, const uint16_t* __restrict__ flags,
                                      const Lat& lat, const Cell& c, long long n,
-                                     typename St<S>::R fi[Q], unsigned& solid_links) {
-  const size_t N = (size_t)lat.N;
+                                     typename St<S>::R fi[Q], unsigned& solid_links,
+                                     uint16_t own_flag = F_NEAR) {
+  const size_t N = (size_t)lat.Ns;  // population stride
+  const bool near = (own_flag & F_NEAR) != 0;
   solid_links = 0;
+  fi[0] = St<S>::ld(f, (size_t)n, 0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == 0) {
-      fi[0] = St<S>::ld(f, (size_t)n, 0);
-      continue;
-    }
-    long long s = nbr(c, lat, i, -1);
-    if (__ldg(flags + s) & F_SOLID) {
-      solid_links |= 1u << i;
-      fi[i] = St<S>::ld(f, (size_t)opp_of(i) * N + n, opp_of(i));
-    } else {
-      fi[i] = St<S>::ld(f, (size_t)i * N + s, i);
-    }
+  for (int i = 1; i < Q; ++i) {
+    const long long s = nbr(c, lat, i, -1);
+    const bool sol = near && (__ldg(flags + s) & F_SOLID);
+    solid_links |= (unsigned)sol << i;
+    // St<__half> adds the weight of the direction actually read: opp(i) has the same weight as i
+    fi[i] = St<S>::ld(f, sol ? (size_t)opp_of(i) * N + n : (size_t)i * N + s, i);
+  }
+}
+
+// Guo-forced BGK collision (Eqs. lb_collision, distribution_eq, guo_forcing) of one cell, written
+// to dst. Opposite directions share the even part of f_eq + F_i and flip the odd part:
+// f*_i = (1 - 1/tau) f_i + S_i + A_i, f*_opp = (1 - 1/tau) f_opp + S_i - A_i with
+// S_i = (rho w_i / tau)(1 + 4.5 (c.v)^2 - 1.5 v.v) + (1 - 1/2tau) w_i (9 (c.v)(c.F) - 3 v.F),
+// A_i = 3 w_i ((rho / tau) c.v + (1 - 1/2tau) c.F).
+template <typename S>
+__device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, long long n,
+                                              const typename St<S>::R fi[Q], typename St<S>::R rho,
+                                              typename St<S>::R vx, typename St<S>::R vy, typename St<S>::R vz,
+                                              typename St<S>::R Fx, typename St<S>::R Fy, typename St<S>::R Fz,
+                                              double tau) {
+  using R = typename St<S>::R;
+  const R itau = (R)1 / (R)tau;
+  const R keep = (R)1 - itau;
+  const R pref = (R)1 - (R)0.5 * itau;
+  const R ro = rho * itau;
+  const R uu = vx * vx + vy * vy + vz * vz;
+  const R vF = vx * Fx + vy * Fy + vz * Fz;
+  const R base = (R)1 - (R)1.5 * uu;   // even part without (c.v)^2
+  const R fv = -(R)3 * pref * vF;       // even forcing part without (c.v)(c.F)
+  {
+    const R w = (R)w_of(0);
+    St<S>::st(dst, (size_t)n, 0, keep * fi[0] + w * (ro * base + fv));
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
+    const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
+    const R w = (R)w_of(i);
+    const R sym = w * (ro * (base + (R)4.5 * cu * cu) + fv + (R)9 * pref * cu * cF);
+    const R anti = (R)3 * w * (ro * cu + pref * cF);
+    St<S>::st(dst, (size_t)i * N + n, i, keep * fi[i] + sym + anti);
+    St<S>::st(dst, (size_t)(i + 1) * N + n, i + 1, keep * fi[i + 1] + sym - anti);
   }
 }
 
@@ -121,7 +155,7 @@ __global__ void __launch_bounds__(256) k_density(const S* __restrict__ fa, const
       Cell c = cell_of(n, lat);
       R fi[Q];
       unsigned sl;
-      pull<S>(f, flags, lat, c, n, fi, sl);
+      pull<S>(f, flags, lat, c, n, fi, sl, fl);
       R rho = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) rho += fi[i];
@@ -161,8 +195,11 @@ __device__ __forceinline__ R wall_term(const BodyDev& b, const Cell& c, const La
   return (R)2 * rho * (R)w_of(i) * cu * (R)3;
 }
 
+#ifndef CBL_COLLIDE_MINB
+#define CBL_COLLIDE_MINB 1
+#endif
 template <typename S>
-__global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restrict__ fb,
+__global__ void __launch_bounds__(256, CBL_COLLIDE_MINB) k_collide(S* __restrict__ fa, S* __restrict__ fb,
                                                  const uint16_t* __restrict__ flags,
                                                  const typename St<S>::R* __restrict__ psi,
                                                  const BodyDev* __restrict__ bodies,
@@ -170,7 +207,7 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
                                                  double* __restrict__ diag_rho, double* __restrict__ diag_vel,
                                                  Lat lat, PhysParams pp) {
   using R = typename St<S>::R;
-  const size_t N = (size_t)lat.N;
+  const size_t N = (size_t)lat.Ns;  // population stride
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
@@ -203,7 +240,7 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
     const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
     R fi[Q];
     unsigned sl;
-    pull<S>(src, flags, lat, c, n, fi, sl);
+    pull<S>(src, flags, lat, c, n, fi, sl, fl);
     R rho = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) rho += fi[i];
@@ -237,19 +274,7 @@ __global__ void __launch_bounds__(256) k_collide(S* __restrict__ fa, S* __restri
       vy = my * ir;
       vz = mz * ir;
     }
-    const R itau = (R)1 / (R)pp.tau;
-    const R pref = (R)1 - (R)0.5 * itau;
-    const R uu = vx * vx + vy * vy + vz * vz;
-    const R vF = vx * Fx + vy * Fy + vz * Fz;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
-      const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
-      const R w = (R)w_of(i);
-      const R feq = rho * w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
-      const R Fi = pref * w * ((R)3 * (cF - vF) + (R)9 * cu * cF);
-      St<S>::st(dst, (size_t)i * N + n, i, fi[i] - (fi[i] - feq) * itau + Fi);
-    }
+    collide_store<S>(dst, N, n, fi, rho, vx, vy, vz, Fx, Fy, Fz, pp.tau);
     if (diag) {
       diag_rho[n] = (double)rho;
       diag_vel[3 * n] = (double)vx;
@@ -292,7 +317,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
   __shared__ unsigned s_sl[2][NT];
   __shared__ double s_red[NT / 32];
 
-  const size_t N = (size_t)lat.N;
+  const size_t N = (size_t)lat.Ns;  // population stride
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
@@ -489,7 +514,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM& sm = *reinterpret_cast<SM*>(smem_raw);
 
-  const size_t N = (size_t)lat.N;
+  const size_t N = (size_t)lat.Ns;  // population stride
   const int diag = st->diag;
   const float* __restrict__ src = st->parity ? fb : fa;
   float* __restrict__ dst = st->parity ? fa : fb;
@@ -827,7 +852,7 @@ __global__ void k_init_fluid(S* __restrict__ f, const uint16_t* __restrict__ fla
   using R = typename St<S>::R;
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= lat.N) return;
-  const size_t N = (size_t)lat.N;
+  const size_t N = (size_t)lat.Ns;  // population stride
   if (flags[n] & F_SOLID) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) St<S>::st(f, (size_t)i * N + n, i, (R)0);
@@ -883,7 +908,7 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
       const Cell c = cell_of(m, lat);
       const uint16_t fm = flags[m];
       const bool events = st->ncover != 0;
-      const size_t N = (size_t)lat.N;
+      const size_t N = (size_t)lat.Ns;  // population stride
       auto at = [&](int x, int y, int z) {
         return (long long)wrapi(x, lat.nx) + (long long)lat.nx * (wrapi(y, lat.ny) + (long long)lat.ny * wrapi(z, lat.nz));
       };
