@@ -50,33 +50,44 @@ struct St<__half> {
   __device__ static void st(__half* p, size_t k, int i, R v) { p[k] = __float2half_rn(v - c_wh[i]); }
 };
 
+// A lattice cell with its neighbour offsets: nbr(c, i, s) is the index of x + s c_i, built from
+// per-axis offsets for -1, 0, +1 that already contain the periodic wrap (32-bit: the lattice holds
+// fewer than 2^31 cells).
 struct Cell {
   int x, y, z;
-  int xm, xp, ym, yp, zm, zp;
+  unsigned n;
+  int ox[3], oy[3], oz[3];
 };
 
-__device__ __forceinline__ Cell cell_of(long long n, const Lat& lat) {
+__device__ __forceinline__ Cell make_cell(int x, int y, int z, const Lat& lat) {
   Cell c;
-  c.x = (int)(n % lat.nx);
-  long long r = n / lat.nx;
-  c.y = (int)(r % lat.ny);
-  c.z = (int)(r / lat.ny);
-  c.xm = c.x ? c.x - 1 : lat.nx - 1;
-  c.xp = c.x + 1 < lat.nx ? c.x + 1 : 0;
-  c.ym = c.y ? c.y - 1 : lat.ny - 1;
-  c.yp = c.y + 1 < lat.ny ? c.y + 1 : 0;
-  c.zm = c.z ? c.z - 1 : lat.nz - 1;
-  c.zp = c.z + 1 < lat.nz ? c.z + 1 : 0;
+  c.x = x;
+  c.y = y;
+  c.z = z;
+  const int nx = lat.nx, nxy = lat.nx * lat.ny;
+  c.n = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)lat.ny * (unsigned)z);
+  c.ox[0] = x ? -1 : nx - 1;
+  c.ox[1] = 0;
+  c.ox[2] = x + 1 < nx ? 1 : -(nx - 1);
+  c.oy[0] = y ? -nx : nx * (lat.ny - 1);
+  c.oy[1] = 0;
+  c.oy[2] = y + 1 < lat.ny ? nx : -nx * (lat.ny - 1);
+  c.oz[0] = z ? -nxy : nxy * (lat.nz - 1);
+  c.oz[1] = 0;
+  c.oz[2] = z + 1 < lat.nz ? nxy : -nxy * (lat.nz - 1);
   return c;
+}
+
+__device__ __forceinline__ Cell cell_of(long long n, const Lat& lat) {
+  const unsigned u = (unsigned)n, nx = (unsigned)lat.nx, ny = (unsigned)lat.ny;
+  const unsigned r = u / nx;
+  return make_cell((int)(u - r * nx), (int)(r % ny), (int)(r / ny), lat);
 }
 
 // neighbour x + s * c_i (s = +1 downstream, -1 upstream)
 __device__ __forceinline__ long long nbr(const Cell& c, const Lat& lat, int i, int s) {
-  int dx = s * cx_of(i), dy = s * cy_of(i), dz = s * cz_of(i);
-  int X = dx > 0 ? c.xp : (dx < 0 ? c.xm : c.x);
-  int Y = dy > 0 ? c.yp : (dy < 0 ? c.ym : c.y);
-  int Z = dz > 0 ? c.zp : (dz < 0 ? c.zm : c.z);
-  return (long long)X + (long long)lat.nx * ((long long)Y + (long long)lat.ny * Z);
+  (void)lat;
+  return (long long)(c.n + (unsigned)(c.ox[1 + s * cx_of(i)] + c.oy[1 + s * cy_of(i)] + c.oz[1 + s * cz_of(i)]));
 }
 
 // Pull: f_i(x) = f*_i(x - c_i) from a fluid source, else f*_opp(i)(x) (half-way bounce-back).
@@ -137,32 +148,31 @@ __device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, lon
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256) k_density(const S* __restrict__ fa, const S* __restrict__ fb,
+__global__ void __launch_bounds__(128) k_density(const S* __restrict__ fa, const S* __restrict__ fb,
                                                  const StepState* __restrict__ st,
                                                  const uint16_t* __restrict__ flags,
                                                  const BodyDev* __restrict__ bodies,
                                                  typename St<S>::R* __restrict__ psi, Lat lat, double rho0) {
   using R = typename St<S>::R;
   const S* __restrict__ f = st->parity ? fb : fa;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-#pragma unroll 1
-  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < lat.N; n += stride) {
-    uint16_t fl = flags[n];
-    R ps;
-    if (fl & F_SOLID) {
-      ps = (R)bodies[fl & F_OWNER].psi_wet;
-    } else {
-      Cell c = cell_of(n, lat);
-      R fi[Q];
-      unsigned sl;
-      pull<S>(f, flags, lat, c, n, fi, sl, fl);
-      R rho = 0;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (x >= lat.nx || y >= lat.ny) return;
+  const Cell c = make_cell(x, y, z, lat);
+  const long long n = c.n;
+  const uint16_t fl = flags[n];
+  R ps;
+  if (fl & F_SOLID) {
+    ps = (R)bodies[fl & F_OWNER].psi_wet;
+  } else {
+    R fi[Q];
+    unsigned sl;
+    pull<S>(f, flags, lat, c, n, fi, sl, fl);
+    R rho = 0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) rho += fi[i];
-      ps = (R)1 - exp(-rho / (R)rho0);
-    }
-    psi[n] = ps;
+    for (int i = 0; i < Q; ++i) rho += fi[i];
+    ps = (R)1 - exp(-rho / (R)rho0);
   }
+  psi[n] = ps;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -196,10 +206,10 @@ __device__ __forceinline__ R wall_term(const BodyDev& b, const Cell& c, const La
 }
 
 #ifndef CBL_COLLIDE_MINB
-#define CBL_COLLIDE_MINB 1
+#define CBL_COLLIDE_MINB 5
 #endif
 template <typename S>
-__global__ void __launch_bounds__(256, CBL_COLLIDE_MINB) k_collide(S* __restrict__ fa, S* __restrict__ fb,
+__global__ void __launch_bounds__(128, CBL_COLLIDE_MINB) k_collide(S* __restrict__ fa, S* __restrict__ fb,
                                                  const uint16_t* __restrict__ flags,
                                                  const typename St<S>::R* __restrict__ psi,
                                                  const BodyDev* __restrict__ bodies,
@@ -211,10 +221,13 @@ __global__ void __launch_bounds__(256, CBL_COLLIDE_MINB) k_collide(S* __restrict
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  const bool valid = x < lat.nx && y < lat.ny;
+  const Cell c = make_cell(valid ? x : 0, valid ? y : 0, z, lat);
+  const long long n = c.n;
   R my_mass = 0;
-  const uint16_t fl = n < lat.N ? flags[n] : (uint16_t)0;
-  if (n < lat.N && (fl & F_SOLID)) {
+  const uint16_t fl = valid ? flags[n] : (uint16_t)0;
+  if (valid && (fl & F_SOLID)) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
     if (diag) {
@@ -223,8 +236,7 @@ __global__ void __launch_bounds__(256, CBL_COLLIDE_MINB) k_collide(S* __restrict
       diag_vel[3 * n + 1] = 0.0;
       diag_vel[3 * n + 2] = 0.0;
     }
-  } else if (n < lat.N) {
-    Cell c = cell_of(n, lat);
+  } else if (valid) {
     // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
     // it needs only psi, so the populations are not yet live
     const R ps = psi[n];
@@ -286,12 +298,17 @@ __global__ void __launch_bounds__(256, CBL_COLLIDE_MINB) k_collide(S* __restrict
   // body kernel adds the slots in a fixed order and clears them
   __shared__ double wsum[8];
   double m = warp_sum((double)my_mass);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = m;
+  {
+    const int l = threadIdx.x + blockDim.x * threadIdx.y;
+    if ((l & 31) == 0) wsum[l >> 5] = m;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  const int lin = threadIdx.x + blockDim.x * threadIdx.y;
+  if (lin == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-    if (t != 0.0) atomicAdd(mass_part + (blockIdx.x & (MASS_SLOTS - 1)), t);
+    for (int w = 0; w < (int)((blockDim.x * blockDim.y) >> 5); ++w) t += wsum[w];
+    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (t != 0.0) atomicAdd(mass_part + (b & (MASS_SLOTS - 1)), t);
   }
 }
 
@@ -396,16 +413,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
       for (int i = 0; i < Q; ++i) rho += fi[i];
       my_mass += rho;
       if (sl) {
-        Cell c;
-        c.x = x;
-        c.y = y;
-        c.z = z;
-        c.xm = x ? x - 1 : lat.nx - 1;
-        c.xp = x + 1 < lat.nx ? x + 1 : 0;
-        c.ym = y ? y - 1 : lat.ny - 1;
-        c.yp = y + 1 < lat.ny ? y + 1 : 0;
-        c.zm = z ? z - 1 : lat.nz - 1;
-        c.zp = z + 1 < lat.nz ? z + 1 : 0;
+        const Cell c = make_cell(x, y, z, lat);
         R drho = 0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
@@ -666,16 +674,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
         for (int i = 0; i < Q; ++i) rho += fi[i];
         my_mass += rho;
         if (sl) {
-          Cell c;
-          c.x = x;
-          c.y = y;
-          c.z = z;
-          c.xm = x ? x - 1 : lat.nx - 1;
-          c.xp = x + 1 < lat.nx ? x + 1 : 0;
-          c.ym = y ? y - 1 : lat.ny - 1;
-          c.yp = y + 1 < lat.ny ? y + 1 : 0;
-          c.zm = z ? z - 1 : lat.nz - 1;
-          c.zp = z + 1 < lat.nz ? z + 1 : 0;
+          const Cell c = make_cell(x, y, z, lat);
           R drho = 0;
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
@@ -1066,10 +1065,13 @@ static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void
                        double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
                        const PhysParams& pp, cudaStream_t s, int phases) {
   using R = typename St<S>::R;
-  if (phases & 1) k_density<S><<<blocks, 256, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
+  (void)blocks;
+  const dim3 blk(32, 4, 1);
+  const dim3 grid((lat.nx + 31) / 32, (lat.ny + 3) / 4, lat.nz);
+  if (phases & 1) k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
   if (phases & 2)
-    k_collide<S><<<(unsigned)((lat.N + 255) / 256), 256, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st,
-                                                                  diag_rho, diag_vel, lat, pp);
+    k_collide<S><<<grid, blk, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel, lat,
+                                      pp);
 }
 
 void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
