@@ -205,11 +205,21 @@ __device__ __forceinline__ R wall_term(const BodyDev& b, const Cell& c, const La
   return (R)2 * rho * (R)w_of(i) * cu * (R)3;
 }
 
+// Resident 128-thread blocks per SM requested for the collision kernel: occupancy matters more
+// than the few registers it spills (FP32: 64 registers, a 32-byte spill); FP64 needs more room.
 #ifndef CBL_COLLIDE_MINB
-#define CBL_COLLIDE_MINB 5
+#define CBL_COLLIDE_MINB 8
 #endif
 template <typename S>
-__global__ void __launch_bounds__(128, CBL_COLLIDE_MINB) k_collide(S* __restrict__ fa, S* __restrict__ fb,
+struct CollideMinBlocks {
+  static constexpr int value = CBL_COLLIDE_MINB;
+};
+template <>
+struct CollideMinBlocks<double> {
+  static constexpr int value = 4;
+};
+template <typename S>
+__global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* __restrict__ fa, S* __restrict__ fb,
                                                  const uint16_t* __restrict__ flags,
                                                  const typename St<S>::R* __restrict__ psi,
                                                  const BodyDev* __restrict__ bodies,
