@@ -245,7 +245,7 @@ def bench_cuda(args, rank, world, local_rank):
                        "inputs_vs_l2": "populations 2 x %.0f MB > 129 MB L2 (no flush needed)"
                                        % (w.ncells * 19 * POP_BYTES[prec] / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "k_collide" if prec == "fp64" else "k_lbm_fused", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "alg_bytes_per_cell": bpc,
                          "step_frac": bpc * w.ncells / (ms_max / args.steps * 1e-3) / 1e9 / peak},

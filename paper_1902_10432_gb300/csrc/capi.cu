@@ -160,7 +160,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   cudaMemsetAsync(ctx->st, 0, sizeof(StepState), ctx->s);
   cudaMemsetAsync(ctx->mass_part, 0, (size_t)ctx->n_mass_part * 8, ctx->s);
   set_fp16_weights(ctx->s);
-  set_repulsion_offsets(p.rc, ctx->s);
+  set_repulsion_offsets(p.rc, p.e0, p.nrep, ctx->s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     dfree_all(ctx);

@@ -65,7 +65,7 @@ inline long long pop_stride(long long N) { return ((N + 127) / 128) * 128 + CBL_
 // at `off` in the arena: buffer 0 is the current field.
 struct BodyDev {
   double X[3], Xprev[3], V[3], W[3], Q[4];
-  double M, Ib[9];
+  double M, Ib[9], Ibinv[9];  // body-frame inertia and its inverse
   double wet, psi_wet, vol_ref, rho_s;
   double c0[3], radius, half[3], q0[4];
   int fixed, shape;
@@ -100,6 +100,11 @@ struct PhysParams {
   double solid_threshold, member_threshold;
   int mpf;
 };
+
+// Bit-pattern tests of doubles on the integer pipe (GB300 issues FP64 at a small fraction of the
+// FP32 rate). For any double v and a positive threshold t: v > t <=> bits(v) > bits(t) as signed
+// 64-bit integers, since negative v have the sign bit set.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
 
 __host__ __device__ inline int wrapi(int a, int n) {
   int r = a % n;
@@ -151,7 +156,7 @@ void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double*
                    double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf,
                    double* volacc, StepState* st, cudaStream_t s);
-void set_repulsion_offsets(double rc, cudaStream_t s);
+void set_repulsion_offsets(double rc, double e0, int nrep, cudaStream_t s);
 void launch_kinetics(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena,
                      const double* volacc, const PhysParams& pp, cudaStream_t s);
 void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena,

@@ -24,10 +24,14 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double PHI_EPS = 1e-12;
 constexpr int MAXOFF = 512;
 __constant__ int c_off[3 * MAXOFF];
+__constant__ double c_offf[3 * MAXOFF];  // force on the first point of a pair at offset d: f(d)
 __constant__ int c_noff;
 
-void set_repulsion_offsets(double rc, cudaStream_t s) {
+// Offsets d with 0 < |d| < r_c and the pair force e0 (n / r_c) |(|d| - r_c) / r_c|^(n-1) (-d/|d|)
+// (Eq. solid_solid_force) that a point feels from a point at x + d.
+void set_repulsion_offsets(double rc, double e0, int nrep, cudaStream_t s) {
   int off[3 * MAXOFF];
+  double ff[3 * MAXOFF];
   int n = 0;
   int R = (int)ceil(rc);
   for (int dz = -R; dz <= R; ++dz)
@@ -38,10 +42,16 @@ void set_repulsion_offsets(double rc, cudaStream_t s) {
           off[3 * n] = dx;
           off[3 * n + 1] = dy;
           off[3 * n + 2] = dz;
+          const double d = sqrt((double)d2);
+          const double mag = e0 * nrep / rc * pow(fabs((d - rc) / rc), (double)(nrep - 1));
+          ff[3 * n] = -dx / d * mag;
+          ff[3 * n + 1] = -dy / d * mag;
+          ff[3 * n + 2] = -dz / d * mag;
           n++;
         }
       }
   cudaMemcpyToSymbolAsync(c_off, off, sizeof(int) * 3 * n, 0, cudaMemcpyHostToDevice, s);
+  cudaMemcpyToSymbolAsync(c_offf, ff, sizeof(double) * 3 * n, 0, cudaMemcpyHostToDevice, s);
   cudaMemcpyToSymbolAsync(c_noff, &n, sizeof(int), 0, cudaMemcpyHostToDevice, s);
 }
 
@@ -281,20 +291,36 @@ __global__ void k_body_props_finish(BodyDev* bodies, int nb, const double* scrat
           for (int l = 0; l < 3; ++l) acc += R[3 * k + a] * (rho_s * s[3 * k + l]) * R[3 * l + c];
         b.Ib[3 * a + c] = acc;
       }
+    const double* I = b.Ib;
+    const double det = I[0] * (I[4] * I[8] - I[5] * I[7]) - I[1] * (I[3] * I[8] - I[5] * I[6]) +
+                       I[2] * (I[3] * I[7] - I[4] * I[6]);
+    b.Ibinv[0] = (I[4] * I[8] - I[5] * I[7]) / det;
+    b.Ibinv[1] = (I[2] * I[7] - I[1] * I[8]) / det;
+    b.Ibinv[2] = (I[1] * I[5] - I[2] * I[4]) / det;
+    b.Ibinv[3] = (I[5] * I[6] - I[3] * I[8]) / det;
+    b.Ibinv[4] = (I[0] * I[8] - I[2] * I[6]) / det;
+    b.Ibinv[5] = (I[2] * I[3] - I[0] * I[5]) / det;
+    b.Ibinv[6] = (I[3] * I[7] - I[4] * I[6]) / det;
+    b.Ibinv[7] = (I[1] * I[6] - I[0] * I[7]) / det;
+    b.Ibinv[8] = (I[0] * I[4] - I[1] * I[3]) / det;
   }
 }
 
 // ---- solid-solid repulsion ---------------------------------------------------------------------
-__global__ void k_repulsion(const BodyDev* bodies, const double* arena, double* acc, Lat lat, double e0, double rc,
-                            int nrep, double thr) {
+// For a point x of body A (phi_A >= the membership threshold) and every body B whose tile overlaps
+// A's: sum the table forces f(d) over the points x + d of B; torque (x - X_A) x (sum f).
+__global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const double* arena, double* acc, Lat lat,
+                                                   double rc, double thr) {
   const int self = blockIdx.y;
   const BodyDev& a = bodies[self];
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
   if (a.nnb == 0) return;  // block-uniform
-  if (t < a.sz && arena[a.off + t] >= thr) {
-    TileCell c = tile_cell(a, t, lat);
-    double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tb = dbits(thr);
+  double F[3] = {0, 0, 0};
+  bool has = false;
+  TileCell c;
+  if (t < a.sz && dbits(arena[a.off + t]) >= tb) {
+    c = tile_cell(a, t, lat);
     const int R = (int)ceil(rc);
     const int g[3] = {c.gx, c.gy, c.gz};
     const int nn[3] = {lat.nx, lat.ny, lat.nz};
@@ -310,23 +336,21 @@ __global__ void k_repulsion(const BodyDev* bodies, const double* arena, double* 
       if (!near) continue;
       const double* bb = arena + b.off;
       for (int j = 0; j < c_noff; ++j) {
-        int dx = c_off[3 * j], dy = c_off[3 * j + 1], dz = c_off[3 * j + 2];
-        long long q = tile_index(b.o, b.L, c.gx + dx, c.gy + dy, c.gz + dz, lat);
-        if (q < 0 || bb[q] < thr) continue;
-        double d = sqrt((double)(dx * dx + dy * dy + dz * dz));
-        double mag = e0 * nrep / rc * pow(fabs((d - rc) / rc), (double)(nrep - 1));
-        double fv[3] = {-dx / d * mag, -dy / d * mag, -dz / d * mag};
-        double tq[3];
-        xcross(arm, fv, tq);
-        for (int p = 0; p < 3; ++p) {
-          F[p] += fv[p];
-          T[p] += tq[p];
-        }
+        const long long q = tile_index(b.o, b.L, c.gx + c_off[3 * j], c.gy + c_off[3 * j + 1], c.gz + c_off[3 * j + 2], lat);
+        if (q < 0 || dbits(bb[q]) < tb) continue;
+        F[0] += c_offf[3 * j];
+        F[1] += c_offf[3 * j + 1];
+        F[2] += c_offf[3 * j + 2];
+        has = true;
       }
     }
   }
-  const bool has = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0;
   if (__ballot_sync(0xffffffffu, has) == 0) return;
+  double T[3] = {0, 0, 0};
+  if (has) {
+    const double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
+    xcross(arm, F, T);
+  }
   for (int p = 0; p < 3; ++p) {
     double sf = dwarp_sum(F[p]), st = dwarp_sum(T[p]);
     if ((threadIdx.x & 31) == 0) {
@@ -361,27 +385,16 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
     if (x < 0) x += n[a];
     b.X[a] = x;
   }
-  double R[9], Iw[9];
+  // I_w^-1 = R I_body^-1 R^T (the body-frame inverse is computed once, at set-up)
+  double R[9], inv[9];
   quat_R(b.Q, R);
   for (int a = 0; a < 3; ++a)
     for (int c = 0; c < 3; ++c) {
       double acc = 0;
       for (int k = 0; k < 3; ++k)
-        for (int l = 0; l < 3; ++l) acc += R[3 * a + k] * b.Ib[3 * k + l] * R[3 * c + l];
-      Iw[3 * a + c] = acc;
+        for (int l = 0; l < 3; ++l) acc += R[3 * a + k] * b.Ibinv[3 * k + l] * R[3 * c + l];
+      inv[3 * a + c] = acc;
     }
-  double det = Iw[0] * (Iw[4] * Iw[8] - Iw[5] * Iw[7]) - Iw[1] * (Iw[3] * Iw[8] - Iw[5] * Iw[6]) +
-               Iw[2] * (Iw[3] * Iw[7] - Iw[4] * Iw[6]);
-  double inv[9];
-  inv[0] = (Iw[4] * Iw[8] - Iw[5] * Iw[7]) / det;
-  inv[1] = (Iw[2] * Iw[7] - Iw[1] * Iw[8]) / det;
-  inv[2] = (Iw[1] * Iw[5] - Iw[2] * Iw[4]) / det;
-  inv[3] = (Iw[5] * Iw[6] - Iw[3] * Iw[8]) / det;
-  inv[4] = (Iw[0] * Iw[8] - Iw[2] * Iw[6]) / det;
-  inv[5] = (Iw[2] * Iw[3] - Iw[0] * Iw[5]) / det;
-  inv[6] = (Iw[3] * Iw[7] - Iw[4] * Iw[6]) / det;
-  inv[7] = (Iw[1] * Iw[6] - Iw[0] * Iw[7]) / det;
-  inv[8] = (Iw[0] * Iw[4] - Iw[1] * Iw[3]) / det;
   for (int a = 0; a < 3; ++a) b.W[a] += inv[3 * a] * T[0] + inv[3 * a + 1] * T[1] + inv[3 * a + 2] * T[2];
   double wn = sqrt(b.W[0] * b.W[0] + b.W[1] * b.W[1] + b.W[2] * b.W[2]);
   if (wn > 0) {
@@ -494,7 +507,8 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
       const int l = in_local(li[d], k - 2, b.L[d], b.L[d] == nn[d] ? nn[d] : -1);
       p[k] = (ok && l >= 0 && l < b.L[d]) ? in[base + l * sd] : 0.0;
     }
-    if (p[0] == p[2] && p[1] == p[2] && p[3] == p[2] && p[4] == p[2]) {
+    const long long b2 = dbits(p[2]);
+    if (dbits(p[0]) == b2 && dbits(p[1]) == b2 && dbits(p[3]) == b2 && dbits(p[4]) == b2) {
       // flat stencil: both face fluxes are u * p with the same u, so the update is exactly zero
       v = p[2];
     } else {
@@ -519,7 +533,7 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
       v = p[2] - (Fr - Fl);
     }
     arena[b.off + (long long)out_buf * b.sz + t] = v;
-    if (last && v != 0.0) {
+    if (last && (dbits(v) << 1) != 0) {  // v != +-0
       // the outer two layers must stay empty (they are the stencil halo)
       bool edge = false;
       for (int a = 0; a < 3; ++a)
@@ -528,10 +542,13 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
     }
   }
   if (last) {
-    const bool live = inside && v != 0.0;
+    const long long vb = dbits(v);
+    const bool live = inside && (vb << 1) != 0;
     if (__ballot_sync(0xffffffffu, live)) {
       double sv = dwarp_sum(live ? v : 0.0);
-      double sc = dwarp_sum((live && v > PHI_EPS && v < 1.0 - PHI_EPS) ? 1.0 : 0.0);
+      const bool in_if = live && vb > dbits(PHI_EPS) && vb < dbits(1.0 - PHI_EPS);
+      const int cnt = __popc(__ballot_sync(0xffffffffu, in_if));
+      double sc = (double)cnt;
       if ((threadIdx.x & 31) == 0) {
         if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
         if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
@@ -603,9 +620,10 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
   }
   double pa[7];
   tile_val7(in, b.L, ii, nn, pa);
+  const long long eb = dbits(PHI_EPS);
   bool act_a = false;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) act_a |= pa[k] > PHI_EPS;
+  for (int k = 0; k < 7; ++k) act_a |= dbits(pa[k]) > eb;
   if (!act_a) {
     out[t] = pa[0];
     return;
@@ -645,7 +663,7 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     double v7[7];
     tile_val7(arena + o.off + o.sz, o.L, lo, nn, v7);
     bool on = false;
-    for (int k = 0; k < 7; ++k) on |= v7[k] > PHI_EPS;
+    for (int k = 0; k < 7; ++k) on |= dbits(v7[k]) > eb;
     if (!on) continue;
     if (na < MAXACT - (pos_self < 0 ? 1 : 0)) {  // always keep a slot for self
       for (int k = 0; k < 7; ++k) {
@@ -752,8 +770,7 @@ void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, do
 void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
                       const PhysParams& pp, cudaStream_t s) {
   if (nb > 1 && pp.e0 != 0.0)
-    k_repulsion<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, acc, lat, pp.e0, pp.rc, pp.nrep,
-                                                       pp.member_threshold);
+    k_repulsion<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, acc, lat, pp.rc, pp.member_threshold);
 }
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
                    double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {

@@ -153,3 +153,22 @@ def test_spheres2_full_size_fp32_500_steps():
     assert e["flag_mismatch"] <= 8
     assert e["rho"] < 1e-4 and e["vel"] < 1e-3
     assert e["force"] < 1e-3
+
+
+@pytest.mark.parametrize("d", [(1, 0, 0), (0, 2, 0), (1, 1, 1), (2, 2, 1), (0, 0, 3)])
+def test_repulsion_pairs_match_oracle(d):
+    # two one-point bodies (sphere of radius 1/2 centred on a cell: that cell has phi >= 1/2);
+    # the repulsion part of the force must match the oracle's pair sum
+    import oracle
+    from paper_1902_10432_gb300 import cbl
+
+    sims = [cbl.Sim(16, 16, 16, prec="fp64"), oracle.Oracle(16, 16, 16)]
+    for s in sims:
+        s.add_body("sphere", (7.0, 7.0, 7.0), radius=0.5, mass_density=1.0, wetting_rho=1.0, fixed=True)
+        s.add_body("sphere", (7.0 + d[0], 7.0 + d[1], 7.0 + d[2]), radius=0.5, mass_density=1.0, wetting_rho=1.0,
+                   fixed=True)
+        s.init_fluid(1.0, 1.0)
+        s.step(1)
+    pg = sims[0].body_forces()[2][:, 2, :]
+    po = sims[1].body_forces()[2][:, 2, :]
+    assert np.allclose(pg, po, rtol=1e-12, atol=1e-18), (pg, po)
