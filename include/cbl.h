@@ -129,6 +129,12 @@ cbl_status cbl_read_fields(cbl_ctx* ctx, double* rho, double* vel, double* phi_f
 /* Obstacle flags: solid (N bytes, 0/1) and owner body id (N int32, -1 on fluid). Host pointers. */
 cbl_status cbl_read_flags(cbl_ctx* ctx, unsigned char* solid, int32_t* owner);
 
+/* Post-collision populations of the current state as doubles, laid out [direction][cell] (19 * N),
+ * in this library's direction order: rest, +x, -x, +y, -y, +z, -z, then the edge directions
+ * (+x+y), (-x-y), (+x-y), (-x+y), (+x+z), (-x-z), (+x-z), (-x+z), (+y+z), (-y-z), (+y-z), (-y+z).
+ * on_device != 0: `out` is a device pointer; otherwise a host pointer. */
+cbl_status cbl_read_populations(cbl_ctx* ctx, double* out, int on_device);
+
 /* Dense phase field of one body (N doubles, host). */
 cbl_status cbl_read_phi(cbl_ctx* ctx, int body, double* phi_host);
 

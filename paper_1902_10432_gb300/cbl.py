@@ -68,6 +68,7 @@ SIGNATURES = {
     "cbl_init_fluid_fields": (ctypes.c_int, [_P, _P, _P]),
     "cbl_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "cbl_read_fields": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "cbl_read_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "cbl_read_flags": (ctypes.c_int, [_P, _P, _P]),
     "cbl_read_phi": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cbl_read_body_forces": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -227,6 +228,12 @@ class Sim:
         """Read into device tensors (torch, float64, contiguous)."""
         ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
         self._ck(self._lib.cbl_read_fields(self._h, ptr(rho), ptr(vel), ptr(phi_fluid), 1))
+
+    def populations(self):
+        """Current post-collision populations, float64 [19][nz][ny][nx] in the library's order."""
+        out = np.empty(19 * self.N)
+        self._ck(self._lib.cbl_read_populations(self._h, _vp(out), 0))
+        return out.reshape((19,) + self.shape)
 
     def flags(self):
         s = np.empty(self.N, np.uint8)

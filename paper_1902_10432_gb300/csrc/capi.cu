@@ -25,7 +25,7 @@ struct cbl_ctx {
   PhysParams pp;
   void *fa = nullptr, *fb = nullptr, *psi = nullptr;
   uint16_t* flags = nullptr;
-  double *diag_rho = nullptr, *diag_vel = nullptr, *dense = nullptr;
+  double *diag_rho = nullptr, *diag_vel = nullptr, *dense = nullptr, *popbuf = nullptr;
   std::vector<BodyDev> hb;
   BodyDev* db = nullptr;
   double* arena = nullptr;
@@ -415,6 +415,22 @@ cbl_status cbl_read_fields(cbl_ctx* ctx, double* rho, double* vel, double* phi_f
     CK(cudaMemcpyAsync(phi_fluid, ctx->dense, N * 8, k, ctx->s));
   }
   CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
+cbl_status cbl_read_populations(cbl_ctx* ctx, double* out, int on_device) {
+  if (!ctx || !out) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const size_t bytes = (size_t)Q * ctx->lat.N * 8;
+  double* dst = out;
+  if (!on_device) {
+    if (!ctx->popbuf && !(ctx->popbuf = (double*)dalloc(ctx, bytes))) return fail(ctx, CBL_ERR_OOM, "population buffer");
+    dst = ctx->popbuf;
+  }
+  launch_read_populations(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, dst, ctx->s);
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   return CBL_OK;
 }

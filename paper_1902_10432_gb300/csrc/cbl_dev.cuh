@@ -138,6 +138,8 @@ void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16
 void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
                      const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st,
                      double G, double rho0, cudaStream_t s);
+void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
+                             double* out, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags,

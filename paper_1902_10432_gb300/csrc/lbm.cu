@@ -1016,6 +1016,25 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
   }
 }
 
+// current populations, widened to double, [direction][cell]
+template <typename S>
+__global__ void k_read_pop(const S* __restrict__ fa, const S* __restrict__ fb, const StepState* __restrict__ st,
+                           double* __restrict__ out, Lat lat) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= lat.N) return;
+  const S* f = st->parity ? fb : fa;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) out[(size_t)i * lat.N + n] = (double)St<S>::ld(f, (size_t)i * lat.Ns + n, i);
+}
+
+void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
+                             double* out, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((lat.N + 255) / 256);
+  if (prec == 0) k_read_pop<double><<<blocks, 256, 0, s>>>((const double*)fa, (const double*)fb, st, out, lat);
+  else if (prec == 1) k_read_pop<float><<<blocks, 256, 0, s>>>((const float*)fa, (const float*)fb, st, out, lat);
+  else k_read_pop<__half><<<blocks, 256, 0, s>>>((const __half*)fa, (const __half*)fb, st, out, lat);
+}
+
 // ---- launchers -------------------------------------------------------------------------------
 static int sm_count() {
   int dev = 0, sms = 148;
