@@ -181,6 +181,24 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 
+/* One lattice-Boltzmann time step that allocates nothing, for callers that cannot allocate device
+ * memory (their memory belongs to another framework's pool, or their process must not call
+ * cudaMalloc once running). The paper has no counterpart: this is plumbing, not method.
+ * The step is the plain fluid part of cbl_step on a lattice without solid bodies: pull streaming,
+ * psi, Shan-Chen force, Guo-forced BGK collision; FP32 populations, SoA [direction][cell] with a
+ * stride of nx*ny*nz, in the direction order of cbl_read_populations. f_in and f_out are the
+ * caller's device buffers (19 * nx*ny*nz floats each, distinct); mass_out (device, may be NULL)
+ * receives the fluid mass of the step. Scratch (psi, flags, mass slots) is a fixed set of device
+ * arrays inside the library, sized for CBL_NOALLOC_MAX_CELLS cells and held on every GPU that
+ * loads the library until the process exits; larger lattices return CBL_ERR_ARG. The first call
+ * on a device looks up those arrays with that device current and synchronises the device: make it
+ * before any stream capture. All calls share the arrays: calls that overlap on the GPU (other
+ * streams, other threads) race. Work is enqueued on `stream` (NULL = legacy default stream).
+ * Returns CBL_ERR_ARG for bad sizes or pointers, CBL_ERR_CUDA if a CUDA call fails. */
+#define CBL_NOALLOC_MAX_CELLS (1 << 20)
+cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int nx, int ny, int nz, double tau, double G,
+                                double rho0, const double* ext_force, double* mass_out, void* stream);
+
 /* Release every device allocation and the context. */
 cbl_status cbl_destroy(cbl_ctx* ctx);
 

@@ -79,6 +79,8 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_int)]),
     "cbl_time_phases": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "cbl_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
+    "cbl_lbm_step_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "cbl_destroy": (ctypes.c_int, [_P]),
     "cbl_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -295,3 +297,23 @@ class Sim:
         err = ctypes.c_int()
         self._ck(self._lib.cbl_info(self._h, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(err)))
         return dict(nbodies=nb.value, ncells=nc.value, device_error=err.value)
+
+
+NOALLOC_MAX_CELLS = 1 << 20
+
+
+def lbm_step_noalloc(f_in, f_out, nx, ny, nz, tau=1.0, G=-5.0, rho0=1.0, ext_force=None, mass_out=None,
+                     stream=None):
+    """One fluid-only LBM step on caller-owned device tensors (float32, 19*nx*ny*nz each) with no
+    device allocation inside the library (see cbl_lbm_step_noalloc in include/cbl.h)."""
+    lib = load()
+    ext = None
+    if ext_force is not None:
+        ext = (ctypes.c_double * 3)(*ext_force)
+    st = lib.cbl_lbm_step_noalloc(ctypes.c_void_p(f_in.data_ptr()), ctypes.c_void_p(f_out.data_ptr()), nx, ny, nz,
+                                  float(tau), float(G), float(rho0), ext,
+                                  None if mass_out is None else ctypes.c_void_p(mass_out.data_ptr()),
+                                  None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise CblError(st, "cbl_lbm_step_noalloc")
+

@@ -16,6 +16,9 @@
 //
 // Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights. The
 // two lattice-wide kernels use a grid-stride loop over a grid of a few blocks per SM.
+#include <mutex>
+
+#include "../../include/cbl.h"
 #include "cbl_dev.cuh"
 
 namespace cbl {
@@ -1155,3 +1158,90 @@ void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags
 }
 
 }  // namespace cbl
+
+// ---- one lattice-Boltzmann step with no allocation --------------------------------------------
+// For callers that cannot allocate device memory (an allocator owned by another framework, a
+// pre-reserved memory pool, a process that forbids cudaMalloc after start-up): the scratch this
+// step needs (psi, an all-fluid flag field, the mass slots and the step state) lives in file-scope
+// device arrays sized for CBL_NOALLOC_MAX_CELLS cells. Every GPU that loads the library holds them
+// until the process exits.
+namespace {
+__device__ __align__(256) float g_na_psi[CBL_NOALLOC_MAX_CELLS];
+__device__ __align__(256) uint16_t g_na_flags[CBL_NOALLOC_MAX_CELLS];
+__device__ __align__(256) double g_na_mass[cbl::MASS_SLOTS];
+__device__ __align__(256) cbl::StepState g_na_state;
+
+struct NaScratch {
+  float* psi = nullptr;
+  uint16_t* flags = nullptr;
+  double* mass = nullptr;
+  cbl::StepState* state = nullptr;
+};
+constexpr int NA_MAX_DEVICES = 64;
+NaScratch g_na[NA_MAX_DEVICES];
+bool g_na_ready[NA_MAX_DEVICES];
+std::mutex g_na_mutex;
+
+__global__ void k_na_mass(const double* __restrict__ slots, double* __restrict__ out) {
+  __shared__ double red[256];
+  red[threadIdx.x] = slots[threadIdx.x];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+}  // namespace
+
+extern "C" cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int nx, int ny, int nz, double tau,
+                                           double G, double rho0, const double* ext_force, double* mass_out,
+                                           void* stream) {
+  using namespace cbl;
+  if (!f_in || !f_out || f_in == f_out) return CBL_ERR_ARG;
+  if (nx < 4 || ny < 4 || nz < 4) return CBL_ERR_ARG;
+  const long long N = (long long)nx * ny * nz;
+  if (N > CBL_NOALLOC_MAX_CELLS) return CBL_ERR_ARG;
+  if (!(tau > 0.5) || !(rho0 > 0)) return CBL_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return CBL_ERR_CUDA;
+  {
+    // once per device, with that device current: host code needs the arrays' device addresses
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ready[dev]) {
+      NaScratch& a = g_na[dev];
+      if (cudaGetSymbolAddress((void**)&a.psi, g_na_psi) != cudaSuccess) return CBL_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&a.flags, g_na_flags) != cudaSuccess) return CBL_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&a.mass, g_na_mass) != cudaSuccess) return CBL_ERR_CUDA;
+      if (cudaGetSymbolAddress((void**)&a.state, g_na_state) != cudaSuccess) return CBL_ERR_CUDA;
+      // all fluid, parity 0 (read f_in, write f_out), no field record
+      if (cudaMemset(a.flags, 0, sizeof(uint16_t) * CBL_NOALLOC_MAX_CELLS) != cudaSuccess) return CBL_ERR_CUDA;
+      if (cudaMemset(a.state, 0, sizeof(StepState)) != cudaSuccess) return CBL_ERR_CUDA;
+      if (cudaDeviceSynchronize() != cudaSuccess) return CBL_ERR_CUDA;
+      g_na_ready[dev] = true;
+    }
+  }
+  const NaScratch& a = g_na[dev];
+  Lat lat;
+  lat.nx = nx;
+  lat.ny = ny;
+  lat.nz = nz;
+  lat.N = N;
+  lat.Ns = N;  // the caller's arrays are packed
+  PhysParams pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.tau = tau;
+  pp.G = G;
+  pp.rho0 = rho0;
+  for (int k = 0; k < 3; ++k) pp.ext[k] = ext_force ? ext_force[k] : 0.0;
+  if (cudaMemsetAsync(a.mass, 0, sizeof(double) * MASS_SLOTS, s) != cudaSuccess) return CBL_ERR_CUDA;
+  const dim3 blk(32, 4, 1);
+  const dim3 grid((nx + 31) / 32, (ny + 3) / 4, nz);
+  k_density<float><<<grid, blk, 0, s>>>(f_in, f_in, a.state, a.flags, nullptr, a.psi, lat, rho0);
+  k_collide<float><<<grid, blk, 0, s>>>(const_cast<float*>(f_in), f_out, a.flags, a.psi, nullptr, a.mass, a.state,
+                                        nullptr, nullptr, lat, pp);
+  if (mass_out) k_na_mass<<<1, 256, 0, s>>>(a.mass, mass_out);
+  return cudaGetLastError() == cudaSuccess ? CBL_OK : CBL_ERR_CUDA;
+}
+
