@@ -175,6 +175,66 @@ def bench_reference(args, rank, world):
     return 0
 
 
+def bench_batch(args, rank, world, local_rank):
+    """64 independent two-sphere instances: one batched graph vs the instances run one after another."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+
+    if not os.path.exists(os.path.join(ROOT, "paper_1902_10432_gb300", "_lib", "libcbl.so")):
+        __graft_entry__.build()
+    from paper_1902_10432_gb300 import autotune, cbl, workloads
+
+    ws = workloads.batch64(seed=0, prec=args.precision)
+    cells = sum(w.ncells for w in ws)
+    sims = []
+    choices = {}
+    for w in ws:
+        s = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
+        workloads.build(s, w)
+        c, _ = autotune.tune(s, steps=3)
+        choices[json.dumps(c, sort_keys=True)] = choices.get(json.dumps(c, sort_keys=True), 0) + 1
+        sims.append(s)
+    # sequential: each instance alone, one after another
+    for s in sims:
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(args.steps)
+        torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    batch = cbl.Batch(sims)
+    batch.step(args.warmup)
+    batch.sync()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.Stream()
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        batch.step(args.steps)
+        batch.sync()
+        bat_s = time.perf_counter() - t1
+    value = world * cells * args.steps / bat_s / 1e6
+    line = {"metric": "aggregate MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * bat_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "batch64: 64 two-sphere instances, boxes U{64..128}^3, R U[10,24], "
+                                   "liquid fraction U[0.01,0.2], angle U[30,90] deg, seed 0",
+                       "cells": cells, "autotune_choices": choices},
+            "sequential_mlups": cells * args.steps / seq_s / 1e6,
+            "speedup_vs_sequential": seq_s / bat_s, "clocks": clk.summary(),
+            "gpu_launches": KERNELS[args.precision] * args.steps * len(sims)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def bench_cuda(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -285,7 +345,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
-    ap.add_argument("--workload", default="spheres2", choices=["spheres2", "plates48", "tetra4"])
+    ap.add_argument("--workload", default="spheres2", choices=["spheres2", "plates48", "tetra4", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -295,6 +355,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return bench_reference(args, rank, world)
+    if args.workload == "batch64":
+        return bench_batch(args, rank, world, local_rank)
     return bench_cuda(args, rank, world, local_rank)
 
 

@@ -175,9 +175,10 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
 
 /* Execution options (no effect on the results beyond rounding order):
  *   "lbm_variant"  0 = split density and collision kernels (default), 1 = single fused pass that
- *                  marches along z with prefetch into shared memory (FP32 and FP16-deviation storage
- *                  only; CBL_ERR_UNSUPPORTED for FP64);
- *   "fused_tz"     z extent of a fused block (0 = derived from the SM count).
+ *                  marches along z with prefetch into shared memory (FP32 storage only;
+ *                  CBL_ERR_UNSUPPORTED otherwise);
+ *   "fused_tz"     z extent of a fused block (0 = derived from the SM count);
+ *   "lbm_block_x"  x extent of the 128-thread blocks of the split kernels: 32 (default), 64, 128.
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 
@@ -198,6 +199,19 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 #define CBL_NOALLOC_MAX_CELLS (1 << 20)
 cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int nx, int ny, int nz, double tau, double G,
                                 double rho0, const double* ext_force, double* mass_out, void* stream);
+
+/* Batches: advance many independent contexts with one call. One CUDA graph holds one step of every
+ * instance, each instance on its own branch (fork/join), so the kernels of independent instances
+ * run concurrently. The contexts must be initialised (cbl_init_fluid), live on the current device
+ * and outlive the batch; while in a batch they must not be stepped on their own. `stream` (may be
+ * NULL: the library creates one) orders the batch's work. */
+typedef struct cbl_batch cbl_batch;
+cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch** out);
+/* Advance every instance nsteps steps (asynchronous); the fields of the last step are kept. */
+cbl_status cbl_batch_step(cbl_batch* batch, int nsteps);
+/* Wait for the batch's stream. */
+cbl_status cbl_batch_sync(cbl_batch* batch);
+cbl_status cbl_batch_destroy(cbl_batch* batch);
 
 /* Release every device allocation and the context. */
 cbl_status cbl_destroy(cbl_ctx* ctx);

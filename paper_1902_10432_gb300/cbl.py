@@ -81,6 +81,10 @@ SIGNATURES = {
     "cbl_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
     "cbl_lbm_step_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _P, _P, _P]),
+    "cbl_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "cbl_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cbl_batch_sync": (ctypes.c_int, [_P]),
+    "cbl_batch_destroy": (ctypes.c_int, [_P]),
     "cbl_destroy": (ctypes.c_int, [_P]),
     "cbl_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -297,6 +301,41 @@ class Sim:
         err = ctypes.c_int()
         self._ck(self._lib.cbl_info(self._h, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(err)))
         return dict(nbodies=nb.value, ncells=nc.value, device_error=err.value)
+
+
+class Batch:
+    """Independent simulations advanced together: one CUDA graph holds one step of every instance,
+    each on its own branch (cbl_batch_* in include/cbl.h). The simulations must outlive the batch."""
+
+    def __init__(self, sims, stream=None):
+        self._lib = load()
+        self.sims = list(sims)
+        arr = (_P * len(self.sims))(*[s._h.value for s in self.sims])
+        h = _P()
+        st = self._lib.cbl_batch_create(arr, len(self.sims),
+                                        None if stream is None else _P(stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(None).decode())
+        self._h = h
+
+    def step(self, n=1):
+        st = self._lib.cbl_batch_step(self._h, int(n))
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(None).decode())
+
+    def sync(self):
+        self._lib.cbl_batch_sync(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cbl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_CELLS = 1 << 20

@@ -37,6 +37,7 @@ struct cbl_ctx {
   int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
   int fused_tz = 0;      // > 0: FP32 / FP16 storage steps with the fused single-pass kernel
   int fused_tz_req = 0;  // requested z extent of a fused block (0 = derived)
+  int block_x = 32;      // x extent of the split kernels' 128-thread blocks
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -306,7 +307,7 @@ static void enqueue_lbm(cbl_ctx* ctx, int phases) {
                        ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->s);
   } else {
     launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                    lbm_blocks(ctx->lat), ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, phases);
+                    (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, phases);
   }
 }
 
@@ -553,13 +554,17 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
   if (k == "lbm_variant") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "lbm_variant must be 0 or 1");
-    if (v == 1 && ctx->prec == 0) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass stores FP32 or FP16");
+    if (v == 1 && ctx->prec != 1) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass stores FP32");
     ctx->fused_tz = v ? (ctx->fused_tz_req > 0 ? ctx->fused_tz_req : fused_tz(ctx->lat, 2)) : 0;
   } else if (k == "fused_tz") {
     const int v = (int)value;
     if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
     ctx->fused_tz_req = v;
     if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : fused_tz(ctx->lat, 2);
+  } else if (k == "lbm_block_x") {
+    const int v = (int)value;
+    if (v != 32 && v != 64 && v != 128) return fail(ctx, CBL_ERR_ARG, "lbm_block_x must be 32, 64 or 128");
+    ctx->block_x = v;
   } else {
     return fail(ctx, CBL_ERR_ARG, "unknown option " + k);
   }
@@ -570,6 +575,105 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     ctx->gexec = nullptr;
     ctx->graph = nullptr;
   }
+  return CBL_OK;
+}
+
+struct cbl_batch {
+  std::vector<cbl_ctx*> ctxs;
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> events;  // [0] fork, [1..n] joins
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  cudaGraph_t graph[2] = {nullptr, nullptr};      // [0] no field record, [1] record fields
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+
+static cudaError_t batch_capture(cbl_batch* b, int diag, cudaGraph_t* g) {
+  cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(b->events[0], b->s);
+  for (size_t k = 0; k < b->ctxs.size(); ++k) {
+    cbl_ctx* c = b->ctxs[k];
+    cudaStream_t br = b->branches[k];
+    cudaStreamWaitEvent(br, b->events[0], 0);
+    cudaStream_t keep = c->s;
+    c->s = br;
+    cudaMemsetAsync(&c->st->diag, diag, sizeof(int), br);
+    enqueue_step(c);
+    c->s = keep;
+    cudaEventRecord(b->events[k + 1], br);
+    cudaStreamWaitEvent(b->s, b->events[k + 1], 0);
+  }
+  cudaError_t e1 = cudaGetLastError();
+  cudaError_t e2 = cudaStreamEndCapture(b->s, g);
+  return e1 != cudaSuccess ? e1 : e2;
+}
+
+cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch** out) {
+  if (!ctxs || n <= 0 || !out) return fail(nullptr, CBL_ERR_ARG, "batch needs contexts");
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return fail(nullptr, CBL_ERR_ARG, "NULL context in batch");
+    if (!ctxs[k]->ready) return fail(nullptr, CBL_ERR_STATE, "batch contexts must be initialised");
+    // finish whatever the context has queued on its own stream before the batch takes over
+    if (cudaStreamSynchronize(ctxs[k]->s) != cudaSuccess) return fail(nullptr, CBL_ERR_CUDA, "sync");
+  }
+  cbl_batch* b = new cbl_batch();
+  b->ctxs.assign(ctxs, ctxs + n);
+  if (stream) {
+    b->s = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return fail(nullptr, CBL_ERR_CUDA, "stream");
+    }
+    b->own_stream = true;
+  }
+  b->branches.resize(n);
+  b->events.resize(n + 1);
+  bool ok = true;
+  for (int k = 0; k < n; ++k) ok &= cudaStreamCreateWithFlags(&b->branches[k], cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k <= n; ++k) ok &= cudaEventCreateWithFlags(&b->events[k], cudaEventDisableTiming) == cudaSuccess;
+  for (int d = 0; d < 2 && ok; ++d) {
+    ok &= batch_capture(b, d, &b->graph[d]) == cudaSuccess;
+    ok &= ok && cudaGraphInstantiate(&b->gexec[d], b->graph[d], 0) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    cbl_batch_destroy(b);
+    return fail(nullptr, CBL_ERR_CUDA, "batch graph capture failed");
+  }
+  *out = b;
+  return CBL_OK;
+}
+
+cbl_status cbl_batch_step(cbl_batch* b, int nsteps) {
+  if (!b) return fail(nullptr, CBL_ERR_ARG, "NULL batch");
+  if (nsteps < 0) return fail(nullptr, CBL_ERR_ARG, "nsteps must be >= 0");
+  for (int k = 0; k < nsteps; ++k)
+    if (cudaGraphLaunch(b->gexec[k == nsteps - 1 ? 1 : 0], b->s) != cudaSuccess)
+      return fail(nullptr, CBL_ERR_CUDA, "batch graph launch failed");
+  for (cbl_ctx* c : b->ctxs) c->t += nsteps;
+  return CBL_OK;
+}
+
+cbl_status cbl_batch_sync(cbl_batch* b) {
+  if (!b) return fail(nullptr, CBL_ERR_ARG, "NULL batch");
+  return cudaStreamSynchronize(b->s) == cudaSuccess ? CBL_OK : fail(nullptr, CBL_ERR_CUDA, "sync");
+}
+
+cbl_status cbl_batch_destroy(cbl_batch* b) {
+  if (!b) return CBL_OK;
+  if (b->s) cudaStreamSynchronize(b->s);
+  for (int d = 0; d < 2; ++d) {
+    if (b->gexec[d]) cudaGraphExecDestroy(b->gexec[d]);
+    if (b->graph[d]) cudaGraphDestroy(b->graph[d]);
+  }
+  for (cudaStream_t br : b->branches)
+    if (br) cudaStreamDestroy(br);
+  for (cudaEvent_t e : b->events)
+    if (e) cudaEventDestroy(e);
+  if (b->own_stream) cudaStreamDestroy(b->s);
+  delete b;
   return CBL_OK;
 }
 

@@ -1097,9 +1097,10 @@ static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void
                        double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
                        const PhysParams& pp, cudaStream_t s, int phases) {
   using R = typename St<S>::R;
-  (void)blocks;
-  const dim3 blk(32, 4, 1);
-  const dim3 grid((lat.nx + 31) / 32, (lat.ny + 3) / 4, lat.nz);
+  // `blocks` carries the x extent of the 128-thread blocks (32, 64 or 128)
+  const int bx = blocks == 64 || blocks == 128 ? (int)blocks : 32, by = 128 / bx;
+  const dim3 blk(bx, by, 1);
+  const dim3 grid((lat.nx + bx - 1) / bx, (lat.ny + by - 1) / by, lat.nz);
   if (phases & 1) k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
   if (phases & 2)
     k_collide<S><<<grid, blk, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel, lat,

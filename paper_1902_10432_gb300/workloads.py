@@ -148,6 +148,38 @@ def tetra4(seed=0, prec="fp32", n=256, R=24.0, f=0.05, theta=60.0, surface_gap=8
                     meta=dict(seed=seed, liquid_fraction_of_solid=f, theta_deg=theta, varrho=varrho))
 
 
+def batch64(seed=0, n=64, prec="fp32", mpf=1, rho_s=4.0, gap=4.0):
+    """Independent two-sphere bridges of uneven box size, liquid fraction and contact angle: box edges
+    U{64..128} per axis, radius U[10, 24] clamped to fit the box (pair on the longest axis, surface gap
+    4), liquid fraction U[0.01, 0.2] of the solid volume, contact angle U[30, 90] deg, all from one
+    seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = [int(v) for v in rng.integers(64, 129, size=3)]
+        R = float(rng.uniform(10.0, 24.0))
+        f = float(rng.uniform(0.01, 0.2))
+        theta = float(rng.uniform(30.0, 90.0))
+        ax = int(np.argmax(L))
+        others = [L[a] for a in range(3) if a != ax]
+        R = min(R, (L[ax] - 4 - 2 * 4) / 4.0, (min(others) - 8) / 2.0)
+        varrho = varrho_for_angle(theta)
+        c = [v / 2.0 for v in L]
+        centers = []
+        for sgn in (-1, 1):
+            p = list(c)
+            p[ax] += sgn * (R + gap / 2.0)
+            centers.append(tuple(p))
+        VS = 2 * 4.0 / 3.0 * math.pi * R ** 3
+        mask, r = _bridge_mask(L[0], L[1], L[2], centers, R, f * VS, tuple(c))
+        bodies = [_sphere_body(p, R, rho_s, varrho) for p in centers]
+        params = dict(tau=1.0, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=mpf)
+        out.append(Workload("batch%02d" % k, L[0], L[1], L[2], params, bodies, mask, steps=500,
+                            meta=dict(seed=seed, index=k, R=R, liquid_fraction_of_solid=f, theta_deg=theta,
+                                      varrho=varrho)))
+    return out
+
+
 def small_spheres(seed=0, prec="fp64", nx=40, ny=36, nz=64, R=8.0, gap=3.0, mpf=1, rho_s=4.0,
                   theta=45.0, f=0.3, mobility=1e-5):
     """A reduced two-sphere bridge (the paper's mass density 4; the spheres move by cells within a
