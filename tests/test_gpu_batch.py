@@ -36,7 +36,10 @@ def test_batch_matches_individual_steps():
     for a, g in zip(alone, grouped):
         ra, va, pa = a.fields()
         rg, vg, pg = g.fields()
-        assert np.array_equal(ra, rg) and np.array_equal(va, vg) and np.array_equal(pa, pg)
+        # the per-body and per-phase FP64 sums are atomics: equal up to their addition order
+        assert np.abs(ra - rg).max() <= 1e-12 * np.abs(ra).max()
+        assert np.abs(va - vg).max() <= 1e-10 * max(np.abs(va).max(), 1e-30)
+        assert np.abs(pa - pg).max() <= 1e-12
         Fa, _, _ = a.body_forces()
         Fg, _, _ = g.body_forces()
         assert np.allclose(Fa, Fg, rtol=1e-12, atol=1e-15)  # FP64 atomics may add in another order
