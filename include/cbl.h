@@ -213,6 +213,33 @@ cbl_status cbl_batch_step(cbl_batch* batch, int nsteps);
 cbl_status cbl_batch_sync(cbl_batch* batch);
 cbl_status cbl_batch_destroy(cbl_batch* batch);
 
+/* Force surrogate network (no counterpart in the paper's method: it stands in for the force
+ * evaluation between full lattice-Boltzmann force evaluations). A multilayer perceptron
+ * n_in -> hidden x n_hidden_layers -> n_out with tanh hidden units and a linear output; the built
+ * configuration is 4 -> 64 -> 64 -> 64 -> 6 (inputs: gap, liquid volume, contact angle, radius ratio,
+ * standardised by the caller; outputs: force and torque). Weights are used in bfloat16 with FP32
+ * accumulation; an FP32 master copy is updated by Adam. Parameter layout (n = cbl_mlp_num_params
+ * floats): for each layer W (out x in, row-major) then b (out). Device memory comes from cudaMalloc
+ * (9,030 parameters, a few hundred kB). x, y, t are device pointers, [sample][feature] floats. */
+typedef struct cbl_mlp cbl_mlp;
+cbl_status cbl_mlp_create(int n_in, int hidden, int n_hidden_layers, int n_out, void* stream, cbl_mlp** out);
+int64_t cbl_mlp_num_params(const cbl_mlp* mlp);
+/* Set the FP32 master weights from a host array (resets Adam's moments), or read them back. */
+cbl_status cbl_mlp_set_params(cbl_mlp* mlp, const float* params_host);
+cbl_status cbl_mlp_get_params(cbl_mlp* mlp, float* params_host);
+/* y = network(x) for n samples. */
+cbl_status cbl_mlp_forward(cbl_mlp* mlp, const float* x, float* y, int n);
+/* Add the gradient of the mean squared error over the n samples and 6 outputs to the internal
+ * FP32 gradient; loss_host (may be NULL) receives the loss (synchronises the stream). */
+cbl_status cbl_mlp_grad(cbl_mlp* mlp, const float* x, const float* t, int n, float* loss_host);
+cbl_status cbl_mlp_read_grad(cbl_mlp* mlp, float* grad_host);
+cbl_status cbl_mlp_zero_grad(cbl_mlp* mlp);
+/* One Adam update of the master weights from the accumulated gradient, refresh the bfloat16
+ * copy, clear the gradient. */
+cbl_status cbl_mlp_adam_step(cbl_mlp* mlp, float lr, float beta1, float beta2, float eps);
+cbl_status cbl_mlp_sync(cbl_mlp* mlp);
+cbl_status cbl_mlp_destroy(cbl_mlp* mlp);
+
 /* Release every device allocation and the context. */
 cbl_status cbl_destroy(cbl_ctx* ctx);
 

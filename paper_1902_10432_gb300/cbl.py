@@ -85,6 +85,18 @@ SIGNATURES = {
     "cbl_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "cbl_batch_sync": (ctypes.c_int, [_P]),
     "cbl_batch_destroy": (ctypes.c_int, [_P]),
+    "cbl_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                      ctypes.POINTER(_P)]),
+    "cbl_mlp_num_params": (ctypes.c_int64, [_P]),
+    "cbl_mlp_set_params": (ctypes.c_int, [_P, _P]),
+    "cbl_mlp_get_params": (ctypes.c_int, [_P, _P]),
+    "cbl_mlp_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "cbl_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+    "cbl_mlp_read_grad": (ctypes.c_int, [_P, _P]),
+    "cbl_mlp_zero_grad": (ctypes.c_int, [_P]),
+    "cbl_mlp_adam_step": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "cbl_mlp_sync": (ctypes.c_int, [_P]),
+    "cbl_mlp_destroy": (ctypes.c_int, [_P]),
     "cbl_destroy": (ctypes.c_int, [_P]),
     "cbl_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -329,6 +341,82 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.cbl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """Force surrogate network on the GPU (cbl_mlp_* in include/cbl.h): 4 -> 64 -> 64 -> 64 -> 6, tanh,
+    bfloat16 weights with FP32 accumulation, FP32 master weights updated by Adam. Tensors are torch
+    CUDA float32, [sample][feature]."""
+
+    def __init__(self, stream=None):
+        import torch
+
+        self._lib = load()
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        h = _P()
+        st = self._lib.cbl_mlp_create(4, 64, 3, 6, _P(self._stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise CblError(st, "cbl_mlp_create")
+        self._h = h
+        self.n_params = int(self._lib.cbl_mlp_num_params(h))
+
+    def _ck(self, st, what):
+        if st != 0:
+            raise CblError(st, what)
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, np.float32)
+        assert a.size == self.n_params
+        self._ck(self._lib.cbl_mlp_set_params(self._h, _vp(a)), "set_params")
+
+    def params(self):
+        a = np.empty(self.n_params, np.float32)
+        self._ck(self._lib.cbl_mlp_get_params(self._h, _vp(a)), "get_params")
+        return a
+
+    def forward(self, x, y=None):
+        import torch
+
+        n = x.shape[0]
+        if y is None:
+            y = torch.empty((n, 6), dtype=torch.float32, device=x.device)
+        self._ck(self._lib.cbl_mlp_forward(self._h, _P(x.data_ptr()), _P(y.data_ptr()), n), "forward")
+        return y
+
+    def grad(self, x, t, want_loss=True):
+        loss = ctypes.c_float()
+        self._ck(self._lib.cbl_mlp_grad(self._h, _P(x.data_ptr()), _P(t.data_ptr()), x.shape[0],
+                                        ctypes.byref(loss) if want_loss else None), "grad")
+        return loss.value if want_loss else None
+
+    def read_grad(self):
+        a = np.empty(self.n_params, np.float32)
+        self._ck(self._lib.cbl_mlp_read_grad(self._h, _vp(a)), "read_grad")
+        return a
+
+    def zero_grad(self):
+        self._ck(self._lib.cbl_mlp_zero_grad(self._h), "zero_grad")
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._ck(self._lib.cbl_mlp_adam_step(self._h, lr, beta1, beta2, eps), "adam_step")
+
+    def sync(self):
+        self._lib.cbl_mlp_sync(self._h)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cbl_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):
