@@ -387,10 +387,16 @@ class MLP:
         n = x.shape[0]
         if y is None:
             y = torch.empty((n, 6), dtype=torch.float32, device=x.device)
+        # inputs written on the caller's stream must be complete; the result is complete on return
+        torch.cuda.current_stream().synchronize()
         self._ck(self._lib.cbl_mlp_forward(self._h, _P(x.data_ptr()), _P(y.data_ptr()), n), "forward")
+        self._lib.cbl_mlp_sync(self._h)
         return y
 
     def grad(self, x, t, want_loss=True):
+        import torch
+
+        torch.cuda.current_stream().synchronize()
         loss = ctypes.c_float()
         self._ck(self._lib.cbl_mlp_grad(self._h, _P(x.data_ptr()), _P(t.data_ptr()), x.shape[0],
                                         ctypes.byref(loss) if want_loss else None), "grad")
