@@ -235,6 +235,58 @@ def bench_batch(args, rank, world, local_rank):
     return 0
 
 
+def bench_surrogate(args, rank, world, local_rank):
+    """Learned surrogate: data from batched two-sphere runs, GPU training, then the surrogate-driven
+    advance of a 512^3 packing of 200 spheres against plain stepping over the same number of steps."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+
+    if not os.path.exists(os.path.join(ROOT, "paper_1902_10432_gb300", "_lib", "libcbl.so")):
+        __graft_entry__.build()
+    from paper_1902_10432_gb300 import cbl, surrogate, workloads
+
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    t0 = time.perf_counter()
+    ws = workloads.batch64(seed=0, prec="fp32")
+    X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, every=10, records=args.sur_records, log=log)
+    gen_s = time.perf_counter() - t0
+    sur, tr = surrogate.train(X, Y, inst, iters=args.sur_iters, log=log)
+    w, pairs, VL = workloads.packing(seed=0, L=args.sur_box)
+    R = [b["radius"] for b in w.bodies]
+    dims = (w.nx, w.ny, w.nz)
+    theta = w.meta["theta_deg"]
+    hyb = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
+    workloads.build(hyb, w)
+    hyb.step(5)
+    torch.cuda.synchronize()
+    res = surrogate.hybrid_run(hyb, sur, R, pairs, VL, theta, dims, windows=args.sur_windows, K=args.sur_k,
+                               W=args.sur_w, log=log)
+    hyb.close()
+    del hyb
+    plain = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
+    workloads.build(plain, w)
+    plain.step(5)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    plain.step(res["steps"])
+    plain.total_mass()
+    plain_s = time.perf_counter() - t1
+    line = {"metric": "surrogate vs plain time-to-solution", "value": plain_s / res["wall_seconds"],
+            "unit": "x (plain wall / surrogate wall)", "n_gpus": world, "steps": res["steps"], "warmup": 5,
+            "higher_is_better": True, "dtype": "f32 populations, bf16 network", "data": "synthetic",
+            "config": {"workload": "packing %d^3, %d spheres R U[12,20], %d bridged pairs, liquid 0.1 of solid"
+                                   % (w.nx, len(R), len(pairs)),
+                       "windows": args.sur_windows, "K_lbm": args.sur_k, "W_surrogate": args.sur_w},
+            "surrogate_wall_s": res["wall_seconds"], "plain_wall_s": plain_s,
+            "force_rel_err_median": res["force_rel_err_median"], "force_rel_err_p95": res["force_rel_err_p95"],
+            "training": tr, "samples": int(len(X)), "data_generation_s": gen_s}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def bench_cuda(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -345,7 +397,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
-    ap.add_argument("--workload", default="spheres2", choices=["spheres2", "plates48", "tetra4", "batch64"])
+    ap.add_argument("--workload", default="spheres2",
+                    choices=["spheres2", "plates48", "tetra4", "batch64", "surrogate"])
+    ap.add_argument("--sur-equil", type=int, default=1000)
+    ap.add_argument("--sur-records", type=int, default=160)
+    ap.add_argument("--sur-iters", type=int, default=3000)
+    ap.add_argument("--sur-box", type=int, default=512)
+    ap.add_argument("--sur-windows", type=int, default=4)
+    ap.add_argument("--sur-k", type=int, default=20)
+    ap.add_argument("--sur-w", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -357,6 +417,8 @@ def main():
         return bench_reference(args, rank, world)
     if args.workload == "batch64":
         return bench_batch(args, rank, world, local_rank)
+    if args.workload == "surrogate":
+        return bench_surrogate(args, rank, world, local_rank)
     return bench_cuda(args, rank, world, local_rank)
 
 

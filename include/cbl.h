@@ -148,6 +148,13 @@ cbl_status cbl_read_body_forces(cbl_ctx* ctx, double* F, double* T, double* part
 cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double* Q, double* M,
                           double* I);
 
+/* Move bodies without stepping the fluid: centres X (nb*3), orientations Q (nb*4; NULL keeps them),
+ * velocities V and W (nb*3; NULL keeps them), host arrays. The phase fields are rebuilt from the
+ * body shapes at the new poses (Sec. 3.1 profile), the obstacle flags recomputed, nodes that became
+ * solid hand their populations to their fluid neighbours and nodes that became fluid start empty
+ * (Sec. 3.2.2). Mass, inertia and reference volumes are kept. */
+cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Q, const double* V, const double* W);
+
 /* Set body velocities (host arrays nb*3, either may be NULL). */
 cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W);
 

@@ -74,6 +74,7 @@ SIGNATURES = {
     "cbl_read_body_forces": (ctypes.c_int, [_P, _P, _P, _P]),
     "cbl_get_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cbl_set_body_velocities": (ctypes.c_int, [_P, _P, _P]),
+    "cbl_move_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "cbl_total_mass": (ctypes.c_int, [_P, _D]),
     "cbl_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int)]),
@@ -286,6 +287,11 @@ class Sim:
         v = None if V is None else np.ascontiguousarray(V, np.float64).reshape(-1)
         w = None if W is None else np.ascontiguousarray(W, np.float64).reshape(-1)
         self._ck(self._lib.cbl_set_body_velocities(self._h, _vp(v), _vp(w)))
+
+    def move_bodies(self, X, Q=None, V=None, W=None):
+        f = lambda a: None if a is None else np.ascontiguousarray(a, np.float64).reshape(-1)
+        X, Q, V, W = f(X), f(Q), f(V), f(W)
+        self._ck(self._lib.cbl_move_bodies(self._h, _vp(X), _vp(Q), _vp(V), _vp(W)))
 
     def total_mass(self):
         m = ctypes.c_double()

@@ -506,6 +506,55 @@ cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double*
   return CBL_OK;
 }
 
+cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, const double* V, const double* W) {
+  if (!ctx || !X) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const int nb = (int)ctx->hb.size();
+  if (!nb) return CBL_OK;
+  std::vector<BodyDev> h(nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  const int n[3] = {ctx->p.nx, ctx->p.ny, ctx->p.nz};
+  for (int b = 0; b < nb; ++b) {
+    BodyDev& d = h[b];
+    for (int a = 0; a < 3; ++a) {
+      double x = std::fmod(X[3 * b + a], (double)n[a]);
+      if (x < 0) x += n[a];
+      d.X[a] = d.Xprev[a] = d.c0[a] = x;
+      if (V) d.V[a] = V[3 * b + a];
+      if (W) d.W[a] = W[3 * b + a];
+    }
+    if (Qn) {
+      const double* q = Qn + 4 * b;
+      const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+      if (!(qn > 0)) return fail(ctx, CBL_ERR_ARG, "zero quaternion");
+      for (int a = 0; a < 4; ++a) d.Q[a] = d.q0[a] = q[a] / qn;
+    } else {
+      for (int a = 0; a < 4; ++a) d.q0[a] = d.Q[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      if (d.L[a] < n[a]) d.o[a] = (int)std::floor(d.X[a] + 0.5) - d.L[a] / 2;
+      d.o_prev[a] = d.o[a];
+    }
+  }
+  // clear the flags under the old tiles; cells solid before and after then read as covered, which
+  // is harmless: solid cells hold zero populations, so their refill hands over nothing
+  launch_clear_tile_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->flags, ctx->s);
+  CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
+  launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
+  launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
+  // cover events are counted by the flag pass; the boundary list is rebuilt by the refill pass
+  CK(cudaMemsetAsync(&ctx->st->ncover, 0, sizeof(unsigned), ctx->s));
+  CK(cudaMemsetAsync(&ctx->st->nbnd, 0, sizeof(unsigned), ctx->s));
+  launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
+               ctx->s);
+  launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                ctx->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
 cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W) {
   if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");

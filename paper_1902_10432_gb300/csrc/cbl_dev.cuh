@@ -145,6 +145,8 @@ void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags,
                    const BodyDev* bodies, int nb, int max_tile, StepState* st, int* blist, cudaStream_t s);
 
+void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
+                             cudaStream_t s);
 void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
                       double eta, cudaStream_t s);
 void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st, cudaStream_t s);

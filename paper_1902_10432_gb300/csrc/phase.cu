@@ -743,6 +743,15 @@ __global__ void k_phi_scatter(const BodyDev* bodies, const double* arena, double
   out[n] = 1.0 - S;
 }
 
+// clear the flags of every cell of the bodies' current tiles (before the bodies are moved)
+__global__ void k_clear_tile_flags(const BodyDev* bodies, uint16_t* flags, Lat lat) {
+  const BodyDev& b = bodies[blockIdx.y];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  const TileCell c = tile_cell(b, t, lat);
+  flags[c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz)] = 0;
+}
+
 // ---- launchers ---------------------------------------------------------------------------------
 static dim3 tile_grid(int max_tile, int nb) { return dim3((unsigned)((max_tile + 255) / 256), (unsigned)nb); }
 
@@ -796,6 +805,11 @@ void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_til
   if (!nb) return;
   dim3 g = tile_grid(max_tile, body >= 0 ? 1 : nb);
   k_phi_scatter<<<g, 256, 0, s>>>(bodies, arena, out, lat, body);
+}
+
+void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
+                             cudaStream_t s) {
+  if (nb) k_clear_tile_flags<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, flags, lat);
 }
 
 }  // namespace cbl

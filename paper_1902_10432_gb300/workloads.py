@@ -96,6 +96,89 @@ def _bridge_mask(nx, ny, nz, centers, R, volume, around):
     return (outside & (dc2 <= hi * hi)).astype(np.uint8), hi
 
 
+def _bridge_mask_radii(nx, ny, nz, centers, radii, volume, around, box=None):
+    """Like _bridge_mask with one radius per sphere; optionally restricted to a local box
+    (x0, x1, y0, y1, z0, z1) of periodic coordinates to keep large lattices cheap."""
+    if box is None:
+        box = (0, nx, 0, ny, 0, nz)
+    x0, x1, y0, y1, z0, z1 = box
+    zz, yy, xx = np.mgrid[z0:z1, y0:y1, x0:x1].astype(np.float32)
+
+    def mind(a, c, n):
+        d = np.abs(a - c) % n
+        return np.minimum(d, n - d)
+
+    outside = np.ones(zz.shape, bool)
+    for c, R in zip(centers, radii):
+        d2 = mind(xx, c[0], nx) ** 2 + mind(yy, c[1], ny) ** 2 + mind(zz, c[2], nz) ** 2
+        outside &= d2 > R * R
+    dc2 = mind(xx, around[0], nx) ** 2 + mind(yy, around[1], ny) ** 2 + mind(zz, around[2], nz) ** 2
+    target = int(round(volume))
+    lo, hi = 0.0, float(max(x1 - x0, y1 - y0, z1 - z0))
+    for _ in range(50):
+        mid = 0.5 * (lo + hi)
+        if np.count_nonzero(outside & (dc2 <= mid * mid)) < target:
+            lo = mid
+        else:
+            hi = mid
+    local = (outside & (dc2 <= hi * hi))
+    if box == (0, nx, 0, ny, 0, nz):
+        return local.astype(np.uint8)
+    return local, (zz.astype(np.int64) % nz, yy.astype(np.int64) % ny, xx.astype(np.int64) % nx)
+
+
+def packing(seed=0, n_spheres=200, L=512, Rmin=12.0, Rmax=20.0, min_gap=2.0, liquid_fraction=0.1,
+            bridge_gap=8.0, theta=45.0, prec="fp32", mpf=1, rho_s=4.0):
+    """Many spheres in a periodic cube by random sequential addition (surface gaps >= min_gap), radii
+    U[Rmin, Rmax]; liquid = liquid_fraction of the solid volume, seeded as equal drops at the midpoints
+    of the pairs closer than bridge_gap (surface to surface). Returns the workload and the list of
+    bridged pairs with their drop volumes."""
+    rng = np.random.default_rng(seed)
+    C, R = [], []
+    tries = 0
+    while len(C) < n_spheres and tries < 200000:
+        tries += 1
+        r = float(rng.uniform(Rmin, Rmax))
+        c = rng.uniform(0, L, size=3)
+        ok = True
+        for cj, rj in zip(C, R):
+            d = np.abs(c - cj)
+            d = np.minimum(d, L - d)
+            if np.sqrt((d * d).sum()) < r + rj + min_gap:
+                ok = False
+                break
+        if ok:
+            C.append(c)
+            R.append(r)
+    pairs = []
+    for i in range(len(C)):
+        for j in range(i + 1, len(C)):
+            d = np.abs(C[i] - C[j])
+            d = np.minimum(d, L - d)
+            if np.sqrt((d * d).sum()) - R[i] - R[j] < bridge_gap:
+                pairs.append((i, j))
+    VS = sum(4.0 / 3.0 * math.pi * r ** 3 for r in R)
+    VL = liquid_fraction * VS
+    vol = VL / max(1, len(pairs))
+    mask = np.zeros((L, L, L), np.uint8)
+    for (i, j) in pairs:
+        d = C[j] - C[i]
+        d = (d + L / 2) % L - L / 2
+        mid = (C[i] + d / 2) % L
+        h = int(max(R[i], R[j]) + 8)
+        lo = np.floor(mid - h).astype(int)
+        box = (lo[0], lo[0] + 2 * h, lo[1], lo[1] + 2 * h, lo[2], lo[2] + 2 * h)
+        local, (zi, yi, xi) = _bridge_mask_radii(L, L, L, [tuple(C[i]), tuple(C[j])], [R[i], R[j]], vol,
+                                                 tuple(mid), box=box)
+        mask[zi[local], yi[local], xi[local]] = 1
+    varrho = varrho_for_angle(theta)
+    bodies = [_sphere_body(tuple(float(v) for v in c), r, rho_s, varrho) for c, r in zip(C, R)]
+    params = dict(tau=1.0, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=mpf)
+    w = Workload("packing", L, L, L, params, bodies, mask, steps=500,
+                 meta=dict(seed=seed, n_spheres=len(C), theta_deg=theta, varrho=varrho, liquid_fraction=liquid_fraction))
+    return w, pairs, {p: vol for p in pairs}
+
+
 def plates48(theta_deg=60.0, prec="fp64", n=48, gap=12, r_bridge=10.0, layers=3, width=32, tau=1.0):
     """Two fixed parallel plates (normal z) joined by a cylindrical bridge (Sec. 4.2 set-up)."""
     c = (n - 1) / 2.0
@@ -157,22 +240,26 @@ def batch64(seed=0, n=64, prec="fp32", mpf=1, rho_s=4.0, gap=4.0):
     out = []
     for k in range(n):
         L = [int(v) for v in rng.integers(64, 129, size=3)]
-        R = float(rng.uniform(10.0, 24.0))
+        Rs = [float(v) for v in rng.uniform(10.0, 24.0, size=2)]  # each sphere its own radius
         f = float(rng.uniform(0.01, 0.2))
         theta = float(rng.uniform(30.0, 90.0))
         ax = int(np.argmax(L))
         others = [L[a] for a in range(3) if a != ax]
-        R = min(R, (L[ax] - 4 - 2 * 4) / 4.0, (min(others) - 8) / 2.0)
+        cap = min((L[ax] - 4 - 2 * 4) / 4.0, (min(others) - 8) / 2.0)
+        Rs = [min(r, cap) for r in Rs]
         varrho = varrho_for_angle(theta)
         c = [v / 2.0 for v in L]
+        # surface gap `gap` centred on the box centre along the longest axis
         centers = []
-        for sgn in (-1, 1):
-            p = list(c)
-            p[ax] += sgn * (R + gap / 2.0)
-            centers.append(tuple(p))
-        VS = 2 * 4.0 / 3.0 * math.pi * R ** 3
-        mask, r = _bridge_mask(L[0], L[1], L[2], centers, R, f * VS, tuple(c))
-        bodies = [_sphere_body(p, R, rho_s, varrho) for p in centers]
+        p0 = list(c)
+        p0[ax] -= gap / 2.0 + Rs[0]
+        p1 = list(c)
+        p1[ax] += gap / 2.0 + Rs[1]
+        centers = [tuple(p0), tuple(p1)]
+        VS = sum(4.0 / 3.0 * math.pi * r ** 3 for r in Rs)
+        mask = _bridge_mask_radii(L[0], L[1], L[2], centers, Rs, f * VS, tuple(c))
+        R = Rs[0]
+        bodies = [_sphere_body(p, r, rho_s, varrho) for p, r in zip(centers, Rs)]
         params = dict(tau=1.0, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=mpf)
         out.append(Workload("batch%02d" % k, L[0], L[1], L[2], params, bodies, mask, steps=500,
                             meta=dict(seed=seed, index=k, R=R, liquid_fraction_of_solid=f, theta_deg=theta,
