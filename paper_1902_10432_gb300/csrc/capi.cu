@@ -429,7 +429,7 @@ cbl_status cbl_read_populations(cbl_ctx* ctx, double* out, int on_device) {
     if (!ctx->popbuf && !(ctx->popbuf = (double*)dalloc(ctx, bytes))) return fail(ctx, CBL_ERR_OOM, "population buffer");
     dst = ctx->popbuf;
   }
-  launch_read_populations(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, dst, ctx->s);
+  launch_read_populations(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, dst, ctx->s);
   CK(cudaGetLastError());
   if (!on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
@@ -538,7 +538,9 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
     }
   }
   // clear the flags under the old tiles; cells solid before and after then read as covered, which
-  // is harmless: solid cells hold zero populations, so their refill hands over nothing
+  // is harmless once solid cells hold zero populations (a node covered in the last step still holds
+  // its stale ones, already handed to its neighbours): zero them first
+  launch_zero_solid(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->s);
   launch_clear_tile_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->flags, ctx->s);
   CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
   launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);

@@ -139,7 +139,9 @@ void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, c
                      const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st,
                      double G, double rho0, cudaStream_t s);
 void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
-                             double* out, cudaStream_t s);
+                             const uint16_t* flags, double* out, cudaStream_t s);
+void launch_zero_solid(int prec, const Lat& lat, void* fa, void* fb, const StepState* st, const uint16_t* flags,
+                       const BodyDev* bodies, int nb, int max_tile, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags,

@@ -1019,23 +1019,57 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
   }
 }
 
-// current populations, widened to double, [direction][cell]
+// current populations, widened to double, [direction][cell]; solid cells read zero (a node covered
+// in the last step keeps its stale populations until the next collision overwrites them)
 template <typename S>
 __global__ void k_read_pop(const S* __restrict__ fa, const S* __restrict__ fb, const StepState* __restrict__ st,
-                           double* __restrict__ out, Lat lat) {
+                           const uint16_t* __restrict__ flags, double* __restrict__ out, Lat lat) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= lat.N) return;
   const S* f = st->parity ? fb : fa;
+  const bool solid = flags[n] & F_SOLID;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) out[(size_t)i * lat.N + n] = (double)St<S>::ld(f, (size_t)i * lat.Ns + n, i);
+  for (int i = 0; i < Q; ++i)
+    out[(size_t)i * lat.N + n] = solid ? 0.0 : (double)St<S>::ld(f, (size_t)i * lat.Ns + n, i);
 }
 
 void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
-                             double* out, cudaStream_t s) {
+                             const uint16_t* flags, double* out, cudaStream_t s) {
   const unsigned blocks = (unsigned)((lat.N + 255) / 256);
-  if (prec == 0) k_read_pop<double><<<blocks, 256, 0, s>>>((const double*)fa, (const double*)fb, st, out, lat);
-  else if (prec == 1) k_read_pop<float><<<blocks, 256, 0, s>>>((const float*)fa, (const float*)fb, st, out, lat);
-  else k_read_pop<__half><<<blocks, 256, 0, s>>>((const __half*)fa, (const __half*)fb, st, out, lat);
+  if (prec == 0)
+    k_read_pop<double><<<blocks, 256, 0, s>>>((const double*)fa, (const double*)fb, st, flags, out, lat);
+  else if (prec == 1)
+    k_read_pop<float><<<blocks, 256, 0, s>>>((const float*)fa, (const float*)fb, st, flags, out, lat);
+  else
+    k_read_pop<__half><<<blocks, 256, 0, s>>>((const __half*)fa, (const __half*)fb, st, flags, out, lat);
+}
+
+// zero the current populations of every solid cell in the bodies' tiles
+template <typename S>
+__global__ void k_zero_solid(S* __restrict__ fa, S* __restrict__ fb, const StepState* __restrict__ st,
+                             const uint16_t* __restrict__ flags, const BodyDev* __restrict__ bodies, Lat lat) {
+  using R = typename St<S>::R;
+  const BodyDev& b = bodies[blockIdx.y];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];
+  const unsigned r = u / L0;
+  const int gx = wrapi(b.o[0] + (int)(u - r * L0), lat.nx), gy = wrapi(b.o[1] + (int)(r % L1), lat.ny),
+            gz = wrapi(b.o[2] + (int)(r / L1), lat.nz);
+  const long long n = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
+  if (!(flags[n] & F_SOLID)) return;
+  S* f = st->parity ? fb : fa;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) St<S>::st(f, (size_t)i * lat.Ns + n, i, (R)0);
+}
+
+void launch_zero_solid(int prec, const Lat& lat, void* fa, void* fb, const StepState* st, const uint16_t* flags,
+                       const BodyDev* bodies, int nb, int max_tile, cudaStream_t s) {
+  if (!nb) return;
+  dim3 grid((unsigned)((max_tile + 255) / 256), (unsigned)nb);
+  if (prec == 0) k_zero_solid<double><<<grid, 256, 0, s>>>((double*)fa, (double*)fb, st, flags, bodies, lat);
+  else if (prec == 1) k_zero_solid<float><<<grid, 256, 0, s>>>((float*)fa, (float*)fb, st, flags, bodies, lat);
+  else k_zero_solid<__half><<<grid, 256, 0, s>>>((__half*)fa, (__half*)fb, st, flags, bodies, lat);
 }
 
 // ---- launchers -------------------------------------------------------------------------------

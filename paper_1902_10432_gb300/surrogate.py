@@ -83,7 +83,11 @@ def generate(ws, equil=1000, every=10, records=160, log=None):
     batch.close()
     for s in sims:
         s.close()
-    return np.array(X), np.array(Y), np.array(inst)
+    X, Y, inst = np.array(X), np.array(Y), np.array(inst)
+    ok = np.isfinite(X).all(1) & np.isfinite(Y).all(1)
+    if log and not ok.all():
+        log("dropping %d non-finite samples from instances %s" % (int((~ok).sum()), sorted(set(inst[~ok].tolist()))))
+    return X[ok], Y[ok], inst[ok]
 
 
 class Surrogate:
