@@ -152,7 +152,11 @@ cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double*
  * velocities V and W (nb*3; NULL keeps them), host arrays. The phase fields are rebuilt from the
  * body shapes at the new poses (Sec. 3.1 profile), the obstacle flags recomputed, nodes that became
  * solid hand their populations to their fluid neighbours and nodes that became fluid start empty
- * (Sec. 3.2.2). Mass, inertia and reference volumes are kept. */
+ * (Sec. 3.2.2). A move whose surface displacement exceeds half a cell is carried out as a chain of
+ * sub-moves of at most half a cell each (linear in X, normalised blend of Q along the shorter arc),
+ * so every newly covered node has a fluid neighbour to receive its populations. Mass, inertia and
+ * reference volumes are kept. CBL_ERR_ARG for a non-finite position or a zero quaternion. Not
+ * part of the paper's method: it serves the learned-force surrogate. */
 cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Q, const double* V, const double* W);
 
 /* Set body velocities (host arrays nb*3, either may be NULL). */

@@ -196,7 +196,9 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   b.wet = body->wetting_rho;
   b.psi_wet = 1.0 - std::exp(-body->wetting_rho / ctx->p.rho0);
   b.fixed = body->fixed;
-  // tile: support half-extent + 2 halo layers + 1 cell of motion before recentring
+  // tile: support half-extent + 2 halo layers + half a cell of recentring offset + 1.5 cells for the
+  // discrete profile and the advection tail, which reach about one cell past R + eta/2 on a moving
+  // body
   double h[3];
   if (b.shape == 0) {
     if (!(b.radius > 0)) return fail(ctx, CBL_ERR_ARG, "sphere radius must be > 0");
@@ -212,7 +214,7 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   const int n[3] = {ctx->p.nx, ctx->p.ny, ctx->p.nz};
   long long sz = 1;
   for (int a = 0; a < 3; ++a) {
-    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 3.0);
+    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 4.0);
     int L = 2 * half + 1;
     if (L >= n[a]) {
       L = n[a];
@@ -511,49 +513,96 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
   const int nb = (int)ctx->hb.size();
   if (!nb) return CBL_OK;
-  std::vector<BodyDev> h(nb);
-  CK(cudaMemcpyAsync(h.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
+  std::vector<BodyDev> h0(nb), h(nb);
+  CK(cudaMemcpyAsync(h0.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   const int n[3] = {ctx->p.nx, ctx->p.ny, ctx->p.nz};
+  // target poses, and the largest displacement of a body surface point (translation plus rotation
+  // angle times the body's extent; a sphere's rotation does not move its phase field)
+  std::vector<double> Xt(3 * nb), Qt(4 * nb);
+  double disp = 0.0;
   for (int b = 0; b < nb; ++b) {
-    BodyDev& d = h[b];
+    const BodyDev& d = h0[b];
+    double dx2 = 0.0;
     for (int a = 0; a < 3; ++a) {
+      if (!std::isfinite(X[3 * b + a])) return fail(ctx, CBL_ERR_ARG, "non-finite body position");
       double x = std::fmod(X[3 * b + a], (double)n[a]);
       if (x < 0) x += n[a];
-      d.X[a] = d.Xprev[a] = d.c0[a] = x;
-      if (V) d.V[a] = V[3 * b + a];
-      if (W) d.W[a] = W[3 * b + a];
+      Xt[3 * b + a] = x;
+      const double dd = mimg(x - d.X[a], n[a]);
+      dx2 += dd * dd;
     }
+    double dot = 0.0;
     if (Qn) {
       const double* q = Qn + 4 * b;
       const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-      if (!(qn > 0)) return fail(ctx, CBL_ERR_ARG, "zero quaternion");
-      for (int a = 0; a < 4; ++a) d.Q[a] = d.q0[a] = q[a] / qn;
+      if (!(qn > 0) || !std::isfinite(qn)) return fail(ctx, CBL_ERR_ARG, "zero or non-finite quaternion");
+      for (int a = 0; a < 4; ++a) {
+        Qt[4 * b + a] = q[a] / qn;
+        dot += Qt[4 * b + a] * d.Q[a];
+      }
     } else {
-      for (int a = 0; a < 4; ++a) d.q0[a] = d.Q[a];
+      for (int a = 0; a < 4; ++a) Qt[4 * b + a] = d.Q[a];
+      dot = 1.0;
     }
-    for (int a = 0; a < 3; ++a) {
-      if (d.L[a] < n[a]) d.o[a] = (int)std::floor(d.X[a] + 0.5) - d.L[a] / 2;
-      d.o_prev[a] = d.o[a];
-    }
+    const double ext = d.shape == 0 ? 0.0 : std::sqrt(d.half[0] * d.half[0] + d.half[1] * d.half[1] + d.half[2] * d.half[2]);
+    const double ang = 2.0 * std::acos(std::min(1.0, std::fabs(dot)));
+    disp = std::max(disp, std::sqrt(dx2) + ang * ext);
   }
-  // clear the flags under the old tiles; cells solid before and after then read as covered, which
-  // is harmless once solid cells hold zero populations (a node covered in the last step still holds
-  // its stale ones, already handed to its neighbours): zero them first
-  launch_zero_solid(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->s);
-  launch_clear_tile_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->flags, ctx->s);
-  CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
-  launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
-  launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
-  // cover events are counted by the flag pass; the boundary list is rebuilt by the refill pass
-  CK(cudaMemsetAsync(&ctx->st->ncover, 0, sizeof(unsigned), ctx->s));
-  CK(cudaMemsetAsync(&ctx->st->nbnd, 0, sizeof(unsigned), ctx->s));
-  launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
-               ctx->s);
-  launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                ctx->s);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(ctx->s));
+  // a move of at most half a cell per sub-move keeps a fluid node next to every newly covered one,
+  // so each cover refill finds a receiver
+  const int nsub = (int)std::min(4096.0, std::max(1.0, std::ceil(disp / 0.5)));
+  for (int k = 1; k <= nsub; ++k) {
+    const double s = (double)k / nsub;
+    for (int b = 0; b < nb; ++b) {
+      BodyDev d = h0[b];
+      for (int a = 0; a < 3; ++a) {
+        double x = k == nsub ? Xt[3 * b + a] : d.X[a] + s * mimg(Xt[3 * b + a] - d.X[a], n[a]);
+        x = std::fmod(x, (double)n[a]);
+        if (x < 0) x += n[a];
+        d.X[a] = d.Xprev[a] = d.c0[a] = x;
+      }
+      // normalised linear blend of the quaternions, taken along the shorter arc
+      double q[4], sgn = 0.0, qn = 0.0;
+      for (int a = 0; a < 4; ++a) sgn += h0[b].Q[a] * Qt[4 * b + a];
+      sgn = sgn < 0 ? -1.0 : 1.0;
+      for (int a = 0; a < 4; ++a) {
+        q[a] = k == nsub ? Qt[4 * b + a] : (1.0 - s) * h0[b].Q[a] + s * sgn * Qt[4 * b + a];
+        qn += q[a] * q[a];
+      }
+      qn = std::sqrt(qn);
+      for (int a = 0; a < 4; ++a) d.Q[a] = d.q0[a] = q[a] / qn;
+      if (k == nsub) {
+        for (int a = 0; a < 3; ++a) {
+          if (V) d.V[a] = V[3 * b + a];
+          if (W) d.W[a] = W[3 * b + a];
+        }
+      }
+      for (int a = 0; a < 3; ++a) {
+        if (d.L[a] < n[a]) d.o[a] = (int)std::floor(d.X[a] + 0.5) - d.L[a] / 2;
+        d.o_prev[a] = d.o[a];
+      }
+      h[b] = d;
+    }
+    // solid cells hand nothing over (a node covered by the last pass still holds its populations,
+    // already given to its neighbours): zero them, then clear the flags under the current tiles
+    launch_zero_solid(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->s);
+    launch_clear_tile_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->flags, ctx->s);
+    CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
+    launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
+    launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
+    // cover events are counted by the flag pass; the boundary list is rebuilt by the refill pass
+    CK(cudaMemsetAsync(&ctx->st->ncover, 0, sizeof(unsigned), ctx->s));
+    CK(cudaMemsetAsync(&ctx->st->nbnd, 0, sizeof(unsigned), ctx->s));
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
+                 ctx->s);
+    launch_clear_stale(ctx->lat, ctx->flags, ctx->s);
+    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                  ctx->s);
+    CK(cudaGetLastError());
+    // the host copy h (and the device memcpy source) must outlive the copy
+    CK(cudaStreamSynchronize(ctx->s));
+  }
   return CBL_OK;
 }
 

@@ -38,6 +38,7 @@ constexpr uint16_t F_COVER = 0x4000;
 constexpr uint16_t F_NEAR = 0x2000;
 constexpr uint16_t F_OWNER = 0x1FFF;
 constexpr int MAX_BODIES = 0x1FFF;
+constexpr uint16_t F_STALE = 0x1FFF;  // owner id of a cell solid before a body move (never a body)
 constexpr int MAXNB = 24;  // neighbour-list capacity per body (tiles that overlap)
 
 // Fluid-mass accumulation slots written by the collision kernel and summed by the body kernel.
@@ -149,6 +150,7 @@ void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags
 
 void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
                              cudaStream_t s);
+void launch_clear_stale(const Lat& lat, uint16_t* flags, cudaStream_t s);
 void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
                       double eta, cudaStream_t s);
 void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st, cudaStream_t s);

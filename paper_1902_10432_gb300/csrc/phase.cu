@@ -743,13 +743,23 @@ __global__ void k_phi_scatter(const BodyDev* bodies, const double* arena, double
   out[n] = 1.0 - S;
 }
 
-// clear the flags of every cell of the bodies' current tiles (before the bodies are moved)
+// before the bodies are moved: every cell of their current tiles loses its flags, except that a
+// solid cell keeps the solid bit under the owner id F_STALE, so the next flag pass does not count
+// it as covered again
 __global__ void k_clear_tile_flags(const BodyDev* bodies, uint16_t* flags, Lat lat) {
   const BodyDev& b = bodies[blockIdx.y];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= b.sz) return;
   const TileCell c = tile_cell(b, t, lat);
-  flags[c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz)] = 0;
+  uint16_t& f = flags[c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz)];
+  f = (f & F_SOLID) ? (uint16_t)(F_SOLID | F_STALE) : (uint16_t)0;
+}
+
+// after the flag pass at the new poses: cells still marked stale lie outside every new tile and
+// are uncovered (their populations were zeroed while they were solid)
+__global__ void k_clear_stale(uint16_t* flags, long long N) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N && flags[n] == (uint16_t)(F_SOLID | F_STALE)) flags[n] = 0;
 }
 
 // ---- launchers ---------------------------------------------------------------------------------
@@ -810,6 +820,9 @@ void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_til
 void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
                              cudaStream_t s) {
   if (nb) k_clear_tile_flags<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, flags, lat);
+}
+void launch_clear_stale(const Lat& lat, uint16_t* flags, cudaStream_t s) {
+  k_clear_stale<<<(unsigned)((lat.N + 255) / 256), 256, 0, s>>>(flags, lat.N);
 }
 
 }  // namespace cbl

@@ -21,6 +21,7 @@ import time
 import numpy as np
 
 SIGMA = 3.583e-2
+LOST_REFILL = 4  # device error bit: a covered node found no fluid neighbour
 
 
 def _mimg(d, dims):
@@ -67,27 +68,32 @@ def generate(ws, equil=1000, every=10, records=160, log=None):
     batch.step(equil)
     batch.sync()
     X, Y, inst = [], [], []
+    stopped = {}  # instance -> record at which it lost mass in a refill or turned non-finite
     t0 = time.perf_counter()
     for rec in range(records):
         batch.step(every)
         batch.sync()
         for k, (s, m) in enumerate(zip(sims, meta)):
+            if k in stopped:
+                continue
             b = s.bodies()
             F, T, _ = s.body_forces()
             x, frame = features(b["X"][0], b["X"][1], m["R"][0], m["R"][1], m["VL"], m["theta"], m["dims"])
+            y = targets(F[0], T[0], frame, m["R"][0])
+            if (s.info()["device_error"] & LOST_REFILL) or not (np.isfinite(x).all() and np.isfinite(y).all()):
+                stopped[k] = rec
+                continue
             X.append(x)
-            Y.append(targets(F[0], T[0], frame, m["R"][0]))
+            Y.append(y)
             inst.append(k)
         if log and rec % 40 == 0:
             log("record %d / %d (%.1f s)" % (rec, records, time.perf_counter() - t0))
     batch.close()
     for s in sims:
         s.close()
-    X, Y, inst = np.array(X), np.array(Y), np.array(inst)
-    ok = np.isfinite(X).all(1) & np.isfinite(Y).all(1)
-    if log and not ok.all():
-        log("dropping %d non-finite samples from instances %s" % (int((~ok).sum()), sorted(set(inst[~ok].tolist()))))
-    return X[ok], Y[ok], inst[ok]
+    if log and stopped:
+        log("instances stopped early (instance: record): %s" % stopped)
+    return np.array(X), np.array(Y), np.array(inst)
 
 
 class Surrogate:
