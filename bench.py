@@ -257,9 +257,10 @@ def bench_surrogate(args, rank, world, local_rank):
     R = [b["radius"] for b in w.bodies]
     dims = (w.nx, w.ny, w.nz)
     theta = w.meta["theta_deg"]
+    # both runs start from the same state with the bridges formed (untimed)
     hyb = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
     workloads.build(hyb, w)
-    hyb.step(5)
+    hyb.step(args.sur_pack_equil)
     torch.cuda.synchronize()
     res = surrogate.hybrid_run(hyb, sur, R, pairs, VL, theta, dims, windows=args.sur_windows, K=args.sur_k,
                                W=args.sur_w, log=log)
@@ -267,7 +268,7 @@ def bench_surrogate(args, rank, world, local_rank):
     del hyb
     plain = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
     workloads.build(plain, w)
-    plain.step(5)
+    plain.step(args.sur_pack_equil)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     plain.step(res["steps"])
@@ -278,9 +279,12 @@ def bench_surrogate(args, rank, world, local_rank):
             "higher_is_better": True, "dtype": "f32 populations, bf16 network", "data": "synthetic",
             "config": {"workload": "packing %d^3, %d spheres R U[12,20], %d bridged pairs, liquid 0.1 of solid"
                                    % (w.nx, len(R), len(pairs)),
-                       "windows": args.sur_windows, "K_lbm": args.sur_k, "W_surrogate": args.sur_w},
+                       "windows": args.sur_windows, "K_lbm": args.sur_k, "W_surrogate": args.sur_w,
+                       "equilibration_steps": args.sur_pack_equil},
             "surrogate_wall_s": res["wall_seconds"], "plain_wall_s": plain_s,
             "force_rel_err_median": res["force_rel_err_median"], "force_rel_err_p95": res["force_rel_err_p95"],
+            "corrected_force_rel_err_median": res.get("corrected_force_rel_err_median"),
+            "corrected_force_rel_err_p95": res.get("corrected_force_rel_err_p95"),
             "training": tr, "samples": int(len(X)), "data_generation_s": gen_s}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -406,6 +410,7 @@ def main():
     ap.add_argument("--sur-windows", type=int, default=4)
     ap.add_argument("--sur-k", type=int, default=20)
     ap.add_argument("--sur-w", type=int, default=200)
+    ap.add_argument("--sur-pack-equil", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

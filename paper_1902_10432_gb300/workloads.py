@@ -130,9 +130,9 @@ def _bridge_mask_radii(nx, ny, nz, centers, radii, volume, around, box=None):
 def packing(seed=0, n_spheres=200, L=512, Rmin=12.0, Rmax=20.0, min_gap=2.0, liquid_fraction=0.1,
             bridge_gap=8.0, theta=45.0, prec="fp32", mpf=1, rho_s=4.0):
     """Many spheres in a periodic cube by random sequential addition (surface gaps >= min_gap), radii
-    U[Rmin, Rmax]; liquid = liquid_fraction of the solid volume, seeded as equal drops at the midpoints
-    of the pairs closer than bridge_gap (surface to surface). Returns the workload and the list of
-    bridged pairs with their drop volumes."""
+    U[Rmin, Rmax]; a drop of liquid_fraction times the pair's solid volume (the two-sphere workload's
+    definition) at the midpoint of every pair closer than bridge_gap (surface to surface). Returns the
+    workload, the bridged pairs and their drop volumes."""
     rng = np.random.default_rng(seed)
     C, R = [], []
     tries = 0
@@ -157,11 +157,10 @@ def packing(seed=0, n_spheres=200, L=512, Rmin=12.0, Rmax=20.0, min_gap=2.0, liq
             d = np.minimum(d, L - d)
             if np.sqrt((d * d).sum()) - R[i] - R[j] < bridge_gap:
                 pairs.append((i, j))
-    VS = sum(4.0 / 3.0 * math.pi * r ** 3 for r in R)
-    VL = liquid_fraction * VS
-    vol = VL / max(1, len(pairs))
+    vols = {(i, j): liquid_fraction * 4.0 / 3.0 * math.pi * (R[i] ** 3 + R[j] ** 3) for (i, j) in pairs}
     mask = np.zeros((L, L, L), np.uint8)
     for (i, j) in pairs:
+        vol = vols[(i, j)]
         d = C[j] - C[i]
         d = (d + L / 2) % L - L / 2
         mid = (C[i] + d / 2) % L
@@ -176,7 +175,7 @@ def packing(seed=0, n_spheres=200, L=512, Rmin=12.0, Rmax=20.0, min_gap=2.0, liq
     params = dict(tau=1.0, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=mpf)
     w = Workload("packing", L, L, L, params, bodies, mask, steps=500,
                  meta=dict(seed=seed, n_spheres=len(C), theta_deg=theta, varrho=varrho, liquid_fraction=liquid_fraction))
-    return w, pairs, {p: vol for p in pairs}
+    return w, pairs, vols
 
 
 def plates48(theta_deg=60.0, prec="fp64", n=48, gap=12, r_bridge=10.0, layers=3, width=32, tau=1.0):

@@ -1,0 +1,58 @@
+"""Seeded input generators: the shapes and invariants their docstrings promise (no GPU, no oracle)."""
+import math
+
+import numpy as np
+
+from paper_1902_10432_gb300 import surrogate, workloads
+
+
+def _min_image(d, L):
+    d = np.asarray(d, float)
+    return (d + L / 2.0) % L - L / 2.0
+
+
+def test_packing_gaps_pairs_and_drop_volumes():
+    w, pairs, vols = workloads.packing(seed=3, n_spheres=12, L=64, Rmin=5.0, Rmax=7.0, bridge_gap=6.0)
+    C = [np.array(b["center"]) for b in w.bodies]
+    R = [b["radius"] for b in w.bodies]
+    assert len(C) == 12 and all(5.0 <= r <= 7.0 for r in R)
+    for i in range(len(C)):
+        for j in range(i + 1, len(C)):
+            gap = np.linalg.norm(_min_image(C[j] - C[i], 64)) - R[i] - R[j]
+            assert gap >= 2.0 - 1e-9  # random sequential addition keeps the minimum surface gap
+            assert ((i, j) in pairs) == (gap < 6.0)
+    for (i, j), v in vols.items():
+        assert math.isclose(v, 0.1 * 4.0 / 3.0 * math.pi * (R[i] ** 3 + R[j] ** 3))
+    # liquid cells are outside every sphere; each drop holds its volume unless drops overlap
+    z, y, x = np.nonzero(w.mask)
+    P = np.stack([x, y, z], 1).astype(float)
+    for c, r in zip(C, R):
+        assert (np.linalg.norm(_min_image(P - c, 64), axis=1) > r - 1e-9).all()
+    assert w.mask.sum() <= sum(round(v) for v in vols.values())
+    if len(pairs) == 1:
+        assert w.mask.sum() == round(next(iter(vols.values())))
+
+
+def test_batch64_radii_fit_and_gap():
+    for w in workloads.batch64(seed=1, n=16):
+        L = [w.nx, w.ny, w.nz]
+        ax = int(np.argmax(L))
+        c0, c1 = (np.array(b["center"]) for b in w.bodies)
+        r0, r1 = (b["radius"] for b in w.bodies)
+        assert math.isclose(abs(c1[ax] - c0[ax]) - r0 - r1, 4.0)
+        others = [L[a] for a in range(3) if a != ax]
+        assert max(r0, r1) <= (min(others) - 8) / 2.0 + 1e-12
+        assert 30.0 <= w.meta["theta_deg"] <= 90.0
+
+
+def test_pair_frame_and_targets_rotate_with_the_pair():
+    # the frame is orthonormal, e_z points from i to j (minimum image), and the targets are the force
+    # and torque in that frame, scaled by sigma R and sigma R^2
+    frame, r = surrogate.pair_frame((60.0, 3.0, 5.0), (2.0, 3.0, 5.0), (64, 64, 64))
+    assert math.isclose(r, 6.0)
+    assert np.allclose(frame @ frame.T, np.eye(3))
+    assert np.allclose(frame[2], [1.0, 0.0, 0.0])
+    F, T = np.array([1.0, 2.0, 3.0]), np.array([0.5, -1.0, 0.25])
+    y = surrogate.targets(F, T, frame, 4.0)
+    assert np.allclose(frame.T @ y[:3] * surrogate.SIGMA * 4.0, F)
+    assert np.allclose(frame.T @ y[3:] * surrogate.SIGMA * 16.0, T)
