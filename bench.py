@@ -249,11 +249,12 @@ def bench_surrogate(args, rank, world, local_rank):
 
     log = lambda m: print(m, file=sys.stderr, flush=True)
     t0 = time.perf_counter()
-    ws = workloads.batch64(seed=0, prec="fp32")
-    X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, every=10, records=args.sur_records, log=log)
+    ws = workloads.batch64(seed=0, prec="fp32", gap=(2.5, 3.5), fixed=True)
+    X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, every=10, records=args.sur_records,
+                                    pull=args.sur_pull, log=log)
     gen_s = time.perf_counter() - t0
     sur, tr = surrogate.train(X, Y, inst, iters=args.sur_iters, log=log)
-    w, pairs, VL = workloads.packing(seed=0, L=args.sur_box)
+    w, pairs, VL = workloads.packing(seed=0, L=args.sur_box, rho_s=args.sur_rho_s)
     R = [b["radius"] for b in w.bodies]
     dims = (w.nx, w.ny, w.nz)
     theta = w.meta["theta_deg"]
@@ -280,7 +281,9 @@ def bench_surrogate(args, rank, world, local_rank):
             "config": {"workload": "packing %d^3, %d spheres R U[12,20], %d bridged pairs, liquid 0.1 of solid"
                                    % (w.nx, len(R), len(pairs)),
                        "windows": args.sur_windows, "K_lbm": args.sur_k, "W_surrogate": args.sur_w,
-                       "equilibration_steps": args.sur_pack_equil},
+                       "equilibration_steps": args.sur_pack_equil, "sphere_mass_density": args.sur_rho_s,
+                       "training": "64 two-sphere instances, fixed spheres drawn apart at %g cells/step, "
+                                   "%d records of both bodies" % (args.sur_pull, args.sur_records)},
             "surrogate_wall_s": res["wall_seconds"], "plain_wall_s": plain_s,
             "force_rel_err_median": res["force_rel_err_median"], "force_rel_err_p95": res["force_rel_err_p95"],
             "corrected_force_rel_err_median": res.get("corrected_force_rel_err_median"),
@@ -403,8 +406,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
     ap.add_argument("--workload", default="spheres2",
                     choices=["spheres2", "plates48", "tetra4", "batch64", "surrogate"])
-    ap.add_argument("--sur-equil", type=int, default=1000)
-    ap.add_argument("--sur-records", type=int, default=160)
+    ap.add_argument("--sur-equil", type=int, default=600)
+    ap.add_argument("--sur-records", type=int, default=80)
+    ap.add_argument("--sur-pull", type=float, default=0.004)
+    ap.add_argument("--sur-rho-s", type=float, default=200.0)
     ap.add_argument("--sur-iters", type=int, default=3000)
     ap.add_argument("--sur-box", type=int, default=512)
     ap.add_argument("--sur-windows", type=int, default=4)

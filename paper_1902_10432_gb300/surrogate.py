@@ -6,7 +6,8 @@ between full evaluations, and the plain method is both its fallback and the judg
 * Features of a pair (i, j) in the frame of i (e_z from i to j): gap / R_i, liquid volume / R_i^3,
   contact angle (rad), R_i / R_j. Targets: force and torque on i in that frame, divided by sigma R_i
   and sigma R_i^2 (sigma = 3.583e-2, the paper's liquid-vapour tension, Sec. 4.1).
-* Training data come from batched two-sphere runs of the plain method (the 64-instance workload).
+* Training data come from batched two-sphere runs of the plain method (the 64-instance workload),
+  the spheres held fixed and drawn apart slowly between records: quasi-static force-gap sweeps.
 * The hybrid advance alternates a K-step lattice-Boltzmann burst (true forces; the per-body residual
   becomes a bias) with a W-step window in which the bodies move under the network's pair forces plus
   the bias while the fluid is frozen; the bodies' phase fields are then rebuilt at the new poses.
@@ -50,8 +51,18 @@ def targets(F, T, frame, Ri):
     return np.concatenate([frame @ np.asarray(F, float) / (SIGMA * Ri), frame @ np.asarray(T, float) / (SIGMA * Ri * Ri)])
 
 
-def generate(ws, equil=1000, every=10, records=160, log=None):
-    """Run the two-sphere instances `ws` as one batch and record (features, targets, instance) of body 0."""
+def _pair_axis(Xi, Xj, dims):
+    d = _mimg(np.asarray(Xj, float) - np.asarray(Xi, float), dims)
+    return d / np.linalg.norm(d)
+
+
+def generate(ws, equil=600, every=10, records=80, pull=0.004, min_gap=1.5, log=None):
+    """Run the two-sphere instances `ws` as one batch and record (features, targets, instance) of both
+    bodies. With pull > 0 the (fixed) spheres are drawn apart between records so that the surface gap
+    grows by `pull` cells per step: a quasi-static sweep of the bridge force over the gap. Each
+    recorded force is the mean of two consecutive steps (the lattice carries a period-2 mode). An
+    instance stops recording once it loses mass in a refill, turns non-finite, or its gap falls
+    below min_gap."""
     from paper_1902_10432_gb300 import cbl, workloads
 
     sims = []
@@ -68,25 +79,43 @@ def generate(ws, equil=1000, every=10, records=160, log=None):
     batch.step(equil)
     batch.sync()
     X, Y, inst = [], [], []
-    stopped = {}  # instance -> record at which it lost mass in a refill or turned non-finite
+    stopped = {}  # instance -> record at which it stopped
     t0 = time.perf_counter()
     for rec in range(records):
-        batch.step(every)
+        if pull > 0 and rec > 0:
+            for k, (s, m) in enumerate(zip(sims, meta)):
+                if k in stopped:
+                    continue
+                P = s.bodies()["X"]
+                e = _pair_axis(P[0], P[1], m["dims"])
+                h = 0.5 * pull * every
+                s.move_bodies(np.stack([P[0] - h * e, P[1] + h * e]))
+        batch.step(every - 1)
+        batch.sync()
+        F1 = [None if k in stopped else s.body_forces()[:2] for k, s in enumerate(sims)]
+        batch.step(1)
         batch.sync()
         for k, (s, m) in enumerate(zip(sims, meta)):
             if k in stopped:
                 continue
             b = s.bodies()
-            F, T, _ = s.body_forces()
-            x, frame = features(b["X"][0], b["X"][1], m["R"][0], m["R"][1], m["VL"], m["theta"], m["dims"])
-            y = targets(F[0], T[0], frame, m["R"][0])
-            if (s.info()["device_error"] & LOST_REFILL) or not (np.isfinite(x).all() and np.isfinite(y).all()):
+            F2, T2, _ = s.body_forces()
+            F = 0.5 * (F1[k][0] + F2)
+            T = 0.5 * (F1[k][1] + T2)
+            rows = []
+            for i, j in ((0, 1), (1, 0)):
+                x, frame = features(b["X"][i], b["X"][j], m["R"][i], m["R"][j], m["VL"], m["theta"], m["dims"])
+                rows.append((x, targets(F[i], T[i], frame, m["R"][i])))
+            bad = (s.info()["device_error"] & LOST_REFILL) or not all(
+                np.isfinite(x).all() and np.isfinite(y).all() for x, y in rows)
+            if bad or rows[0][0][0] * m["R"][0] < min_gap:
                 stopped[k] = rec
                 continue
-            X.append(x)
-            Y.append(y)
-            inst.append(k)
-        if log and rec % 40 == 0:
+            for x, y in rows:
+                X.append(x)
+                Y.append(y)
+                inst.append(k)
+        if log and rec % 20 == 0:
             log("record %d / %d (%.1f s)" % (rec, records, time.perf_counter() - t0))
     batch.close()
     for s in sims:
@@ -186,8 +215,11 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=20, W=200, log=
     bias = None
     t0 = time.perf_counter()
     for win in range(windows):
-        sim.step(K)
+        sim.step(K - 1)
+        F_a, _, _ = sim.body_forces()
+        sim.step(1)
         F_lbm, _, _ = sim.body_forces()
+        F_lbm = 0.5 * (F_a + F_lbm)  # the lattice carries a period-2 mode
         b = sim.bodies()
         X, V = b["X"].copy(), b["V"].copy()
         F_mlp = pair_forces(sur, X, R, pairs, VL, theta, dims)

@@ -230,39 +230,43 @@ def tetra4(seed=0, prec="fp32", n=256, R=24.0, f=0.05, theta=60.0, surface_gap=8
                     meta=dict(seed=seed, liquid_fraction_of_solid=f, theta_deg=theta, varrho=varrho))
 
 
-def batch64(seed=0, n=64, prec="fp32", mpf=1, rho_s=4.0, gap=4.0):
+def batch64(seed=0, n=64, prec="fp32", mpf=1, rho_s=4.0, gap=4.0, fixed=False):
     """Independent two-sphere bridges of uneven box size, liquid fraction and contact angle: box edges
     U{64..128} per axis, radius U[10, 24] clamped to fit the box (pair on the longest axis, surface gap
-    4), liquid fraction U[0.01, 0.2] of the solid volume, contact angle U[30, 90] deg, all from one
-    seed."""
+    `gap`, or U[gap[0], gap[1]] per instance for a pair), liquid fraction U[0.01, 0.2] of the solid
+    volume, contact angle U[30, 90] deg, all from one seed. `fixed` holds the spheres in place."""
     rng = np.random.default_rng(seed)
     out = []
+    g_fixed = not isinstance(gap, (tuple, list))
     for k in range(n):
         L = [int(v) for v in rng.integers(64, 129, size=3)]
         Rs = [float(v) for v in rng.uniform(10.0, 24.0, size=2)]  # each sphere its own radius
         f = float(rng.uniform(0.01, 0.2))
         theta = float(rng.uniform(30.0, 90.0))
+        g = float(gap) if g_fixed else float(rng.uniform(gap[0], gap[1]))
         ax = int(np.argmax(L))
         others = [L[a] for a in range(3) if a != ax]
-        cap = min((L[ax] - 4 - 2 * 4) / 4.0, (min(others) - 8) / 2.0)
+        cap = min((L[ax] - g - 2 * 4) / 4.0, (min(others) - 8) / 2.0)
         Rs = [min(r, cap) for r in Rs]
         varrho = varrho_for_angle(theta)
         c = [v / 2.0 for v in L]
         # surface gap `gap` centred on the box centre along the longest axis
         centers = []
         p0 = list(c)
-        p0[ax] -= gap / 2.0 + Rs[0]
+        p0[ax] -= g / 2.0 + Rs[0]
         p1 = list(c)
-        p1[ax] += gap / 2.0 + Rs[1]
+        p1[ax] += g / 2.0 + Rs[1]
         centers = [tuple(p0), tuple(p1)]
         VS = sum(4.0 / 3.0 * math.pi * r ** 3 for r in Rs)
         mask = _bridge_mask_radii(L[0], L[1], L[2], centers, Rs, f * VS, tuple(c))
         R = Rs[0]
         bodies = [_sphere_body(p, r, rho_s, varrho) for p, r in zip(centers, Rs)]
+        for b in bodies:
+            b["fixed"] = bool(fixed)
         params = dict(tau=1.0, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=mpf)
         out.append(Workload("batch%02d" % k, L[0], L[1], L[2], params, bodies, mask, steps=500,
                             meta=dict(seed=seed, index=k, R=R, liquid_fraction_of_solid=f, theta_deg=theta,
-                                      varrho=varrho)))
+                                      varrho=varrho, gap=g, axis=ax)))
     return out
 
 
