@@ -250,8 +250,8 @@ def bench_surrogate(args, rank, world, local_rank):
     log = lambda m: print(m, file=sys.stderr, flush=True)
     t0 = time.perf_counter()
     ws = workloads.batch64(seed=0, prec="fp32", gap=(2.5, 3.5), fixed=True)
-    X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, every=10, records=args.sur_records,
-                                    pull=args.sur_pull, log=log)
+    X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, hold=args.sur_hold, avg=args.sur_hold // 2,
+                                    records=args.sur_records, dgap=args.sur_dgap, log=log)
     gen_s = time.perf_counter() - t0
     sur, tr = surrogate.train(X, Y, inst, iters=args.sur_iters, log=log)
     w, pairs, VL = workloads.packing(seed=0, L=args.sur_box, rho_s=args.sur_rho_s)
@@ -282,12 +282,16 @@ def bench_surrogate(args, rank, world, local_rank):
                                    % (w.nx, len(R), len(pairs)),
                        "windows": args.sur_windows, "K_lbm": args.sur_k, "W_surrogate": args.sur_w,
                        "equilibration_steps": args.sur_pack_equil, "sphere_mass_density": args.sur_rho_s,
-                       "training": "64 two-sphere instances, fixed spheres drawn apart at %g cells/step, "
-                                   "%d records of both bodies" % (args.sur_pull, args.sur_records)},
+                       "training": "64 two-sphere instances, fixed spheres drawn apart by %g cells of gap "
+                                   "per record, %d-step holds, force mean over the last half, %d records of "
+                                   "both bodies" % (args.sur_dgap, args.sur_hold, args.sur_records)},
             "surrogate_wall_s": res["wall_seconds"], "plain_wall_s": plain_s,
             "force_rel_err_median": res["force_rel_err_median"], "force_rel_err_p95": res["force_rel_err_p95"],
             "corrected_force_rel_err_median": res.get("corrected_force_rel_err_median"),
             "corrected_force_rel_err_p95": res.get("corrected_force_rel_err_p95"),
+            "force_rel_err_bodies": res["n_rel"],
+            "force_err_over_2piRsigma_median": res["force_err_over_2piRsigma_median"],
+            "force_err_over_2piRsigma_p95": res["force_err_over_2piRsigma_p95"],
             "training": tr, "samples": int(len(X)), "data_generation_s": gen_s}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -406,14 +410,15 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
     ap.add_argument("--workload", default="spheres2",
                     choices=["spheres2", "plates48", "tetra4", "batch64", "surrogate"])
-    ap.add_argument("--sur-equil", type=int, default=600)
+    ap.add_argument("--sur-equil", type=int, default=1500)
     ap.add_argument("--sur-records", type=int, default=80)
-    ap.add_argument("--sur-pull", type=float, default=0.004)
+    ap.add_argument("--sur-hold", type=int, default=150)
+    ap.add_argument("--sur-dgap", type=float, default=0.05)
     ap.add_argument("--sur-rho-s", type=float, default=200.0)
     ap.add_argument("--sur-iters", type=int, default=3000)
     ap.add_argument("--sur-box", type=int, default=512)
     ap.add_argument("--sur-windows", type=int, default=4)
-    ap.add_argument("--sur-k", type=int, default=20)
+    ap.add_argument("--sur-k", type=int, default=100)
     ap.add_argument("--sur-w", type=int, default=200)
     ap.add_argument("--sur-pack-equil", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
