@@ -253,6 +253,10 @@ def bench_surrogate(args, rank, world, local_rank):
     X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, hold=args.sur_hold, avg=args.sur_hold // 2,
                                     records=args.sur_records, dgap=args.sur_dgap, log=log)
     gen_s = time.perf_counter() - t0
+    if args.sur_save:
+        import numpy as np
+
+        np.savez(args.sur_save, X=X, Y=Y, inst=inst)
     sur, tr = surrogate.train(X, Y, inst, iters=args.sur_iters, log=log)
     w, pairs, VL = workloads.packing(seed=0, L=args.sur_box, rho_s=args.sur_rho_s)
     R = [b["radius"] for b in w.bodies]
@@ -421,6 +425,7 @@ def main():
     ap.add_argument("--sur-k", type=int, default=100)
     ap.add_argument("--sur-w", type=int, default=200)
     ap.add_argument("--sur-pack-equil", type=int, default=1000)
+    ap.add_argument("--sur-save", default="", help="write the training samples to this .npz")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -3,9 +3,12 @@
 Not part of the paper's method: the network stands in for the lattice-Boltzmann force evaluation
 between full evaluations, and the plain method is both its fallback and the judge of its error.
 
-* Features of a pair (i, j) in the frame of i (e_z from i to j): gap / R_i, liquid volume / R_i^3,
-  contact angle (rad), R_i / R_j. Targets: force and torque on i in that frame, divided by sigma R_i
-  and sigma R_i^2 (sigma = 3.583e-2, the paper's liquid-vapour tension, Sec. 4.1).
+* Features of a pair (i, j), with R* = 2 R_i R_j / (R_i + R_j) and bridge volume V_L: the scaled gap
+  s sqrt(R* / V_L) of a pendular bridge, cos(contact angle), R_i / R_j and V_L / R*^3. Targets: force
+  and torque on i in the frame of i (e_z from i to j) over the capillary scales 2 pi R* sigma and
+  2 pi R*^2 sigma (sigma = 3.583e-2, the liquid-vapour tension). In these variables the axial force of
+  a pendular bridge is close to one curve, cos(theta) times a decreasing function of the scaled gap,
+  so a few dozen force-gap sweeps cover it.
 * Training data come from batched two-sphere runs of the plain method (the 64-instance workload),
   the spheres held fixed and drawn apart step by step, the force averaged after each step has
   relaxed: quasi-static force-gap sweeps. (A node that turns fluid starts empty, Sec. 3.2.2, so a
@@ -44,13 +47,24 @@ def pair_frame(Xi, Xj, dims):
     return np.stack([ex, ey, ez]), r
 
 
+def rstar(Ri, Rj):
+    return 2.0 * Ri * Rj / (Ri + Rj)
+
+
+def force_scale(Ri, Rj):
+    return 2.0 * math.pi * rstar(Ri, Rj) * SIGMA
+
+
 def features(Xi, Xj, Ri, Rj, VL, theta_deg, dims):
     frame, r = pair_frame(Xi, Xj, dims)
-    return np.array([(r - Ri - Rj) / Ri, VL / Ri ** 3, math.radians(theta_deg), Ri / Rj]), frame
+    Rs = rstar(Ri, Rj)
+    return np.array([(r - Ri - Rj) * math.sqrt(Rs / VL), math.cos(math.radians(theta_deg)), Ri / Rj,
+                     VL / Rs ** 3]), frame
 
 
-def targets(F, T, frame, Ri):
-    return np.concatenate([frame @ np.asarray(F, float) / (SIGMA * Ri), frame @ np.asarray(T, float) / (SIGMA * Ri * Ri)])
+def targets(F, T, frame, Ri, Rj):
+    s = force_scale(Ri, Rj)
+    return np.concatenate([frame @ np.asarray(F, float) / s, frame @ np.asarray(T, float) / (s * rstar(Ri, Rj))])
 
 
 def _pair_axis(Xi, Xj, dims):
@@ -106,10 +120,11 @@ def generate(ws, equil=1500, hold=150, avg=75, records=80, dgap=0.05, min_gap=1.
             rows = []
             for i, j in ((0, 1), (1, 0)):
                 x, frame = features(b["X"][i], b["X"][j], m["R"][i], m["R"][j], m["VL"], m["theta"], m["dims"])
-                rows.append((x, targets(Fs[k][i], Ts[k][i], frame, m["R"][i])))
+                rows.append((x, targets(Fs[k][i], Ts[k][i], frame, m["R"][i], m["R"][j])))
             bad = (s.info()["device_error"] & LOST_REFILL) or not all(
                 np.isfinite(x).all() and np.isfinite(y).all() for x, y in rows)
-            if bad or rows[0][0][0] * m["R"][0] < min_gap:
+            gap = pair_frame(b["X"][0], b["X"][1], m["dims"])[1] - m["R"][0] - m["R"][1]
+            if bad or gap < min_gap:
                 stopped[k] = rec
                 continue
             for x, y in rows:
@@ -171,17 +186,17 @@ def train(X, Y, inst, iters=3000, lr=3e-3, holdout=0.1, seed=0, log=None):
     net.sync()
     train_s = time.perf_counter() - t0
     sur = Surrogate(net, xm, xs, ym, ys, X[~te].min(0), X[~te].max(0))
-    # held-out force error; targets are F / (sigma R), so the capillary scale 2 pi R sigma is 2 pi
+    # held-out force error; the targets are already in units of 2 pi R* sigma
     pred = sur.predict(X[te])
     d = np.linalg.norm(pred[:, :3] - Y[te][:, :3], axis=1)
     n = np.linalg.norm(Y[te][:, :3], axis=1)
-    big = n >= 0.1 * 2.0 * math.pi
+    big = n >= 0.1
     q = lambda v, p: float(np.percentile(v, p)) if len(v) else None
     return sur, dict(train_seconds=train_s, n_train=int((~te).sum()), n_test=int(te.sum()),
                      heldout_force_rel_err_median=q(d[big] / n[big], 50),
                      heldout_force_rel_err_p95=q(d[big] / n[big], 95), heldout_rel_samples=int(big.sum()),
-                     heldout_force_err_over_2piRsigma_median=q(d / (2.0 * math.pi), 50),
-                     heldout_force_err_over_2piRsigma_p95=q(d / (2.0 * math.pi), 95), final_loss=float(loss))
+                     heldout_force_err_over_2piRsigma_median=q(d, 50),
+                     heldout_force_err_over_2piRsigma_p95=q(d, 95), final_loss=float(loss))
 
 
 def _glorot(seed, sizes=(4, 64, 64, 64, 6)):
@@ -200,16 +215,17 @@ def pair_forces(sur, X, R, pairs, VL, theta, dims):
     F = np.zeros_like(X)
     if not pairs:
         return F
-    feats, frames, idx = [], [], []
+    feats, frames, idx, idx_b = [], [], [], []
     for (i, j) in pairs:
         for a, b in ((i, j), (j, i)):
             f, fr = features(X[a], X[b], R[a], R[b], VL[(i, j)], theta, dims)
             feats.append(f)
             frames.append(fr)
             idx.append(a)
+            idx_b.append(b)
     y = sur.predict(np.array(feats))
     for k, a in enumerate(idx):
-        F[a] += frames[k].T @ (y[k, :3] * SIGMA * R[a])
+        F[a] += frames[k].T @ (y[k, :3] * force_scale(R[a], R[idx_b[k]]))
     return F
 
 

@@ -47,12 +47,15 @@ def test_batch64_radii_fit_and_gap():
 
 def test_pair_frame_and_targets_rotate_with_the_pair():
     # the frame is orthonormal, e_z points from i to j (minimum image), and the targets are the force
-    # and torque in that frame, scaled by sigma R and sigma R^2
+    # and torque in that frame over 2 pi R* sigma and 2 pi R*^2 sigma, R* = 2 Ri Rj / (Ri + Rj)
     frame, r = surrogate.pair_frame((60.0, 3.0, 5.0), (2.0, 3.0, 5.0), (64, 64, 64))
     assert math.isclose(r, 6.0)
     assert np.allclose(frame @ frame.T, np.eye(3))
     assert np.allclose(frame[2], [1.0, 0.0, 0.0])
     F, T = np.array([1.0, 2.0, 3.0]), np.array([0.5, -1.0, 0.25])
-    y = surrogate.targets(F, T, frame, 4.0)
-    assert np.allclose(frame.T @ y[:3] * surrogate.SIGMA * 4.0, F)
-    assert np.allclose(frame.T @ y[3:] * surrogate.SIGMA * 16.0, T)
+    y = surrogate.targets(F, T, frame, 2.0, 6.0)
+    s = 2.0 * math.pi * 3.0 * surrogate.SIGMA
+    assert np.allclose(frame.T @ y[:3] * s, F)
+    assert np.allclose(frame.T @ y[3:] * s * 3.0, T)
+    x, _ = surrogate.features((0.0, 0.0, 0.0), (0.0, 0.0, 10.0), 2.0, 6.0, 12.0, 60.0, (64, 64, 64))
+    assert np.allclose(x, [2.0 * math.sqrt(3.0 / 12.0), 0.5, 1.0 / 3.0, 12.0 / 27.0])
