@@ -28,6 +28,7 @@ import numpy as np
 
 SIGMA = 3.583e-2
 LOST_REFILL = 4  # device error bit: a covered node found no fluid neighbour
+RHO_MID = 0.5 * (1.88844 + 0.11942)  # halfway between the coexisting liquid and vapour densities
 
 
 def _mimg(d, dims):
@@ -67,6 +68,32 @@ def targets(F, T, frame, Ri, Rj):
     return np.concatenate([frame @ np.asarray(F, float) / s, frame @ np.asarray(T, float) / (s * rstar(Ri, Rj))])
 
 
+def bridge_state(rho, Xi, Xj, Ri, Rj, dims):
+    """Liquid volume of the bridge between spheres i and j and whether it still spans the gap.
+
+    rho: the density field as a device tensor [nz][ny][nx] (solid cells read 0). The volume counts the
+    cells denser than RHO_MID in the cube of half-width max(Ri, Rj) about the middle of the gap; the
+    bridge is intact if the mean density of the 2x2x2 cells about that point exceeds RHO_MID. A bridge
+    evaporates or condenses towards the vapour's saturation (Laplace pressure), so its volume is
+    measured, not taken from the initial drop."""
+    import torch
+
+    frame, r = pair_frame(Xi, Xj, dims)
+    e = frame[2]
+    mid = np.asarray(Xi, float) + e * (Ri + 0.5 * (r - Ri - Rj))
+    h = int(math.ceil(max(Ri, Rj)))
+    nx, ny, nz = dims
+    dev = rho.device
+    ax = lambda c, n, w: torch.remainder(torch.arange(-w, w + 1, device=dev) + int(math.floor(c)), n)
+    ix, iy, iz = ax(mid[0], nx, h), ax(mid[1], ny, h), ax(mid[2], nz, h)
+    box = rho.index_select(0, iz).index_select(1, iy).index_select(2, ix)
+    vol = float((box > RHO_MID).sum())
+    cx, cy, cz = ax(mid[0], nx, 0), ax(mid[1], ny, 0), ax(mid[2], nz, 0)
+    core = rho.index_select(0, torch.cat([cz, (cz + 1) % nz])).index_select(1, torch.cat([cy, (cy + 1) % ny]))
+    core = core.index_select(2, torch.cat([cx, (cx + 1) % nx]))
+    return vol, float(core.mean()) > RHO_MID
+
+
 def _pair_axis(Xi, Xj, dims):
     d = _mimg(np.asarray(Xj, float) - np.asarray(Xi, float), dims)
     return d / np.linalg.norm(d)
@@ -76,8 +103,9 @@ def generate(ws, equil=1500, hold=150, avg=75, records=80, dgap=0.05, min_gap=1.
     """Run the two-sphere instances `ws` (spheres held fixed) as one batch and record (features,
     targets, instance) of both bodies, step and hold: before each record but the first the spheres are
     drawn apart along their axis by dgap cells of surface gap (cbl_move_bodies), the fluid relaxes for
-    hold - avg steps, and the recorded force and torque are the means over the last avg steps. An
-    instance stops recording once it loses mass in a refill, turns non-finite, or its gap falls below
+    hold - avg steps, and the recorded force and torque are the means over the last avg steps. The
+    liquid-volume feature is the bridge's measured volume (bridge_state). An instance stops recording
+    once its bridge ruptures, it loses mass in a refill, turns non-finite, or its gap falls below
     min_gap."""
     from paper_1902_10432_gb300 import cbl, workloads
 
@@ -91,11 +119,14 @@ def generate(ws, equil=1500, hold=150, avg=75, records=80, dgap=0.05, min_gap=1.
         VS = sum(4.0 / 3.0 * math.pi * r ** 3 for r in R)
         meta.append(dict(R=R, VL=w.meta["liquid_fraction_of_solid"] * VS, theta=w.meta["theta_deg"],
                          dims=(w.nx, w.ny, w.nz)))
+    import torch
+
+    rho = [torch.empty((w.nz, w.ny, w.nx), dtype=torch.float64, device="cuda") for w in ws]
     batch = cbl.Batch(sims)
     batch.step(equil)
     batch.sync()
     X, Y, inst = [], [], []
-    stopped = {}  # instance -> record at which it stopped
+    stopped = {}  # instance -> record at which it stopped (rupture, instability or contact)
     t0 = time.perf_counter()
     for rec in range(records):
         live = [k for k in range(len(sims)) if k not in stopped]
@@ -117,14 +148,17 @@ def generate(ws, equil=1500, hold=150, avg=75, records=80, dgap=0.05, min_gap=1.
         for k in live:
             s, m = sims[k], meta[k]
             b = s.bodies()
+            s.fields_device(rho[k])
+            VL, intact = bridge_state(rho[k], b["X"][0], b["X"][1], m["R"][0], m["R"][1], m["dims"])
             rows = []
             for i, j in ((0, 1), (1, 0)):
-                x, frame = features(b["X"][i], b["X"][j], m["R"][i], m["R"][j], m["VL"], m["theta"], m["dims"])
+                x, frame = features(b["X"][i], b["X"][j], m["R"][i], m["R"][j], max(VL, 1.0), m["theta"],
+                                    m["dims"])
                 rows.append((x, targets(Fs[k][i], Ts[k][i], frame, m["R"][i], m["R"][j])))
             bad = (s.info()["device_error"] & LOST_REFILL) or not all(
                 np.isfinite(x).all() and np.isfinite(y).all() for x, y in rows)
             gap = pair_frame(b["X"][0], b["X"][1], m["dims"])[1] - m["R"][0] - m["R"][1]
-            if bad or gap < min_gap:
+            if bad or not intact or gap < min_gap:
                 stopped[k] = rec
                 continue
             for x, y in rows:
@@ -211,7 +245,8 @@ def _glorot(seed, sizes=(4, 64, 64, 64, 6)):
 
 
 def pair_forces(sur, X, R, pairs, VL, theta, dims):
-    """Network forces on every body (world frame) from the bridged pairs."""
+    """Network forces on every body (world frame) from the bridged pairs; VL maps a pair to its
+    measured bridge volume (pairs whose bridge has ruptured are left out by the caller)."""
     F = np.zeros_like(X)
     if not pairs:
         return F
@@ -238,6 +273,9 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
     Errors, over the bodies with a bridge: relative |F_MLP - F_LBM| / |F_LBM| where |F_LBM| is at least
     a tenth of the capillary force scale 2 pi R sigma (smaller forces make the ratio meaningless), and
     |F_MLP - F_LBM| / (2 pi R sigma) for all of them. "corrected" adds the bias of the window before."""
+    import torch
+
+    rho = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float64, device="cuda")
     b = sim.bodies()
     M = b["M"]
     bridged = np.array(sorted({i for p in pairs for i in p}), int)
@@ -258,7 +296,14 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
         F_lbm = burst()
         b = sim.bodies()
         X, V = b["X"].copy(), b["V"].copy()
-        F_mlp = pair_forces(sur, X, R, pairs, VL, theta, dims)
+        sim.fields_device(rho)
+        VLm, live = {}, []
+        for (i, j) in pairs:
+            v, ok = bridge_state(rho, X[i], X[j], R[i], R[j], dims)
+            if ok:
+                VLm[(i, j)] = v
+                live.append((i, j))
+        F_mlp = pair_forces(sur, X, R, live, VLm, theta, dims)
         d = np.linalg.norm(F_mlp[bridged] - F_lbm[bridged], axis=1)
         n = np.linalg.norm(F_lbm[bridged], axis=1)
         big = n >= 0.1 * scale
@@ -269,13 +314,14 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
             corr.append(dc[big] / n[big])
         bias = F_lbm - F_mlp
         for _ in range(W):
-            F = pair_forces(sur, X, R, pairs, VL, theta, dims) + bias
+            F = pair_forces(sur, X, R, live, VLm, theta, dims) + bias
             V += F / M[:, None]
             X = (X + V) % np.asarray(dims, float)
         sim.move_bodies(X, V=V)
         if log:
-            log("window %d: median relative force error %.3f over %d bodies" % (
-                win, float(np.median(errs[-1])) if len(errs[-1]) else float("nan"), len(errs[-1])))
+            log("window %d: %d of %d bridges intact; median relative force error %.3f over %d bodies" % (
+                win, len(live), len(pairs), float(np.median(errs[-1])) if len(errs[-1]) else float("nan"),
+                len(errs[-1])))
     burst()
     wall = time.perf_counter() - t0
     e, a = np.concatenate(errs), np.concatenate(absd)

@@ -59,3 +59,23 @@ def test_pair_frame_and_targets_rotate_with_the_pair():
     assert np.allclose(frame.T @ y[3:] * s * 3.0, T)
     x, _ = surrogate.features((0.0, 0.0, 0.0), (0.0, 0.0, 10.0), 2.0, 6.0, 12.0, 60.0, (64, 64, 64))
     assert np.allclose(x, [2.0 * math.sqrt(3.0 / 12.0), 0.5, 1.0 / 3.0, 12.0 / 27.0])
+
+
+def test_bridge_state_counts_liquid_and_detects_rupture():
+    import torch
+
+    # two spheres on the x axis of a periodic 40^3 box (centres across the boundary), surface gap 4,
+    # a liquid cylinder of radius 3 spanning the gap
+    n, R = 40, 6.0
+    Xi, Xj = np.array([35.0, 20.0, 20.0]), np.array([51.0 - 40.0, 20.0, 20.0])
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    rho = np.full((n, n, n), 0.12)
+    xs = (x - 35.0 + 20.0) % 40.0 - 20.0  # x relative to sphere i, minimum image
+    cyl = (xs >= 6.0) & (xs <= 10.0) & ((y - 20.0) ** 2 + (z - 20.0) ** 2 <= 9.0)
+    rho[cyl] = 1.9
+    t = torch.tensor(rho)
+    vol, intact = surrogate.bridge_state(t, Xi, Xj, R, R, (n, n, n))
+    assert intact and vol == cyl.sum()
+    rho[cyl & (xs >= 7.0) & (xs <= 9.0)] = 0.12  # cut the neck about the gap's middle
+    vol2, intact2 = surrogate.bridge_state(torch.tensor(rho), Xi, Xj, R, R, (n, n, n))
+    assert not intact2 and vol2 < vol
