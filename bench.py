@@ -249,7 +249,9 @@ def bench_surrogate(args, rank, world, local_rank):
 
     log = lambda m: print(m, file=sys.stderr, flush=True)
     t0 = time.perf_counter()
-    ws = workloads.batch64(seed=0, prec="fp32", gap=(2.5, 3.5), fixed=True)
+    ws = []
+    for sd in range(args.sur_seeds):
+        ws += workloads.batch64(seed=sd, prec="fp32", gap=(3.0, 7.0), fixed=True)
     X, Y, inst = surrogate.generate(ws, equil=args.sur_equil, hold=args.sur_hold, avg=args.sur_hold // 2,
                                     records=args.sur_records, dgap=args.sur_dgap, log=log)
     gen_s = time.perf_counter() - t0
@@ -286,9 +288,10 @@ def bench_surrogate(args, rank, world, local_rank):
                                    % (w.nx, len(R), len(pairs)),
                        "windows": args.sur_windows, "K_lbm": args.sur_k, "W_surrogate": args.sur_w,
                        "equilibration_steps": args.sur_pack_equil, "sphere_mass_density": args.sur_rho_s,
-                       "training": "64 two-sphere instances, fixed spheres drawn apart by %g cells of gap "
-                                   "per record, %d-step holds, force mean over the last half, %d records of "
-                                   "both bodies" % (args.sur_dgap, args.sur_hold, args.sur_records)},
+                       "training": "%d two-sphere instances (gap U[3,7]), fixed spheres moved by %g cells "
+                                   "of gap per record, %d-step holds, force mean over the last half, up to %d "
+                                   "records of both bodies while the bridge is intact"
+                                   % (64 * args.sur_seeds, args.sur_dgap, args.sur_hold, args.sur_records)},
             "surrogate_wall_s": res["wall_seconds"], "plain_wall_s": plain_s,
             "force_rel_err_median": res["force_rel_err_median"], "force_rel_err_p95": res["force_rel_err_p95"],
             "corrected_force_rel_err_median": res.get("corrected_force_rel_err_median"),
@@ -414,10 +417,11 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
     ap.add_argument("--workload", default="spheres2",
                     choices=["spheres2", "plates48", "tetra4", "batch64", "surrogate"])
-    ap.add_argument("--sur-equil", type=int, default=1500)
+    ap.add_argument("--sur-equil", type=int, default=800)
+    ap.add_argument("--sur-seeds", type=int, default=2, help="64-instance batches of training runs")
     ap.add_argument("--sur-records", type=int, default=80)
     ap.add_argument("--sur-hold", type=int, default=150)
-    ap.add_argument("--sur-dgap", type=float, default=0.05)
+    ap.add_argument("--sur-dgap", type=float, default=-0.04)
     ap.add_argument("--sur-rho-s", type=float, default=200.0)
     ap.add_argument("--sur-iters", type=int, default=3000)
     ap.add_argument("--sur-box", type=int, default=512)

@@ -10,8 +10,8 @@ between full evaluations, and the plain method is both its fallback and the judg
   a pendular bridge is close to one curve, cos(theta) times a decreasing function of the scaled gap,
   so a few dozen force-gap sweeps cover it.
 * Training data come from batched two-sphere runs of the plain method (the 64-instance workload),
-  the spheres held fixed and drawn apart step by step, the force averaged after each step has
-  relaxed: quasi-static force-gap sweeps. (A node that turns fluid starts empty, Sec. 3.2.2, so a
+  the spheres held fixed and moved together step by step, the force averaged after each step has
+  relaxed: quasi-static force-gap sweeps of intact bridges. (A node that turns fluid starts empty, Sec. 3.2.2, so a
   body move launches pressure pulses that the hold lets decay.)
 * The hybrid advance alternates a K-step lattice-Boltzmann burst (true forces; the per-body residual
   becomes a bias) with a W-step window in which the bodies move under the network's pair forces plus
@@ -99,10 +99,11 @@ def _pair_axis(Xi, Xj, dims):
     return d / np.linalg.norm(d)
 
 
-def generate(ws, equil=1500, hold=150, avg=75, records=80, dgap=0.05, min_gap=1.5, log=None):
+def generate(ws, equil=800, hold=150, avg=75, records=80, dgap=-0.04, min_gap=1.5, log=None):
     """Run the two-sphere instances `ws` (spheres held fixed) as one batch and record (features,
-    targets, instance) of both bodies, step and hold: before each record but the first the spheres are
-    drawn apart along their axis by dgap cells of surface gap (cbl_move_bodies), the fluid relaxes for
+    targets, instance) of both bodies, step and hold: before each record but the first the surface gap
+    changes by dgap cells (negative: the spheres close in, as bridges pull them; cbl_move_bodies),
+    the fluid relaxes for
     hold - avg steps, and the recorded force and torque are the means over the last avg steps. The
     liquid-volume feature is the bridge's measured volume (bridge_state). An instance stops recording
     once its bridge ruptures, it loses mass in a refill, turns non-finite, or its gap falls below
@@ -270,7 +271,7 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
     bodies moved by cbl_move_bodies; a final K-step burst closes the run. Returns the force errors of
     the network at the corrections and the wall time.
 
-    Errors, over the bodies with a bridge: relative |F_MLP - F_LBM| / |F_LBM| where |F_LBM| is at least
+    Errors, over the bodies with an intact bridge: relative |F_MLP - F_LBM| / |F_LBM| where |F_LBM| is at least
     a tenth of the capillary force scale 2 pi R sigma (smaller forces make the ratio meaningless), and
     |F_MLP - F_LBM| / (2 pi R sigma) for all of them. "corrected" adds the bias of the window before."""
     import torch
@@ -278,10 +279,9 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
     rho = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float64, device="cuda")
     b = sim.bodies()
     M = b["M"]
-    bridged = np.array(sorted({i for p in pairs for i in p}), int)
-    scale = 2.0 * math.pi * np.asarray(R, float)[bridged] * SIGMA
     errs, corr, absd = [], [], []
     bias = None
+    Rv = np.asarray(R, float)
     t0 = time.perf_counter()
 
     def burst():
@@ -304,27 +304,31 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
                 VLm[(i, j)] = v
                 live.append((i, j))
         F_mlp = pair_forces(sur, X, R, live, VLm, theta, dims)
-        d = np.linalg.norm(F_mlp[bridged] - F_lbm[bridged], axis=1)
-        n = np.linalg.norm(F_lbm[bridged], axis=1)
-        big = n >= 0.1 * scale
-        errs.append(d[big] / n[big])
-        absd.append(d / scale)
-        if bias is not None:
-            dc = np.linalg.norm(F_mlp[bridged] + bias[bridged] - F_lbm[bridged], axis=1)
-            corr.append(dc[big] / n[big])
+        on = np.array(sorted({i for p in live for i in p}), int)  # bodies with an intact bridge
+        if len(on):
+            sc = 2.0 * math.pi * Rv[on] * SIGMA
+            d = np.linalg.norm(F_mlp[on] - F_lbm[on], axis=1)
+            n = np.linalg.norm(F_lbm[on], axis=1)
+            big = n >= 0.1 * sc
+            errs.append(d[big] / n[big])
+            absd.append(d / sc)
+            if bias is not None:
+                dc = np.linalg.norm(F_mlp[on] + bias[on] - F_lbm[on], axis=1)
+                corr.append(dc[big] / n[big])
         bias = F_lbm - F_mlp
         for _ in range(W):
             F = pair_forces(sur, X, R, live, VLm, theta, dims) + bias
             V += F / M[:, None]
             X = (X + V) % np.asarray(dims, float)
         sim.move_bodies(X, V=V)
-        if log:
+        if log and errs:
             log("window %d: %d of %d bridges intact; median relative force error %.3f over %d bodies" % (
                 win, len(live), len(pairs), float(np.median(errs[-1])) if len(errs[-1]) else float("nan"),
                 len(errs[-1])))
     burst()
     wall = time.perf_counter() - t0
-    e, a = np.concatenate(errs), np.concatenate(absd)
+    e = np.concatenate(errs) if errs else np.zeros(0)
+    a = np.concatenate(absd) if absd else np.zeros(0)
     q = lambda v, p: float(np.percentile(v, p)) if len(v) else None
     out = dict(wall_seconds=wall, steps=windows * (K + W) + K, force_rel_err_median=q(e, 50),
                force_rel_err_p95=q(e, 95), n_rel=int(len(e)), force_err_over_2piRsigma_median=q(a, 50),
