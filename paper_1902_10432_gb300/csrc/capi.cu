@@ -24,6 +24,7 @@ struct cbl_ctx {
   size_t elem = 4;
   PhysParams pp;
   void *fa = nullptr, *fb = nullptr, *psi = nullptr;
+  void* nbuf = nullptr;  // (rho, psi) of the fluid cells next to a solid, written by the collision
   uint16_t* flags = nullptr;
   double *diag_rho = nullptr, *diag_vel = nullptr, *dense = nullptr, *popbuf = nullptr;
   std::vector<BodyDev> hb;
@@ -32,6 +33,9 @@ struct cbl_ctx {
   long long arena_n = 0;
   int max_tile = 0;
   double *acc = nullptr, *last = nullptr, *volacc = nullptr, *scratch = nullptr;
+  double* rtab = nullptr;  // per body and axis: minimum-image offsets of the tile coordinates
+  int* mbox = nullptr;     // per body: tile-coordinate box of its member cells (lo[3], hi[3])
+  int Lmax = 1;            // longest tile side
   double* mass_part = nullptr;
   unsigned n_mass_part = 0;
   int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
@@ -137,6 +141,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   pp.solid_threshold = p.solid_threshold;
   pp.member_threshold = p.member_threshold;
   pp.mpf = p.mpf_kinetics;
+  fill_float_params(pp);
 
   const size_t N = (size_t)ctx->lat.N;
   ctx->fa = dalloc(ctx, (size_t)ctx->lat.Ns * Q * ctx->elem);
@@ -144,14 +149,15 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   // the split density + collision pair is the default; the fused single-pass variant is chosen
   // per lattice by cbl_tune (it needs no psi array but holds fewer threads per SM)
   ctx->psi = dalloc(ctx, N * (ctx->prec == 0 ? 8 : 4));
+  ctx->nbuf = dalloc(ctx, N * 2 * (ctx->prec == 0 ? 8 : 4));
   ctx->flags = (uint16_t*)dalloc(ctx, N * 2);
   ctx->diag_rho = (double*)dalloc(ctx, N * 8);
   ctx->diag_vel = (double*)dalloc(ctx, N * 24);
   ctx->n_mass_part = MASS_SLOTS;
   ctx->mass_part = (double*)dalloc(ctx, (size_t)ctx->n_mass_part * 8);
   ctx->st = (StepState*)dalloc(ctx, sizeof(StepState));
-  if (!ctx->fa || !ctx->fb || !ctx->psi || !ctx->flags || !ctx->diag_rho || !ctx->diag_vel || !ctx->mass_part ||
-      !ctx->st) {
+  if (!ctx->fa || !ctx->fb || !ctx->psi || !ctx->nbuf || !ctx->flags || !ctx->diag_rho || !ctx->diag_vel ||
+      !ctx->mass_part || !ctx->st) {
     dfree_all(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->s);
     delete ctx;
@@ -195,6 +201,7 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   b.rho_s = body->mass_density;
   b.wet = body->wetting_rho;
   b.psi_wet = 1.0 - std::exp(-body->wetting_rho / ctx->p.rho0);
+  b.psi_wet_f = (float)b.psi_wet;
   b.fixed = body->fixed;
   // tile: support half-extent + 2 halo layers + half a cell of recentring offset + 1.5 cells for the
   // discrete profile and the advection tail, which reach about one cell past R + eta/2 on a moving
@@ -235,6 +242,10 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   return CBL_OK;
 }
 
+// member boxes to empty before a refill pass outside the step (the step resets them in the body
+// kernel); the refill pass rebuilds them
+static void reset_member_boxes(cbl_ctx* ctx) { launch_reset_member_boxes(ctx->mbox, (int)ctx->hb.size(), ctx->s); }
+
 static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double* u_host) {
   const size_t N = (size_t)ctx->lat.N;
   const int nb = (int)ctx->hb.size();
@@ -245,9 +256,15 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
     ctx->last = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
     ctx->volacc = (double*)dalloc(ctx, sizeof(double) * 2 * nb);
     ctx->scratch = (double*)dalloc(ctx, sizeof(double) * 9 * nb);
+    for (const BodyDev& b : ctx->hb)
+      for (int a = 0; a < 3; ++a) ctx->Lmax = std::max(ctx->Lmax, b.L[a]);
+    ctx->rtab = (double*)dalloc(ctx, sizeof(double) * 3 * (size_t)ctx->Lmax * nb);
+    ctx->mbox = (int*)dalloc(ctx, sizeof(int) * 6 * nb);
     ctx->blist = (int*)dalloc(ctx, sizeof(int) * (size_t)(ctx->arena_n / 3));
-    if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch || !ctx->blist)
+    if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch || !ctx->blist ||
+        !ctx->rtab || !ctx->mbox)
       return fail(ctx, CBL_ERR_OOM, "device allocation failed (bodies)");
+    for (BodyDev& b : ctx->hb) mirror_f(b);
     CK(cudaMemcpyAsync(ctx->db, ctx->hb.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
     CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * ACC_N * nb, ctx->s));
     CK(cudaMemsetAsync(ctx->last, 0, sizeof(double) * ACC_N * nb, ctx->s));
@@ -264,9 +281,10 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
   CK(cudaMemcpyAsync(drho, rho_host, N * 8, cudaMemcpyHostToDevice, ctx->s));
   if (du) CK(cudaMemcpyAsync(du, u_host, N * 24, cudaMemcpyHostToDevice, ctx->s));
   launch_init_fluid(ctx->prec, ctx->lat, ctx->fa, ctx->flags, drho, du, ctx->s);
-  // first boundary-cell list (no cover events yet, so the pass only scans)
+  // first boundary-cell list (no cover events yet, so the pass only scans) and member boxes
+  reset_member_boxes(ctx);
   launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                ctx->s);
+                ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
   CK(cudaMemsetAsync(ctx->diag_rho, 0, N * 8, ctx->s));
   CK(cudaMemsetAsync(ctx->diag_vel, 0, N * 24, ctx->s));
   CK(cudaGetLastError());
@@ -306,10 +324,10 @@ static void enqueue_lbm(cbl_ctx* ctx, int phases) {
   if (ctx->fused_tz) {
     if (phases & 2)
       launch_lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
-                       ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->s);
+                       ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->nbuf, ctx->s);
   } else {
     launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                    (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->s, phases);
+                    (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->s, phases);
   }
 }
 
@@ -317,17 +335,18 @@ static void enqueue_step(cbl_ctx* ctx) {
   const int nb = (int)ctx->hb.size();
   enqueue_lbm(ctx, 3);
   launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
-                  ctx->pp.G, ctx->pp.rho0, ctx->s);
-  if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
+                  ctx->nbuf, ctx->pp.G, ctx->s);
+  if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
   launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
-                ctx->s);
+                ctx->rtab, ctx->Lmax, ctx->mbox, ctx->s);
   if (nb) {
-    launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
+    launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->rtab,
+                  ctx->Lmax, ctx->s);
     if (ctx->pp.mpf) launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
     launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
                  ctx->s);
     launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                  ctx->s);
+                  ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
   }
 }
 
@@ -370,14 +389,16 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     enqueue_lbm(ctx, 2);
     CK(cudaEventRecord(ev[2], ctx->s));
     launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
-                    ctx->pp.G, ctx->pp.rho0, ctx->s);
+                    ctx->nbuf, ctx->pp.G, ctx->s);
     CK(cudaEventRecord(ev[3], ctx->s));
-    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->s);
+    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
     CK(cudaEventRecord(ev[4], ctx->s));
     launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part,
-                  ctx->st, ctx->s);
+                  ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox, ctx->s);
     CK(cudaEventRecord(ev[5], ctx->s));
-    if (nb) launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->s);
+    if (nb)
+      launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->rtab,
+                    ctx->Lmax, ctx->s);
     CK(cudaEventRecord(ev[6], ctx->s));
     if (nb && ctx->pp.mpf)
       launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
@@ -388,7 +409,7 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     CK(cudaEventRecord(ev[8], ctx->s));
     if (nb)
       launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                    ctx->s);
+                    ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
     CK(cudaEventRecord(ev[9], ctx->s));
     CK(cudaGetLastError());
     CK(cudaEventSynchronize(ev[9]));
@@ -588,6 +609,7 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
     // already given to its neighbours): zero them, then clear the flags under the current tiles
     launch_zero_solid(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->s);
     launch_clear_tile_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->flags, ctx->s);
+    for (BodyDev& b : h) mirror_f(b);
     CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
     launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
     launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
@@ -597,8 +619,9 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
     launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
                  ctx->s);
     launch_clear_stale(ctx->lat, ctx->flags, ctx->s);
+    reset_member_boxes(ctx);
     launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                  ctx->s);
+                  ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
     CK(cudaGetLastError());
     // the host copy h (and the device memcpy source) must outlive the copy
     CK(cudaStreamSynchronize(ctx->s));
@@ -619,6 +642,7 @@ cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* 
       if (V) h[b].V[a] = V[3 * b + a];
       if (W) h[b].W[a] = W[3 * b + a];
     }
+  for (BodyDev& b : h) mirror_f(b);
   CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   return CBL_OK;

@@ -68,6 +68,9 @@ struct BodyDev {
   double X[3], Xprev[3], V[3], W[3], Q[4];
   double M, Ib[9], Ibinv[9];  // body-frame inertia and its inverse
   double wet, psi_wet, vol_ref, rho_s;
+  float psi_wet_f;  // psi_wet rounded once on the host for the FP32 kernels
+  // X, V, W rounded to float for the FP32 kernels' wall terms (mirror_f after every update)
+  float Xf[3], Vf[3], Wf[3];
   double c0[3], radius, half[3], q0[4];
   int fixed, shape;
   int o[3], o_prev[3], L[3];
@@ -75,6 +78,14 @@ struct BodyDev {
   int nnb;
   int nbl[MAXNB];
 };
+
+__host__ __device__ inline void mirror_f(BodyDev& b) {
+  for (int a = 0; a < 3; ++a) {
+    b.Xf[a] = (float)b.X[a];
+    b.Vf[a] = (float)b.V[a];
+    b.Wf[a] = (float)b.W[a];
+  }
+}
 
 // Per-step accumulator layout per body (18 doubles).
 constexpr int ACC_MOM_F = 0, ACC_MOM_T = 3, ACC_ADH_F = 6, ACC_ADH_T = 9, ACC_REP_F = 12,
@@ -100,7 +111,25 @@ struct PhysParams {
   int nrep;
   double solid_threshold, member_threshold;
   int mpf;
+  // FP32 copies for the FP32 kernels, rounded once on the host (fill_float_params): a per-thread
+  // double-to-float conversion is an FP64-pipe instruction, and GB300 issues FP64 at 1/64 rate
+  float tau_f, G_f, rho0_f, ext_f[3];
 };
+
+inline void fill_float_params(PhysParams& p) {
+  p.tau_f = (float)p.tau;
+  p.G_f = (float)p.G;
+  p.rho0_f = (float)p.rho0;
+  for (int k = 0; k < 3; ++k) p.ext_f[k] = (float)p.ext[k];
+}
+
+// a parameter in the working precision R: the double itself, or its host-rounded float copy
+template <typename R>
+__device__ __forceinline__ R par(double d, float f);
+template <>
+__device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float par<float>(double, float f) { return f; }
 
 // Bit-pattern tests of doubles on the integer pipe (GB300 issues FP64 at a small fraction of the
 // FP32 rate). For any double v and a positive threshold t: v > t <=> bits(v) > bits(t) as signed
@@ -127,30 +156,31 @@ void set_fp16_weights(cudaStream_t s);
 unsigned lbm_blocks(const Lat& lat);
 // phases: bit 0 launches the density kernel, bit 1 the collision kernel
 void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
-                     const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st,
-                     double* diag_rho, double* diag_vel, const PhysParams& pp, cudaStream_t s,
-                     int phases = 3);
+                     const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
+                     double* diag_vel, const PhysParams& pp, void* nbuf, cudaStream_t s, int phases = 3);
 // fused single-pass LBM step for FP32 and FP16-deviation storage (prec 1, 2); tz = z extent of a
 // block (see fused_tz)
 int fused_tz(const Lat& lat, int blocks_per_sm);
 void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
                       double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
-                      int tz, cudaStream_t s);
+                      int tz, void* nbuf, cudaStream_t s);
 void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
                      const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st,
-                     double G, double rho0, cudaStream_t s);
+                     const void* nbuf, double G, cudaStream_t s);
 void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
                              const uint16_t* flags, double* out, cudaStream_t s);
 void launch_zero_solid(int prec, const Lat& lat, void* fa, void* fb, const StepState* st, const uint16_t* flags,
                        const BodyDev* bodies, int nb, int max_tile, cudaStream_t s);
 void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
                        const double* u, cudaStream_t s);
-void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags,
-                   const BodyDev* bodies, int nb, int max_tile, StepState* st, int* blist, cudaStream_t s);
+void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, int nb,
+                   int max_tile, StepState* st, int* blist, const double* arena, double member_thr, int* mbox,
+                   cudaStream_t s);
 
 void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
                              cudaStream_t s);
 void launch_clear_stale(const Lat& lat, uint16_t* flags, cudaStream_t s);
+void launch_reset_member_boxes(int* mbox, int nb, cudaStream_t s);
 void launch_rasterize(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
                       double eta, cudaStream_t s);
 void launch_neighbour_lists(BodyDev* bodies, int nb, const Lat& lat, StepState* st, cudaStream_t s);
@@ -158,12 +188,13 @@ void launch_flags(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double*
                   double threshold, int init, StepState* st, cudaStream_t s);
 void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, double* arena,
                        double* scratch, cudaStream_t s);
-void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena,
-                      double* acc, const PhysParams& pp, cudaStream_t s);
+void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
+                      const PhysParams& pp, const int* mbox, cudaStream_t s);
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
-void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf,
-                   double* volacc, StepState* st, cudaStream_t s);
+                   double* mass_part, unsigned n_mass_part, StepState* st, double* rtab, int Lmax, int* mbox,
+                   cudaStream_t s);
+void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
+                   StepState* st, const double* rtab, int Lmax, cudaStream_t s);
 void set_repulsion_offsets(double rc, double e0, int nrep, cudaStream_t s);
 void launch_kinetics(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena,
                      const double* volacc, const PhysParams& pp, cudaStream_t s);

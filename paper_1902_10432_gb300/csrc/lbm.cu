@@ -18,6 +18,7 @@
 // two lattice-wide kernels use a grid-stride loop over a grid of a few blocks per SM.
 #include <mutex>
 
+#include <climits>
 #include "../../include/cbl.h"
 #include "cbl_dev.cuh"
 
@@ -51,6 +52,13 @@ struct St<__half> {
   // f = h + w_hat: zero populations (solid cells) are stored exactly as h = -w_hat.
   __device__ static R ld(const __half* p, size_t k, int i) { return __half2float(p[k]) + c_wh[i]; }
   __device__ static void st(__half* p, size_t k, int i, R v) { p[k] = __float2half_rn(v - c_wh[i]); }
+};
+
+// Density and pseudo-potential of a fluid cell next to a solid, as its collision used them; the
+// solid-fluid force pass reads them back, so its g_i and psi are the collision's own.
+template <typename R>
+struct RhoPsi {
+  R rho, psi;
 };
 
 // A lattice cell with its neighbour offsets: nbr(c, i, s) is the index of x + s c_i, built from
@@ -124,9 +132,9 @@ __device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, lon
                                               const typename St<S>::R fi[Q], typename St<S>::R rho,
                                               typename St<S>::R vx, typename St<S>::R vy, typename St<S>::R vz,
                                               typename St<S>::R Fx, typename St<S>::R Fy, typename St<S>::R Fz,
-                                              double tau) {
+                                              typename St<S>::R tau) {
   using R = typename St<S>::R;
-  const R itau = (R)1 / (R)tau;
+  const R itau = (R)1 / tau;
   const R keep = (R)1 - itau;
   const R pref = (R)1 - (R)0.5 * itau;
   const R ro = rho * itau;
@@ -155,7 +163,8 @@ __global__ void __launch_bounds__(128) k_density(const S* __restrict__ fa, const
                                                  const StepState* __restrict__ st,
                                                  const uint16_t* __restrict__ flags,
                                                  const BodyDev* __restrict__ bodies,
-                                                 typename St<S>::R* __restrict__ psi, Lat lat, double rho0) {
+                                                 typename St<S>::R* __restrict__ psi, Lat lat, double rho0,
+                                                 float rho0_f) {
   using R = typename St<S>::R;
   const S* __restrict__ f = st->parity ? fb : fa;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(128) k_density(const S* __restrict__ fa, const
   const uint16_t fl = flags[n];
   R ps;
   if (fl & F_SOLID) {
-    ps = (R)bodies[fl & F_OWNER].psi_wet;
+    ps = par<R>(bodies[fl & F_OWNER].psi_wet, bodies[fl & F_OWNER].psi_wet_f);
   } else {
     R fi[Q];
     unsigned sl;
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(128) k_density(const S* __restrict__ fa, const
     R rho = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) rho += fi[i];
-    ps = (R)1 - exp(-rho / (R)rho0);
+    ps = (R)1 - exp(-rho / par<R>(rho0, rho0_f));
   }
   psi[n] = ps;
 }
@@ -182,6 +191,29 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Sum of one value per lane, returned in FP64 to every lane. FP64 values go through the FP64
+// butterfly. FP32 values go through an FP32 butterfly that carries each rounding error (Knuth's
+// TwoSum, exact in round-to-nearest) in a second float, so the result is the exact warp sum to
+// about 2^-48 relative without the 5 FP64 adds and the conversion per lane of the plain form
+// (GB300 issues FP64 at 1/64 of the FP32 rate).
+__device__ __forceinline__ double warp_mass(double v) { return warp_sum(v); }
+__device__ __forceinline__ double warp_mass(float v) {
+  float hi = v, lo = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, bl), err);
+  }
+  // every lane holds the same pair; only lane 0's result is used, so only lane 0 converts
+  const unsigned lin = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  return (lin & 31) == 0 ? (double)hi + (double)lo : 0.0;
 }
 
 // minimum image of a coordinate difference in (-1.5 n, 1.5 n): one wrap gives the same result as
@@ -198,12 +230,12 @@ __device__ __forceinline__ R mimg1(R d, int n) {
 template <typename R>
 __device__ __forceinline__ R wall_term(const BodyDev& b, const Cell& c, const Lat& lat, int i, R rho) {
   const R mx = (R)c.x - (R)0.5 * (R)cx_of(i), my = (R)c.y - (R)0.5 * (R)cy_of(i), mz = (R)c.z - (R)0.5 * (R)cz_of(i);
-  const R ax = mimg1<R>(mx - (R)b.X[0], lat.nx), ay = mimg1<R>(my - (R)b.X[1], lat.ny),
-          az = mimg1<R>(mz - (R)b.X[2], lat.nz);
-  const R wx = (R)b.W[0], wy = (R)b.W[1], wz = (R)b.W[2];
-  const R ux = (R)b.V[0] + (wy * az - wz * ay);
-  const R uy = (R)b.V[1] + (wz * ax - wx * az);
-  const R uz = (R)b.V[2] + (wx * ay - wy * ax);
+  const R ax = mimg1<R>(mx - par<R>(b.X[0], b.Xf[0]), lat.nx), ay = mimg1<R>(my - par<R>(b.X[1], b.Xf[1]), lat.ny),
+          az = mimg1<R>(mz - par<R>(b.X[2], b.Xf[2]), lat.nz);
+  const R wx = par<R>(b.W[0], b.Wf[0]), wy = par<R>(b.W[1], b.Wf[1]), wz = par<R>(b.W[2], b.Wf[2]);
+  const R ux = par<R>(b.V[0], b.Vf[0]) + (wy * az - wz * ay);
+  const R uy = par<R>(b.V[1], b.Vf[1]) + (wz * ax - wx * az);
+  const R uz = par<R>(b.V[2], b.Vf[2]) + (wx * ay - wy * ax);
   const R cu = (R)cx_of(i) * ux + (R)cy_of(i) * uy + (R)cz_of(i) * uz;
   return (R)2 * rho * (R)w_of(i) * cu * (R)3;
 }
@@ -228,7 +260,8 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
                                                  const BodyDev* __restrict__ bodies,
                                                  double* __restrict__ mass_part, const StepState* __restrict__ st,
                                                  double* __restrict__ diag_rho, double* __restrict__ diag_vel,
-                                                 Lat lat, PhysParams pp) {
+                                                 Lat lat, PhysParams pp,
+                                                 RhoPsi<typename St<S>::R>* __restrict__ nbuf) {
   using R = typename St<S>::R;
   const size_t N = (size_t)lat.Ns;  // population stride
   const int diag = st->diag;
@@ -261,8 +294,8 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
       if (cy_of(i)) sy += wp * (R)cy_of(i);
       if (cz_of(i)) sz += wp * (R)cz_of(i);
     }
-    const R mG = -(R)pp.G * ps;
-    const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
+    const R mG = -par<R>(pp.G, pp.G_f) * ps;
+    const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
     R fi[Q];
     unsigned sl;
     pull<S>(src, flags, lat, c, n, fi, sl, fl);
@@ -271,6 +304,7 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
     for (int i = 0; i < Q; ++i) rho += fi[i];
     my_mass = rho;
     if (sl) {
+      nbuf[n] = RhoPsi<R>{rho, ps};
       // moving-wall term on each solid link and the mass correction delta rho = -sum g_i on the
       // rest population (Eqs. lb_bounce_back_us, lb_bounce_back_mass)
       R drho = 0;
@@ -299,7 +333,7 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
       vy = my * ir;
       vz = mz * ir;
     }
-    collide_store<S>(dst, N, n, fi, rho, vx, vy, vz, Fx, Fy, Fz, pp.tau);
+    collide_store<S>(dst, N, n, fi, rho, vx, vy, vz, Fx, Fy, Fz, par<R>(pp.tau, pp.tau_f));
     if (diag) {
       diag_rho[n] = (double)rho;
       diag_vel[3 * n] = (double)vx;
@@ -310,7 +344,7 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
   // fluid mass in FP64: block sums added into one of MASS_SLOTS slots (spreads the atomics); the
   // body kernel adds the slots in a fixed order and clears them
   __shared__ double wsum[8];
-  double m = warp_sum((double)my_mass);
+  double m = warp_mass(my_mass);
   {
     const int l = threadIdx.x + blockDim.x * threadIdx.y;
     if ((l & 31) == 0) wsum[l >> 5] = m;
@@ -339,7 +373,8 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
                                                       double* __restrict__ mass_part,
                                                       const StepState* __restrict__ st,
                                                       double* __restrict__ diag_rho, double* __restrict__ diag_vel,
-                                                      Lat lat, PhysParams pp, int tz) {
+                                                      Lat lat, PhysParams pp, int tz,
+                                                      RhoPsi<float>* __restrict__ nbuf) {
   using R = typename St<S>::R;
   constexpr int NT = TX * TY, EX = TX + 2, EY = TY + 2, EP = EX * EY;
   __shared__ R s_psi[3][EP];
@@ -354,7 +389,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
   const int zend = min(z0 + tz, lat.nz);
-  const R rho0 = (R)pp.rho0;
+  const R rho0 = par<R>(pp.rho0, pp.rho0_f);
   R my_mass = 0;
 
   // psi (and, for interior cells of the tile, the pulled populations) of plane z into ring slot
@@ -372,7 +407,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
       const bool interior = buf >= 0 && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
       const int ii = (ey - 1) * TX + (ex - 1);
       if (fl & F_SOLID) {
-        s_psi[slot][p] = (R)bodies[fl & F_OWNER].psi_wet;
+        s_psi[slot][p] = par<R>(bodies[fl & F_OWNER].psi_wet, bodies[fl & F_OWNER].psi_wet_f);
         if (interior) s_sl[buf][ii] = 0xFFFFFFFFu;  // marks a solid cell
         continue;
       }
@@ -416,8 +451,8 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
         if (cy_of(i)) sy += wp * (R)cy_of(i);
         if (cz_of(i)) sz += wp * (R)cz_of(i);
       }
-      const R mG = -(R)pp.G * ps;
-      const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
+      const R mG = -par<R>(pp.G, pp.G_f) * ps;
+      const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
       R fi[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) fi[i] = s_f[buf][i][tid];
@@ -426,6 +461,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
       for (int i = 0; i < Q; ++i) rho += fi[i];
       my_mass += rho;
       if (sl) {
+        nbuf[n] = RhoPsi<R>{rho, ps};
         const Cell c = make_cell(x, y, z, lat);
         R drho = 0;
 #pragma unroll
@@ -452,7 +488,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
         vy = my * ir;
         vz = mz * ir;
       }
-      const R itau = (R)1 / (R)pp.tau;
+      const R itau = (R)1 / par<R>(pp.tau, pp.tau_f);
       const R pref = (R)1 - (R)0.5 * itau;
       const R uu = vx * vx + vy * vy + vz * vz;
       const R vF = vx * Fx + vy * Fy + vz * Fz;
@@ -484,7 +520,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __
     }
     __syncthreads();
   }
-  double m = warp_sum((double)my_mass);
+  double m = warp_mass(my_mass);
   if ((tid & 31) == 0) s_red[tid >> 5] = m;
   __syncthreads();
   if (tid == 0) {
@@ -528,7 +564,8 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
                                                             const StepState* __restrict__ st,
                                                             double* __restrict__ diag_rho,
                                                             double* __restrict__ diag_vel, Lat lat, PhysParams pp,
-                                                            int tz) {
+                                                            int tz,
+                                                            RhoPsi<float>* __restrict__ nbuf) {
   using R = float;
   using SM = AsyncSmem<TX, TY>;
   constexpr int NT = SM::NT, EX = SM::EX, EP = SM::EP;
@@ -542,7 +579,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
   const int zend = min(z0 + tz, lat.nz);
-  const R rho0 = (R)pp.rho0;
+  const R rho0 = par<R>(pp.rho0, pp.rho0_f);
   R my_mass = 0;
   auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
   auto stage = [&](int z) { return (z - z0 + 1) % 3; };
@@ -600,7 +637,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
       const bool interior = keep && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
       const int ii = (ey - 1) * TX + (ex - 1);
       if (fl & F_SOLID) {
-        sm.psi[slot][p] = (R)bodies[fl & F_OWNER].psi_wet;
+        sm.psi[slot][p] = par<R>(bodies[fl & F_OWNER].psi_wet, bodies[fl & F_OWNER].psi_wet_f);
         if (interior) sm.sl[sg][ii] = 0xFFFFFFFFu;
         continue;
       }
@@ -677,8 +714,8 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
           if (cy_of(i)) sy += wp * (R)cy_of(i);
           if (cz_of(i)) sz += wp * (R)cz_of(i);
         }
-        const R mG = -(R)pp.G * ps;
-        const R Fx = mG * sx + (R)pp.ext[0], Fy = mG * sy + (R)pp.ext[1], Fz = mG * sz + (R)pp.ext[2];
+        const R mG = -par<R>(pp.G, pp.G_f) * ps;
+        const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
         R fi[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) fi[i] = sm.pull[sg][i][pc];
@@ -687,6 +724,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
         for (int i = 0; i < Q; ++i) rho += fi[i];
         my_mass += rho;
         if (sl) {
+          nbuf[n] = RhoPsi<R>{rho, ps};
           const Cell c = make_cell(x, y, z, lat);
           R drho = 0;
 #pragma unroll
@@ -713,7 +751,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
           vy = my * ir;
           vz = mz * ir;
         }
-        const R itau = (R)1 / (R)pp.tau;
+        const R itau = (R)1 / par<R>(pp.tau, pp.tau_f);
         const R pref = (R)1 - (R)0.5 * itau;
         const R uu = vx * vx + vy * vy + vz * vz;
         const R vF = vx * Fx + vy * Fy + vz * Fz;
@@ -739,7 +777,7 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
     cp_async_commit();
   }
   cp_async_wait<0>();
-  double m = warp_sum((double)my_mass);
+  double m = warp_mass(my_mass);
   if ((tid & 31) == 0) sm.red[tid >> 5] = m;
   __syncthreads();
   if (tid == 0) {
@@ -756,105 +794,171 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
 // for a solid downstream neighbour x + c_i (owner B), the reaction of the Shan-Chen force,
 // +G psi(x) w_i psi(x + c_i) c_i, arm x + c_i - X_B (Sec. 3.2.3). It reads the same source
 // populations and psi as the collision, so g_i and rho are bit-identical to the ones it used.
+// compensated float sum (Knuth's TwoSum): hi + lo carries the exact sum of the added values to about
+// 2^-48 relative, so the per-body sums keep FP64-level accuracy while only the last step per block
+// runs on the FP64 pipe (GB300 issues FP64 at 1/64 of the FP32 rate)
+struct Sum2 {
+  float hi, lo;
+};
+__device__ __forceinline__ Sum2 sum2_add(Sum2 a, Sum2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return Sum2{s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+template <typename R>
+struct LinkSum;
+template <>
+struct LinkSum<float> {
+  Sum2 v;
+  __device__ void set(float x) { v = Sum2{x, 0.0f}; }
+  __device__ void add(const LinkSum& o) { v = sum2_add(v, o.v); }
+  __device__ LinkSum shfl_xor(int m) const {
+    LinkSum r;
+    r.v.hi = __shfl_xor_sync(0xffffffffu, v.hi, m);
+    r.v.lo = __shfl_xor_sync(0xffffffffu, v.lo, m);
+    return r;
+  }
+  __device__ double value() const { return (double)v.hi + (double)v.lo; }
+};
+template <>
+struct LinkSum<double> {
+  double v;
+  __device__ void set(double x) { v = x; }
+  __device__ void add(const LinkSum& o) { v += o.v; }
+  __device__ LinkSum shfl_xor(int m) const {
+    LinkSum r;
+    r.v = __shfl_xor_sync(0xffffffffu, v, m);
+    return r;
+  }
+  __device__ double value() const { return v; }
+};
+
+// One thread per (list cell, direction): ~18x the parallelism of a thread per cell, which matters
+// because the list is short (the fluid cells next to a solid) and each link's work is a chain of
+// dependent loads (flags -> population or body). The 12 sums per body (momentum exchange F, T;
+// adhesion F, T) are reduced in compensated precision over the warp and the block and added to the
+// FP64 accumulators once per block and body.
 template <typename S>
-__global__ void __launch_bounds__(64) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
-                                                 const uint16_t* __restrict__ flags,
-                                                 const BodyDev* __restrict__ bodies, double* __restrict__ acc,
-                                                 const int* __restrict__ blist, const StepState* __restrict__ st,
-                                                 Lat lat, double G, double rho0) {
+__global__ void __launch_bounds__(256) k_boundary(const S* __restrict__ fa, const S* __restrict__ fb,
+                                                  const uint16_t* __restrict__ flags,
+                                                  const BodyDev* __restrict__ bodies, double* __restrict__ acc,
+                                                  const int* __restrict__ blist, const StepState* __restrict__ st,
+                                                  const RhoPsi<typename St<S>::R>* __restrict__ nbuf, Lat lat,
+                                                  double G, float G_f) {
   using R = typename St<S>::R;
-  const unsigned count = st->nbnd;
+  constexpr int NW = 8;  // warps per block
+  __shared__ LinkSum<R> part[NW][12];
+  __shared__ int pown[NW];
+  const unsigned total = st->nbnd * (unsigned)(Q - 1);
   const S* __restrict__ src = st->parity ? fb : fa;
-  const unsigned stride = gridDim.x * blockDim.x;
-  // whole-block rounds so that every lane reaches the shuffles below
-  for (unsigned base = blockIdx.x * blockDim.x; base < count; base += stride) {
+  const size_t N = (size_t)lat.Ns;  // population stride
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // whole-block rounds so that every thread reaches the barriers
+  for (unsigned base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
     const unsigned k = base + threadIdx.x;
-    // per-thread sums in the working precision (a cell has at most 18 links); FP64 from the
-    // warp reduction on
-    R a12[12];
+    R v[12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) a12[q] = 0;
-    int cur = -1;
-    auto flush = [&](int B) {
-      if (B < 0) return;
-#pragma unroll
-      for (int q = 0; q < 12; ++q)
-        if (a12[q] != (R)0) atomicAdd(acc + (size_t)B * ACC_N + q, (double)a12[q]);
-    };
-    auto select = [&](int B) {
-      if (B != cur) {
-        flush(cur);
-#pragma unroll
-        for (int q = 0; q < 12; ++q) a12[q] = 0;
-        cur = B;
-      }
-    };
-    if (k < count) {
-      const long long n = blist[k];
+    for (int q = 0; q < 12; ++q) v[q] = 0;
+    int Bm = -1, Ba = -1;  // body of the momentum-exchange term, of the adhesion term
+    if (k < total) {
+      const unsigned cell = k / (unsigned)(Q - 1);
+      const int i = 1 + (int)(k - cell * (unsigned)(Q - 1));
+      const long long n = blist[cell];
       const Cell c = cell_of(n, lat);
-      R fi[Q];
-      unsigned sl;
-      pull<S>(src, flags, lat, c, n, fi, sl);
-      R rho = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) rho += fi[i];
-      // psi from the same pulled density as the step's own psi pass (bit-identical)
-      const R ps = (R)1 - exp(-rho / (R)rho0);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        if (sl & (1u << i)) {
-          const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
-          const BodyDev& b = bodies[B];
-          const R g = wall_term<R>(b, c, lat, i, rho);
-          const R m2 = (R)2 * fi[i] + g;  // fi[i] = f*_opp(i)(x) on a solid link
-          const R dPx = -(R)cx_of(i) * m2, dPy = -(R)cy_of(i) * m2, dPz = -(R)cz_of(i) * m2;
-          const R ax = mimg1<R>((R)c.x - (R)0.5 * (R)cx_of(i) - (R)b.X[0], lat.nx);
-          const R ay = mimg1<R>((R)c.y - (R)0.5 * (R)cy_of(i) - (R)b.X[1], lat.ny);
-          const R az = mimg1<R>((R)c.z - (R)0.5 * (R)cz_of(i) - (R)b.X[2], lat.nz);
-          select(B);
-          a12[0] += dPx;
-          a12[1] += dPy;
-          a12[2] += dPz;
-          a12[3] += ay * dPz - az * dPy;
-          a12[4] += az * dPx - ax * dPz;
-          a12[5] += ax * dPy - ay * dPx;
-        }
-        const long long m = nbr(c, lat, i, +1);
-        const uint16_t fm = __ldg(flags + m);
-        if (fm & F_SOLID) {
-          const int B = fm & F_OWNER;
-          const BodyDev& b = bodies[B];
-          const R gpw = (R)G * ps * ((R)w_of(i) * (R)b.psi_wet);
-          const R fx = gpw * (R)cx_of(i), fy = gpw * (R)cy_of(i), fz = gpw * (R)cz_of(i);
-          const R ax = mimg1<R>((R)c.x + (R)cx_of(i) - (R)b.X[0], lat.nx);
-          const R ay = mimg1<R>((R)c.y + (R)cy_of(i) - (R)b.X[1], lat.ny);
-          const R az = mimg1<R>((R)c.z + (R)cz_of(i) - (R)b.X[2], lat.nz);
-          select(B);
-          a12[6] += fx;
-          a12[7] += fy;
-          a12[8] += fz;
-          a12[9] += ay * fz - az * fy;
-          a12[10] += az * fx - ax * fz;
-          a12[11] += ax * fy - ay * fx;
-        }
+      const uint16_t up = __ldg(flags + nbr(c, lat, i, -1)), dn = __ldg(flags + nbr(c, lat, i, +1));
+      if (up & F_SOLID) {
+        // link to a solid upstream: the pulled value is f*_opp(i)(x) (half-way bounce-back)
+        const int B = up & F_OWNER;
+        const BodyDev& b = bodies[B];
+        const RhoPsi<R> rp = nbuf[n];
+        const R fi = St<S>::ld(src, (size_t)opp_of(i) * N + n, i);
+        const R g = wall_term<R>(b, c, lat, i, rp.rho);
+        const R m2 = (R)2 * fi + g;
+        const R dPx = -(R)cx_of(i) * m2, dPy = -(R)cy_of(i) * m2, dPz = -(R)cz_of(i) * m2;
+        const R ax = mimg1<R>((R)c.x - (R)0.5 * (R)cx_of(i) - par<R>(b.X[0], b.Xf[0]), lat.nx);
+        const R ay = mimg1<R>((R)c.y - (R)0.5 * (R)cy_of(i) - par<R>(b.X[1], b.Xf[1]), lat.ny);
+        const R az = mimg1<R>((R)c.z - (R)0.5 * (R)cz_of(i) - par<R>(b.X[2], b.Xf[2]), lat.nz);
+        v[0] = dPx;
+        v[1] = dPy;
+        v[2] = dPz;
+        v[3] = ay * dPz - az * dPy;
+        v[4] = az * dPx - ax * dPz;
+        v[5] = ax * dPy - ay * dPx;
+        Bm = B;
+      }
+      if (dn & F_SOLID) {
+        // solid downstream: reaction of the Shan-Chen force on that body
+        const int B = dn & F_OWNER;
+        const BodyDev& b = bodies[B];
+        const R ps = nbuf[n].psi;
+        const R gpw = par<R>(G, G_f) * ps * ((R)w_of(i) * par<R>(b.psi_wet, b.psi_wet_f));
+        const R fx = gpw * (R)cx_of(i), fy = gpw * (R)cy_of(i), fz = gpw * (R)cz_of(i);
+        const R ax = mimg1<R>((R)c.x + (R)cx_of(i) - par<R>(b.X[0], b.Xf[0]), lat.nx);
+        const R ay = mimg1<R>((R)c.y + (R)cy_of(i) - par<R>(b.X[1], b.Xf[1]), lat.ny);
+        const R az = mimg1<R>((R)c.z + (R)cz_of(i) - par<R>(b.X[2], b.Xf[2]), lat.nz);
+        v[6] = fx;
+        v[7] = fy;
+        v[8] = fz;
+        v[9] = ay * fz - az * fy;
+        v[10] = az * fx - ax * fz;
+        v[11] = ax * fy - ay * fx;
+        Ba = B;
       }
     }
-    // warp-uniform body -> shuffle sum in FP64, else per-lane atomics
-    const unsigned any = __ballot_sync(0xffffffffu, cur >= 0);
+    // one body for the whole warp (the usual case): compensated warp sums; otherwise per-lane
+    // FP64 atomics
+    const int Bt = Bm >= 0 ? Bm : Ba;
+    const bool mixed = Bm >= 0 && Ba >= 0 && Bm != Ba;
+    const unsigned any = __ballot_sync(0xffffffffu, Bt >= 0);
+    int b0 = -1;
     if (any) {
-      const int lead = __ffs(any) - 1;
-      const int b0 = __shfl_sync(0xffffffffu, cur, lead);
-      const bool uniform = __all_sync(0xffffffffu, cur < 0 || cur == b0);
-      if (uniform) {
+      b0 = __shfl_sync(0xffffffffu, Bt, __ffs(any) - 1);
+      if (!__all_sync(0xffffffffu, (Bt < 0 || Bt == b0) && !mixed)) {
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
-          double v = warp_sum(cur >= 0 ? (double)a12[q] : 0.0);
-          if ((int)(threadIdx.x & 31) == lead && v != 0.0) atomicAdd(acc + (size_t)b0 * ACC_N + q, v);
+          const int B = q < 6 ? Bm : Ba;
+          if (B >= 0 && v[q] != (R)0) atomicAdd(acc + (size_t)B * ACC_N + q, (double)v[q]);
         }
+        b0 = -1;
       } else {
-        flush(cur);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          LinkSum<R> a;
+          a.set(v[q]);
+#pragma unroll
+          for (int m = 16; m > 0; m >>= 1) a.add(a.shfl_xor(m));
+          if (lane == 0) part[w][q] = a;
+        }
       }
     }
+    if (lane == 0) pown[w] = b0;
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      // warps of the same body in a row are combined before one FP64 atomic
+      const int q = threadIdx.x;
+      int cur = -1;
+      LinkSum<R> run;
+      run.set((R)0);
+      for (int ww = 0; ww < NW; ++ww) {
+        const int B = pown[ww];
+        if (B < 0) continue;
+        if (B != cur) {
+          if (cur >= 0) {
+            const double x = run.value();
+            if (x != 0.0) atomicAdd(acc + (size_t)cur * ACC_N + q, x);
+          }
+          cur = B;
+          run.set((R)0);
+        }
+        run.add(part[ww][q]);
+      }
+      if (cur >= 0) {
+        const double x = run.value();
+        if (x != 0.0) atomicAdd(acc + (size_t)cur * ACC_N + q, x);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -902,7 +1006,8 @@ template <typename S>
 __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restrict__ fb,
                                                 uint16_t* __restrict__ flags,
                                                 const BodyDev* __restrict__ bodies, StepState* st, int* blist,
-                                                Lat lat) {
+                                                Lat lat, const double* __restrict__ arena, double member_thr,
+                                                int* __restrict__ mbox) {
   using R = typename St<S>::R;
   S* __restrict__ f = st->parity ? fb : fa;  // the state buffer written by this step's collision
   const int self = blockIdx.y;
@@ -910,10 +1015,18 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool boundary = false;
   long long m = 0;
+  // member cells (phi >= member_thr) of this body: their tile-coordinate bounding box, for the
+  // repulsion pass of the next step
+  bool member = false;
+  int mi[3] = {0, 0, 0};
   if (t < b.sz) {
     const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];  // tiles hold < 2^31 cells
     const unsigned r = u / L0;
     const int i0 = (int)(u - r * L0), i1 = (int)(r % L1), i2 = (int)(r / L1);
+    member = dbits(arena[b.off + t]) >= dbits(member_thr);
+    mi[0] = i0;
+    mi[1] = i1;
+    mi[2] = i2;
     const int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
     m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
     if (!(b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat))) {
@@ -1006,6 +1119,28 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
         }
       }
     }
+  }
+  // warp, then block, then one set of global atomics per block (all warps of a block hit the same
+  // six words, so per-warp global atomics would queue up)
+  __shared__ int sbox[6];
+  if (threadIdx.x < 6) sbox[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
+  __syncthreads();
+  if (__ballot_sync(0xffffffffu, member)) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int lo = __reduce_min_sync(0xffffffffu, member ? mi[a] : INT_MAX);
+      const int hi = __reduce_max_sync(0xffffffffu, member ? mi[a] : INT_MIN);
+      if (lane == 0) {
+        atomicMin(sbox + a, lo);
+        atomicMax(sbox + 3 + a, hi);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6 && sbox[0] <= sbox[3]) {
+    if (threadIdx.x < 3) atomicMin(mbox + 6 * self + threadIdx.x, sbox[threadIdx.x]);
+    else atomicMax(mbox + 6 * self + threadIdx.x, sbox[threadIdx.x]);
   }
   // warp-aggregated append to the boundary list
   const unsigned mask = __ballot_sync(0xffffffffu, boundary);
@@ -1101,17 +1236,18 @@ int fused_tz(const Lat& lat, int blocks_per_sm) {
 
 template <typename S>
 static void fused_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, const BodyDev* bodies, double* mass_part,
-                    StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp, int tz, cudaStream_t s) {
+                    StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp, int tz, void* nbuf,
+                    cudaStream_t s) {
   dim3 grid((lat.nx + FTX - 1) / FTX, (lat.ny + FTY - 1) / FTY, (lat.nz + tz - 1) / tz);
   k_lbm_fused<S, FTX, FTY><<<grid, FTX * FTY, 0, s>>>(fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, lat,
-                                                      pp, tz);
+                                                      pp, tz, (RhoPsi<float>*)nbuf);
 }
 
 size_t fused_async_smem() { return sizeof(AsyncSmem<FTX, FTY>); }
 
 void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
                       double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
-                      int tz, cudaStream_t s) {
+                      int tz, void* nbuf, cudaStream_t s) {
   if (prec == 1) {
     static bool attr = false;
     const size_t bytes = fused_async_smem();
@@ -1121,56 +1257,60 @@ void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16
     }
     dim3 grid((lat.nx + FTX - 1) / FTX, (lat.ny + FTY - 1) / FTY, (lat.nz + tz - 1) / tz);
     k_lbm_fused_async<FTX, FTY><<<grid, FTX * FTY, bytes, s>>>((float*)fa, (float*)fb, flags, bodies, mass_part, st,
-                                                               diag_rho, diag_vel, lat, pp, tz);
+                                                               diag_rho, diag_vel, lat, pp, tz, (RhoPsi<float>*)nbuf);
   } else if (prec == 2)
-    fused_t<__half>(lat, (__half*)fa, (__half*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+    fused_t<__half>(lat, (__half*)fa, (__half*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, nbuf, s);
 }
 
 template <typename S>
 static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
                        double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
-                       const PhysParams& pp, cudaStream_t s, int phases) {
+                       const PhysParams& pp, void* nbuf, cudaStream_t s, int phases) {
   using R = typename St<S>::R;
   // `blocks` carries the x extent of the 128-thread blocks (32, 64 or 128)
   const int bx = blocks == 64 || blocks == 128 ? (int)blocks : 32, by = 128 / bx;
   const dim3 blk(bx, by, 1);
   const dim3 grid((lat.nx + bx - 1) / bx, (lat.ny + by - 1) / by, lat.nz);
-  if (phases & 1) k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0);
+  if (phases & 1) k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0, pp.rho0_f);
   if (phases & 2)
     k_collide<S><<<grid, blk, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel, lat,
-                                      pp);
+                                      pp, (RhoPsi<R>*)nbuf);
 }
 
 void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
                      const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
-                     double* diag_vel, const PhysParams& pp, cudaStream_t s, int phases) {
+                     double* diag_vel, const PhysParams& pp, void* nbuf, cudaStream_t s, int phases) {
   if (prec == 0)
     lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                       pp, s, phases);
+                       pp, nbuf, s, phases);
   else if (prec == 1)
     lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                      pp, s, phases);
+                      pp, nbuf, s, phases);
   else
     lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                       pp, s, phases);
+                       pp, nbuf, s, phases);
 }
 
 template <typename S>
 static void boundary_t(const Lat& lat, const S* fa, const S* fb, const uint16_t* flags, const BodyDev* bodies,
-                       double* acc, const int* blist, const StepState* st, double G, double rho0, cudaStream_t s) {
-  k_boundary<S><<<4 * sm_count(), 64, 0, s>>>(fa, fb, flags, bodies, acc, blist, st, lat, G, rho0);
+                       double* acc, const int* blist, const StepState* st, const void* nbuf, double G,
+                       cudaStream_t s) {
+  using R = typename St<S>::R;
+  // whole-lattice grid-stride rounds; the list length is only known on the device
+  k_boundary<S><<<8 * sm_count(), 256, 0, s>>>(fa, fb, flags, bodies, acc, blist, st, (const RhoPsi<R>*)nbuf, lat, G,
+                                                (float)G);
 }
 
 void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
-                     const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st, double G,
-                     double rho0, cudaStream_t s) {
+                     const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st,
+                     const void* nbuf, double G, cudaStream_t s) {
   if (nb == 0) return;
   if (prec == 0)
-    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, bodies, acc, blist, st, G, rho0, s);
+    boundary_t<double>(lat, (const double*)fa, (const double*)fb, flags, bodies, acc, blist, st, nbuf, G, s);
   else if (prec == 1)
-    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, bodies, acc, blist, st, G, rho0, s);
+    boundary_t<float>(lat, (const float*)fa, (const float*)fb, flags, bodies, acc, blist, st, nbuf, G, s);
   else
-    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, bodies, acc, blist, st, G, rho0, s);
+    boundary_t<__half>(lat, (const __half*)fa, (const __half*)fb, flags, bodies, acc, blist, st, nbuf, G, s);
 }
 
 void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags, const double* rho, const double* u,
@@ -1183,13 +1323,18 @@ void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags,
 }
 
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, int nb,
-                   int max_tile, StepState* st, int* blist, cudaStream_t s) {
+                   int max_tile, StepState* st, int* blist, const double* arena, double member_thr, int* mbox,
+                   cudaStream_t s) {
   if (nb == 0) return;
   const int T = 256;
   dim3 grid((unsigned)((max_tile + T - 1) / T), (unsigned)nb);
-  if (prec == 0) k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, blist, lat);
-  else if (prec == 1) k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, blist, lat);
-  else k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, blist, lat);
+  if (prec == 0)
+    k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, blist, lat, arena, member_thr, mbox);
+  else if (prec == 1)
+    k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, blist, lat, arena, member_thr, mbox);
+  else
+    k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, blist, lat, arena, member_thr,
+                                        mbox);
 }
 
 }  // namespace cbl
@@ -1270,12 +1415,13 @@ extern "C" cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int 
   pp.G = G;
   pp.rho0 = rho0;
   for (int k = 0; k < 3; ++k) pp.ext[k] = ext_force ? ext_force[k] : 0.0;
+  fill_float_params(pp);
   if (cudaMemsetAsync(a.mass, 0, sizeof(double) * MASS_SLOTS, s) != cudaSuccess) return CBL_ERR_CUDA;
   const dim3 blk(32, 4, 1);
   const dim3 grid((nx + 31) / 32, (ny + 3) / 4, nz);
-  k_density<float><<<grid, blk, 0, s>>>(f_in, f_in, a.state, a.flags, nullptr, a.psi, lat, rho0);
+  k_density<float><<<grid, blk, 0, s>>>(f_in, f_in, a.state, a.flags, nullptr, a.psi, lat, rho0, (float)rho0);
   k_collide<float><<<grid, blk, 0, s>>>(const_cast<float*>(f_in), f_out, a.flags, a.psi, nullptr, a.mass, a.state,
-                                        nullptr, nullptr, lat, pp);
+                                        nullptr, nullptr, lat, pp, nullptr);
   if (mass_out) k_na_mass<<<1, 256, 0, s>>>(a.mass, mass_out);
   return cudaGetLastError() == cudaSuccess ? CBL_OK : CBL_ERR_CUDA;
 }

@@ -13,6 +13,7 @@
 //  k_sweep        : one conservative MUSCL sweep with the monotonized-central limiter of
 //                   d(phi)/dt = -u_B . grad(phi) (Eq. phase_advection, Sec. 3.3), x, y, z in turn.
 //  k_kinetics     : Eq. sim_proc_phase_field_dynamics with the volume-restoring Delta g (Sec. 3.3).
+#include <climits>
 #include "cbl_dev.cuh"
 
 namespace cbl {
@@ -194,6 +195,26 @@ __global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat
       ids[m++] = b.nbl[k];
     }
   }
+  const long long n_idx = c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz);
+  if (m == 1) {
+    // one body: phi exactly +0 or 1 passes the clamp, the flush and the renormalisation unchanged,
+    // and 1 - S is 1 (fluid) or 0 (solid, below any positive threshold)
+    const long long vb = dbits(*ptr[0]);
+    if (vb == 0 || vb == dbits(1.0)) {
+      uint16_t nf = 0;
+      // 1 - S < thr with S = 0 or 1, on the bit pattern of thr (signed order = numeric order)
+      const long long tb = dbits(thr);
+      if (vb != 0 ? tb > 0 : tb > dbits(1.0)) {
+        nf = F_SOLID | (uint16_t)self;
+        if (!init && !(flags[n_idx] & F_SOLID)) {
+          nf |= F_COVER;
+          atomicAdd(&st->ncover, 1u);
+        }
+      }
+      flags[n_idx] = nf;
+      return;
+    }
+  }
   double S = 0.0;
   for (int k = 0; k < m; ++k) {
     double v = *ptr[k];
@@ -278,6 +299,7 @@ __global__ void k_body_props_finish(BodyDev* bodies, int nb, const double* scrat
       b.X[a] = X;
       b.Xprev[a] = X;
     }
+    mirror_f(b);
     b.M = b.rho_s * s[0];
     b.vol_ref = s[0];
   } else {
@@ -309,11 +331,34 @@ __global__ void k_body_props_finish(BodyDev* bodies, int nb, const double* scrat
 // ---- solid-solid repulsion ---------------------------------------------------------------------
 // For a point x of body A (phi_A >= the membership threshold) and every body B whose tile overlaps
 // A's: sum the table forces f(d) over the points x + d of B; torque (x - X_A) x (sum f).
+__device__ __forceinline__ double support_radius(const BodyDev& b, double eta) {
+  const double h = b.shape == 0 ? b.radius : sqrt(b.half[0] * b.half[0] + b.half[1] * b.half[1] + b.half[2] * b.half[2]);
+  return h + 0.5 * eta;
+}
+
 __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const double* arena, double* acc, Lat lat,
-                                                   double rc, double thr) {
+                                                   double rc, int Rc, double thr, double eta,
+                                                   const int* __restrict__ mbox) {
   const int self = blockIdx.y;
   const BodyDev& a = bodies[self];
   if (a.nnb == 0) return;  // block-uniform
+  // block-uniform cull: member points (phi >= 1/2) lie within the support of the profile, the
+  // shape's bounding sphere grown by eta/2; no pair can be within rc unless two such spheres are
+  __shared__ int s_near;
+  if (threadIdx.x == 0) {
+    int nearby = 0;
+    const double ea = support_radius(a, eta);
+    for (int k = 0; k < a.nnb && !nearby; ++k) {
+      const BodyDev& b = bodies[a.nbl[k]];
+      const double dx = mimg(b.X[0] - a.X[0], lat.nx), dy = mimg(b.X[1] - a.X[1], lat.ny),
+                   dz = mimg(b.X[2] - a.X[2], lat.nz);
+      const double lim = ea + support_radius(b, eta) + rc + 1.0;
+      nearby = dx * dx + dy * dy + dz * dz <= lim * lim;
+    }
+    s_near = nearby;
+  }
+  __syncthreads();
+  if (!s_near) return;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tb = dbits(thr);
   double F[3] = {0, 0, 0};
@@ -321,27 +366,57 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
   TileCell c;
   if (t < a.sz && dbits(arena[a.off + t]) >= tb) {
     c = tile_cell(a, t, lat);
-    const int R = (int)ceil(rc);
     const int g[3] = {c.gx, c.gy, c.gz};
     const int nn[3] = {lat.nx, lat.ny, lat.nz};
     for (int k = 0; k < a.nnb; ++k) {
       const BodyDev& b = bodies[a.nbl[k]];
-      // skip unless this point lies within rc of the other body's tile
+      // this point's coordinates in the other body's tile, wrapped to [0, n); skip unless the point
+      // lies within rc of that tile
+      // tile coordinates of the other body's member cells (phi >= thr) lie in its box mbox (built by
+      // the refill pass after the last flag update); the offsets reach Rc cells per axis, so a point
+      // outside the box grown by Rc (periodically) finds no partner
+      const int* bx = mbox + 6 * a.nbl[k];
+      int l[3];
       bool near = true;
       for (int d = 0; d < 3; ++d) {
-        if (b.L[d] >= nn[d]) continue;
-        const int l = wrapi(g[d] - b.o[d], nn[d]);
-        if (l >= b.L[d] + R && l < nn[d] - R) near = false;
+        l[d] = wrapi(g[d] - b.o[d], nn[d]);
+        const int lo = bx[d] - Rc, hi = bx[3 + d] + Rc;
+        const bool in = (l[d] >= lo && l[d] <= hi) || (l[d] - nn[d] >= lo && l[d] - nn[d] <= hi) ||
+                        (l[d] + nn[d] >= lo && l[d] + nn[d] <= hi);
+        if (bx[d] > bx[3 + d] || !in) near = false;  // an empty box has no members
       }
       if (!near) continue;
       const double* bb = arena + b.off;
-      for (int j = 0; j < c_noff; ++j) {
-        const long long q = tile_index(b.o, b.L, c.gx + c_off[3 * j], c.gy + c_off[3 * j + 1], c.gz + c_off[3 * j + 2], lat);
-        if (q < 0 || dbits(bb[q]) < tb) continue;
-        F[0] += c_offf[3 * j];
-        F[1] += c_offf[3 * j + 1];
-        F[2] += c_offf[3 * j + 2];
-        has = true;
+      // offsets in groups of 8: the group's loads are issued before any of them is tested (a
+      // test per load would wait for each load in turn); contributions are added in offset order
+      for (int j0 = 0; j0 < c_noff; j0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + u;
+          long long q = -1;
+          if (j < c_noff) {
+            int m[3];
+            bool in = true;
+            for (int d = 0; d < 3; ++d) {
+              m[d] = l[d] + c_off[3 * j + d];  // |offset| <= 6: at most two wraps on a 4-cell side
+              while (m[d] < 0) m[d] += nn[d];
+              while (m[d] >= nn[d]) m[d] -= nn[d];
+              in &= m[d] < b.L[d];
+            }
+            if (in) q = (long long)m[0] + (long long)b.L[0] * ((long long)m[1] + (long long)b.L[1] * m[2]);
+          }
+          v[u] = q >= 0 ? __ldg(bb + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + u;
+          if (j >= c_noff || dbits(v[u]) < tb) continue;
+          F[0] += c_offf[3 * j];
+          F[1] += c_offf[3 * j + 1];
+          F[2] += c_offf[3 * j + 2];
+          has = true;
+        }
       }
     }
   }
@@ -412,22 +487,35 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
 
 __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
                                                 double* mass_part, unsigned n_mass_part, StepState* st,
-                                                Lat lat) {
+                                                Lat lat, double* rtab, int Lmax, int* mbox) {
   const int n[3] = {lat.nx, lat.ny, lat.nz};
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     BodyDev& b = bodies[i];
     double* a = acc + (size_t)i * ACC_N;
     integrate(b, a, lat);
+    mirror_f(b);
     for (int k = 0; k < ACC_N; ++k) {
       last[(size_t)i * ACC_N + k] = a[k];
       a[k] = 0.0;
     }
     volacc[2 * i] = 0.0;
     volacc[2 * i + 1] = 0.0;
+    for (int a = 0; a < 3; ++a) {  // member box: rebuilt by this step's refill pass
+      mbox[6 * i + a] = INT_MAX;
+      mbox[6 * i + 3 + a] = INT_MIN;
+    }
     for (int d = 0; d < 3; ++d) {
       b.o_prev[d] = b.o[d];
       if (b.L[d] < n[d]) b.o[d] = (int)floor(b.X[d] + 0.5) - b.L[d] / 2;
     }
+  }
+  __syncthreads();
+  // per body and axis, the minimum-image offset of every tile coordinate from the pre-update centre
+  // (the advection's face velocities need it; the table saves each cell the FP64 wrap)
+  for (int k = threadIdx.x; k < nb * 3 * Lmax; k += blockDim.x) {
+    const int i = k / (3 * Lmax), a = (k / Lmax) % 3, l = k % Lmax;
+    const BodyDev& b = bodies[i];
+    if (l < b.L[a]) rtab[k] = mimg(wrapi(b.o[a] + l, n[a]) - b.Xprev[a], n[a]);
   }
   // fluid mass of this step: fixed-order sum of the per-block partials
   __shared__ double red[256];
@@ -452,10 +540,23 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
 }
 
 // ---- advection ---------------------------------------------------------------------------------
+// Monotonized-central slope: 0 unless dm and dp have the same sign, else
+// sign(dm) min(2|dm|, |dm + dp| / 2, 2|dp|). Evaluated on bit patterns, with the same result as the
+// plain FP64 form: doubling and halving a normal double add to or subtract from its exponent field,
+// and non-negative doubles order like their bit patterns. Only dm + dp is an FP64 operation (GB300
+// issues FP64 at 1/64 of the FP32 rate). The differences of phase-field values that reach this
+// function are 0 or far above the subnormal range, so no product underflows and no half is
+// subnormal.
 __device__ __forceinline__ double mc_slope(double dm, double dp) {
-  if (dm * dp <= 0.0) return 0.0;
-  double s = fmin(fmin(2.0 * fabs(dm), 0.5 * fabs(dm + dp)), 2.0 * fabs(dp));
-  return dm > 0 ? s : -s;
+  const long long bm = dbits(dm), bp = dbits(dp);
+  const long long mag = 0x7FFFFFFFFFFFFFFFLL, one_exp = 1LL << 52;
+  const long long am = bm & mag, ap = bp & mag;
+  if (((bm ^ bp) < 0) || am == 0 || ap == 0) return 0.0;
+  const long long two_am = am + one_exp, two_ap = ap + one_exp;
+  const long long half_s = (dbits(dm + dp) & mag) - one_exp;
+  long long m = two_am < half_s ? two_am : half_s;
+  m = m < two_ap ? m : two_ap;
+  return __longlong_as_double(m | (bm & (long long)0x8000000000000000ULL));
 }
 
 // one sweep along axis d: out (origin b.o) <- in (origin o_in). The x-sweep reads with the previous
@@ -469,7 +570,8 @@ __device__ __forceinline__ int in_local(int i, int shift, int L, int n) {
 }
 
 __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* arena, Lat lat, int d, int in_buf,
-                                               int out_buf, int use_prev, int last, double* volacc, StepState* st) {
+                                               int out_buf, int use_prev, int last, double* volacc, StepState* st,
+                                               const double* __restrict__ rtab, int Lmax) {
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -514,10 +616,11 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
     } else {
       // face velocity u_d (the d-component of V + omega x r, r about X_prev): it depends only on the
       // two other coordinates, so both faces of the cell share it
-      const int g[3] = {wrapi(b.o[0] + ii[0], nn[0]), wrapi(b.o[1] + ii[1], nn[1]), wrapi(b.o[2] + ii[2], nn[2])};
+      // r_a = mimg(wrap(o_a + i_a) - Xprev_a) from the per-body table built by k_bodies
       const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-      const double r1 = mimg(g[d1] - b.Xprev[d1], nn[d1]);
-      const double r2 = mimg(g[d2] - b.Xprev[d2], nn[d2]);
+      const double* rt = rtab + (size_t)self * 3 * Lmax;
+      const double r1 = rt[d1 * Lmax + ii[d1]];
+      const double r2 = rt[d2 * Lmax + ii[d2]];
       const double u = b.V[d] + (b.W[d1] * r2 - b.W[d2] * r1);
       double Fl, Fr;
       {
@@ -577,6 +680,15 @@ __global__ void k_volume(const BodyDev* bodies, const double* arena, double* vol
 // with I = lap(phi) + (pi/eta)^2 phi, D_B = (V_B(0) - sum phi_B) / #{0 < phi_B < 1}, D_fluid = 0.
 constexpr int MAXACT = 8;
 
+// Kinetics constants evaluated once on the host with the same expressions the kernel used per cell
+// (IEEE division is correctly rounded on both sides, so the values are identical): pi^2 / eta^2 and
+// M / N for every possible number of active phases N (an FP64 division costs many FP64-pipe
+// instructions, and GB300 issues FP64 at 1/64 of the FP32 rate).
+struct KinParams {
+  double k2, s_sf, s_ss;
+  double mobN[MAXACT + 2];
+};
+
 // phi at a cell of a tile given in tile-local coordinates l and its 6 face neighbours (order: self,
 // +x, -x, +y, -y, +z, -z); periodic tile axes wrap, other axes read zero outside the tile
 __device__ __forceinline__ void tile_val7(const double* buf, const int L[3], const int l[3], const int nn[3],
@@ -602,10 +714,19 @@ __device__ __forceinline__ void tile_val7(const double* buf, const int L[3], con
 }
 
 __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double* arena, const double* volacc, Lat lat,
-                                                  double eta, double mob, double s_sf, double s_ss) {
+                                                  KinParams kp) {
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // volume-restoring term D of this body (slot 0) and of each listed neighbour (slot k + 1), once per
+  // block: D = (V(0) - sum phi) / #{0 < phi < 1}, 0 without interface cells
+  __shared__ double sD[MAXNB + 1];
+  for (int k = threadIdx.x; k <= b.nnb; k += blockDim.x) {
+    const int id = k == 0 ? self : b.nbl[k - 1];
+    const double cnt = volacc[2 * id + 1];
+    sD[k] = cnt > 0.0 ? (bodies[id].vol_ref - volacc[2 * id]) / cnt : 0.0;
+  }
+  __syncthreads();
   if (t >= b.sz) return;
   const double* in = arena + b.off + b.sz;  // buffer 1: advected field
   double* out = arena + b.off;              // buffer 0: new field
@@ -629,9 +750,61 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     return;
   }
   const int g[3] = {wrapi(b.o[0] + ii[0], nn[0]), wrapi(b.o[1] + ii[1], nn[1]), wrapi(b.o[2] + ii[2], nn[2])};
+  // is any other body present in this cell's 7-point stencil?
+  bool others = false;
+  for (int k = 0; k < b.nnb && !others; ++k) {
+    const BodyDev& o = bodies[b.nbl[k]];
+    int lo[3];
+    bool near = true;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = wrapi(g[a] - o.o[a], nn[a]);
+      if (o.L[a] < nn[a]) {
+        if (lo[a] > nn[a] - 2) lo[a] -= nn[a];
+        if (lo[a] < -1 || lo[a] > o.L[a]) near = false;
+      }
+    }
+    if (!near) continue;
+    double v7[7];
+    tile_val7(arena + o.off + o.sz, o.L, lo, nn, v7);
+    for (int k2 = 0; k2 < 7; ++k2) others |= dbits(v7[k2]) > eb;
+  }
+  if (!others) {
+    // one solid phase and possibly the fluid: the general form below with na = 1, in the same
+    // operation order (S = 0 + phi, fluid values 1 - S), without its per-phase arrays
+    double S[7];
+    const long long one_eb = dbits(1.0 - PHI_EPS);
+    bool fl = false;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      S[k] = 0.0 + pa[k];
+      fl |= dbits(S[k]) < one_eb;
+    }
+    if (!fl) {  // N = 1
+      out[t] = pa[0];
+      return;
+    }
+    const double k2 = kp.k2;
+    double lap = 0.0;
+#pragma unroll
+    for (int k = 1; k < 7; ++k) lap += pa[k];
+    lap -= 6.0 * pa[0];
+    const double Is = lap + k2 * pa[0];
+    double lapf = 0.0;
+#pragma unroll
+    for (int k = 1; k < 7; ++k) lapf += 1.0 - S[k];
+    lapf -= 6.0 * (1.0 - S[0]);
+    const double If = lapf + k2 * (1.0 - S[0]);
+    double term = kp.s_sf * (Is - If);
+    if (dbits(pa[0]) > eb && dbits(pa[0]) < one_eb) term += sD[0] - 0.0;
+    double rate = 0.0;
+    rate += kp.mobN[2] * term;
+    out[t] = pa[0] + rate;
+    return;
+  }
   // active solids in ascending id order, with their 7-point values
   double vals[MAXACT][7];
   int ids[MAXACT];
+  int dslot[MAXACT];  // slot of each active phase in sD
   int na = 0;
   int pos_self = -1;
   double S[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -646,9 +819,11 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
         vals[na][k] = pa[k];
         S[k] += pa[k];
       }
+      dslot[na] = 0;
       ids[na++] = self;
       continue;
     }
+    const int slot = k_nb;  // b.nbl[slot - 1] == id
     const BodyDev& o = bodies[id];
     int lo[3];
     bool near = true;
@@ -670,25 +845,27 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
         vals[na][k] = v7[k];
         S[k] += v7[k];
       }
+      dslot[na] = slot;
       ids[na++] = id;
     }
   }
+  // S >= 0, so the signed bit patterns order like the values
+  const long long one_eb = dbits(1.0 - PHI_EPS);
   bool fl = false;
-  for (int k = 0; k < 7; ++k) fl |= S[k] < 1.0 - PHI_EPS;
+  for (int k = 0; k < 7; ++k) fl |= dbits(S[k]) < one_eb;
   const int N = na + (fl ? 1 : 0);
   if (N <= 1) {
     out[t] = pa[0];
     return;
   }
-  const double k2 = PI * PI / (eta * eta);
+  const double k2 = kp.k2;
   double I[MAXACT + 1], D[MAXACT + 1];
   for (int j = 0; j < na; ++j) {
     double lap = 0.0;
     for (int k = 1; k < 7; ++k) lap += vals[j][k];
     lap -= 6.0 * vals[j][0];
     I[j] = lap + k2 * vals[j][0];
-    const double cnt = volacc[2 * ids[j] + 1];
-    D[j] = cnt > 0.0 ? (bodies[ids[j]].vol_ref - volacc[2 * ids[j]]) / cnt : 0.0;
+    D[j] = sD[dslot[j]];
   }
   if (fl) {
     double lap = 0.0;
@@ -697,9 +874,10 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     I[na] = lap + k2 * (1.0 - S[0]);
     D[na] = 0.0;
   }
+  const double s_sf = kp.s_sf, s_ss = kp.s_ss;
   auto sig = [&](int p, int q) { return (p == na || q == na) ? s_sf : s_ss; };
   const int a = pos_self;
-  const bool in_if = pa[0] > PHI_EPS && pa[0] < 1.0 - PHI_EPS;
+  const bool in_if = dbits(pa[0]) > eb && dbits(pa[0]) < one_eb;
   double rate = 0.0;
   for (int bq = 0; bq < N; ++bq) {
     if (bq == a) continue;
@@ -709,7 +887,7 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
       term += (sig(bq, gg) - sig(a, gg)) * I[gg];
     }
     if (in_if) term += D[a] - D[bq];
-    rate += mob / N * term;
+    rate += kp.mobN[N] * term;
   }
   out[t] = pa[0] + rate;
 }
@@ -787,27 +965,33 @@ void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, do
   k_body_props_finish<<<(nb + 127) / 128, 128, 0, s>>>(bodies, nb, scratch, lat, 1);
 }
 void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
-                      const PhysParams& pp, cudaStream_t s) {
+                      const PhysParams& pp, const int* mbox, cudaStream_t s) {
   if (nb > 1 && pp.e0 != 0.0)
-    k_repulsion<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, acc, lat, pp.rc, pp.member_threshold);
+    k_repulsion<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, acc, lat, pp.rc, (int)std::ceil(pp.rc),
+                                                       pp.member_threshold, pp.eta, mbox);
 }
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {
-  k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, mass_part, n_mass_part, st, lat);
+                   double* mass_part, unsigned n_mass_part, StepState* st, double* rtab, int Lmax, int* mbox,
+                   cudaStream_t s) {
+  k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, mass_part, n_mass_part, st, lat, rtab, Lmax, mbox);
 }
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
-                   StepState* st, cudaStream_t s) {
+                   StepState* st, const double* rtab, int Lmax, cudaStream_t s) {
   if (!nb) return;
   dim3 g = tile_grid(max_tile, nb);
-  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 0, 0, 1, 1, 0, volacc, st);
-  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 1, 1, 2, 0, 0, volacc, st);
-  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 2, 2, mpf ? 1 : 0, 0, 1, volacc, st);
+  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 0, 0, 1, 1, 0, volacc, st, rtab, Lmax);
+  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 1, 1, 2, 0, 0, volacc, st, rtab, Lmax);
+  k_sweep<<<g, 256, 0, s>>>(bodies, arena, lat, 2, 2, mpf ? 1 : 0, 0, 1, volacc, st, rtab, Lmax);
 }
 void launch_kinetics(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, const double* volacc,
                      const PhysParams& pp, cudaStream_t s) {
-  if (nb)
-    k_kinetics<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, volacc, lat, pp.eta, pp.mobility, pp.sigma_sf,
-                                                      pp.sigma_ss);
+  if (!nb) return;
+  KinParams kp;
+  kp.k2 = PI * PI / (pp.eta * pp.eta);
+  kp.s_sf = pp.sigma_sf;
+  kp.s_ss = pp.sigma_ss;
+  for (int k = 0; k < MAXACT + 2; ++k) kp.mobN[k] = k ? pp.mobility / k : 0.0;
+  k_kinetics<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, volacc, lat, kp);
 }
 void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, int body,
                       double* out, cudaStream_t s) {
@@ -820,6 +1004,13 @@ void launch_phi_dense(const Lat& lat, const BodyDev* bodies, int nb, int max_til
 void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
                              cudaStream_t s) {
   if (nb) k_clear_tile_flags<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, flags, lat);
+}
+__global__ void k_reset_member_boxes(int* mbox, int nb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < 6 * nb) mbox[k] = (k % 6) < 3 ? INT_MAX : INT_MIN;
+}
+void launch_reset_member_boxes(int* mbox, int nb, cudaStream_t s) {
+  if (nb) k_reset_member_boxes<<<(6 * nb + 255) / 256, 256, 0, s>>>(mbox, nb);
 }
 void launch_clear_stale(const Lat& lat, uint16_t* flags, cudaStream_t s) {
   k_clear_stale<<<(unsigned)((lat.N + 255) / 256), 256, 0, s>>>(flags, lat.N);
