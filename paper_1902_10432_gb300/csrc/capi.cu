@@ -327,7 +327,8 @@ static void enqueue_lbm(cbl_ctx* ctx, int phases) {
                        ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->nbuf, ctx->s);
   } else {
     launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                    (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->s, phases);
+                    (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
+                    ctx->s, phases);
   }
 }
 

@@ -253,36 +253,25 @@ template <>
 struct CollideMinBlocks<double> {
   static constexpr int value = 4;
 };
-template <typename S>
-__global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* __restrict__ fa, S* __restrict__ fb,
-                                                 const uint16_t* __restrict__ flags,
-                                                 const typename St<S>::R* __restrict__ psi,
-                                                 const BodyDev* __restrict__ bodies,
-                                                 double* __restrict__ mass_part, const StepState* __restrict__ st,
-                                                 double* __restrict__ diag_rho, double* __restrict__ diag_vel,
-                                                 Lat lat, PhysParams pp,
-                                                 RhoPsi<typename St<S>::R>* __restrict__ nbuf) {
+// Collision of one fluid cell: Shan-Chen force with wetting, pull, moving-wall terms on solid links,
+// Guo-forced BGK, store. NEAR: the cell has a solid neighbour along a lattice direction (bounce-back
+// sources, wall terms, (rho, psi) for the force pass); without it the pull reads no flags at all, so
+// the bulk kernel carries neither the flag loads (on which the population addresses would depend)
+// nor the registers of the wall terms. Returns rho.
+template <typename S, bool NEAR>
+__device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__ src, S* __restrict__ dst,
+                                                           const uint16_t* __restrict__ flags,
+                                                           const typename St<S>::R* __restrict__ psi,
+                                                           const BodyDev* __restrict__ bodies, int diag,
+                                                           double* __restrict__ diag_rho,
+                                                           double* __restrict__ diag_vel, const Lat& lat,
+                                                           const PhysParams& pp,
+                                                           RhoPsi<typename St<S>::R>* __restrict__ nbuf,
+                                                           const Cell& c, long long n) {
   using R = typename St<S>::R;
   const size_t N = (size_t)lat.Ns;  // population stride
-  const int diag = st->diag;
-  const S* __restrict__ src = st->parity ? fb : fa;
-  S* __restrict__ dst = st->parity ? fa : fb;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-  const bool valid = x < lat.nx && y < lat.ny;
-  const Cell c = make_cell(valid ? x : 0, valid ? y : 0, z, lat);
-  const long long n = c.n;
   R my_mass = 0;
-  const uint16_t fl = valid ? flags[n] : (uint16_t)0;
-  if (valid && (fl & F_SOLID)) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
-    if (diag) {
-      diag_rho[n] = 0.0;
-      diag_vel[3 * n] = 0.0;
-      diag_vel[3 * n + 1] = 0.0;
-      diag_vel[3 * n + 2] = 0.0;
-    }
-  } else if (valid) {
+  {
     // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
     // it needs only psi, so the populations are not yet live
     const R ps = psi[n];
@@ -298,13 +287,13 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
     const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
     R fi[Q];
     unsigned sl;
-    pull<S>(src, flags, lat, c, n, fi, sl, fl);
+    pull<S>(src, flags, lat, c, n, fi, sl, NEAR ? F_NEAR : (uint16_t)0);
     R rho = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) rho += fi[i];
     my_mass = rho;
     if (sl) {
-      nbuf[n] = RhoPsi<R>{rho, ps};
+      if (NEAR) nbuf[n] = RhoPsi<R>{rho, ps};
       // moving-wall term on each solid link and the mass correction delta rho = -sum g_i on the
       // rest population (Eqs. lb_bounce_back_us, lb_bounce_back_mass)
       R drho = 0;
@@ -341,22 +330,86 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
       diag_vel[3 * n + 2] = (double)vz;
     }
   }
-  // fluid mass in FP64: block sums added into one of MASS_SLOTS slots (spreads the atomics); the
-  // body kernel adds the slots in a fixed order and clears them
-  __shared__ double wsum[8];
-  double m = warp_mass(my_mass);
-  {
-    const int l = threadIdx.x + blockDim.x * threadIdx.y;
-    if ((l & 31) == 0) wsum[l >> 5] = m;
-  }
-  __syncthreads();
+  return my_mass;
+}
+
+template <typename S>
+__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, double m, unsigned slot) {
+  // block sum of the warp sums, added into one of MASS_SLOTS slots (spreads the atomics); the body
+  // kernel adds the slots in a fixed order and clears them
+  __shared__ double wsum[32];
   const int lin = threadIdx.x + blockDim.x * threadIdx.y;
+  if ((lin & 31) == 0) wsum[lin >> 5] = m;
+  __syncthreads();
   if (lin == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)((blockDim.x * blockDim.y) >> 5); ++w) t += wsum[w];
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (t != 0.0) atomicAdd(mass_part + (b & (MASS_SLOTS - 1)), t);
+    if (t != 0.0) atomicAdd(mass_part + (slot & (MASS_SLOTS - 1)), t);
   }
+}
+
+// Bulk collision: solid cells store zeros, fluid cells without a solid neighbour collide; fluid cells
+// next to a solid are left to k_collide_near.
+template <typename S>
+__global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* __restrict__ fa, S* __restrict__ fb,
+                                                 const uint16_t* __restrict__ flags,
+                                                 const typename St<S>::R* __restrict__ psi,
+                                                 const BodyDev* __restrict__ bodies,
+                                                 double* __restrict__ mass_part, const StepState* __restrict__ st,
+                                                 double* __restrict__ diag_rho, double* __restrict__ diag_vel,
+                                                 Lat lat, PhysParams pp,
+                                                 RhoPsi<typename St<S>::R>* __restrict__ nbuf) {
+  using R = typename St<S>::R;
+  const size_t N = (size_t)lat.Ns;  // population stride
+  const int diag = st->diag;
+  const S* __restrict__ src = st->parity ? fb : fa;
+  S* __restrict__ dst = st->parity ? fa : fb;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  const bool valid = x < lat.nx && y < lat.ny;
+  const Cell c = make_cell(valid ? x : 0, valid ? y : 0, z, lat);
+  const long long n = c.n;
+  R my_mass = 0;
+  const uint16_t fl = valid ? flags[n] : (uint16_t)0;
+  if (valid && (fl & F_SOLID)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
+    if (diag) {
+      diag_rho[n] = 0.0;
+      diag_vel[3 * n] = 0.0;
+      diag_vel[3 * n + 1] = 0.0;
+      diag_vel[3 * n + 2] = 0.0;
+    }
+  } else if (valid && !(fl & F_NEAR)) {
+    my_mass = collide_fluid<S, false>(src, dst, flags, psi, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
+  }
+  const double m = warp_mass(my_mass);
+  add_mass_slot<S>(mass_part, m, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+}
+
+// Collision of the fluid cells next to a solid (the boundary-cell list built by the refill pass).
+template <typename S>
+__global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __restrict__ fb,
+                                                      const uint16_t* __restrict__ flags,
+                                                      const typename St<S>::R* __restrict__ psi,
+                                                      const BodyDev* __restrict__ bodies,
+                                                      double* __restrict__ mass_part,
+                                                      const StepState* __restrict__ st,
+                                                      double* __restrict__ diag_rho, double* __restrict__ diag_vel,
+                                                      const int* __restrict__ blist, Lat lat, PhysParams pp,
+                                                      RhoPsi<typename St<S>::R>* __restrict__ nbuf) {
+  using R = typename St<S>::R;
+  const int diag = st->diag;
+  const S* __restrict__ src = st->parity ? fb : fa;
+  S* __restrict__ dst = st->parity ? fa : fb;
+  const unsigned count = st->nbnd;
+  R my_mass = 0;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    const long long n = blist[k];
+    const Cell c = cell_of(n, lat);
+    my_mass += collide_fluid<S, true>(src, dst, flags, psi, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
+  }
+  const double m = warp_mass(my_mass);
+  add_mass_slot<S>(mass_part, m, blockIdx.x * 7u + 3u);
 }
 
 // ---- fused step: pull + density + psi + Shan-Chen force + collision in one pass ----------------
@@ -1265,30 +1318,35 @@ void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16
 template <typename S>
 static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
                        double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
-                       const PhysParams& pp, void* nbuf, cudaStream_t s, int phases) {
+                       const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s, int phases) {
   using R = typename St<S>::R;
   // `blocks` carries the x extent of the 128-thread blocks (32, 64 or 128)
   const int bx = blocks == 64 || blocks == 128 ? (int)blocks : 32, by = 128 / bx;
   const dim3 blk(bx, by, 1);
   const dim3 grid((lat.nx + bx - 1) / bx, (lat.ny + by - 1) / by, lat.nz);
   if (phases & 1) k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0, pp.rho0_f);
-  if (phases & 2)
+  if (phases & 2) {
     k_collide<S><<<grid, blk, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel, lat,
                                       pp, (RhoPsi<R>*)nbuf);
+    if (blist)
+      k_collide_near<S><<<2 * sm_count(), 128, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho,
+                                                        diag_vel, blist, lat, pp, (RhoPsi<R>*)nbuf);
+  }
 }
 
 void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
                      const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
-                     double* diag_vel, const PhysParams& pp, void* nbuf, cudaStream_t s, int phases) {
+                     double* diag_vel, const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s,
+                     int phases) {
   if (prec == 0)
     lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                       pp, nbuf, s, phases);
+                       pp, nbuf, blist, s, phases);
   else if (prec == 1)
     lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                      pp, nbuf, s, phases);
+                      pp, nbuf, blist, s, phases);
   else
     lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                       pp, nbuf, s, phases);
+                       pp, nbuf, blist, s, phases);
 }
 
 template <typename S>
