@@ -28,8 +28,16 @@ sys.path.insert(0, ROOT)
 # algorithmic bytes per cell update of the collision kernel: read 19 populations, write 19,
 # read the uint16 flag (the density pass and psi are implementation overhead)
 POP_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
-KERNELS = {"fp64": 11, "fp32": 10, "fp16dev": 10}  # [density,] collide/fused, boundary, repulsion, bodies,
-# 3 sweeps, kinetics, flags, refill
+
+
+def kernels_per_step(nb, mpf, fused):
+    """Kernel launches of one step of the library's graph: density + bulk collision + near-solid
+    collision (or the single fused pass), then with bodies the force pass, repulsion (two or more
+    bodies), body update, three advection sweeps, kinetics (MPF on), flags and refill."""
+    k = 1 if fused else 2
+    if nb:
+        k += (0 if fused else 1) + 1 + (1 if nb > 1 else 0) + 1 + 3 + (1 if mpf else 0) + 2
+    return k
 
 
 # DRAM bytes per k_collide launch from the committed ncu capture (profiles/k_collide_spheres2_fp32.md),
@@ -228,7 +236,8 @@ def bench_batch(args, rank, world, local_rank):
                        "cells": cells, "autotune_choices": choices},
             "sequential_mlups": cells * args.steps / seq_s / 1e6,
             "speedup_vs_sequential": seq_s / bat_s, "clocks": clk.summary(),
-            "gpu_launches": KERNELS[args.precision] * args.steps * len(sims)}
+            "gpu_launches": args.steps * sum(n * kernels_per_step(2, 1, json.loads(c).get("lbm_variant") == 1)
+                                             for c, n in choices.items())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
@@ -388,12 +397,13 @@ def bench_cuda(args, rank, world, local_rank):
                        "inputs_vs_l2": "populations 2 x %.0f MB > 129 MB L2 (no flush needed)"
                                        % (w.ncells * 19 * POP_BYTES[prec] / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": "collision pass (k_collide + k_collide_near)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(w.name, prec), "peak_kind": peak_kind,
                          "alg_bytes_per_cell": bpc,
                          "step_frac": bpc * w.ncells / (ms_max / args.steps * 1e-3) / 1e9 / peak},
             "phases_ms": {k: round(v, 5) for k, v in phases.items()},
-            "gpu_launches": KERNELS[prec] * args.steps,
+            "gpu_launches": kernels_per_step(len(w.bodies), w.params.get("mpf_kinetics", 1), False) * args.steps,
             "clocks": clk.summary(),
             "e2e": {"value": w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,

@@ -50,7 +50,7 @@ template <>
 struct St<__half> {
   using R = float;
   // f = h + w_hat: zero populations (solid cells) are stored exactly as h = -w_hat.
-  __device__ static R ld(const __half* p, size_t k, int i) { return __half2float(p[k]) + c_wh[i]; }
+  __device__ static R ld(const __half* p, size_t k, int i) { return __half2float(__ldg(p + k)) + c_wh[i]; }
   __device__ static void st(__half* p, size_t k, int i, R v) { p[k] = __float2half_rn(v - c_wh[i]); }
 };
 

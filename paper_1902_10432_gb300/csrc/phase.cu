@@ -645,17 +645,33 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
     }
   }
   if (last) {
+    // volume (sum phi) and interface-cell count of the body: warp sums, then one FP64 atomic per
+    // block (per-warp atomics on the same two words would queue up)
+    __shared__ double wv[8];
+    __shared__ int wc[8];
     const long long vb = dbits(v);
     const bool live = inside && (vb << 1) != 0;
+    double sv = 0.0;
+    int cnt = 0;
     if (__ballot_sync(0xffffffffu, live)) {
-      double sv = dwarp_sum(live ? v : 0.0);
+      sv = dwarp_sum(live ? v : 0.0);
       const bool in_if = live && vb > dbits(PHI_EPS) && vb < dbits(1.0 - PHI_EPS);
-      const int cnt = __popc(__ballot_sync(0xffffffffu, in_if));
-      double sc = (double)cnt;
-      if ((threadIdx.x & 31) == 0) {
-        if (sv != 0.0) atomicAdd(volacc + 2 * self, sv);
-        if (sc != 0.0) atomicAdd(volacc + 2 * self + 1, sc);
+      cnt = __popc(__ballot_sync(0xffffffffu, in_if));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wv[threadIdx.x >> 5] = sv;
+      wc[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bv = 0.0;
+      int bc = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        bv += wv[w];
+        bc += wc[w];
       }
+      if (bv != 0.0) atomicAdd(volacc + 2 * self, bv);
+      if (bc != 0) atomicAdd(volacc + 2 * self + 1, (double)bc);
     }
   }
 }
@@ -769,36 +785,29 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     for (int k2 = 0; k2 < 7; ++k2) others |= dbits(v7[k2]) > eb;
   }
   if (!others) {
-    // one solid phase and possibly the fluid: the general form below with na = 1, in the same
-    // operation order (S = 0 + phi, fluid values 1 - S), without its per-phase arrays
-    double S[7];
-    const long long one_eb = dbits(1.0 - PHI_EPS);
+    // one solid phase a and the fluid f = 1 - phi: N = 2 where the fluid is present at the cell or a
+    // face neighbour, and then the rate is (M/2) [sigma_sf (I_a - I_f) + D_a (interface cells)]. With
+    // lap = the 7-point Laplacian of phi, I_a = lap + k2 phi and I_f = -lap + k2 (1 - phi), so
+    // I_a - I_f = 2 lap + k2 (2 phi - 1) (the same quantity as the general form below, up to
+    // rounding). Presence of the fluid (1 - phi > PHI_EPS) is tested on bit patterns.
+    const long long one_eb = dbits(1.0 - PHI_EPS), neg0 = (long long)0x8000000000000000ULL;
     bool fl = false;
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
-      S[k] = 0.0 + pa[k];
-      fl |= dbits(S[k]) < one_eb;
+      const long long bk = dbits(pa[k]);
+      fl |= (bk == neg0 ? 0LL : bk) < one_eb;
     }
-    if (!fl) {  // N = 1
+    if (!fl) {  // N = 1: no kinetics
       out[t] = pa[0];
       return;
     }
-    const double k2 = kp.k2;
     double lap = 0.0;
 #pragma unroll
     for (int k = 1; k < 7; ++k) lap += pa[k];
     lap -= 6.0 * pa[0];
-    const double Is = lap + k2 * pa[0];
-    double lapf = 0.0;
-#pragma unroll
-    for (int k = 1; k < 7; ++k) lapf += 1.0 - S[k];
-    lapf -= 6.0 * (1.0 - S[0]);
-    const double If = lapf + k2 * (1.0 - S[0]);
-    double term = kp.s_sf * (Is - If);
-    if (dbits(pa[0]) > eb && dbits(pa[0]) < one_eb) term += sD[0] - 0.0;
-    double rate = 0.0;
-    rate += kp.mobN[2] * term;
-    out[t] = pa[0] + rate;
+    double term = kp.s_sf * (2.0 * lap + kp.k2 * (2.0 * pa[0] - 1.0));
+    if (dbits(pa[0]) > eb && dbits(pa[0]) < one_eb) term += sD[0];
+    out[t] = pa[0] + kp.mobN[2] * term;
     return;
   }
   // active solids in ascending id order, with their 7-point values
