@@ -189,7 +189,10 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
  *                  marches along z with prefetch into shared memory (FP32 storage only;
  *                  CBL_ERR_UNSUPPORTED otherwise);
  *   "fused_tz"     z extent of a fused block (0 = derived from the SM count);
- *   "lbm_block_x"  x extent of the 128-thread blocks of the split kernels: 32 (default), 64, 128.
+ *   "lbm_block_x"  x extent of the 128-thread blocks of the split kernels: 32 (default), 64, 128;
+ *   "graph_branches" 1 (default) = with bodies, the collision of the fluid cells next to a solid and
+ *                  the solid-solid repulsion run on a second branch of the step graph beside the
+ *                  bulk collision; 0 = one chain.
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 

@@ -19,6 +19,11 @@ struct cbl_ctx {
   bool user_alloc = false;
   cudaStream_t s = nullptr;
   bool own_stream = false;
+  // side branch of the captured step (near-solid collision and repulsion run beside the bulk
+  // collision): its stream and the fork / join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int branches = 1;  // 0: the step graph is one chain
   Lat lat;
   int prec = 1;
   size_t elem = 4;
@@ -119,6 +124,13 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
     }
     ctx->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+    delete ctx;
+    return fail(nullptr, CBL_ERR_CUDA, "stream or event creation failed");
+  }
   ctx->lat.nx = p.nx;
   ctx->lat.ny = p.ny;
   ctx->lat.nz = p.nz;
@@ -160,6 +172,9 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
       !ctx->mass_part || !ctx->st) {
     dfree_all(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+    cudaStreamDestroy(ctx->side);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
     delete ctx;
     return fail(nullptr, CBL_ERR_OOM, "device allocation failed");
   }
@@ -320,24 +335,43 @@ cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const dou
   return init_common(ctx, rho_host, u_host);
 }
 
-static void enqueue_lbm(cbl_ctx* ctx, int phases) {
+// phases: 1 density, 2 bulk collision, 4 collision of the cells next to a solid (the fused pass does
+// all of it under 2)
+static void enqueue_lbm(cbl_ctx* ctx, int phases, cudaStream_t s) {
   if (ctx->fused_tz) {
     if (phases & 2)
       launch_lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
-                       ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->nbuf, ctx->s);
+                       ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->nbuf, s);
   } else {
     launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
                     (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
-                    ctx->s, phases);
+                    s, phases);
   }
 }
 
+// One step, enqueued for capture into a graph. With bodies, the collision of the cells next to a
+// solid and the solid-solid repulsion run on a side branch beside the bulk collision (they touch
+// other cells, or only the phase fields, and add into the force accumulators with atomics); the
+// force pass joins both.
 static void enqueue_step(cbl_ctx* ctx) {
   const int nb = (int)ctx->hb.size();
-  enqueue_lbm(ctx, 3);
-  launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
-                  ctx->nbuf, ctx->pp.G, ctx->s);
-  if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
+  if (nb && !ctx->fused_tz && ctx->branches) {
+    enqueue_lbm(ctx, 1, ctx->s);
+    cudaEventRecord(ctx->ev_fork, ctx->s);
+    cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    enqueue_lbm(ctx, 4, ctx->side);
+    launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->side);
+    cudaEventRecord(ctx->ev_join, ctx->side);
+    enqueue_lbm(ctx, 2, ctx->s);
+    cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0);
+    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+                    ctx->nbuf, ctx->pp.G, ctx->s);
+  } else {
+    enqueue_lbm(ctx, 7, ctx->s);
+    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+                    ctx->nbuf, ctx->pp.G, ctx->s);
+    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
+  }
   launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
                 ctx->rtab, ctx->Lmax, ctx->mbox, ctx->s);
   if (nb) {
@@ -385,9 +419,9 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
   CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
   for (int it = 0; it < nsteps; ++it) {
     CK(cudaEventRecord(ev[0], ctx->s));
-    enqueue_lbm(ctx, 1);
+    enqueue_lbm(ctx, 1, ctx->s);
     CK(cudaEventRecord(ev[1], ctx->s));
-    enqueue_lbm(ctx, 2);
+    enqueue_lbm(ctx, 6, ctx->s);
     CK(cudaEventRecord(ev[2], ctx->s));
     launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->s);
@@ -686,6 +720,10 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
     ctx->fused_tz_req = v;
     if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : fused_tz(ctx->lat, 2);
+  } else if (k == "graph_branches") {
+    const int v = (int)value;
+    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "graph_branches must be 0 or 1");
+    ctx->branches = v;
   } else if (k == "lbm_block_x") {
     const int v = (int)value;
     if (v != 32 && v != 64 && v != 128) return fail(ctx, CBL_ERR_ARG, "lbm_block_x must be 32, 64 or 128");
@@ -809,6 +847,9 @@ cbl_status cbl_destroy(cbl_ctx* ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   dfree_all(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+  cudaStreamDestroy(ctx->side);
+  cudaEventDestroy(ctx->ev_fork);
+  cudaEventDestroy(ctx->ev_join);
   delete ctx;
   return CBL_OK;
 }

@@ -158,7 +158,7 @@ unsigned lbm_blocks(const Lat& lat);
 void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
                      const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
                      double* diag_vel, const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s,
-                     int phases = 3);
+                     int phases = 7);
 // fused single-pass LBM step for FP32 and FP16-deviation storage (prec 1, 2); tz = z extent of a
 // block (see fused_tz)
 int fused_tz(const Lat& lat, int blocks_per_sm);
