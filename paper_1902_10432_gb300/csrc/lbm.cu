@@ -112,27 +112,30 @@ __device__ __forceinline__ void pull(const S* __restrict__ f, const uint16_t* __
   const size_t N = (size_t)lat.Ns;  // population stride
   const bool near = (own_flag & F_NEAR) != 0;
   solid_links = 0;
-  size_t idx[Q];
-  idx[0] = (size_t)n;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const long long s = nbr(c, lat, i, -1);
-    const bool sol = near && (__ldg(flags + s) & F_SOLID);
-    solid_links |= (unsigned)sol << i;
-    idx[i] = sol ? (size_t)opp_of(i) * N + n : (size_t)i * N + s;
-  }
   if constexpr (sizeof(S) == 2) {
     // binary16: all 19 raw loads are issued before any conversion (converting each value as it
     // arrives made every load wait for the one before: 2.5x slower); St<__half> adds the weight of
     // the direction actually read, and opp(i) has the same weight as i
     unsigned short raw[Q];
+    raw[0] = __ldg(reinterpret_cast<const unsigned short*>(f) + n);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) raw[i] = __ldg(reinterpret_cast<const unsigned short*>(f) + idx[i]);
+    for (int i = 1; i < Q; ++i) {
+      const long long s = nbr(c, lat, i, -1);
+      const bool sol = near && (__ldg(flags + s) & F_SOLID);
+      solid_links |= (unsigned)sol << i;
+      raw[i] = __ldg(reinterpret_cast<const unsigned short*>(f) + (sol ? (size_t)opp_of(i) * N + n : (size_t)i * N + s));
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) fi[i] = St<S>::from_raw(raw[i], i);
   } else {
+    fi[0] = St<S>::ld(f, (size_t)n, 0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fi[i] = St<S>::ld(f, idx[i], i);
+    for (int i = 1; i < Q; ++i) {
+      const long long s = nbr(c, lat, i, -1);
+      const bool sol = near && (__ldg(flags + s) & F_SOLID);
+      solid_links |= (unsigned)sol << i;
+      fi[i] = St<S>::ld(f, sol ? (size_t)opp_of(i) * N + n : (size_t)i * N + s, i);
+    }
   }
 }
 
@@ -267,6 +270,11 @@ template <>
 struct CollideMinBlocks<double> {
   static constexpr int value = 4;
 };
+// binary16 storage: 7 blocks (72 registers) avoids a register spill that 8 blocks force, and is faster
+template <>
+struct CollideMinBlocks<__half> {
+  static constexpr int value = 7;
+};
 // Collision of one fluid cell: Shan-Chen force with wetting, pull, moving-wall terms on solid links,
 // Guo-forced BGK, store. NEAR: the cell has a solid neighbour along a lattice direction (bounce-back
 // sources, wall terms, (rho, psi) for the force pass); without it the pull reads no flags at all, so
@@ -347,17 +355,51 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
   return my_mass;
 }
 
-template <typename S>
-__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, double m, unsigned slot) {
-  // block sum of the warp sums, added into one of MASS_SLOTS slots (spreads the atomics); the body
-  // kernel adds the slots in a fixed order and clears them
+// Block sum of the cells' densities, added into one of MASS_SLOTS slots (spreads the atomics); the
+// body kernel adds the slots in a fixed order and clears them. FP64 values are summed in FP64; FP32
+// values in compensated float pairs (exact to about 2^-48) up to one FP64 conversion per block
+// (GB300 issues FP64 at 1/64 of the FP32 rate).
+__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, double v, unsigned slot) {
   __shared__ double wsum[32];
   const int lin = threadIdx.x + blockDim.x * threadIdx.y;
+  const double m = warp_sum(v);
   if ((lin & 31) == 0) wsum[lin >> 5] = m;
   __syncthreads();
   if (lin == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)((blockDim.x * blockDim.y) >> 5); ++w) t += wsum[w];
+    if (t != 0.0) atomicAdd(mass_part + (slot & (MASS_SLOTS - 1)), t);
+  }
+}
+__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, float v, unsigned slot) {
+  __shared__ float whi[32], wlo[32];
+  const int lin = threadIdx.x + blockDim.x * threadIdx.y;
+  float hi = v, lo = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, bl), err);
+  }
+  if ((lin & 31) == 0) {
+    whi[lin >> 5] = hi;
+    wlo[lin >> 5] = lo;
+  }
+  __syncthreads();
+  if (lin == 0) {
+    float h = 0.0f, l = 0.0f;
+    for (int w = 0; w < (int)((blockDim.x * blockDim.y) >> 5); ++w) {
+      const float s = __fadd_rn(h, whi[w]);
+      const float bb = __fsub_rn(s, h);
+      const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(whi[w], bb));
+      h = s;
+      l = __fadd_rn(__fadd_rn(l, wlo[w]), err);
+    }
+    const double t = (double)h + (double)l;
     if (t != 0.0) atomicAdd(mass_part + (slot & (MASS_SLOTS - 1)), t);
   }
 }
@@ -396,8 +438,7 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
   } else if (valid && !(fl & F_NEAR)) {
     my_mass = collide_fluid<S, false>(src, dst, flags, psi, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
   }
-  const double m = warp_mass(my_mass);
-  add_mass_slot<S>(mass_part, m, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+  add_mass_slot(mass_part, my_mass, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 // Collision of the fluid cells next to a solid (the boundary-cell list built by the refill pass).
@@ -422,8 +463,7 @@ __global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __r
     const Cell c = cell_of(n, lat);
     my_mass += collide_fluid<S, true>(src, dst, flags, psi, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
   }
-  const double m = warp_mass(my_mass);
-  add_mass_slot<S>(mass_part, m, blockIdx.x * 7u + 3u);
+  add_mass_slot(mass_part, my_mass, blockIdx.x * 7u + 3u);
 }
 
 // ---- fused step: pull + density + psi + Shan-Chen force + collision in one pass ----------------
@@ -1132,7 +1172,8 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
           for (int dz = -1; dz <= 1 && !any; ++dz)
             for (int dy = -1; dy <= 1 && !any; ++dy)
               for (int dx = -1; dx <= 1 && !any; ++dx)
-                if ((dx | dy | dz) && (flags[at(gx + dx, gy + dy, gz + dz)] & F_COVER)) any = true;
+                if ((dx | dy | dz) && (flags[c.n + (unsigned)(c.ox[dx + 1] + c.oy[dy + 1] + c.oz[dz + 1])] & F_COVER))
+                  any = true;
           if (any) {
             R add[Q];
 #pragma unroll
@@ -1143,7 +1184,7 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
                   const int d2 = dx * dx + dy * dy + dz * dz;
                   if (d2 == 0) continue;
                   const int nxp = gx + dx, nyp = gy + dy, nzp = gz + dz;
-                  const long long nn = at(nxp, nyp, nzp);
+                  const long long nn = c.n + (unsigned)(c.ox[dx + 1] + c.oy[dy + 1] + c.oz[dz + 1]);
                   if (!(flags[nn] & F_COVER)) continue;
                   const int c6 = fluid_count(nxp, nyp, nzp, true);
                   int cnt;

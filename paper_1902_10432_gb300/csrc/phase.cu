@@ -181,6 +181,38 @@ __global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat
   if (t >= b.sz) return;
   TileCell c = tile_cell(b, t, lat);
   if (b.nnb && covered_by_lower_body(bodies, b, self, c.gx, c.gy, c.gz, lat)) return;
+  const long long n_cell = c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz);
+  bool shared = false;
+  for (int k = 0; k < b.nnb && !shared; ++k) {
+    const BodyDev& o = bodies[b.nbl[k]];
+    shared = tile_index(o.o, o.L, c.gx, c.gy, c.gz, lat) >= 0;
+  }
+  if (!shared) {
+    // this body alone: the general form below with one phase (S = phi after the clamp, which
+    // cannot exceed 1), without its per-phase arrays
+    double* p0 = arena + b.off + t;
+    const long long vb = dbits(*p0);
+    double S;
+    if (vb == 0 || vb == dbits(1.0)) {
+      S = vb == 0 ? 0.0 : 1.0;  // unchanged by the clamp and the flush
+    } else {
+      double v = fmin(1.0, fmax(0.0, *p0));
+      if (v < PHI_EPS) v = 0.0;
+      if (v > 1.0 - PHI_EPS) v = 1.0;
+      *p0 = v;
+      S = v;
+    }
+    uint16_t nf = 0;
+    if (1.0 - S < thr) {
+      nf = F_SOLID | (uint16_t)self;
+      if (!init && !(flags[n_cell] & F_SOLID)) {
+        nf |= F_COVER;
+        atomicAdd(&st->ncover, 1u);
+      }
+    }
+    flags[n_cell] = nf;
+    return;
+  }
   // bodies covering this cell, ascending id (self is the lowest)
   double* ptr[MAXNB + 1];
   int ids[MAXNB + 1];
@@ -193,26 +225,6 @@ __global__ void k_flags(BodyDev* bodies, double* arena, uint16_t* flags, Lat lat
     if (j >= 0) {
       ptr[m] = arena + o.off + j;
       ids[m++] = b.nbl[k];
-    }
-  }
-  const long long n_idx = c.gx + (long long)lat.nx * (c.gy + (long long)lat.ny * c.gz);
-  if (m == 1) {
-    // one body: phi exactly +0 or 1 passes the clamp, the flush and the renormalisation unchanged,
-    // and 1 - S is 1 (fluid) or 0 (solid, below any positive threshold)
-    const long long vb = dbits(*ptr[0]);
-    if (vb == 0 || vb == dbits(1.0)) {
-      uint16_t nf = 0;
-      // 1 - S < thr with S = 0 or 1, on the bit pattern of thr (signed order = numeric order)
-      const long long tb = dbits(thr);
-      if (vb != 0 ? tb > 0 : tb > dbits(1.0)) {
-        nf = F_SOLID | (uint16_t)self;
-        if (!init && !(flags[n_idx] & F_SOLID)) {
-          nf |= F_COVER;
-          atomicAdd(&st->ncover, 1u);
-        }
-      }
-      flags[n_idx] = nf;
-      return;
     }
   }
   double S = 0.0;
