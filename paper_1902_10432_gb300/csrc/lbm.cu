@@ -257,8 +257,9 @@ __device__ __forceinline__ R wall_term(const BodyDev& b, const Cell& c, const La
   return (R)2 * rho * (R)w_of(i) * cu * (R)3;
 }
 
-// Resident 128-thread blocks per SM requested for the collision kernel: occupancy matters more
-// than the few registers it spills (FP32: 64 registers, a 32-byte spill); FP64 needs more room.
+// Resident 128-thread blocks per SM requested for the bulk collision kernel: for FP32 occupancy
+// matters more than the few registers it spills (64 registers, a 20-byte spill; 7 blocks without a
+// spill measure the same); FP64 needs more room.
 #ifndef CBL_COLLIDE_MINB
 #define CBL_COLLIDE_MINB 8
 #endif
