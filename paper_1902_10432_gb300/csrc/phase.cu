@@ -451,6 +451,9 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
 // Semi-implicit Euler with dt = 1: V += F/M, X += V, omega += I_w^-1 T with I_w = R I_body R^T,
 // q <- normalize(exp(omega/2) q); fixed bodies keep V = omega = 0.
 __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
+  // FP64 throughout (GB300 issues FP64 at 1/64 of the FP32 rate and one thread runs this chain, so
+  // the operation count is kept small: one reciprocal of M and of |q|, sincos, and the world-frame
+  // inverse inertia applied as R (I_body^-1 (R^T T)) instead of being formed)
   double F[3], T[3];
   for (int a = 0; a < 3; ++a) {
     F[a] = parts[ACC_MOM_F + a] + parts[ACC_ADH_F + a] + parts[ACC_REP_F + a];
@@ -465,35 +468,34 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
     return;
   }
   const int n[3] = {lat.nx, lat.ny, lat.nz};
+  const double iM = 1.0 / b.M;
   for (int a = 0; a < 3; ++a) {
-    b.V[a] += F[a] / b.M;
+    b.V[a] += F[a] * iM;
     double x = b.X[a] + b.V[a];
-    x = fmod(x, (double)n[a]);
-    if (x < 0) x += n[a];
+    // periodic wrap (a move of less than a lattice side wraps once: the same value as fmod)
+    while (x >= (double)n[a]) x -= n[a];
+    while (x < 0) x += n[a];
     b.X[a] = x;
   }
-  // I_w^-1 = R I_body^-1 R^T (the body-frame inverse is computed once, at set-up)
-  double R[9], inv[9];
+  double R[9];
   quat_R(b.Q, R);
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) {
-      double acc = 0;
-      for (int k = 0; k < 3; ++k)
-        for (int l = 0; l < 3; ++l) acc += R[3 * a + k] * b.Ibinv[3 * k + l] * R[3 * c + l];
-      inv[3 * a + c] = acc;
-    }
-  for (int a = 0; a < 3; ++a) b.W[a] += inv[3 * a] * T[0] + inv[3 * a + 1] * T[1] + inv[3 * a + 2] * T[2];
-  double wn = sqrt(b.W[0] * b.W[0] + b.W[1] * b.W[1] + b.W[2] * b.W[2]);
+  double t1[3], t2[3];
+  for (int k = 0; k < 3; ++k) t1[k] = R[k] * T[0] + R[3 + k] * T[1] + R[6 + k] * T[2];  // R^T T
+  for (int k = 0; k < 3; ++k) t2[k] = b.Ibinv[3 * k] * t1[0] + b.Ibinv[3 * k + 1] * t1[1] + b.Ibinv[3 * k + 2] * t1[2];
+  for (int a = 0; a < 3; ++a) b.W[a] += R[3 * a] * t2[0] + R[3 * a + 1] * t2[1] + R[3 * a + 2] * t2[2];
+  const double wn = sqrt(b.W[0] * b.W[0] + b.W[1] * b.W[1] + b.W[2] * b.W[2]);
   if (wn > 0) {
-    double h = 0.5 * wn, s = sin(h) / wn;
-    double dq[4] = {cos(h), b.W[0] * s, b.W[1] * s, b.W[2] * s};
+    double sn, cs;
+    sincos(0.5 * wn, &sn, &cs);
+    const double s = sn / wn;
+    const double dq[4] = {cs, b.W[0] * s, b.W[1] * s, b.W[2] * s};
     const double* q = b.Q;
     double nq[4] = {dq[0] * q[0] - dq[1] * q[1] - dq[2] * q[2] - dq[3] * q[3],
                     dq[0] * q[1] + dq[1] * q[0] + dq[2] * q[3] - dq[3] * q[2],
                     dq[0] * q[2] - dq[1] * q[3] + dq[2] * q[0] + dq[3] * q[1],
                     dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0]};
-    double qn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
-    for (int a = 0; a < 4; ++a) b.Q[a] = nq[a] / qn;
+    const double iq = 1.0 / sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+    for (int a = 0; a < 4; ++a) b.Q[a] = nq[a] * iq;
   }
 }
 
