@@ -40,9 +40,10 @@ def kernels_per_step(nb, mpf, fused):
     return k
 
 
-# DRAM bytes per k_collide launch from the committed ncu capture (profiles/k_collide_spheres2_fp32.md),
-# valid only for the source it was taken on
-PROFILED = {("spheres2", "fp32", "7b0303e2e1ff"): 344204800 + 281772032}
+# DRAM bytes of one collision pass (k_collide + k_collide_near) from the committed one-pass ncu
+# captures (profiles/collision_pass_spheres2_*.md), valid only for the source they were taken on
+PROFILED = {("spheres2", "fp32", "7e864b04922e"): 347381248 + 272935936 + 12042240 + 272128,
+            ("spheres2", "fp16dev", "7e864b04922e"): 187728384 + 123556608 + 11989504 + 223744}
 
 
 def profiled_traffic(workload_name, prec):
