@@ -32,9 +32,10 @@ POP_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 
 def kernels_per_step(nb, mpf, fused):
     """Kernel launches of one step of the library's graph: density + bulk collision + near-solid
-    collision (or the single fused pass), then with bodies the force pass, repulsion (two or more
-    bodies), body update, three advection sweeps, kinetics (MPF on), flags and refill."""
-    k = 1 if fused else 2
+    collision (or the single fused pass), with bodies the force pass, repulsion (two or more bodies),
+    body update, three advection sweeps, kinetics (MPF on), flags and refill, and the closing kernel
+    (fluid mass, buffer flip)."""
+    k = (1 if fused else 2) + 1
     if nb:
         k += (0 if fused else 1) + 1 + (1 if nb > 1 else 0) + 1 + 3 + (1 if mpf else 0) + 2
     return k

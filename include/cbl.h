@@ -176,8 +176,8 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
  * and FP16-deviation storage this is the single fused pass that also computes psi), 2 solid-fluid
  * force on the
  * bodies (momentum exchange and adhesion, FP64 sums), 3 solid-solid repulsion, 4 rigid-body update,
- * 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle flags, 8 cover refill
- * and boundary-cell list. */
+ * 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle flags, 8 cover refill,
+ * boundary-cell list and the end of the step (fluid mass, buffer flip). */
 
 /* Run nsteps time steps launched kernel by kernel (not through the graph) with CUDA events recorded
  * on the context's stream between the phases, synchronise, and write the mean duration per step of
@@ -190,9 +190,9 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
  *                  CBL_ERR_UNSUPPORTED otherwise);
  *   "fused_tz"     z extent of a fused block (0 = derived from the SM count);
  *   "lbm_block_x"  x extent of the 128-thread blocks of the split kernels: 32 (default), 64, 128;
- *   "graph_branches" 1 (default) = with bodies, the collision of the fluid cells next to a solid and
- *                  the solid-solid repulsion run on a second branch of the step graph beside the
- *                  bulk collision; 0 = one chain.
+ *   "graph_branches" 1 (default) = with bodies, the collision of the fluid cells next to a solid,
+ *                  the solid-fluid force pass and the solid-solid repulsion run on a second branch
+ *                  of the step graph beside the bulk collision; 0 = one chain.
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 

@@ -124,7 +124,11 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
     }
     ctx->own_stream = true;
   }
-  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+  // the side branch carries the chain of short latency-bound kernels: highest priority, so that
+  // their blocks are scheduled ahead of the queued blocks of the bulk collision
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->s);
@@ -299,7 +303,7 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
   // first boundary-cell list (no cover events yet, so the pass only scans) and member boxes
   reset_member_boxes(ctx);
   launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
+                ctx->arena, ctx->p.member_threshold, ctx->mbox, 0, ctx->s);
   CK(cudaMemsetAsync(ctx->diag_rho, 0, N * 8, ctx->s));
   CK(cudaMemsetAsync(ctx->diag_vel, 0, N * 24, ctx->s));
   CK(cudaGetLastError());
@@ -350,39 +354,56 @@ static void enqueue_lbm(cbl_ctx* ctx, int phases, cudaStream_t s) {
 }
 
 // One step, enqueued for capture into a graph. With bodies, the collision of the cells next to a
-// solid and the solid-solid repulsion run on a side branch beside the bulk collision (they touch
-// other cells, or only the phase fields, and add into the force accumulators with atomics); the
-// force pass joins both.
+// solid, the solid-fluid force pass and the solid-solid repulsion run on a side branch beside the
+// bulk collision (they touch other cells, or only the phase fields, and add into the force
+// accumulators with atomics); the body update joins both.
 static void enqueue_step(cbl_ctx* ctx) {
   const int nb = (int)ctx->hb.size();
+  auto phase_update = [&](cudaStream_t s) {
+    launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->rtab,
+                  ctx->Lmax, s);
+    if (ctx->pp.mpf) launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, s);
+  };
+  auto flags_refill = [&](cudaStream_t s) {
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
+                 s);
+    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                  ctx->arena, ctx->p.member_threshold, ctx->mbox, 1, s);
+  };
   if (nb && !ctx->fused_tz && ctx->branches) {
+    // The bulk collision (every cell without a solid neighbour) runs beside the chain that needs only
+    // the source populations, psi and the phase fields: collision of the cells next to a solid, force
+    // pass, repulsion, body update, advection, kinetics. That chain is the longer path and is made
+    // of small latency-bound kernels, so it runs on the high-priority side stream, whose blocks are
+    // scheduled ahead of the bulk collision's queued ones. The flag update and the refill rewrite
+    // what the bulk collision reads and writes, so they wait for both.
     enqueue_lbm(ctx, 1, ctx->s);
     cudaEventRecord(ctx->ev_fork, ctx->s);
     cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     enqueue_lbm(ctx, 4, ctx->side);
+    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+                    ctx->nbuf, ctx->pp.G, ctx->side);
     launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->side);
+    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox,
+                  ctx->side);
+    phase_update(ctx->side);
     cudaEventRecord(ctx->ev_join, ctx->side);
     enqueue_lbm(ctx, 2, ctx->s);
     cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0);
-    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
-                    ctx->nbuf, ctx->pp.G, ctx->s);
+    flags_refill(ctx->s);
   } else {
     enqueue_lbm(ctx, 7, ctx->s);
     launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->s);
-    if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
+    if (nb) {
+      launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
+      launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax,
+                    ctx->mbox, ctx->s);
+      phase_update(ctx->s);
+      flags_refill(ctx->s);
+    }
   }
-  launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part, ctx->st,
-                ctx->rtab, ctx->Lmax, ctx->mbox, ctx->s);
-  if (nb) {
-    launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->rtab,
-                  ctx->Lmax, ctx->s);
-    if (ctx->pp.mpf) launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
-    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
-                 ctx->s);
-    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                  ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
-  }
+  launch_finish(ctx->mass_part, ctx->n_mass_part, ctx->st, ctx->s);
 }
 
 cbl_status cbl_step(cbl_ctx* ctx, int nsteps) {
@@ -428,8 +449,8 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     CK(cudaEventRecord(ev[3], ctx->s));
     if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
     CK(cudaEventRecord(ev[4], ctx->s));
-    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->mass_part, ctx->n_mass_part,
-                  ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox, ctx->s);
+    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox,
+                  ctx->s);
     CK(cudaEventRecord(ev[5], ctx->s));
     if (nb)
       launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->rtab,
@@ -444,7 +465,8 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     CK(cudaEventRecord(ev[8], ctx->s));
     if (nb)
       launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                    ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
+                    ctx->arena, ctx->p.member_threshold, ctx->mbox, 1, ctx->s);
+    launch_finish(ctx->mass_part, ctx->n_mass_part, ctx->st, ctx->s);
     CK(cudaEventRecord(ev[9], ctx->s));
     CK(cudaGetLastError());
     CK(cudaEventSynchronize(ev[9]));
@@ -656,7 +678,7 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
     launch_clear_stale(ctx->lat, ctx->flags, ctx->s);
     reset_member_boxes(ctx);
     launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
-                  ctx->arena, ctx->p.member_threshold, ctx->mbox, ctx->s);
+                  ctx->arena, ctx->p.member_threshold, ctx->mbox, 0, ctx->s);
     CK(cudaGetLastError());
     // the host copy h (and the device memcpy source) must outlive the copy
     CK(cudaStreamSynchronize(ctx->s));

@@ -176,7 +176,7 @@ void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags
                        const double* u, cudaStream_t s);
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, int nb,
                    int max_tile, StepState* st, int* blist, const double* arena, double member_thr, int* mbox,
-                   cudaStream_t s);
+                   int next, cudaStream_t s);
 
 void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
                              cudaStream_t s);
@@ -192,8 +192,8 @@ void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, do
 void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
                       const PhysParams& pp, const int* mbox, cudaStream_t s);
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   double* mass_part, unsigned n_mass_part, StepState* st, double* rtab, int Lmax, int* mbox,
-                   cudaStream_t s);
+                   StepState* st, double* rtab, int Lmax, int* mbox, cudaStream_t s);
+void launch_finish(double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
                    StepState* st, const double* rtab, int Lmax, cudaStream_t s);
 void set_repulsion_offsets(double rc, double e0, int nrep, cudaStream_t s);

@@ -1115,9 +1115,11 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
                                                 uint16_t* __restrict__ flags,
                                                 const BodyDev* __restrict__ bodies, StepState* st, int* blist,
                                                 Lat lat, const double* __restrict__ arena, double member_thr,
-                                                int* __restrict__ mbox) {
+                                                int* __restrict__ mbox, int next) {
   using R = typename St<S>::R;
-  S* __restrict__ f = st->parity ? fb : fa;  // the state buffer written by this step's collision
+  // the current state: the buffer this step's collision wrote (next = 1: the parity flips at the end
+  // of the step) or, outside a step, the buffer the parity names
+  S* __restrict__ f = (st->parity ^ next) ? fb : fa;
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1437,17 +1439,19 @@ void launch_init_fluid(int prec, const Lat& lat, void* f, const uint16_t* flags,
 
 void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, int nb,
                    int max_tile, StepState* st, int* blist, const double* arena, double member_thr, int* mbox,
-                   cudaStream_t s) {
+                   int next, cudaStream_t s) {
   if (nb == 0) return;
   const int T = 256;
   dim3 grid((unsigned)((max_tile + T - 1) / T), (unsigned)nb);
   if (prec == 0)
-    k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, blist, lat, arena, member_thr, mbox);
+    k_refill<double><<<grid, T, 0, s>>>((double*)fa, (double*)fb, flags, bodies, st, blist, lat, arena, member_thr,
+                                        mbox, next);
   else if (prec == 1)
-    k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, blist, lat, arena, member_thr, mbox);
+    k_refill<float><<<grid, T, 0, s>>>((float*)fa, (float*)fb, flags, bodies, st, blist, lat, arena, member_thr, mbox,
+                                       next);
   else
     k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, blist, lat, arena, member_thr,
-                                        mbox);
+                                        mbox, next);
 }
 
 }  // namespace cbl

@@ -500,8 +500,7 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
 }
 
 __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                                                double* mass_part, unsigned n_mass_part, StepState* st,
-                                                Lat lat, double* rtab, int Lmax, int* mbox) {
+                                                StepState* st, Lat lat, double* rtab, int Lmax, int* mbox) {
   const int n[3] = {lat.nx, lat.ny, lat.nz};
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     BodyDev& b = bodies[i];
@@ -531,7 +530,17 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
     const BodyDev& b = bodies[i];
     if (l < b.L[a]) rtab[k] = mimg(wrapi(b.o[a] + l, n[a]) - b.Xprev[a], n[a]);
   }
-  // fluid mass of this step: fixed-order sum of the per-block partials
+  build_lists(bodies, nb, lat, st);
+  if (threadIdx.x == 0) {
+    st->nbnd = 0;    // the boundary list is rebuilt by the refill pass after the new flags
+    st->ncover = 0;  // counted by the flag pass
+  }
+}
+
+// End of a step: the fluid mass (fixed-order sum of the collision's per-block partials, which are
+// cleared) and the population buffer flip. The bulk collision may run beside the body update, so
+// neither can happen earlier.
+__global__ void __launch_bounds__(256) k_finish(double* mass_part, unsigned n_mass_part, StepState* st) {
   __shared__ double red[256];
   double sm = 0.0;
   for (unsigned k = threadIdx.x; k < n_mass_part; k += blockDim.x) {
@@ -544,12 +553,9 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  build_lists(bodies, nb, lat, st);
   if (threadIdx.x == 0) {
     st->last_mass = red[0];
     st->parity ^= 1;
-    st->nbnd = 0;    // the boundary list is rebuilt by the refill pass after the new flags
-    st->ncover = 0;  // counted by the flag pass
   }
 }
 
@@ -994,9 +1000,11 @@ void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_til
                                                        pp.member_threshold, pp.eta, mbox);
 }
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   double* mass_part, unsigned n_mass_part, StepState* st, double* rtab, int Lmax, int* mbox,
-                   cudaStream_t s) {
-  k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, mass_part, n_mass_part, st, lat, rtab, Lmax, mbox);
+                   StepState* st, double* rtab, int Lmax, int* mbox, cudaStream_t s) {
+  if (nb) k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, st, lat, rtab, Lmax, mbox);
+}
+void launch_finish(double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {
+  k_finish<<<1, 256, 0, s>>>(mass_part, n_mass_part, st);
 }
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
                    StepState* st, const double* rtab, int Lmax, cudaStream_t s) {
