@@ -186,7 +186,9 @@ def bench_reference(args, rank, world):
 
 
 def bench_batch(args, rank, world, local_rank):
-    """64 independent two-sphere instances: one batched graph vs the instances run one after another."""
+    """64 independent two-sphere instances: one batched graph vs the instances run one after another.
+    On several GPUs each rank runs its share of the instances (no collective on the data path); the
+    time is the slowest rank's and the work is the total."""
     import torch
 
     torch.cuda.set_device(local_rank)
@@ -194,10 +196,12 @@ def bench_batch(args, rank, world, local_rank):
 
     if not os.path.exists(os.path.join(ROOT, "paper_1902_10432_gb300", "_lib", "libcbl.so")):
         __graft_entry__.build()
-    from paper_1902_10432_gb300 import autotune, cbl, workloads
+    from paper_1902_10432_gb300 import autotune, cbl, ranks, workloads
 
-    ws = workloads.batch64(seed=0, prec=args.precision)
-    cells = sum(w.ncells for w in ws)
+    rk = ranks.Ranks("nccl")
+    ws_all = workloads.batch64(seed=0, prec=args.precision)
+    ws = [ws_all[i] for i in ranks.shard(len(ws_all), rk.rank, rk.world)]
+    cells_mine = sum(w.ncells for w in ws)
     sims = []
     choices = {}
     for w in ws:
@@ -210,11 +214,12 @@ def bench_batch(args, rank, world, local_rank):
     for s in sims:
         s.step(args.warmup)
     torch.cuda.synchronize()
+    rk.barrier()
     t0 = time.perf_counter()
     for s in sims:
         s.step(args.steps)
         torch.cuda.synchronize()
-    seq_s = time.perf_counter() - t0
+    seq_s = rk.max(time.perf_counter() - t0)
     batch = cbl.Batch(sims)
     batch.step(args.warmup)
     batch.sync()
@@ -223,24 +228,29 @@ def bench_batch(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
+        rk.barrier()
         t1 = time.perf_counter()
         batch.step(args.steps)
         batch.sync()
         bat_s = time.perf_counter() - t1
-    value = world * cells * args.steps / bat_s / 1e6
+        rk.barrier()
+    bat_s = rk.max(bat_s)
+    cells = rk.sum(cells_mine)
+    value = cells * args.steps / bat_s / 1e6
     line = {"metric": "aggregate MLUPS (batched)", "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * bat_s / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": "batch64: 64 two-sphere instances, boxes U{64..128}^3, R U[10,24], "
                                    "liquid fraction U[0.01,0.2], angle U[30,90] deg, seed 0",
-                       "cells": cells, "autotune_choices": choices},
+                       "cells": int(cells), "autotune_choices": choices,
+                       "parallelism": "instances sharded over %d GPUs" % world if world > 1 else "single GPU"},
             "sequential_mlups": cells * args.steps / seq_s / 1e6,
             "speedup_vs_sequential": seq_s / bat_s, "clocks": clk.summary(),
             "gpu_launches": args.steps * sum(n * kernels_per_step(2, 1, json.loads(c).get("lbm_variant") == 1)
                                              for c, n in choices.items())}
-    if rank == 0:
+    if rk.root:
         print(json.dumps(line), flush=True)
     batch.close()
     return 0
@@ -327,17 +337,12 @@ def bench_cuda(args, rank, world, local_rank):
         __graft_entry__.build()
     from paper_1902_10432_gb300 import cbl, workloads
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+    from paper_1902_10432_gb300 import ranks
 
-        dist.init_process_group("nccl")
+    rk = ranks.Ranks("nccl")
     w = workload(args.workload, args.precision)
     prec = args.precision
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = rk.barrier
 
     sim = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
     workloads.build(sim, w)
@@ -355,11 +360,7 @@ def bench_cuda(args, rank, world, local_rank):
         ev1.synchronize()
         torch.cuda.synchronize()
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = rk.max(ev0.elapsed_time(ev1))
     value = world * w.ncells * args.steps / (ms_max * 1e-3) / 1e6
 
     # per-kernel durations (CUDA events between the phases, same stream, kernel-by-kernel launch)
@@ -377,7 +378,7 @@ def bench_cuda(args, rank, world, local_rank):
     s2.step(args.steps)
     rho, vel, phf = s2.fields()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = rk.max(time.perf_counter() - t0)
     s2.close()
     h2d = w.ncells * (1 + 8)  # liquid mask -> initial density field uploaded by cbl_init_fluid
     d2h = w.ncells * (8 + 24 + 8)
@@ -407,7 +408,7 @@ def bench_cuda(args, rank, world, local_rank):
             "phases_ms": {k: round(v, 5) for k, v in phases.items()},
             "gpu_launches": kernels_per_step(len(w.bodies), w.params.get("mpf_kinetics", 1), False) * args.steps,
             "clocks": clk.summary(),
-            "e2e": {"value": w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+            "e2e": {"value": world * w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "what": "create + bodies + init from host mask + K steps + fields to host, wall clock"},
             "fluid_mass": mass, "device_error": err,
@@ -415,8 +416,7 @@ def bench_cuda(args, rank, world, local_rank):
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rk.close()
     return 0
 
 
