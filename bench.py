@@ -55,8 +55,8 @@ def profiled_traffic(workload_name, prec):
     return PROFILED.get((workload_name, prec, h))
 
 
-def alg_bytes_per_cell(prec):
-    return 2 * 19 * POP_BYTES[prec] + 2
+def alg_bytes_per_cell(prec, q=19):
+    return 2 * q * POP_BYTES[prec] + 2
 
 
 def measured_peaks():
@@ -68,16 +68,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def workload(name, prec):
+def workload(name, prec, q=19):
     from paper_1902_10432_gb300 import workloads
 
     if name == "spheres2":
-        return workloads.spheres2(seed=0, prec=prec)
-    if name == "plates48":
-        return workloads.plates48(prec=prec)
-    if name == "tetra4":
-        return workloads.tetra4(seed=0, prec=prec)
-    raise ValueError(name)
+        w = workloads.spheres2(seed=0, prec=prec)
+    elif name == "plates48":
+        w = workloads.plates48(prec=prec)
+    elif name == "tetra4":
+        w = workloads.tetra4(seed=0, prec=prec)
+    else:
+        raise ValueError(name)
+    w.params["q"] = q
+    return w
 
 
 class ClockSampler:
@@ -168,7 +171,7 @@ def cpu_baseline(w, budget_s=20.0):
 def bench_reference(args, rank, world):
     if rank != 0:
         return 0
-    w = workload(args.workload, args.precision)
+    w = workload(args.workload, args.precision, args.q)
     threads = os.cpu_count() or 1
     times = run_oracle_steps(w, args.steps, args.warmup, threads)
     tot = sum(times)
@@ -176,7 +179,7 @@ def bench_reference(args, rank, world):
     line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "%s %dx%dx%d D3Q19, 2 free spheres R=20" % (w.name, w.nx, w.ny, w.nz),
+            "config": {"workload": "%s %dx%dx%d D3Q%d, 2 free spheres R=20" % (w.name, w.nx, w.ny, w.nz, args.q),
                        "cells": w.ncells, "inputs_vs_l2": "CPU run"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                              "sample": "%d time steps after %d warm-up steps, full lattice" % (args.steps, args.warmup)},
@@ -340,7 +343,7 @@ def bench_cuda(args, rank, world, local_rank):
     from paper_1902_10432_gb300 import ranks
 
     rk = ranks.Ranks("nccl")
-    w = workload(args.workload, args.precision)
+    w = workload(args.workload, args.precision, args.q)
     prec = args.precision
     barrier = rk.barrier
 
@@ -385,7 +388,7 @@ def bench_cuda(args, rank, world, local_rank):
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        bpc = alg_bytes_per_cell(prec)
+        bpc = alg_bytes_per_cell(prec, args.q)
         t_col = phases["collide"] * 1e-3
         achieved = bpc * w.ncells / t_col / 1e9
         line = {
@@ -393,8 +396,8 @@ def bench_cuda(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[prec], "data": "synthetic",
-            "config": {"workload": "%s %dx%dx%d D3Q19, 2 free spheres R=20, %s populations, MPF kinetics on"
-                                   % (w.name, w.nx, w.ny, w.nz, prec),
+            "config": {"workload": "%s %dx%dx%d D3Q%d, 2 free spheres R=20, %s populations, MPF kinetics on"
+                                   % (w.name, w.nx, w.ny, w.nz, args.q, prec),
                        "cells": w.ncells, "seed": w.meta.get("seed"), "theta_deg": w.meta.get("theta_deg"),
                        "liquid_fraction_of_solid": round(w.meta.get("liquid_fraction_of_solid", 0), 4),
                        "inputs_vs_l2": "populations 2 x %.0f MB > 129 MB L2 (no flush needed)"
@@ -427,6 +430,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
+    ap.add_argument("--q", type=int, default=19, choices=[19, 27], help="velocity set: D3Q19 or D3Q27")
     ap.add_argument("--workload", default="spheres2",
                     choices=["spheres2", "plates48", "tetra4", "batch64", "surrogate"])
     ap.add_argument("--sur-equil", type=int, default=800)

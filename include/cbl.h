@@ -129,11 +129,17 @@ cbl_status cbl_read_fields(cbl_ctx* ctx, double* rho, double* vel, double* phi_f
 /* Obstacle flags: solid (N bytes, 0/1) and owner body id (N int32, -1 on fluid). Host pointers. */
 cbl_status cbl_read_flags(cbl_ctx* ctx, unsigned char* solid, int32_t* owner);
 
-/* Post-collision populations of the current state as doubles, laid out [direction][cell] (19 * N),
- * in this library's direction order: rest, +x, -x, +y, -y, +z, -z, then the edge directions
- * (+x+y), (-x-y), (+x-y), (-x+y), (+x+z), (-x-z), (+x-z), (-x+z), (+y+z), (-y-z), (+y-z), (-y+z).
+/* Post-collision populations of the current state as doubles, laid out [direction][cell] (q * N),
+ * in this library's direction order (cbl_velocity_set): rest, +x, -x, +y, -y, +z, -z, then the edge
+ * directions (+x+y), (-x-y), (+x-y), (-x+y), (+x+z), (-x-z), (+x-z), (-x+z), (+y+z), (-y-z), (+y-z),
+ * (-y+z), and for D3Q27 the corners (+++), (---), (++-), (--+), (+-+), (-+-), (-++), (+--).
  * on_device != 0: `out` is a device pointer; otherwise a host pointer. */
 cbl_status cbl_read_populations(cbl_ctx* ctx, double* out, int on_device);
+
+/* The context's velocity set (Sec. 3.2.1): q (19 or 27), the directions c (host array q*3 ints,
+ * may be NULL) and the weights w (host array q doubles, may be NULL), in the order of
+ * cbl_read_populations. */
+cbl_status cbl_velocity_set(cbl_ctx* ctx, int* q, int* c, double* w);
 
 /* Dense phase field of one body (N doubles, host). */
 cbl_status cbl_read_phi(cbl_ctx* ctx, int body, double* phi_host);

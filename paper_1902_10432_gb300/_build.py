@@ -9,7 +9,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcbl.so")
-SOURCES = ["lbm.cu", "phase.cu", "capi.cu", "mlp.cu"]
+SOURCES = ["lbm.cu", "lbm27.cu", "phase.cu", "capi.cu", "mlp.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
@@ -32,7 +32,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or _stale(o, [s] + headers):
+        deps = [s] + headers + ([os.path.join(CSRC, "lbm.cu")] if src == "lbm27.cu" else [])
+        if force or _stale(o, deps):
             jobs.append([NVCC, *FLAGS, "-c", s, "-o", o])
 
     def run(cmd):

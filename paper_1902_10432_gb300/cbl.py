@@ -69,6 +69,7 @@ SIGNATURES = {
     "cbl_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "cbl_read_fields": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "cbl_read_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "cbl_velocity_set": (ctypes.c_int, [_P, _P, _P, _P]),
     "cbl_read_flags": (ctypes.c_int, [_P, _P, _P]),
     "cbl_read_phi": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cbl_read_body_forces": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -183,6 +184,7 @@ class Sim:
             p.stream = ctypes.c_void_p(self._stream.cuda_stream)
             self._alloc = torch_allocator(stream=self._stream)
         self.params = cfg
+        self.q = int(cfg["q"])
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         h = ctypes.c_void_p()
@@ -248,11 +250,20 @@ class Sim:
         ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
         self._ck(self._lib.cbl_read_fields(self._h, ptr(rho), ptr(vel), ptr(phi_fluid), 1))
 
+    def velocity_set(self):
+        """Directions c (q x 3 ints) and weights w (q) in the order of populations()."""
+        q = ctypes.c_int()
+        c = np.empty(3 * self.q, np.int32)
+        w = np.empty(self.q)
+        self._ck(self._lib.cbl_velocity_set(self._h, ctypes.byref(q), _vp(c), _vp(w)))
+        return c.reshape(self.q, 3), w
+
     def populations(self):
-        """Current post-collision populations, float64 [19][nz][ny][nx] in the library's order."""
-        out = np.empty(19 * self.N)
+        """Current post-collision populations, float64 [q][nz][ny][nx] in the library's order
+        (velocity_set() gives the directions and weights)."""
+        out = np.empty(self.q * self.N)
         self._ck(self._lib.cbl_read_populations(self._h, _vp(out), 0))
-        return out.reshape((19,) + self.shape)
+        return out.reshape((self.q,) + self.shape)
 
     def flags(self):
         s = np.empty(self.N, np.uint8)

@@ -28,6 +28,7 @@ struct cbl_ctx {
   int prec = 1;
   size_t elem = 4;
   PhysParams pp;
+  LbmOps ops;  // launchers of the context's velocity set
   void *fa = nullptr, *fb = nullptr, *psi = nullptr;
   void* nbuf = nullptr;  // (rho, psi) of the fluid cells next to a solid, written by the collision
   uint16_t* flags = nullptr;
@@ -102,7 +103,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   if (!params || !out) return fail(nullptr, CBL_ERR_ARG, "params and out must not be NULL");
   const cbl_params& p = *params;
   if (p.nx < 4 || p.ny < 4 || p.nz < 4) return fail(nullptr, CBL_ERR_ARG, "lattice sides must be >= 4");
-  if (p.q != 19) return fail(nullptr, CBL_ERR_UNSUPPORTED, "only D3Q19 is built");
+  if (p.q != 19 && p.q != 27) return fail(nullptr, CBL_ERR_UNSUPPORTED, "velocity sets: D3Q19 or D3Q27");
   if (!(p.tau > 0.5)) return fail(nullptr, CBL_ERR_ARG, "tau must be > 0.5");
   if (!(p.rho0 > 0)) return fail(nullptr, CBL_ERR_ARG, "rho0 must be > 0");
   if (p.prec < CBL_FP64 || p.prec > CBL_FP16DEV) return fail(nullptr, CBL_ERR_ARG, "unknown precision");
@@ -111,6 +112,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, CBL_ERR_ARG, "allocator callbacks missing");
   cbl_ctx* ctx = new cbl_ctx();
   ctx->p = p;
+  ctx->ops = lbm_ops(p.q);
   if (alloc) {
     ctx->alloc = *alloc;
     ctx->user_alloc = true;
@@ -160,8 +162,8 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   fill_float_params(pp);
 
   const size_t N = (size_t)ctx->lat.N;
-  ctx->fa = dalloc(ctx, (size_t)ctx->lat.Ns * Q * ctx->elem);
-  ctx->fb = dalloc(ctx, (size_t)ctx->lat.Ns * Q * ctx->elem);
+  ctx->fa = dalloc(ctx, (size_t)ctx->lat.Ns * ctx->ops.q * ctx->elem);
+  ctx->fb = dalloc(ctx, (size_t)ctx->lat.Ns * ctx->ops.q * ctx->elem);
   // the split density + collision pair is the default; the fused single-pass variant is chosen
   // per lattice by cbl_tune (it needs no psi array but holds fewer threads per SM)
   ctx->psi = dalloc(ctx, N * (ctx->prec == 0 ? 8 : 4));
@@ -185,7 +187,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   cudaMemsetAsync(ctx->flags, 0, N * 2, ctx->s);
   cudaMemsetAsync(ctx->st, 0, sizeof(StepState), ctx->s);
   cudaMemsetAsync(ctx->mass_part, 0, (size_t)ctx->n_mass_part * 8, ctx->s);
-  set_fp16_weights(ctx->s);
+  ctx->ops.set_fp16_weights(ctx->s);
   set_repulsion_offsets(p.rc, p.e0, p.nrep, ctx->s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -299,10 +301,10 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
   if (!drho || (u_host && !du)) return fail(ctx, CBL_ERR_OOM, "device allocation failed (initial fields)");
   CK(cudaMemcpyAsync(drho, rho_host, N * 8, cudaMemcpyHostToDevice, ctx->s));
   if (du) CK(cudaMemcpyAsync(du, u_host, N * 24, cudaMemcpyHostToDevice, ctx->s));
-  launch_init_fluid(ctx->prec, ctx->lat, ctx->fa, ctx->flags, drho, du, ctx->s);
+  ctx->ops.init_fluid(ctx->prec, ctx->lat, ctx->fa, ctx->flags, drho, du, ctx->s);
   // first boundary-cell list (no cover events yet, so the pass only scans) and member boxes
   reset_member_boxes(ctx);
-  launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+  ctx->ops.refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
                 ctx->arena, ctx->p.member_threshold, ctx->mbox, 0, ctx->s);
   CK(cudaMemsetAsync(ctx->diag_rho, 0, N * 8, ctx->s));
   CK(cudaMemsetAsync(ctx->diag_vel, 0, N * 24, ctx->s));
@@ -344,10 +346,10 @@ cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const dou
 static void enqueue_lbm(cbl_ctx* ctx, int phases, cudaStream_t s) {
   if (ctx->fused_tz) {
     if (phases & 2)
-      launch_lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
+      ctx->ops.lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
                        ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->nbuf, s);
   } else {
-    launch_lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+    ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
                     (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
                     s, phases);
   }
@@ -367,7 +369,7 @@ static void enqueue_step(cbl_ctx* ctx) {
   auto flags_refill = [&](cudaStream_t s) {
     launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
                  s);
-    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+    ctx->ops.refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
                   ctx->arena, ctx->p.member_threshold, ctx->mbox, 1, s);
   };
   if (nb && !ctx->fused_tz && ctx->branches) {
@@ -381,7 +383,7 @@ static void enqueue_step(cbl_ctx* ctx) {
     cudaEventRecord(ctx->ev_fork, ctx->s);
     cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     enqueue_lbm(ctx, 4, ctx->side);
-    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+    ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->side);
     launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->side);
     launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox,
@@ -393,7 +395,7 @@ static void enqueue_step(cbl_ctx* ctx) {
     flags_refill(ctx->s);
   } else {
     enqueue_lbm(ctx, 7, ctx->s);
-    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+    ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->s);
     if (nb) {
       launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
@@ -444,7 +446,7 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     CK(cudaEventRecord(ev[1], ctx->s));
     enqueue_lbm(ctx, 6, ctx->s);
     CK(cudaEventRecord(ev[2], ctx->s));
-    launch_boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+    ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->s);
     CK(cudaEventRecord(ev[3], ctx->s));
     if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
@@ -464,7 +466,7 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
                    ctx->s);
     CK(cudaEventRecord(ev[8], ctx->s));
     if (nb)
-      launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+      ctx->ops.refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
                     ctx->arena, ctx->p.member_threshold, ctx->mbox, 1, ctx->s);
     launch_finish(ctx->mass_part, ctx->n_mass_part, ctx->st, ctx->s);
     CK(cudaEventRecord(ev[9], ctx->s));
@@ -500,16 +502,31 @@ cbl_status cbl_read_fields(cbl_ctx* ctx, double* rho, double* vel, double* phi_f
   return CBL_OK;
 }
 
+cbl_status cbl_velocity_set(cbl_ctx* ctx, int* q, int* c, double* w) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  const int Qn = ctx->ops.q;
+  if (q) *q = Qn;
+  for (int i = 0; i < Qn; ++i) {
+    if (c) {
+      c[3 * i] = Qn == 27 ? q27::cx_of(i) : q19::cx_of(i);
+      c[3 * i + 1] = Qn == 27 ? q27::cy_of(i) : q19::cy_of(i);
+      c[3 * i + 2] = Qn == 27 ? q27::cz_of(i) : q19::cz_of(i);
+    }
+    if (w) w[i] = Qn == 27 ? q27::w_of(i) : q19::w_of(i);
+  }
+  return CBL_OK;
+}
+
 cbl_status cbl_read_populations(cbl_ctx* ctx, double* out, int on_device) {
   if (!ctx || !out) return fail(ctx, CBL_ERR_ARG, "NULL argument");
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
-  const size_t bytes = (size_t)Q * ctx->lat.N * 8;
+  const size_t bytes = (size_t)ctx->ops.q * ctx->lat.N * 8;
   double* dst = out;
   if (!on_device) {
     if (!ctx->popbuf && !(ctx->popbuf = (double*)dalloc(ctx, bytes))) return fail(ctx, CBL_ERR_OOM, "population buffer");
     dst = ctx->popbuf;
   }
-  launch_read_populations(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, dst, ctx->s);
+  ctx->ops.read_populations(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, dst, ctx->s);
   CK(cudaGetLastError());
   if (!on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
@@ -664,7 +681,7 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
     }
     // solid cells hand nothing over (a node covered by the last pass still holds its populations,
     // already given to its neighbours): zero them, then clear the flags under the current tiles
-    launch_zero_solid(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->s);
+    ctx->ops.zero_solid(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->s);
     launch_clear_tile_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->flags, ctx->s);
     for (BodyDev& b : h) mirror_f(b);
     CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
@@ -677,7 +694,7 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
                  ctx->s);
     launch_clear_stale(ctx->lat, ctx->flags, ctx->s);
     reset_member_boxes(ctx);
-    launch_refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+    ctx->ops.refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
                   ctx->arena, ctx->p.member_threshold, ctx->mbox, 0, ctx->s);
     CK(cudaGetLastError());
     // the host copy h (and the device memcpy source) must outlive the copy
@@ -736,12 +753,13 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "lbm_variant must be 0 or 1");
     if (v == 1 && ctx->prec != 1) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass stores FP32");
-    ctx->fused_tz = v ? (ctx->fused_tz_req > 0 ? ctx->fused_tz_req : fused_tz(ctx->lat, 2)) : 0;
+    if (v == 1 && ctx->ops.q != 19) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass is D3Q19 only");
+    ctx->fused_tz = v ? (ctx->fused_tz_req > 0 ? ctx->fused_tz_req : ctx->ops.fused_tz(ctx->lat, 2)) : 0;
   } else if (k == "fused_tz") {
     const int v = (int)value;
     if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
     ctx->fused_tz_req = v;
-    if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : fused_tz(ctx->lat, 2);
+    if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : ctx->ops.fused_tz(ctx->lat, 2);
   } else if (k == "graph_branches") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "graph_branches must be 0 or 1");

@@ -9,9 +9,12 @@
 namespace cbl {
 
 // ------------------------------------------------------------------------------------------
-// D3Q19 velocity set (Sec. 3.2.1 gives D3Q27; D3Q19 is the textbook |c|^2 <= 2 subset with
-// weights 1/3, 1/18, 1/36). Order: rest, +-x, +-y, +-z, then the 12 edge directions; each odd
-// index i is followed by its opposite, so opp(i) = i + 1 for odd i and i - 1 for even i > 0.
+// Velocity sets. D3Q27 is the set the paper prints (Sec. 3.2.1): weights 8/27 (rest), 2/27 (faces),
+// 1/54 (edges), 1/216 (corners). D3Q19 is its textbook |c|^2 <= 2 subset with weights 1/3, 1/18,
+// 1/36. Order: rest, +-x, +-y, +-z, the 12 edge directions, then (D3Q27) the 8 corners; each odd
+// index i is followed by its opposite, so opp(i) = i + 1 for odd i and i - 1 for even i > 0 in both
+// sets. The lattice-Boltzmann kernels are compiled once per set, in namespace q19 or q27.
+namespace q19 {
 constexpr int Q = 19;
 __host__ __device__ constexpr int cx_of(int i) {
   constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -29,6 +32,27 @@ __host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ?
 __host__ __device__ constexpr double w_of(int i) {
   return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
+}  // namespace q19
+
+namespace q27 {
+constexpr int Q = 27;
+__host__ __device__ constexpr int cx_of(int i) {
+  constexpr int v[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
+  return v[i];
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  constexpr int v[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, -1, 1, 1, -1};
+  return v[i];
+}
+__host__ __device__ constexpr int cz_of(int i) {
+  constexpr int v[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, 1, -1};
+  return v[i];
+}
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double w_of(int i) {
+  return i == 0 ? 8.0 / 27.0 : (i <= 6 ? 2.0 / 27.0 : (i <= 18 ? 1.0 / 54.0 : 1.0 / 216.0));
+}
+}  // namespace q27
 
 // Cell flags (uint16): bit 15 solid, bit 14 "became solid in the last flag update" (cover
 // event, consumed by the refill), bit 13 "fluid cell with a solid neighbour along a lattice
@@ -148,35 +172,63 @@ __host__ __device__ inline double mimg(double d, int n) {
   return d;
 }
 
-// ---- kernel launchers (defined in lbm.cu / phase.cu) --------------------------------------
-void set_fp16_weights(cudaStream_t s);
+// ---- kernel launchers (defined in lbm.cu / lbm27.cu per velocity set, and phase.cu) ------------
 // Populations live in two buffers fa, fb; StepState::parity selects the current state
-// (0: fa, 1: fb). The step reads the current buffer, writes the other, and the body kernel flips
+// (0: fa, 1: fb). The step reads the current buffer, writes the other, and the closing kernel flips
 // the parity, so one captured graph serves every step.
-unsigned lbm_blocks(const Lat& lat);
-// phases: bit 0 launches the density kernel, bit 1 the collision kernel
-void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
-                     const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
-                     double* diag_vel, const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s,
-                     int phases = 7);
-// fused single-pass LBM step for FP32 and FP16-deviation storage (prec 1, 2); tz = z extent of a
-// block (see fused_tz)
-int fused_tz(const Lat& lat, int blocks_per_sm);
-void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
-                      double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
-                      int tz, void* nbuf, cudaStream_t s);
-void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags,
-                     const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st,
-                     const void* nbuf, double G, cudaStream_t s);
-void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
-                             const uint16_t* flags, double* out, cudaStream_t s);
-void launch_zero_solid(int prec, const Lat& lat, void* fa, void* fb, const StepState* st, const uint16_t* flags,
-                       const BodyDev* bodies, int nb, int max_tile, cudaStream_t s);
-void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho,
-                       const double* u, cudaStream_t s);
-void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, int nb,
-                   int max_tile, StepState* st, int* blist, const double* arena, double member_thr, int* mbox,
-                   int next, cudaStream_t s);
+// launch_lbm_step phases: bit 0 density, bit 1 bulk collision, bit 2 collision of the cells next to
+// a solid. launch_lbm_fused: single-pass step for FP32 and FP16-deviation storage (prec 1, 2;
+// D3Q19 only), tz = z extent of a block (see fused_tz).
+#define CBL_LBM_LAUNCHERS                                                                              \
+  void set_fp16_weights(cudaStream_t s);                                                             \
+  void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi, \
+                       const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st,      \
+                       double* diag_rho, double* diag_vel, const PhysParams& pp, void* nbuf,          \
+                       const int* blist, cudaStream_t s, int phases);                                 \
+  int fused_tz(const Lat& lat, int blocks_per_sm);                                                   \
+  void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,         \
+                        const BodyDev* bodies, double* mass_part, StepState* st, double* diag_rho,   \
+                        double* diag_vel, const PhysParams& pp, int tz, void* nbuf, cudaStream_t s); \
+  void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags, \
+                       const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st, \
+                       const void* nbuf, double G, cudaStream_t s);                                   \
+  void launch_read_populations(int prec, const Lat& lat, const void* fa, const void* fb,             \
+                               const StepState* st, const uint16_t* flags, double* out, cudaStream_t s); \
+  void launch_zero_solid(int prec, const Lat& lat, void* fa, void* fb, const StepState* st,          \
+                         const uint16_t* flags, const BodyDev* bodies, int nb, int max_tile,         \
+                         cudaStream_t s);                                                             \
+  void launch_init_fluid(int prec, const Lat& lat, void* fa, const uint16_t* flags, const double* rho, \
+                         const double* u, cudaStream_t s);                                            \
+  void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, \
+                     int nb, int max_tile, StepState* st, int* blist, const double* arena,           \
+                     double member_thr, int* mbox, int next, cudaStream_t s);
+namespace q19 {
+CBL_LBM_LAUNCHERS
+}
+namespace q27 {
+CBL_LBM_LAUNCHERS
+}
+
+// The launchers of one velocity set, chosen when a context is created.
+struct LbmOps {
+  int q;
+  decltype(&q19::set_fp16_weights) set_fp16_weights;
+  decltype(&q19::launch_lbm_step) lbm_step;
+  decltype(&q19::fused_tz) fused_tz;
+  decltype(&q19::launch_lbm_fused) lbm_fused;
+  decltype(&q19::launch_boundary) boundary;
+  decltype(&q19::launch_read_populations) read_populations;
+  decltype(&q19::launch_zero_solid) zero_solid;
+  decltype(&q19::launch_init_fluid) init_fluid;
+  decltype(&q19::launch_refill) refill;
+};
+inline LbmOps lbm_ops(int q) {
+#define CBL_OPS(ns) \
+  LbmOps { q, &ns::set_fp16_weights, &ns::launch_lbm_step, &ns::fused_tz, &ns::launch_lbm_fused, &ns::launch_boundary, \
+           &ns::launch_read_populations, &ns::launch_zero_solid, &ns::launch_init_fluid, &ns::launch_refill }
+  return q == 27 ? CBL_OPS(q27) : CBL_OPS(q19);
+#undef CBL_OPS
+}
 
 void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, uint16_t* flags,
                              cudaStream_t s);

@@ -14,15 +14,29 @@
 //               fluid node's 26 neighbours so that no two threads write the same populations; the
 //               same scan rebuilds the boundary-cell list for the next step.
 //
-// Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights. The
-// two lattice-wide kernels use a grid-stride loop over a grid of a few blocks per SM.
+// Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights.
+//
+// This file is compiled once per velocity set: as itself for D3Q19 (namespace cbl::q19) and through
+// lbm27.cu with CBL_Q = 27 (namespace cbl::q27). The fused single-pass variants and the
+// no-allocation entry point exist for D3Q19 only.
 #include <mutex>
 
 #include <climits>
 #include "../../include/cbl.h"
 #include "cbl_dev.cuh"
 
+#ifndef CBL_Q
+#define CBL_Q 19
+#endif
+
 namespace cbl {
+#if CBL_Q == 27
+namespace q27 {
+#elif CBL_Q == 19
+namespace q19 {
+#else
+#error "CBL_Q must be 19 or 27"
+#endif
 
 __constant__ float c_wh[Q];  // binary16-rounded weights: base of the FP16-deviation storage
 
@@ -467,6 +481,7 @@ __global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __r
   add_mass_slot(mass_part, my_mass, blockIdx.x * 7u + 3u);
 }
 
+#if CBL_Q == 19
 // ---- fused step: pull + density + psi + Shan-Chen force + collision in one pass ----------------
 // A block owns a TX x TY column of cells and marches along z over [z0, z0 + tz). For every plane it
 // pulls the populations of the plane's cells plus a one-cell ring around them (periodic
@@ -902,6 +917,8 @@ __global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__
 // for a solid downstream neighbour x + c_i (owner B), the reaction of the Shan-Chen force,
 // +G psi(x) w_i psi(x + c_i) c_i, arm x + c_i - X_B (Sec. 3.2.3). It reads the same source
 // populations and psi as the collision, so g_i and rho are bit-identical to the ones it used.
+#endif  // CBL_Q == 19 (fused variants)
+
 // compensated float sum (Knuth's TwoSum): hi + lo carries the exact sum of the added values to about
 // 2^-48 relative, so the per-body sums keep FP64-level accuracy while only the last step per block
 // runs on the FP64 pipe (GB300 issues FP64 at 1/64 of the FP32 rate)
@@ -1332,6 +1349,7 @@ unsigned lbm_blocks(const Lat& lat) {
   return (unsigned)(need < cap ? need : cap);
 }
 
+#if CBL_Q == 19
 constexpr int FTX = 32, FTY = 8;
 
 // z extent of a fused block: as long as possible while the grid still fills the GPU
@@ -1372,6 +1390,12 @@ void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16
   } else if (prec == 2)
     fused_t<__half>(lat, (__half*)fa, (__half*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, nbuf, s);
 }
+#else
+// D3Q27: no fused variant (the context refuses lbm_variant 1)
+int fused_tz(const Lat&, int) { return 0; }
+void launch_lbm_fused(int, const Lat&, void*, void*, const uint16_t*, const BodyDev*, double*, StepState*, double*,
+                      double*, const PhysParams&, int, void*, cudaStream_t) {}
+#endif
 
 template <typename S>
 static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
@@ -1454,8 +1478,10 @@ void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags
                                         mbox, next);
 }
 
+}  // namespace q19 / q27
 }  // namespace cbl
 
+#if CBL_Q == 19
 // ---- one lattice-Boltzmann step with no allocation --------------------------------------------
 // For callers that cannot allocate device memory (an allocator owned by another framework, a
 // pre-reserved memory pool, a process that forbids cudaMalloc after start-up): the scratch this
@@ -1495,6 +1521,7 @@ extern "C" cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int 
                                            double G, double rho0, const double* ext_force, double* mass_out,
                                            void* stream) {
   using namespace cbl;
+  using namespace cbl::q19;
   if (!f_in || !f_out || f_in == f_out) return CBL_ERR_ARG;
   if (nx < 4 || ny < 4 || nz < 4) return CBL_ERR_ARG;
   const long long N = (long long)nx * ny * nz;
@@ -1542,4 +1569,4 @@ extern "C" cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int 
   if (mass_out) k_na_mass<<<1, 256, 0, s>>>(a.mass, mass_out);
   return cudaGetLastError() == cudaSuccess ? CBL_OK : CBL_ERR_CUDA;
 }
-
+#endif  // CBL_Q == 19 (no-allocation entry point)
