@@ -99,7 +99,9 @@ typedef struct {
 cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_ctx** out);
 
 /* Add a solid body (before cbl_init_fluid). Its phase-field tile is allocated here. `body_id`
- * (may be NULL) receives the 0-based id. */
+ * (may be NULL) receives the 0-based id. A body whose support (surface + eta/2) covers the whole
+ * periodic length along an axis is infinite along it (the plates of the planar bridge, Sec. 2.1):
+ * it turns only about that axis; the other angular-velocity components are held at zero. */
 cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id);
 
 /* Initialise the phase fields, obstacle flags (Sec. 3.2.2: solid iff fluid phase < threshold),

@@ -110,6 +110,7 @@ struct Body {
   double rho_s;         // mass density rho_alpha
   double wet;           // wetting parameter varrho_B
   int fixed;
+  int rot_lock = 0;     // bit c: the angular velocity component c is held at zero (see spans_lattice)
   double M = 0, Ibody[9] = {0};
   double X[3], Xprev[3], V[3] = {0, 0, 0}, W[3] = {0, 0, 0}, Q[4];
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};  // total force/torque of the last step
@@ -526,6 +527,8 @@ void integrate_body(Oracle& o, Body& b) {
   inv[7] = (Iw[1] * Iw[6] - Iw[0] * Iw[7]) / det;
   inv[8] = (Iw[0] * Iw[4] - Iw[1] * Iw[3]) / det;
   for (int a = 0; a < 3; ++a) b.W[a] += inv[3 * a] * b.T[0] + inv[3 * a + 1] * b.T[1] + inv[3 * a + 2] * b.T[2];
+  for (int a = 0; a < 3; ++a)
+    if (b.rot_lock >> a & 1) b.W[a] = 0.0;
   double wn = std::sqrt(b.W[0] * b.W[0] + b.W[1] * b.W[1] + b.W[2] * b.W[2]);
   if (wn > 0) {
     double h = 0.5 * wn, s = std::sin(h) / wn;
@@ -756,6 +759,31 @@ void* orc_create(const orc_params* p) {
 
 void orc_destroy(void* h) { delete (Oracle*)h; }
 
+// A body whose phi support (surface + eta/2) covers the whole periodic length of the lattice
+// along an axis is infinite along that axis: the plates of the planar bridge of Sec. 2.1, whose
+// length L is the lattice length under periodic boundaries. READING (the paper does not say how
+// such a body turns): it may turn only about that axis, since a turn about any other axis would
+// break its periodicity (and the lever arm at the periodic seam is not defined); the rigid-body
+// update holds the other angular-velocity components at zero. Returns the bit mask of the held
+// components.
+int rotation_lock(const Oracle& o, const Body& b) {
+  double h[3];
+  if (b.shape == 0) {
+    for (int a = 0; a < 3; ++a) h[a] = b.radius;
+  } else {
+    double R[9];
+    quat_to_R(b.q0, R);
+    for (int a = 0; a < 3; ++a)
+      h[a] = std::fabs(R[3 * a]) * b.half[0] + std::fabs(R[3 * a + 1]) * b.half[1] + std::fabs(R[3 * a + 2]) * b.half[2];
+  }
+  int lock = 0;
+  for (int a = 0; a < 3; ++a)
+    if (2.0 * (h[a] + 0.5 * o.p.eta) >= (double)o.dims(a))
+      for (int c = 0; c < 3; ++c)
+        if (c != a) lock |= 1 << c;
+  return lock;
+}
+
 int orc_add_body(void* h, int shape, const double* center, double radius, const double* half,
                  const double* quat, double mass_density, double wetting_rho, int fixed) {
   Oracle* o = (Oracle*)h;
@@ -771,6 +799,7 @@ int orc_add_body(void* h, int shape, const double* center, double radius, const 
   b.rho_s = mass_density;
   b.wet = wetting_rho;
   b.fixed = fixed;
+  b.rot_lock = rotation_lock(*o, b);
   rasterize(*o, b);
   o->bodies.push_back(std::move(b));
   return (int)o->bodies.size() - 1;

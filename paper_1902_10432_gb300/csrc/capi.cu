@@ -224,9 +224,9 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   b.psi_wet = 1.0 - std::exp(-body->wetting_rho / ctx->p.rho0);
   b.psi_wet_f = (float)b.psi_wet;
   b.fixed = body->fixed;
-  // tile: support half-extent + 2 halo layers + half a cell of recentring offset + 1.5 cells for the
-  // discrete profile and the advection tail, which reach about one cell past R + eta/2 on a moving
-  // body
+  // tile: support half-extent + 2 halo layers + half a cell of recentring offset + 2.5 cells for the
+  // discrete profile and the advection tail, which reaches about one cell past R + eta/2 on a body
+  // that moved a cell and keeps growing slowly with the distance travelled
   double h[3];
   if (b.shape == 0) {
     if (!(b.radius > 0)) return fail(ctx, CBL_ERR_ARG, "sphere radius must be > 0");
@@ -240,9 +240,16 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
                                        std::fabs(R[3 * a + 2]) * b.half[2];
   }
   const int n[3] = {ctx->p.nx, ctx->p.ny, ctx->p.nz};
+  // a body whose support (surface + eta/2) covers the whole periodic length along an axis is
+  // infinite along it (the planar-bridge plates of Sec. 2.1): it turns only about that axis
+  b.rot_lock = 0;
+  for (int a = 0; a < 3; ++a)
+    if (2.0 * (h[a] + 0.5 * ctx->p.eta) >= (double)n[a])
+      for (int c = 0; c < 3; ++c)
+        if (c != a) b.rot_lock |= 1 << c;
   long long sz = 1;
   for (int a = 0; a < 3; ++a) {
-    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 4.0);
+    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 5.0);
     int L = 2 * half + 1;
     if (L >= n[a]) {
       L = n[a];

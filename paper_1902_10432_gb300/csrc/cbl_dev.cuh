@@ -97,6 +97,7 @@ struct BodyDev {
   float Xf[3], Vf[3], Wf[3];
   double c0[3], radius, half[3], q0[4];
   int fixed, shape;
+  int rot_lock;  // bit c: angular velocity component c held at zero (body spans the lattice)
   int o[3], o_prev[3], L[3];
   long long off, sz;
   int nnb;

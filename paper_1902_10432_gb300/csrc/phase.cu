@@ -483,6 +483,8 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
   for (int k = 0; k < 3; ++k) t1[k] = R[k] * T[0] + R[3 + k] * T[1] + R[6 + k] * T[2];  // R^T T
   for (int k = 0; k < 3; ++k) t2[k] = b.Ibinv[3 * k] * t1[0] + b.Ibinv[3 * k + 1] * t1[1] + b.Ibinv[3 * k + 2] * t1[2];
   for (int a = 0; a < 3; ++a) b.W[a] += R[3 * a] * t2[0] + R[3 * a + 1] * t2[1] + R[3 * a + 2] * t2[2];
+  for (int a = 0; a < 3; ++a)
+    if (b.rot_lock >> a & 1) b.W[a] = 0.0;
   const double wn = sqrt(b.W[0] * b.W[0] + b.W[1] * b.W[1] + b.W[2] * b.W[2]);
   if (wn > 0) {
     double sn, cs;
@@ -656,8 +658,10 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
       v = p[2] - (Fr - Fl);
     }
     arena[b.off + (long long)out_buf * b.sz + t] = v;
-    if (last && (dbits(v) << 1) != 0) {  // v != +-0
-      // the outer two layers must stay empty (they are the stencil halo)
+    if (last && (dbits(v) << 1) > (dbits(PHI_EPS) << 1)) {  // |v| > PHI_EPS
+      // the outer two layers must stay empty (they are the stencil halo); a moving body's upwind
+      // scheme leaves a geometrically decaying tail ahead of its front, and the tile drops what
+      // reaches past it, so values of at most PHI_EPS there are tolerated
       bool edge = false;
       for (int a = 0; a < 3; ++a)
         if (b.L[a] < nn[a] && (ii[a] < 2 || ii[a] >= b.L[a] - 2)) edge = true;

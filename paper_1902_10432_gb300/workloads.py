@@ -10,6 +10,8 @@ spheres), so these generators stand in for its set-ups at the sizes of the bench
                angle from a seed (Sec. 4.3.1 at R = 20).
   tetra4     : 256^3, four spheres R = 24 in a jittered tetrahedron (Sec. 4.3.2).
   small_*    : reduced versions used by the parity tests.
+  plate_bridge: the plate experiments of Sec. 4.2 (cylindrical or planar bridge at 90 degrees, heavy
+               free plates, R = 20).
 
 A body's shape is the phi = 1/2 surface. Contact angles are turned into the wetting parameter
 varrho_B through the table tests/golden/wetting_table.json (written by the FP64 oracle from
@@ -27,6 +29,8 @@ import numpy as np
 RHO_L, RHO_V = 1.88844, 0.11942  # flat-interface coexistence of G = -5, psi = 1 - exp(-rho)
 _ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 WETTING_TABLE = os.path.join(_ROOT, "tests", "golden", "wetting_table.json")
+WETTING_90 = os.path.join(_ROOT, "tests", "golden", "wetting_90.json")
+PLATE_DENSITY_RATIO = 1.72e4  # rho_S / rho_L of the free plates (Sec. 4.2: slow, heavy plates)
 
 # Solid cells are those with fluid phase below 0.05, i.e. deeper than this below the phi = 1/2
 # surface for eta = 5 ((eta/pi) asin(0.9) = 1.7822): plates are enlarged by it so that the
@@ -64,6 +68,15 @@ def varrho_for_angle(theta_deg: float) -> float:
     if not (th[0] <= theta_deg <= th[-1]):
         raise ValueError("contact angle %.1f outside the calibrated range [%.1f, %.1f]" % (theta_deg, th[0], th[-1]))
     return float(np.interp(theta_deg, th, vr))
+
+
+def varrho_90() -> float:
+    """Wetting parameter of a 90 degree contact angle: the value for which the meniscus of a planar
+    bridge between plates is flat (zero Laplace pressure), from tests/golden/wetting_90.json (written
+    by the FP64 oracle). The sessile-drop table places 90 degrees a few degrees off in the plate
+    geometry, which the plate force is sensitive to."""
+    with open(WETTING_90) as f:
+        return float(json.load(f)["varrho_90"])
 
 
 def _sphere_body(center, R, rho_s, varrho, fixed=False):
@@ -193,6 +206,45 @@ def plates48(theta_deg=60.0, prec="fp64", n=48, gap=12, r_bridge=10.0, layers=3,
     params = dict(tau=tau, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=0)
     return Workload("plates48", n, n, n, params, bodies, mask, steps=500,
                     meta=dict(theta_deg=theta_deg, varrho=varrho, gap=gap, r_bridge=r_bridge))
+
+
+def plate_bridge(kind="cylinder", prec="fp32", R=20, h0=20, layers=3, width=64, depth=None, fixed=False,
+                 density_ratio=PLATE_DENSITY_RATIO, varrho=None, margin=16, below=14):
+    """Two parallel plates (normal z, gap h0) joined by a capillary bridge at 90 degree wetting, the
+    set-ups of the plate experiments (Sec. 4.2, Sec. 2.1):
+
+      kind="cylinder": a liquid cylinder of radius R between square plates of side `width`;
+      kind="planar"  : a liquid slab of width 2R between plates of width `width` in x that span the
+                       periodic y extent, which is the bridge length L (`depth`, default R: the
+                       paper's L = R); the plates are infinite along y.
+
+    The lattice spacing is 1, so R = 20 is the paper's Delta x / R = 0.05. Plates have mass density
+    density_ratio * rho_L (1.72e4 in the paper: the plates move slowly against the fluid) and are
+    free unless `fixed`. The lattice leaves `margin` cells of vapour beside the plates and `below`
+    cells under the lower plate."""
+    if kind not in ("cylinder", "planar"):
+        raise ValueError("kind must be 'cylinder' or 'planar'")
+    varrho = varrho_90() if varrho is None else float(varrho)
+    nx = width + 2 * margin
+    ny = nx if kind == "cylinder" else int(depth if depth is not None else R)
+    nz = h0 + 2 * layers + 2 * below + 2
+    z1 = below + (layers - 1) / 2.0
+    z2 = z1 + layers + h0
+    cx, cy = (nx - 1) / 2.0, (ny - 1) / 2.0
+    hy = width / 2.0 + _PLATE_PAD if kind == "cylinder" else ny / 2.0 + 2 * _PLATE_PAD
+    half = (width / 2.0 + _PLATE_PAD, hy, layers / 2.0 + _PLATE_PAD)
+    rho_s = density_ratio * RHO_L
+    bodies = [dict(shape="box", center=(cx, cy, zc), half=half, mass_density=rho_s, wetting_rho=varrho,
+                   fixed=bool(fixed)) for zc in (z1, z2)]
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx]
+    lo, hi = int(z1 + layers / 2.0 + 0.5), int(z2 - layers / 2.0 - 0.5)
+    inside = ((x - cx) ** 2 + (y - cy) ** 2 <= R * R) if kind == "cylinder" else (np.abs(x - cx) <= R)
+    mask = (inside & (z >= lo) & (z <= hi)).astype(np.uint8)
+    params = dict(tau=1.0, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=0)
+    return Workload("plates_" + kind, nx, ny, nz, params, bodies, mask, steps=500,
+                    meta=dict(kind=kind, R=float(R), h0=float(h0), layers=layers, width=width,
+                              depth=float(ny) if kind == "planar" else None, varrho=varrho,
+                              density_ratio=density_ratio, fixed=bool(fixed)))
 
 
 def spheres2(seed=0, prec="fp32", nx=128, ny=128, nz=256, R=20.0, gap=4.0, mpf=1, rho_s=4.0):

@@ -35,6 +35,9 @@ def compare(g, o):
     out = dict(flag_mismatch=int((sg != so).sum() + ((sg == 1) & (og != oo)).sum()),
                rho=rel_linf(rg, ro, fluid),
                vel=max(rel_linf(vg[..., a], vo[..., a], fluid) for a in range(3)),
+               # the same over the velocity vector (for set-ups where a component is zero up to
+               # round-off by symmetry, whose per-component relative error is noise over noise)
+               vel_vec=rel_linf(vg[fluid], vo[fluid]),
                phi_fluid=float(np.abs(pg - po).max()))
     if o.nbodies:
         Fg, Tg, Pg = g.body_forces()
