@@ -90,7 +90,7 @@ typedef struct {
   double quat[4];        /* initial orientation (w, x, y, z); zero = identity */
   double mass_density;   /* rho_alpha: M = rho_alpha * sum phi */
   double wetting_rho;    /* varrho_B: solid cells act as fluid of this density (Sec. 3.2.3) */
-  int fixed;             /* 1: the body never moves (forces are still reported) */
+  int fixed;             /* 1: the body is held in place (forces are still reported); see cbl_set_bodies_fixed */
 } cbl_body;
 
 /* Create a context. Validates the parameters (CBL_ERR_ARG) and allocates the lattice arrays through
@@ -170,6 +170,13 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Q, const
 /* Set body velocities (host arrays nb*3, either may be NULL). */
 cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W);
 
+/* Hold or release bodies (host array of nb ints, 1 = held in place). A held body keeps its pose,
+ * its V and omega are set to zero, and its forces are still reported; a released body starts from
+ * rest. This is how the paper lets the liquid reach its equilibrium shape before the particles may
+ * move (Sec. 4.3.2: t = 0 is the release). CBL_ERR_ARG for a NULL array, CBL_ERR_STATE before
+ * cbl_init_fluid. Takes effect from the next cbl_step. */
+cbl_status cbl_set_bodies_fixed(cbl_ctx* ctx, const int* fixed);
+
 /* Fluid mass sum_x rho(x) over fluid cells in the last completed step, FP64. Returns
  * CBL_ERR_UNSTABLE if it is not finite. */
 cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass);
@@ -200,7 +207,12 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
  *   "lbm_block_x"  x extent of the 128-thread blocks of the split kernels: 32 (default), 64, 128;
  *   "graph_branches" 1 (default) = with bodies, the collision of the fluid cells next to a solid,
  *                  the solid-fluid force pass and the solid-solid repulsion run on a second branch
- *                  of the step graph beside the bulk collision; 0 = one chain.
+ *                  of the step graph beside the bulk collision; 0 = one chain;
+ *   "tile_tail"    cells of room (default 2.5, at most 64) between a body's phase-field support and
+ *                  the halo of its tile, for the tail that the advection leaves behind a moving
+ *                  body and that grows with the distance travelled; set before the first
+ *                  cbl_add_body (CBL_ERR_STATE after). Results do not depend on it while no phi
+ *                  above 1e-12 reaches the halo (device error bit 0 stays clear).
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 

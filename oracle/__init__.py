@@ -83,6 +83,7 @@ def _load():
             lib.orc_read_body_forces.argtypes = [P, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_get_bodies.argtypes = [P] + [ctypes.c_void_p] * 6
             lib.orc_set_body_velocity.argtypes = [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_set_body_fixed.argtypes = [P, ctypes.c_int, ctypes.c_int]
             lib.orc_integrate_body.argtypes = [P, ctypes.c_int, D, D]
             lib.orc_total_mass.restype = ctypes.c_double
             lib.orc_total_mass.argtypes = [P]
@@ -236,6 +237,12 @@ class Oracle:
         v = None if V is None else np.asarray(V, np.float64)
         w = None if W is None else np.asarray(W, np.float64)
         self._lib.orc_set_body_velocity(self._h, int(body), _vp(v), _vp(w))
+
+    def set_fixed(self, fixed):
+        if len(fixed) != self.nbodies:
+            raise ValueError("one flag per body")
+        for b, f in enumerate(fixed):
+            self._lib.orc_set_body_fixed(self._h, b, 1 if f else 0)
 
     def integrate_body(self, body, F, T=(0.0, 0.0, 0.0)):
         self._lib.orc_integrate_body(self._h, int(body), _dp(np.asarray(F, np.float64)),

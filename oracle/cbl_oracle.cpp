@@ -954,6 +954,15 @@ void orc_set_body_velocity(void* h, int body, const double* V, const double* W) 
   }
 }
 
+// Hold (1) or release (0) a body; a held body is at rest (Sec. 4.3.2: the particles are held while
+// the liquid settles, t = 0 is the release).
+void orc_set_body_fixed(void* h, int body, int fixed) {
+  Body& b = ((Oracle*)h)->bodies[body];
+  b.fixed = fixed ? 1 : 0;
+  if (b.fixed)
+    for (int a = 0; a < 3; ++a) b.V[a] = b.W[a] = 0.0;
+}
+
 // Apply the body integrator to one body with a given force and torque (integrator pin).
 void orc_integrate_body(void* h, int body, const double* F, const double* T) {
   Oracle* o = (Oracle*)h;

@@ -75,6 +75,7 @@ SIGNATURES = {
     "cbl_read_body_forces": (ctypes.c_int, [_P, _P, _P, _P]),
     "cbl_get_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cbl_set_body_velocities": (ctypes.c_int, [_P, _P, _P]),
+    "cbl_set_bodies_fixed": (ctypes.c_int, [_P, _P]),
     "cbl_move_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "cbl_total_mass": (ctypes.c_int, [_P, _D]),
     "cbl_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
@@ -298,6 +299,12 @@ class Sim:
         v = None if V is None else np.ascontiguousarray(V, np.float64).reshape(-1)
         w = None if W is None else np.ascontiguousarray(W, np.float64).reshape(-1)
         self._ck(self._lib.cbl_set_body_velocities(self._h, _vp(v), _vp(w)))
+
+    def set_fixed(self, fixed):
+        f = np.ascontiguousarray([1 if v else 0 for v in fixed], np.int32)
+        if f.size != self.nb:
+            raise ValueError("one flag per body")
+        self._ck(self._lib.cbl_set_bodies_fixed(self._h, _vp(f)))
 
     def move_bodies(self, X, Q=None, V=None, W=None):
         f = lambda a: None if a is None else np.ascontiguousarray(a, np.float64).reshape(-1)

@@ -48,6 +48,7 @@ struct cbl_ctx {
   int fused_tz = 0;      // > 0: FP32 / FP16 storage steps with the fused single-pass kernel
   int fused_tz_req = 0;  // requested z extent of a fused block (0 = derived)
   int block_x = 32;      // x extent of the split kernels' 128-thread blocks
+  double tile_tail = 2.5;  // cells of room for the advection tail in each body tile
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -224,9 +225,9 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   b.psi_wet = 1.0 - std::exp(-body->wetting_rho / ctx->p.rho0);
   b.psi_wet_f = (float)b.psi_wet;
   b.fixed = body->fixed;
-  // tile: support half-extent + 2 halo layers + half a cell of recentring offset + 2.5 cells for the
-  // discrete profile and the advection tail, which reaches about one cell past R + eta/2 on a body
-  // that moved a cell and keeps growing slowly with the distance travelled
+  // tile: support half-extent + 2 halo layers + half a cell of recentring offset + tile_tail cells
+  // (default 2.5) for the discrete profile and the advection tail, which reaches about one cell
+  // past R + eta/2 on a body that moved a cell and keeps growing slowly with the distance travelled
   double h[3];
   if (b.shape == 0) {
     if (!(b.radius > 0)) return fail(ctx, CBL_ERR_ARG, "sphere radius must be > 0");
@@ -249,7 +250,7 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
         if (c != a) b.rot_lock |= 1 << c;
   long long sz = 1;
   for (int a = 0; a < 3; ++a) {
-    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 5.0);
+    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 2.5 + ctx->tile_tail);
     int L = 2 * half + 1;
     if (L >= n[a]) {
       L = n[a];
@@ -729,6 +730,25 @@ cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* 
   return CBL_OK;
 }
 
+cbl_status cbl_set_bodies_fixed(cbl_ctx* ctx, const int* fixed) {
+  if (!ctx || !fixed) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const int nb = (int)ctx->hb.size();
+  if (!nb) return CBL_OK;
+  std::vector<BodyDev> h(nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (int b = 0; b < nb; ++b) {
+    h[b].fixed = ctx->hb[b].fixed = fixed[b] ? 1 : 0;
+    if (h[b].fixed)
+      for (int a = 0; a < 3; ++a) h[b].V[a] = h[b].W[a] = 0.0;
+    mirror_f(h[b]);
+  }
+  CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
 cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass) {
   if (!ctx || !mass) return fail(ctx, CBL_ERR_ARG, "NULL argument");
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
@@ -771,6 +791,11 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "graph_branches must be 0 or 1");
     ctx->branches = v;
+  } else if (k == "tile_tail") {
+    if (!(value >= 0.0 && value <= 64.0)) return fail(ctx, CBL_ERR_ARG, "tile_tail must be in [0, 64]");
+    if (!ctx->hb.empty()) return fail(ctx, CBL_ERR_STATE, "tile_tail must be set before the first body");
+    ctx->tile_tail = value;
+    return CBL_OK;
   } else if (k == "lbm_block_x") {
     const int v = (int)value;
     if (v != 32 && v != 64 && v != 128) return fail(ctx, CBL_ERR_ARG, "lbm_block_x must be 32, 64 or 128");

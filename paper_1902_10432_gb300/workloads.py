@@ -10,6 +10,7 @@ spheres), so these generators stand in for its set-ups at the sizes of the bench
                angle from a seed (Sec. 4.3.1 at R = 20).
   tetra4     : 256^3, four spheres R = 24 in a jittered tetrahedron (Sec. 4.3.2).
   small_*    : reduced versions used by the parity tests.
+  cluster    : two, three or four spheres R = 30 around a central drop (Sec. 4.3 dynamics runs).
   plate_bridge: the plate experiments of Sec. 4.2 (cylindrical or planar bridge at 90 degrees, heavy
                free plates, R = 20).
 
@@ -245,6 +246,49 @@ def plate_bridge(kind="cylinder", prec="fp32", R=20, h0=20, layers=3, width=64, 
                     meta=dict(kind=kind, R=float(R), h0=float(h0), layers=layers, width=width,
                               depth=float(ny) if kind == "planar" else None, varrho=varrho,
                               density_ratio=density_ratio, fixed=bool(fixed)))
+
+
+def cluster(n_particles=2, c=0.2, prec="fp32", R=30.0, h0=20.0, varrho=2.0, rho_s=4.0, mpf=1, margin=20,
+            mobility=1e-5, e0=1.0, tau=1.1, q=27):
+    """Two, three or four spheres of radius R with equal surface gaps h0 (a pair on the z axis, an
+    equilateral triangle in the xy plane, a regular tetrahedron) and a drop of liquid at their centre
+    whose volume gives the liquid volume fraction c = V_L / (V_L + V_S) (Sec. 4.3: R = 30, mass
+    density 4, varrho_B = 2.0, c in {0.2, 0.3, 0.5}; the paper's parameter table: tau = 1.1, and its
+    velocity set D3Q27). The lattice leaves `margin` cells of vapour
+    around the spheres and the drop. The particles start free; the paper holds them while the
+    liquid settles (see cbl_set_bodies_fixed)."""
+    if n_particles not in (2, 3, 4):
+        raise ValueError("2, 3 or 4 particles")
+    if not 0.0 < c < 1.0:
+        raise ValueError("liquid fraction c must be in (0, 1)")
+    a = 2.0 * R + h0  # centre distance of neighbours
+    if n_particles == 2:
+        rel = np.array([[0, 0, -0.5], [0, 0, 0.5]]) * a
+    elif n_particles == 3:
+        rel = np.array([[math.cos(t), math.sin(t), 0.0] for t in (math.pi / 2 + k * 2 * math.pi / 3 for k in range(3))])
+        rel *= a / math.sqrt(3.0)
+    else:
+        rel = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float) * (a / (2 * math.sqrt(2.0)))
+    VS = n_particles * 4.0 / 3.0 * math.pi * R ** 3
+    VL = c / (1.0 - c) * VS
+    r_drop = (3.0 * (VL + VS) / (4.0 * math.pi)) ** (1.0 / 3.0)  # bound on the drop's reach
+    ext = np.maximum(np.abs(rel).max(axis=0) + R, r_drop) + margin
+    dims = [int(2 * math.ceil(e / 2.0) * 2) for e in ext]  # even sides
+    ctr = np.array(dims, float) / 2.0
+    centers = [tuple(ctr + v) for v in rel]
+    mask = _bridge_mask_radii(dims[0], dims[1], dims[2], centers, [R] * n_particles, VL, tuple(ctr))
+    bodies = [_sphere_body(p, R, rho_s, varrho) for p in centers]
+    # repulsion strength (not given in the paper): with e0 = 1e-3 spheres of R = 30 and mass density
+    # 4 arriving at the speeds of these runs pass through each other (the summed potential of the
+    # overlapping member points stays far below their kinetic energy); e0 = 1 stops them within
+    # about a cell of contact
+    params = dict(tau=tau, G=-5.0, rho0=1.0, prec=prec, mpf_kinetics=mpf, mobility=mobility, e0=e0, q=q)
+    name = {2: "pair", 3: "triangle", 4: "tetrahedron"}[n_particles]
+    return Workload("%s_c%.1f" % (name, c), dims[0], dims[1], dims[2], params, bodies, mask, steps=500,
+                    meta=dict(n_particles=n_particles, c=c, R=R, h0=h0, varrho=varrho, rho_s=rho_s, mpf=mpf,
+                              liquid_volume=VL, solid_volume=VS,
+                              # the particles travel ~10 cells: room for the advection tail
+                              options=dict(tile_tail=8.0)))
 
 
 def spheres2(seed=0, prec="fp32", nx=128, ny=128, nz=256, R=20.0, gap=4.0, mpf=1, rho_s=4.0):
