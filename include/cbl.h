@@ -208,6 +208,9 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
  *   "graph_branches" 1 (default) = with bodies, the collision of the fluid cells next to a solid,
  *                  the solid-fluid force pass and the solid-solid repulsion run on a second branch
  *                  of the step graph beside the bulk collision; 0 = one chain;
+ *   "node_priority" 1 (default) = the step graph keeps the side branch's higher stream priority
+ *                  on its kernel nodes (instantiated with cudaGraphInstantiateFlagUseNodePriority);
+ *                  0 = all nodes at the same priority;
  *   "tile_tail"    cells of room (default 2.5, at most 64) between a body's phase-field support and
  *                  the halo of its tile, for the tail that the advection leaves behind a moving
  *                  body and that grows with the distance travelled; set before the first

@@ -49,6 +49,7 @@ struct cbl_ctx {
   int fused_tz_req = 0;  // requested z extent of a fused block (0 = derived)
   int block_x = 32;      // x extent of the split kernels' 128-thread blocks
   double tile_tail = 2.5;  // cells of room for the advection tail in each body tile
+  int node_priority = 1;   // 1: the step graph keeps the side stream's priority on its kernels
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -428,7 +429,9 @@ cbl_status cbl_step(cbl_ctx* ctx, int nsteps) {
     cudaError_t e2 = cudaStreamEndCapture(ctx->s, &ctx->graph);
     CK(e1);
     CK(e2);
-    CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+    // the side stream's priority is recorded on its kernel nodes; the executable graph honours it
+    // only with this flag
+    CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, ctx->node_priority ? cudaGraphInstantiateFlagUseNodePriority : 0));
   }
   // the diag word is tested for non-zero: byte-wise memsets keep the whole call asynchronous
   CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
@@ -787,6 +790,10 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
     ctx->fused_tz_req = v;
     if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : ctx->ops.fused_tz(ctx->lat, 2);
+  } else if (k == "node_priority") {
+    const int v = (int)value;
+    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "node_priority must be 0 or 1");
+    ctx->node_priority = v;
   } else if (k == "graph_branches") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "graph_branches must be 0 or 1");
@@ -870,7 +877,7 @@ cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch
   for (int k = 0; k <= n; ++k) ok &= cudaEventCreateWithFlags(&b->events[k], cudaEventDisableTiming) == cudaSuccess;
   for (int d = 0; d < 2 && ok; ++d) {
     ok &= batch_capture(b, d, &b->graph[d]) == cudaSuccess;
-    ok &= ok && cudaGraphInstantiate(&b->gexec[d], b->graph[d], 0) == cudaSuccess;
+    ok &= ok && cudaGraphInstantiate(&b->gexec[d], b->graph[d], cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
