@@ -594,14 +594,26 @@ __device__ __forceinline__ int in_local(int i, int shift, int L, int n) {
 __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* arena, Lat lat, int d, int in_buf,
                                                int out_buf, int use_prev, int last, double* volacc, StepState* st,
                                                const double* __restrict__ rtab, int Lmax) {
+  // The cells whose stencil is not flat (the interface shell) are gathered into the first lanes of
+  // the block before the flux arithmetic: GB300 issues FP64 at 1/64 of the FP32 rate and a warp
+  // instruction occupies the FP64 pipe for all its lanes, active or not, so scattered interface
+  // cells left most of its time idle. The arithmetic per cell is unchanged.
+  __shared__ double cp[5][256];
+  __shared__ double cr[2][256];
+  __shared__ double cv[256];
+  __shared__ int ncomp;
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x == 0) ncomp = 0;
+  __syncthreads();
   double v = 0.0;
   const bool inside = t < b.sz;
+  bool nonflat = false;
+  double p[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, r1 = 0.0, r2 = 0.0;
+  const int nn[3] = {lat.nx, lat.ny, lat.nz};
+  int ii[3] = {0, 0, 0};
   if (inside) {
-    const int nn[3] = {lat.nx, lat.ny, lat.nz};
-    int ii[3];
     {
       const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];
       const unsigned r = u / L0;
@@ -625,38 +637,66 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
     const double* in = arena + b.off + (long long)in_buf * b.sz;
     const long long sd = d == 0 ? 1 : (d == 1 ? (long long)b.L[0] : (long long)b.L[0] * b.L[1]);
     const long long base = li[0] + (long long)b.L[0] * (li[1] + (long long)b.L[1] * li[2]) - (long long)li[d] * sd;
-    double p[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       const int l = in_local(li[d], k - 2, b.L[d], b.L[d] == nn[d] ? nn[d] : -1);
       p[k] = (ok && l >= 0 && l < b.L[d]) ? in[base + l * sd] : 0.0;
     }
     const long long b2 = dbits(p[2]);
-    if (dbits(p[0]) == b2 && dbits(p[1]) == b2 && dbits(p[3]) == b2 && dbits(p[4]) == b2) {
-      // flat stencil: both face fluxes are u * p with the same u, so the update is exactly zero
-      v = p[2];
-    } else {
-      // face velocity u_d (the d-component of V + omega x r, r about X_prev): it depends only on the
-      // two other coordinates, so both faces of the cell share it
+    // flat stencil: both face fluxes are u * p with the same u, so the update is exactly zero
+    v = p[2];
+    nonflat = !(dbits(p[0]) == b2 && dbits(p[1]) == b2 && dbits(p[3]) == b2 && dbits(p[4]) == b2);
+    if (nonflat) {
+      // the face velocity u_d (the d-component of V + omega x r, r about X_prev) depends only on the
+      // two other coordinates, so both faces of the cell share it;
       // r_a = mimg(wrap(o_a + i_a) - Xprev_a) from the per-body table built by k_bodies
       const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
       const double* rt = rtab + (size_t)self * 3 * Lmax;
-      const double r1 = rt[d1 * Lmax + ii[d1]];
-      const double r2 = rt[d2 * Lmax + ii[d2]];
-      const double u = b.V[d] + (b.W[d1] * r2 - b.W[d2] * r1);
-      double Fl, Fr;
-      {
-        const double face = u >= 0.0 ? p[1] + 0.5 * (1.0 - u) * mc_slope(p[1] - p[0], p[2] - p[1])
-                                     : p[2] - 0.5 * (1.0 + u) * mc_slope(p[2] - p[1], p[3] - p[2]);
-        Fl = u * face;
-      }
-      {
-        const double face = u >= 0.0 ? p[2] + 0.5 * (1.0 - u) * mc_slope(p[2] - p[1], p[3] - p[2])
-                                     : p[3] - 0.5 * (1.0 + u) * mc_slope(p[3] - p[2], p[4] - p[3]);
-        Fr = u * face;
-      }
-      v = p[2] - (Fr - Fl);
+      r1 = rt[d1 * Lmax + ii[d1]];
+      r2 = rt[d2 * Lmax + ii[d2]];
     }
+  }
+  int slot = -1;
+  {
+    const unsigned m = __ballot_sync(0xffffffffu, nonflat);
+    if (m) {
+      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&ncomp, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (nonflat) {
+        slot = base + __popc(m & ((1u << lane) - 1u));
+#pragma unroll
+        for (int k = 0; k < 5; ++k) cp[k][slot] = p[k];
+        cr[0][slot] = r1;
+        cr[1][slot] = r2;
+      }
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < ncomp) {
+    const int c = threadIdx.x;
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    double q[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = cp[k][c];
+    const double u = b.V[d] + (b.W[d1] * cr[1][c] - b.W[d2] * cr[0][c]);
+    double Fl, Fr;
+    {
+      const double face = u >= 0.0 ? q[1] + 0.5 * (1.0 - u) * mc_slope(q[1] - q[0], q[2] - q[1])
+                                   : q[2] - 0.5 * (1.0 + u) * mc_slope(q[2] - q[1], q[3] - q[2]);
+      Fl = u * face;
+    }
+    {
+      const double face = u >= 0.0 ? q[2] + 0.5 * (1.0 - u) * mc_slope(q[2] - q[1], q[3] - q[2])
+                                   : q[3] - 0.5 * (1.0 + u) * mc_slope(q[3] - q[2], q[4] - q[3]);
+      Fr = u * face;
+    }
+    cv[c] = q[2] - (Fr - Fl);
+  }
+  __syncthreads();
+  if (slot >= 0) v = cv[slot];
+  if (inside) {
     arena[b.off + (long long)out_buf * b.sz + t] = v;
     if (last && (dbits(v) << 1) > (dbits(PHI_EPS) << 1)) {  // |v| > PHI_EPS
       // the outer two layers must stay empty (they are the stencil halo); a moving body's upwind
