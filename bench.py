@@ -43,16 +43,24 @@ def kernels_per_step(nb, mpf, fused):
 
 # DRAM bytes of one collision pass (k_collide + k_collide_near) from the committed one-pass ncu
 # captures (profiles/collision_pass_spheres2_*.md), valid only for the source they were taken on
-PROFILED = {("spheres2", "fp32", "7e864b04922e"): 347381248 + 272935936 + 12042240 + 272128,
-            ("spheres2", "fp16dev", "7e864b04922e"): 187728384 + 123556608 + 11989504 + 223744}
+# (source_hash of lbm.cu and cbl_dev.cuh)
+PROFILED = {("spheres2", "fp32", "b51ae6607d17"): (347.8e6 + 338.8e6) + (12.05e6 + 0.28e6),
+            ("spheres2", "fp16dev", "b51ae6607d17"): (187.7e6 + 123.3e6) + (12.0e6 + 0.25e6)}
+
+
+def source_hash():
+    """sha1 prefix of the collision kernels' sources (lbm.cu and the shared device header)."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for name in ("lbm.cu", "cbl_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_1902_10432_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def profiled_traffic(workload_name, prec):
-    import hashlib
-
-    with open(os.path.join(ROOT, "paper_1902_10432_gb300", "csrc", "lbm.cu"), "rb") as f:
-        h = hashlib.sha1(f.read()).hexdigest()[:12]
-    return PROFILED.get((workload_name, prec, h))
+    return PROFILED.get((workload_name, prec, source_hash()))
 
 
 def alg_bytes_per_cell(prec, q=19):
