@@ -170,6 +170,21 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Q, const
 /* Set body velocities (host arrays nb*3, either may be NULL). */
 cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W);
 
+/* Checkpoint (Sec. 3: the state between two steps is the populations, the phase fields, the
+ * obstacle flags and the bodies). cbl_save writes every buffer that carries state from one step to
+ * the next (both population buffers, flags, the last step's fields and forces, the body table, the
+ * phase-field tiles, the boundary-cell list, the step counter) to the file `path`, after
+ * synchronising the context's stream; CBL_ERR_STATE before cbl_init_fluid, CBL_ERR_ARG if the file
+ * cannot be written. cbl_load restores such a file into a context that was created with the same
+ * parameters, had the same bodies added (same shapes, so the same tiles; options that size the
+ * tiles, such as "tile_tail", set the same way) and was not initialised: it takes the place of
+ * cbl_init_fluid, and the restored state is the saved one bit for bit (later steps can differ from
+ * the uninterrupted run only by the order of FP64 atomic sums, as two runs do). CBL_ERR_ARG for
+ * a file of another version or of a different set-up, or a truncated file; CBL_ERR_STATE on an
+ * initialised context. The file is native-endian and tied to this build. */
+cbl_status cbl_save(cbl_ctx* ctx, const char* path);
+cbl_status cbl_load(cbl_ctx* ctx, const char* path);
+
 /* Hold or release bodies (host array of nb ints, 1 = held in place). A held body keeps its pose,
  * its V and omega are set to zero, and its forces are still reported; a released body starts from
  * rest. This is how the paper lets the liquid reach its equilibrium shape before the particles may

@@ -76,6 +76,8 @@ SIGNATURES = {
     "cbl_get_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cbl_set_body_velocities": (ctypes.c_int, [_P, _P, _P]),
     "cbl_set_bodies_fixed": (ctypes.c_int, [_P, _P]),
+    "cbl_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "cbl_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cbl_move_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "cbl_total_mass": (ctypes.c_int, [_P, _D]),
     "cbl_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
@@ -299,6 +301,13 @@ class Sim:
         v = None if V is None else np.ascontiguousarray(V, np.float64).reshape(-1)
         w = None if W is None else np.ascontiguousarray(W, np.float64).reshape(-1)
         self._ck(self._lib.cbl_set_body_velocities(self._h, _vp(v), _vp(w)))
+
+    def save(self, path):
+        self._ck(self._lib.cbl_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Restore a checkpoint instead of init_fluid (same parameters and bodies as the saved run)."""
+        self._ck(self._lib.cbl_load(self._h, os.fsencode(path)))
 
     def set_fixed(self, fixed):
         f = np.ascontiguousarray([1 if v else 0 for v in fixed], np.int32)

@@ -276,24 +276,33 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
 // kernel); the refill pass rebuilds them
 static void reset_member_boxes(cbl_ctx* ctx) { launch_reset_member_boxes(ctx->mbox, (int)ctx->hb.size(), ctx->s); }
 
+// device buffers of the bodies (tables, phase-field arena, per-step sums, boundary list)
+static cbl_status alloc_bodies(cbl_ctx* ctx) {
+  const int nb = (int)ctx->hb.size();
+  if (!nb) return CBL_OK;
+  ctx->db = (BodyDev*)dalloc(ctx, sizeof(BodyDev) * nb);
+  ctx->arena = (double*)dalloc(ctx, sizeof(double) * (size_t)ctx->arena_n);
+  ctx->acc = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
+  ctx->last = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
+  ctx->volacc = (double*)dalloc(ctx, sizeof(double) * 2 * nb);
+  ctx->scratch = (double*)dalloc(ctx, sizeof(double) * 9 * nb);
+  for (const BodyDev& b : ctx->hb)
+    for (int a = 0; a < 3; ++a) ctx->Lmax = std::max(ctx->Lmax, b.L[a]);
+  ctx->rtab = (double*)dalloc(ctx, sizeof(double) * 3 * (size_t)ctx->Lmax * nb);
+  ctx->mbox = (int*)dalloc(ctx, sizeof(int) * 6 * nb);
+  ctx->blist = (int*)dalloc(ctx, sizeof(int) * (size_t)(ctx->arena_n / 3));
+  if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch || !ctx->blist ||
+      !ctx->rtab || !ctx->mbox)
+    return fail(ctx, CBL_ERR_OOM, "device allocation failed (bodies)");
+  return CBL_OK;
+}
+
 static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double* u_host) {
   const size_t N = (size_t)ctx->lat.N;
   const int nb = (int)ctx->hb.size();
   if (nb) {
-    ctx->db = (BodyDev*)dalloc(ctx, sizeof(BodyDev) * nb);
-    ctx->arena = (double*)dalloc(ctx, sizeof(double) * (size_t)ctx->arena_n);
-    ctx->acc = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
-    ctx->last = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
-    ctx->volacc = (double*)dalloc(ctx, sizeof(double) * 2 * nb);
-    ctx->scratch = (double*)dalloc(ctx, sizeof(double) * 9 * nb);
-    for (const BodyDev& b : ctx->hb)
-      for (int a = 0; a < 3; ++a) ctx->Lmax = std::max(ctx->Lmax, b.L[a]);
-    ctx->rtab = (double*)dalloc(ctx, sizeof(double) * 3 * (size_t)ctx->Lmax * nb);
-    ctx->mbox = (int*)dalloc(ctx, sizeof(int) * 6 * nb);
-    ctx->blist = (int*)dalloc(ctx, sizeof(int) * (size_t)(ctx->arena_n / 3));
-    if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch || !ctx->blist ||
-        !ctx->rtab || !ctx->mbox)
-      return fail(ctx, CBL_ERR_OOM, "device allocation failed (bodies)");
+    const cbl_status sa = alloc_bodies(ctx);
+    if (sa != CBL_OK) return sa;
     for (BodyDev& b : ctx->hb) mirror_f(b);
     CK(cudaMemcpyAsync(ctx->db, ctx->hb.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
     CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * ACC_N * nb, ctx->s));
@@ -749,6 +758,164 @@ cbl_status cbl_set_bodies_fixed(cbl_ctx* ctx, const int* fixed) {
   }
   CK(cudaMemcpyAsync(ctx->db, h.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
+  return CBL_OK;
+}
+
+// ---- checkpoint / resume -------------------------------------------------------------------------
+// File: magic, version, the parameters that shape the state, the host scalars, then every device
+// buffer that carries state from one step to the next (both population buffers, flags, the last
+// step's fields, the body table, phase-field arena, force sums, boundary list, step state). The
+// scratch that each step rebuilds (psi, the near-solid side buffer, mass partials, offset tables)
+// is not stored.
+static const char CKPT_MAGIC[8] = {'C', 'B', 'L', 'S', 'T', 'A', 'T', 'E'};
+static const int CKPT_VERSION = 1;
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int version, q, prec, nb;
+  int nx, ny, nz, Lmax;
+  long long N, Ns, arena_n, t;
+  double tau, G, rho0, ext[3], mobility, eta, sigma_sf, sigma_ss, e0, rc, solid_thr, member_thr;
+  int mpf, nrep;
+};
+
+struct Buf {
+  void* dev;
+  size_t bytes;
+};
+}  // namespace
+
+static CkptHeader ckpt_header(const cbl_ctx* ctx) {
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, CKPT_MAGIC, 8);
+  h.version = CKPT_VERSION;
+  h.q = ctx->ops.q;
+  h.prec = ctx->prec;
+  h.nb = (int)ctx->hb.size();
+  h.nx = ctx->p.nx;
+  h.ny = ctx->p.ny;
+  h.nz = ctx->p.nz;
+  h.Lmax = ctx->Lmax;
+  h.N = ctx->lat.N;
+  h.Ns = ctx->lat.Ns;
+  h.arena_n = ctx->arena_n;
+  h.t = ctx->t;
+  h.tau = ctx->p.tau;
+  h.G = ctx->p.G;
+  h.rho0 = ctx->p.rho0;
+  for (int a = 0; a < 3; ++a) h.ext[a] = ctx->p.ext_force[a];
+  h.mobility = ctx->p.mobility;
+  h.eta = ctx->p.eta;
+  h.sigma_sf = ctx->p.sigma_sf;
+  h.sigma_ss = ctx->p.sigma_ss;
+  h.e0 = ctx->p.e0;
+  h.rc = ctx->p.rc;
+  h.solid_thr = ctx->p.solid_threshold;
+  h.member_thr = ctx->p.member_threshold;
+  h.mpf = ctx->p.mpf_kinetics;
+  h.nrep = ctx->p.nrep;
+  return h;
+}
+
+static std::vector<Buf> ckpt_buffers(cbl_ctx* ctx) {
+  const size_t N = (size_t)ctx->lat.N, nb = ctx->hb.size();
+  const size_t pop = (size_t)ctx->lat.Ns * ctx->ops.q * ctx->elem;
+  std::vector<Buf> v = {{ctx->fa, pop},       {ctx->fb, pop},           {ctx->flags, N * 2},
+                        {ctx->diag_rho, N * 8}, {ctx->diag_vel, N * 24}, {ctx->st, sizeof(StepState)}};
+  if (nb) {
+    v.push_back({ctx->arena, sizeof(double) * (size_t)ctx->arena_n});
+    v.push_back({ctx->acc, sizeof(double) * ACC_N * nb});
+    v.push_back({ctx->last, sizeof(double) * ACC_N * nb});
+    v.push_back({ctx->volacc, sizeof(double) * 2 * nb});
+    v.push_back({ctx->mbox, sizeof(int) * 6 * nb});
+    v.push_back({ctx->blist, sizeof(int) * (size_t)(ctx->arena_n / 3)});
+  }
+  return v;
+}
+
+cbl_status cbl_save(cbl_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "cbl_save before cbl_init_fluid");
+  CK(cudaStreamSynchronize(ctx->s));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, CBL_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  const CkptHeader h = ckpt_header(ctx);
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+  const int nb = (int)ctx->hb.size();
+  std::vector<BodyDev> bodies(nb);
+  cbl_status st = CBL_OK;
+  if (nb) {
+    st = cuda_check(ctx, cudaMemcpy(bodies.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost), "save");
+    ok = ok && st == CBL_OK && std::fwrite(bodies.data(), sizeof(BodyDev), nb, f) == (size_t)nb;
+  }
+  std::vector<char> host;
+  for (const Buf& b : ckpt_buffers(ctx)) {
+    if (!ok) break;
+    host.resize(b.bytes);
+    st = cuda_check(ctx, cudaMemcpy(host.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost), "save");
+    ok = st == CBL_OK && std::fwrite(host.data(), 1, b.bytes, f) == b.bytes;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (st != CBL_OK) return st;
+  if (!ok) return fail(ctx, CBL_ERR_ARG, std::string("write to ") + path + " failed");
+  return CBL_OK;
+}
+
+cbl_status cbl_load(cbl_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "cbl_load needs a context that is not initialised yet");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, CBL_ERR_ARG, std::string("cannot open ") + path);
+  CkptHeader h;
+  const CkptHeader mine = ckpt_header(ctx);
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1;
+  if (!ok || std::memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != CKPT_VERSION) {
+    std::fclose(f);
+    return fail(ctx, CBL_ERR_ARG, std::string(path) + " is not a checkpoint of this library version");
+  }
+  // everything but the step counter must match: parameters, velocity set, precision, bodies, tiles
+  CkptHeader a = h, b = mine;
+  a.t = b.t = 0;
+  a.Lmax = b.Lmax = 0;  // derived from the tiles, compared through the body table below
+  if (std::memcmp(&a, &b, sizeof(a)) != 0) {
+    std::fclose(f);
+    return fail(ctx, CBL_ERR_ARG, "the checkpoint's parameters, velocity set, precision or bodies differ from the context's");
+  }
+  const int nb = h.nb;
+  std::vector<BodyDev> bodies(nb);
+  if (nb && std::fread(bodies.data(), sizeof(BodyDev), nb, f) != (size_t)nb) ok = false;
+  for (int i = 0; ok && i < nb; ++i)
+    for (int k = 0; k < 3; ++k)
+      if (bodies[i].L[k] != ctx->hb[i].L[k] || bodies[i].off != ctx->hb[i].off || bodies[i].sz != ctx->hb[i].sz)
+        ok = false;
+  if (!ok) {
+    std::fclose(f);
+    return fail(ctx, CBL_ERR_ARG, "the checkpoint's bodies or their tiles differ from the context's");
+  }
+  const cbl_status sa = alloc_bodies(ctx);
+  if (sa != CBL_OK) {
+    std::fclose(f);
+    return sa;
+  }
+  ctx->hb = bodies;
+  cbl_status st = CBL_OK;
+  if (nb) st = cuda_check(ctx, cudaMemcpy(ctx->db, bodies.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice), "load");
+  std::vector<char> host;
+  for (const Buf& bf : ckpt_buffers(ctx)) {
+    if (st != CBL_OK || !ok) break;
+    host.resize(bf.bytes);
+    ok = std::fread(host.data(), 1, bf.bytes, f) == bf.bytes;
+    if (ok) st = cuda_check(ctx, cudaMemcpy(bf.dev, host.data(), bf.bytes, cudaMemcpyHostToDevice), "load");
+  }
+  std::fclose(f);
+  if (st != CBL_OK) return st;
+  if (!ok) return fail(ctx, CBL_ERR_ARG, std::string(path) + " is truncated");
+  CK(cudaMemsetAsync(ctx->mass_part, 0, (size_t)ctx->n_mass_part * 8, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  ctx->t = h.t;
+  ctx->ready = true;
   return CBL_OK;
 }
 

@@ -54,3 +54,6 @@ def test_argument_errors_without_gpu(lib):
     assert lib.cbl_create(None, None, ctypes.byref(h)) == 1
     assert lib.cbl_step(None, 1) == 1
     assert lib.cbl_destroy(None) == 0
+    assert lib.cbl_save(None, b"/nonexistent/x") == 1
+    assert lib.cbl_load(None, b"/nonexistent/x") == 1
+    assert lib.cbl_set_bodies_fixed(None, None) == 1
