@@ -49,14 +49,17 @@ def test_flat_interface_bulk_densities_and_planar_tension(q, tau):
     assert abs(sig - 3.297e-2) < 0.01 * 3.297e-2, sig  # Sec. 4.1 printed value
 
 
-def test_laplace_law_cylindrical_droplets_d3q27():
+@pytest.mark.parametrize("q,tau,tol,tol_meas", [(27, 1.1, 0.02, 0.05), (19, 1.0, 0.03, 0.06)])
+def test_laplace_law_cylindrical_droplets(q, tau, tol, tol_meas):
     # Sec. 4.1: cylindrical droplets, pressure difference from Eq. pressure vs 1/R; the paper's
-    # fit gives sigma = 3.583e-2. Fitted here against the nominal radii (within 2 %) and
-    # against the radii measured from the liquid area (within 5 %).
+    # fit (D3Q27, tau = 1.1) gives sigma = 3.583e-2. Fitted here against the nominal radii (within
+    # 2 %) and against the radii measured from the liquid area (within 5 %); the D3Q19, tau = 1
+    # fluid of the workloads is within 3 % of the same value with the nominal radii and 6 % with the
+    # measured ones (its fits are printed: 3.50e-2 and 3.40e-2)
     n = 80
     nominal, measured, dps = [], [], []
     for R in (12, 16, 20):
-        o = oracle.Oracle(n, 1, n, q=27, tau=1.1)
+        o = oracle.Oracle(n, 1, n, q=q, tau=tau)
         z, x = np.mgrid[0:n, 0:n]
         mask = (x - n / 2 + 0.5) ** 2 + (z - n / 2 + 0.5) ** 2 <= R * R
         o.init_fluid(RHO_L, RHO_V, mask.reshape(n, 1, n))
@@ -71,7 +74,8 @@ def test_laplace_law_cylindrical_droplets_d3q27():
         dps.append(dp)
     s_nom = an.laplace_slope(nominal, dps)
     s_meas = an.laplace_slope(measured, dps)
-    assert abs(s_nom - 3.583e-2) < 0.02 * 3.583e-2, s_nom
-    assert abs(s_meas - 3.583e-2) < 0.05 * 3.583e-2, s_meas
+    print("D3Q%d tau %.1f: Laplace sigma %.5f (nominal radii), %.5f (measured radii)" % (q, tau, s_nom, s_meas))
+    assert abs(s_nom - 3.583e-2) < tol * 3.583e-2, s_nom
+    assert abs(s_meas - 3.583e-2) < tol_meas * 3.583e-2, s_meas
     # linear in 1/R: each point within 4 % of the fitted line
     assert np.all(np.abs(np.array(dps) / (s_nom * np.array(nominal)) - 1) < 0.04)
