@@ -171,9 +171,12 @@ def cpu_baseline(w, budget_s=20.0):
     times += run_oracle_steps(w, n, 0, threads) if n > 1 else []
     steps = len(times)
     tot = sum(times)
+    one = run_oracle_steps(w, 2, 0, 1)  # the same sample on one core, two steps
     return {"value": w.ncells * steps / tot / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
             "sample": "%s %dx%dx%d, %d time steps of the FP64 oracle (set-up excluded)" % (w.name, w.nx, w.ny, w.nz,
-                                                                                         steps)}
+                                                                                         steps),
+            "one_core": {"value": w.ncells * len(one) / sum(one) / 1e6, "unit": "MLUPS", "cores": 1,
+                         "sample": "the same lattice, %d time steps" % len(one)}}
 
 
 def bench_reference(args, rank, world):
