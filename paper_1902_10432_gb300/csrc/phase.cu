@@ -356,93 +356,117 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
   if (a.nnb == 0) return;  // block-uniform
   // block-uniform cull: member points (phi >= 1/2) lie within the support of the profile, the
   // shape's bounding sphere grown by eta/2; no pair can be within rc unless two such spheres are
+  // and the member boxes: every member point of A lies in A's box, so if along some axis the two
+  // boxes are more than Rc cells apart (periodic distance), no point of A passes the per-point box
+  // test below
   __shared__ int s_near;
   if (threadIdx.x == 0) {
     int nearby = 0;
     const double ea = support_radius(a, eta);
+    const int nn[3] = {lat.nx, lat.ny, lat.nz};
+    const int* ba = mbox + 6 * self;
     for (int k = 0; k < a.nnb && !nearby; ++k) {
       const BodyDev& b = bodies[a.nbl[k]];
       const double dx = mimg(b.X[0] - a.X[0], lat.nx), dy = mimg(b.X[1] - a.X[1], lat.ny),
                    dz = mimg(b.X[2] - a.X[2], lat.nz);
       const double lim = ea + support_radius(b, eta) + rc + 1.0;
-      nearby = dx * dx + dy * dy + dz * dz <= lim * lim;
+      if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
+      const int* bb = mbox + 6 * a.nbl[k];
+      bool boxes = true;
+      for (int d = 0; d < 3 && boxes; ++d) {
+        if (ba[d] > ba[3 + d] || bb[d] > bb[3 + d]) {  // an empty box: no members
+          boxes = false;
+          break;
+        }
+        // centres and half-lengths (in half cells) of the two boxes in lattice coordinates
+        const int ca2 = 2 * a.o[d] + ba[d] + ba[3 + d], cb2 = 2 * b.o[d] + bb[d] + bb[3 + d];
+        const int ha2 = ba[3 + d] - ba[d], hb2 = bb[3 + d] - bb[d];
+        int sep2 = wrapi(cb2 - ca2, 2 * nn[d]);
+        if (sep2 > nn[d]) sep2 = 2 * nn[d] - sep2;  // periodic distance of the centres
+        if (sep2 - ha2 - hb2 > 2 * Rc) boxes = false;
+      }
+      nearby = boxes;
     }
     s_near = nearby;
   }
   __syncthreads();
   if (!s_near) return;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tb = dbits(thr);
-  double F[3] = {0, 0, 0};
-  bool has = false;
-  TileCell c;
-  if (t < a.sz && dbits(arena[a.off + t]) >= tb) {
-    c = tile_cell(a, t, lat);
-    const int g[3] = {c.gx, c.gy, c.gz};
-    const int nn[3] = {lat.nx, lat.ny, lat.nz};
-    for (int k = 0; k < a.nnb; ++k) {
-      const BodyDev& b = bodies[a.nbl[k]];
-      // this point's coordinates in the other body's tile, wrapped to [0, n); skip unless the point
-      // lies within rc of that tile
-      // tile coordinates of the other body's member cells (phi >= thr) lie in its box mbox (built by
-      // the refill pass after the last flag update); the offsets reach Rc cells per axis, so a point
-      // outside the box grown by Rc (periodically) finds no partner
-      const int* bx = mbox + 6 * a.nbl[k];
-      int l[3];
-      bool near = true;
-      for (int d = 0; d < 3; ++d) {
-        l[d] = wrapi(g[d] - b.o[d], nn[d]);
-        const int lo = bx[d] - Rc, hi = bx[3 + d] + Rc;
-        const bool in = (l[d] >= lo && l[d] <= hi) || (l[d] - nn[d] >= lo && l[d] - nn[d] <= hi) ||
-                        (l[d] + nn[d] >= lo && l[d] + nn[d] <= hi);
-        if (bx[d] > bx[3 + d] || !in) near = false;  // an empty box has no members
-      }
-      if (!near) continue;
-      const double* bb = arena + b.off;
-      // offsets in groups of 8: the group's loads are issued before any of them is tested (a
-      // test per load would wait for each load in turn); contributions are added in offset order
-      for (int j0 = 0; j0 < c_noff; j0 += 8) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int j = j0 + u;
-          long long q = -1;
-          if (j < c_noff) {
-            int m[3];
-            bool in = true;
-            for (int d = 0; d < 3; ++d) {
-              m[d] = l[d] + c_off[3 * j + d];  // |offset| <= 6: at most two wraps on a 4-cell side
-              while (m[d] < 0) m[d] += nn[d];
-              while (m[d] >= nn[d]) m[d] -= nn[d];
-              in &= m[d] < b.L[d];
-            }
-            if (in) q = (long long)m[0] + (long long)b.L[0] * ((long long)m[1] + (long long)b.L[1] * m[2]);
-          }
-          v[u] = q >= 0 ? __ldg(bb + q) : 0.0;
+  // grid-stride over the tile: a grid of a few waves, so that the common case (no pair in range,
+  // every block leaves after the cull above) costs one short launch
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < a.sz; base += (long long)gridDim.x * blockDim.x) {
+    const long long t = base + threadIdx.x;
+    double F[3] = {0, 0, 0};
+    bool has = false;
+    TileCell c;
+    if (t < a.sz && dbits(arena[a.off + t]) >= tb) {
+      c = tile_cell(a, t, lat);
+      const int g[3] = {c.gx, c.gy, c.gz};
+      const int nn[3] = {lat.nx, lat.ny, lat.nz};
+      for (int k = 0; k < a.nnb; ++k) {
+        const BodyDev& b = bodies[a.nbl[k]];
+        // this point's coordinates in the other body's tile, wrapped to [0, n); skip unless the point
+        // lies within rc of that tile
+        // tile coordinates of the other body's member cells (phi >= thr) lie in its box mbox (built by
+        // the refill pass after the last flag update); the offsets reach Rc cells per axis, so a point
+        // outside the box grown by Rc (periodically) finds no partner
+        const int* bx = mbox + 6 * a.nbl[k];
+        int l[3];
+        bool near = true;
+        for (int d = 0; d < 3; ++d) {
+          l[d] = wrapi(g[d] - b.o[d], nn[d]);
+          const int lo = bx[d] - Rc, hi = bx[3 + d] + Rc;
+          const bool in = (l[d] >= lo && l[d] <= hi) || (l[d] - nn[d] >= lo && l[d] - nn[d] <= hi) ||
+                          (l[d] + nn[d] >= lo && l[d] + nn[d] <= hi);
+          if (bx[d] > bx[3 + d] || !in) near = false;  // an empty box has no members
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int j = j0 + u;
-          if (j >= c_noff || dbits(v[u]) < tb) continue;
-          F[0] += c_offf[3 * j];
-          F[1] += c_offf[3 * j + 1];
-          F[2] += c_offf[3 * j + 2];
-          has = true;
+        if (!near) continue;
+        const double* bb = arena + b.off;
+        // offsets in groups of 8: the group's loads are issued before any of them is tested (a
+        // test per load would wait for each load in turn); contributions are added in offset order
+        for (int j0 = 0; j0 < c_noff; j0 += 8) {
+          double v[8];
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u;
+            long long q = -1;
+            if (j < c_noff) {
+              int m[3];
+              bool in = true;
+              for (int d = 0; d < 3; ++d) {
+                m[d] = l[d] + c_off[3 * j + d];  // |offset| <= 6: at most two wraps on a 4-cell side
+                while (m[d] < 0) m[d] += nn[d];
+                while (m[d] >= nn[d]) m[d] -= nn[d];
+                in &= m[d] < b.L[d];
+              }
+              if (in) q = (long long)m[0] + (long long)b.L[0] * ((long long)m[1] + (long long)b.L[1] * m[2]);
+            }
+            v[u] = q >= 0 ? __ldg(bb + q) : 0.0;
+          }
+  #pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u;
+            if (j >= c_noff || dbits(v[u]) < tb) continue;
+            F[0] += c_offf[3 * j];
+            F[1] += c_offf[3 * j + 1];
+            F[2] += c_offf[3 * j + 2];
+            has = true;
+          }
         }
       }
     }
-  }
-  if (__ballot_sync(0xffffffffu, has) == 0) return;
-  double T[3] = {0, 0, 0};
-  if (has) {
-    const double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
-    xcross(arm, F, T);
-  }
-  for (int p = 0; p < 3; ++p) {
-    double sf = dwarp_sum(F[p]), st = dwarp_sum(T[p]);
-    if ((threadIdx.x & 31) == 0) {
-      if (sf != 0.0) atomicAdd(acc + (size_t)self * ACC_N + ACC_REP_F + p, sf);
-      if (st != 0.0) atomicAdd(acc + (size_t)self * ACC_N + ACC_REP_T + p, st);
+    if (__ballot_sync(0xffffffffu, has) == 0) continue;
+    double T[3] = {0, 0, 0};
+    if (has) {
+      const double arm[3] = {mimg(c.gx - a.X[0], lat.nx), mimg(c.gy - a.X[1], lat.ny), mimg(c.gz - a.X[2], lat.nz)};
+      xcross(arm, F, T);
+    }
+    for (int p = 0; p < 3; ++p) {
+      double sf = dwarp_sum(F[p]), st = dwarp_sum(T[p]);
+      if ((threadIdx.x & 31) == 0) {
+        if (sf != 0.0) atomicAdd(acc + (size_t)self * ACC_N + ACC_REP_F + p, sf);
+        if (st != 0.0) atomicAdd(acc + (size_t)self * ACC_N + ACC_REP_T + p, st);
+      }
     }
   }
 }
@@ -1039,9 +1063,17 @@ void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, do
 }
 void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
                       const PhysParams& pp, const int* mbox, cudaStream_t s) {
-  if (nb > 1 && pp.e0 != 0.0)
-    k_repulsion<<<tile_grid(max_tile, nb), 256, 0, s>>>(bodies, arena, acc, lat, pp.rc, (int)std::ceil(pp.rc),
-                                                       pp.member_threshold, pp.eta, mbox);
+  if (nb > 1 && pp.e0 != 0.0) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    dim3 g = tile_grid(max_tile, nb);
+    // a few waves in all, but never more than four chunks of the tile per block (many bodies)
+    const unsigned cap = std::max((g.x + 3) / 4, (unsigned)std::max(1, 4 * nsm / nb));
+    if (g.x > cap) g.x = cap;
+    k_repulsion<<<g, 256, 0, s>>>(bodies, arena, acc, lat, pp.rc, (int)std::ceil(pp.rc), pp.member_threshold, pp.eta,
+                                  mbox);
+  }
 }
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
                    StepState* st, double* rtab, int Lmax, int* mbox, cudaStream_t s) {
