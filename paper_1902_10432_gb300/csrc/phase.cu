@@ -900,7 +900,6 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
   }
   // active solids in ascending id order, with their 7-point values
   double vals[MAXACT][7];
-  int ids[MAXACT];
   int dslot[MAXACT];  // slot of each active phase in sD
   int na = 0;
   int pos_self = -1;
@@ -917,7 +916,7 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
         S[k] += pa[k];
       }
       dslot[na] = 0;
-      ids[na++] = self;
+      ++na;
       continue;
     }
     const int slot = k_nb;  // b.nbl[slot - 1] == id
@@ -943,7 +942,7 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
         S[k] += v7[k];
       }
       dslot[na] = slot;
-      ids[na++] = id;
+      ++na;
     }
   }
   // S >= 0, so the signed bit patterns order like the values
