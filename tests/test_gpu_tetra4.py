@@ -9,7 +9,6 @@ states the errors; the FP64 test pins the implementation."""
 import json
 import os
 
-import numpy as np
 import pytest
 
 from paper_1902_10432_gb300 import workloads

@@ -3,7 +3,6 @@
 Sec. 3.2.1 (velocity set, equilibrium, BGK, Guo forcing, streaming) and Sec. 3.2.2
 (bounce-back, momentum exchange, mass correction).
 """
-import math
 
 import numpy as np
 import pytest
