@@ -1,7 +1,8 @@
 """Learned force surrogate for bridged sphere pairs, and the surrogate-driven body advance.
 
 Not part of the paper's method: the network stands in for the lattice-Boltzmann force evaluation
-between full evaluations, and the plain method is both its fallback and the judge of its error.
+between full evaluations, and the plain method is both its fallback and the reference its error is
+measured against.
 
 * Features of a pair (i, j), with R* = 2 R_i R_j / (R_i + R_j) and bridge volume V_L: the scaled gap
   s sqrt(R* / V_L) of a pendular bridge, cos(contact angle), R_i / R_j and V_L / R*^3. Targets: force
