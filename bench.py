@@ -44,8 +44,9 @@ def kernels_per_step(nb, mpf, fused):
 # DRAM bytes of one collision pass (k_collide + k_collide_near) from the committed one-pass ncu
 # captures (profiles/collision_pass_spheres2_*.md), valid only for the source they were taken on
 # (source_hash of lbm.cu and cbl_dev.cuh)
-PROFILED = {("spheres2", "fp32", "b51ae6607d17"): (347.8e6 + 338.8e6) + (12.05e6 + 0.28e6),
-            ("spheres2", "fp16dev", "b51ae6607d17"): (187.7e6 + 123.3e6) + (12.0e6 + 0.25e6)}
+PROFILED = {("spheres2", "fp32", 19, "b51ae6607d17"): (347.8e6 + 338.8e6) + (12.05e6 + 0.28e6),
+            ("spheres2", "fp16dev", 19, "b51ae6607d17"): (187.7e6 + 123.3e6) + (12.0e6 + 0.25e6),
+            ("spheres2", "fp32", 27, "b51ae6607d17"): (483.2e6 + 421.2e6) + (17.15e6 + 0.75e6)}
 
 
 def source_hash():
@@ -59,8 +60,8 @@ def source_hash():
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(workload_name, prec):
-    return PROFILED.get((workload_name, prec, source_hash()))
+def profiled_traffic(workload_name, prec, q=19):
+    return PROFILED.get((workload_name, prec, q, source_hash()))
 
 
 def alg_bytes_per_cell(prec, q=19):
@@ -416,7 +417,7 @@ def bench_cuda(args, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": "collision pass (k_collide + k_collide_near)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(w.name, prec), "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": profiled_traffic(w.name, prec, int(w.params.get("q", 19))), "peak_kind": peak_kind,
                          "alg_bytes_per_cell": bpc,
                          "step_frac": bpc * w.ncells / (ms_max / args.steps * 1e-3) / 1e9 / peak},
             "phases_ms": {k: round(v, 5) for k, v in phases.items()},
