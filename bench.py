@@ -435,6 +435,29 @@ def bench_cuda(args, rank, world, local_rank):
     return 0
 
 
+def pattern_probe():
+    """Bandwidth of the bare D3Q19 pull pattern next to unshifted streams and a copy (the ceiling of
+    the collision pass's access pattern); prints the probe's lines and one JSON summary line."""
+    import re
+    import subprocess
+    import tempfile
+
+    src = os.path.join(ROOT, "paper_1902_10432_gb300", "csrc", "pattern_probe.cu")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "pattern_probe")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    print(out, end="", file=sys.stderr)
+    best = {}
+    for name, us, gbs in re.findall(r"^(\w+)\s+([\d.]+) us\s+([\d.]+) GB/s", out, flags=re.M):
+        best[name] = max(best.get(name, 0.0), float(gbs))
+    peak, _ = measured_peaks()
+    print(json.dumps({"metric": "pattern bandwidth", "unit": "GB/s", "best_of_3": best, "peak": peak,
+                      "frac_of_peak": {k: v / peak for k, v in best.items()},
+                      "check": out.strip().splitlines()[-2] if out.strip() else ""}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -459,7 +482,11 @@ def main():
     ap.add_argument("--sur-pack-equil", type=int, default=1000)
     ap.add_argument("--sur-save", default="", help="write the training samples to this .npz")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pattern-probe", action="store_true",
+                    help="build and run the access-pattern probe of the collision pass (csrc/pattern_probe.cu)")
     args = ap.parse_args()
+    if args.pattern_probe:
+        return pattern_probe()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
