@@ -835,6 +835,13 @@ static std::vector<Buf> ckpt_buffers(cbl_ctx* ctx) {
   return v;
 }
 
+// a copy ordered on the context's stream (its buffers come from a stream-ordered allocator), waited for
+static cbl_status copy_sync(cbl_ctx* ctx, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  cbl_status st = cuda_check(ctx, cudaMemcpyAsync(dst, src, bytes, kind, ctx->s), "checkpoint copy");
+  if (st == CBL_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->s), "checkpoint copy");
+  return st;
+}
+
 cbl_status cbl_save(cbl_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(ctx, CBL_ERR_ARG, "NULL argument");
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "cbl_save before cbl_init_fluid");
@@ -847,14 +854,14 @@ cbl_status cbl_save(cbl_ctx* ctx, const char* path) {
   std::vector<BodyDev> bodies(nb);
   cbl_status st = CBL_OK;
   if (nb) {
-    st = cuda_check(ctx, cudaMemcpy(bodies.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost), "save");
+    st = copy_sync(ctx, bodies.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost);
     ok = ok && st == CBL_OK && std::fwrite(bodies.data(), sizeof(BodyDev), nb, f) == (size_t)nb;
   }
   std::vector<char> host;
   for (const Buf& b : ckpt_buffers(ctx)) {
     if (!ok) break;
     host.resize(b.bytes);
-    st = cuda_check(ctx, cudaMemcpy(host.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost), "save");
+    st = copy_sync(ctx, host.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost);
     ok = st == CBL_OK && std::fwrite(host.data(), 1, b.bytes, f) == b.bytes;
   }
   ok = (std::fclose(f) == 0) && ok;
@@ -901,13 +908,13 @@ cbl_status cbl_load(cbl_ctx* ctx, const char* path) {
   }
   ctx->hb = bodies;
   cbl_status st = CBL_OK;
-  if (nb) st = cuda_check(ctx, cudaMemcpy(ctx->db, bodies.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice), "load");
+  if (nb) st = copy_sync(ctx, ctx->db, bodies.data(), sizeof(BodyDev) * nb, cudaMemcpyHostToDevice);
   std::vector<char> host;
   for (const Buf& bf : ckpt_buffers(ctx)) {
     if (st != CBL_OK || !ok) break;
     host.resize(bf.bytes);
     ok = std::fread(host.data(), 1, bf.bytes, f) == bf.bytes;
-    if (ok) st = cuda_check(ctx, cudaMemcpy(bf.dev, host.data(), bf.bytes, cudaMemcpyHostToDevice), "load");
+    if (ok) st = copy_sync(ctx, bf.dev, host.data(), bf.bytes, cudaMemcpyHostToDevice);
   }
   std::fclose(f);
   if (st != CBL_OK) return st;
