@@ -452,9 +452,11 @@ def pattern_probe():
     for name, us, gbs in re.findall(r"^(\w+)\s+([\d.]+) us\s+([\d.]+) GB/s", out, flags=re.M):
         best[name] = max(best.get(name, 0.0), float(gbs))
     peak, _ = measured_peaks()
+    fma = {name: float(v) for name, v in re.findall(r"^(fma\d+)\s+[\d.]+ us\s+([\d.]+) TFLOP/s", out, flags=re.M)}
+    check = [l for l in out.splitlines() if "mismatches" in l]
     print(json.dumps({"metric": "pattern bandwidth", "unit": "GB/s", "best_of_3": best, "peak": peak,
-                      "frac_of_peak": {k: v / peak for k, v in best.items()},
-                      "check": out.strip().splitlines()[-2] if out.strip() else ""}), flush=True)
+                      "frac_of_peak": {k: v / peak for k, v in best.items()}, "fma_tflops": fma,
+                      "check": check[0] if check else ""}), flush=True)
     return 0
 
 

@@ -5,7 +5,8 @@
 // them at x; pullrow: the same with every load aligned (one block per x-row, the x shift done with
 // warp shuffles and shared memory at the warp edges); local38: 19 loads and 19 stores at x; copy:
 // one contiguous copy of the same bytes. Prints one line per kernel and round, then a check that
-// pull19 and pullrow store the same values.
+// pull19 and pullrow store the same values, then the FP32 and FP64 FMA throughput (independent
+// chains, all SMs).
 #include <cstdio>
 #include <cuda_runtime.h>
 #include <cstdlib>
@@ -77,6 +78,24 @@ __global__ void __launch_bounds__(128) pullrow(const float* __restrict__ a, floa
   for (int i = 0; i < 19; ++i) b[i * st + n] = f[i] + 1e-30f * s;
 }
 
+
+// FMA throughput: 8 independent chains per thread, ITER iterations; one store per thread keeps the
+// chains live
+template <typename T>
+__global__ void __launch_bounds__(256) fma_rate(T* out, int iter, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+  for (int i = 0; i < iter; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = x[k] * a + b;
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(128) local38(const float* __restrict__ a, float* __restrict__ b, int nx, int ny, int nz, long long st) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 4 + (threadIdx.x >> 5);
@@ -127,6 +146,26 @@ int main() {
     long long bad = 0;
     for (int i = 0; i < 19; ++i) for (long long k = 0; k < N; ++k) bad += h[i * st + k] != h2[i * st + k];
     printf("pullrow mismatches vs pull: %lld\n", bad);
+  }
+  {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = nsm * 8, threads = 256;
+    float* o32; double* o64;
+    cudaMalloc(&o32, (size_t)blocks * threads * sizeof(float));
+    cudaMalloc(&o64, (size_t)blocks * threads * sizeof(double));
+    float ms;
+    const int it32 = 4096, it64 = 64;
+    fma_rate<float><<<blocks, threads>>>(o32, it32, 0.999f, 0.001f);
+    cudaEventRecord(e0); fma_rate<float><<<blocks, threads>>>(o32, it32, 0.999f, 0.001f); cudaEventRecord(e1); cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("fma32    %.1f us  %.1f TFLOP/s\n", ms * 1000, 2.0 * 8 * it32 * (double)blocks * threads / (ms * 1e-3) / 1e12);
+    fma_rate<double><<<blocks, threads>>>(o64, it64, 0.999, 0.001);
+    cudaEventRecord(e0); fma_rate<double><<<blocks, threads>>>(o64, it64, 0.999, 0.001); cudaEventRecord(e1); cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("fma64    %.1f us  %.3f TFLOP/s\n", ms * 1000, 2.0 * 8 * it64 * (double)blocks * threads / (ms * 1e-3) / 1e12);
+    cudaFree(o32); cudaFree(o64);
   }
   printf("err %s\n", cudaGetErrorString(cudaGetLastError()));
   return 0;
