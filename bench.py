@@ -1,17 +1,21 @@
 """Benchmark: MLUPS and fraction of the HBM roofline of the capillary-bridge time step on GB300.
 
-Workload (default): two free spheres R = 20 joined by a liquid bridge in a 128 x 128 x 256 periodic
-box, D3Q19, FP32 populations, phase-field kinetics on (the two-sphere set-up of Sec. 4.3.1 at
-R = 20). One step = the whole hot path: pull streaming + bounce-back, density/psi, Shan-Chen force,
-Guo-BGK collision, FP64 body reductions, repulsion, rigid-body update, phase-field advection and
-kinetics, flags and refill.
+Workload (default, tetra4): four free spheres R = 24 in a jittered tetrahedral cluster around a
+central drop (liquid 0.05 of the solid volume, 60 degrees) in a 256^3 periodic box, D3Q19, FP32
+populations, phase-field kinetics on (the four-particle set-up of Sec. 4.3.2 at R = 24). One step =
+the whole hot path: pull streaming + bounce-back, density/psi, Shan-Chen force, Guo-BGK collision,
+FP64 body reductions, repulsion, rigid-body update, phase-field advection and kinetics, flags and
+refill. Other workloads: spheres2 (two spheres in 128x128x256), plates48, batch64, surrogate.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--precision fp32]
 
+The timed region is exactly K steps (one replay of the step graph each), bracketed by a barrier and a
+device synchronisation; it is repeated (at least 5 times, and until about two seconds of load have
+passed, so that the clock sampler sees the GPU busy) and the median repeat is reported.
 N > 1 runs under torchrun as independent replicas (one per GPU, no collective: the step does not
 shard across GPUs in this build); value = cells x steps summed over ranks / max time.
 --impl reference times the FP64 CPU oracle (the slow, plain implementation the CUDA path is
-checked against) on the same workload on the host cores.
+checked against) on the host cores, on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -41,20 +45,19 @@ def kernels_per_step(nb, mpf, fused):
     return k
 
 
-# DRAM bytes of one collision pass (k_collide + k_collide_near) from the committed one-pass ncu
-# captures (profiles/collision_pass_spheres2_*.md), valid only for the source they were taken on
-# (source_hash of lbm.cu and cbl_dev.cuh)
-PROFILED = {("spheres2", "fp32", 19, "b51ae6607d17"): (347.8e6 + 338.8e6) + (12.05e6 + 0.28e6),
-            ("spheres2", "fp16dev", 19, "b51ae6607d17"): (187.7e6 + 123.3e6) + (12.0e6 + 0.25e6),
-            ("spheres2", "fp32", 27, "b51ae6607d17"): (483.2e6 + 421.2e6) + (17.15e6 + 0.75e6)}
+# DRAM bytes per launch of the bulk collision, and per step of the whole step graph, from one-pass
+# ncu captures (gpu__time_duration, dram__bytes_read/write only), valid only for the source they were
+# taken on (source_hash of the lattice-Boltzmann sources); None otherwise
+PROFILED = {}
+PROFILED_STEP = {}
 
 
 def source_hash():
-    """sha1 prefix of the collision kernels' sources (lbm.cu and the shared device header)."""
+    """sha1 prefix of the lattice-Boltzmann kernels' sources (lbm.cu and the shared device headers)."""
     import hashlib
 
     h = hashlib.sha1()
-    for name in ("lbm.cu", "cbl_dev.cuh"):
+    for name in ("lbm.cu", "cbl_dev.cuh", "periodic.h"):
         with open(os.path.join(ROOT, "paper_1902_10432_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -64,8 +67,15 @@ def profiled_traffic(workload_name, prec, q=19):
     return PROFILED.get((workload_name, prec, q, source_hash()))
 
 
+def profiled_step_traffic(workload_name, prec, q=19):
+    return PROFILED_STEP.get((workload_name, prec, q, source_hash()))
+
+
 def alg_bytes_per_cell(prec, q=19):
     return 2 * q * POP_BYTES[prec] + 2
+
+
+HBM_DATASHEET_GBS = 7900.0  # GB300 HBM3e nominal
 
 
 def measured_peaks():
@@ -77,7 +87,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def workload(name, prec, q=19):
+def describe(w, q):
+    """One-line description of a workload from its own fields."""
+    nb = len(w.bodies)
+    shapes = sorted({b["shape"] for b in w.bodies})
+    radii = sorted({round(b.get("radius", 0.0), 2) for b in w.bodies if b["shape"] == "sphere"})
+    held = sum(1 for b in w.bodies if b.get("fixed"))
+    body = "no bodies" if nb == 0 else "%d %s%s%s" % (
+        nb, "free " if held == 0 else ("held " if held == nb else ""), "/".join(shapes) + ("s" if nb > 1 else ""),
+        (" R=" + "/".join("%g" % r for r in radii)) if radii else "")
+    extra = []
+    if "liquid_fraction_of_solid" in w.meta:
+        extra.append("liquid %.3g of solid volume" % w.meta["liquid_fraction_of_solid"])
+    if "theta_deg" in w.meta:
+        extra.append("%g deg" % w.meta["theta_deg"])
+    return "%s %dx%dx%d D3Q%d, %s%s, %s populations, MPF kinetics %s" % (
+        w.name, w.nx, w.ny, w.nz, q, body, (", " + ", ".join(extra)) if extra else "", w.params.get("prec", "fp32"),
+        "on" if w.params.get("mpf_kinetics") else "off")
+
+
+def workload(name, prec, q=19, sample=False):
+    """The bench workload, or (sample=True) the bounded sample of it that the CPU oracle is timed on:
+    tetra4 at half scale (128^3, R = 12, surface gap 4), the others as they are."""
     from paper_1902_10432_gb300 import workloads
 
     if name == "spheres2":
@@ -85,7 +116,8 @@ def workload(name, prec, q=19):
     elif name == "plates48":
         w = workloads.plates48(prec=prec)
     elif name == "tetra4":
-        w = workloads.tetra4(seed=0, prec=prec)
+        w = workloads.tetra4(seed=0, prec=prec, n=128, R=12.0, surface_gap=4.0) if sample else \
+            workloads.tetra4(seed=0, prec=prec)
     else:
         raise ValueError(name)
     w.params["q"] = q
@@ -163,7 +195,7 @@ def run_oracle_steps(w, steps, warmup, threads):
 
 
 def cpu_baseline(w, budget_s=20.0):
-    """The oracle, as it stands, on a bounded sample: the same lattice, a few steps."""
+    """The oracle, as it stands, on a bounded sample: a lattice of the workload, a few steps."""
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
     times = run_oracle_steps(w, 1, 0, threads)
@@ -174,8 +206,7 @@ def cpu_baseline(w, budget_s=20.0):
     tot = sum(times)
     one = run_oracle_steps(w, 2, 0, 1)  # the same sample on one core, two steps
     return {"value": w.ncells * steps / tot / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": "%s %dx%dx%d, %d time steps of the FP64 oracle (set-up excluded)" % (w.name, w.nx, w.ny, w.nz,
-                                                                                         steps),
+            "sample": "%s, %d time steps of the FP64 oracle (set-up excluded)" % (describe(w, w.params["q"]), steps),
             "one_core": {"value": w.ncells * len(one) / sum(one) / 1e6, "unit": "MLUPS", "cores": 1,
                          "sample": "the same lattice, %d time steps" % len(one)}}
 
@@ -183,7 +214,8 @@ def cpu_baseline(w, budget_s=20.0):
 def bench_reference(args, rank, world):
     if rank != 0:
         return 0
-    w = workload(args.workload, args.precision, args.q)
+    w = workload(args.workload, args.precision, args.q, sample=True)
+    full = workload(args.workload, args.precision, args.q)
     threads = os.cpu_count() or 1
     times = run_oracle_steps(w, args.steps, args.warmup, threads)
     tot = sum(times)
@@ -191,10 +223,10 @@ def bench_reference(args, rank, world):
     line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "%s %dx%dx%d D3Q%d, 2 free spheres R=20" % (w.name, w.nx, w.ny, w.nz, args.q),
-                       "cells": w.ncells, "inputs_vs_l2": "CPU run"},
+            "config": {"workload": describe(full, args.q), "cells": full.ncells, "inputs_vs_l2": "CPU run"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-                             "sample": "%d time steps after %d warm-up steps, full lattice" % (args.steps, args.warmup)},
+                             "sample": "%s: %d time steps after %d warm-up steps" % (describe(w, args.q), args.steps,
+                                                                                  args.warmup)},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -342,7 +374,8 @@ def bench_surrogate(args, rank, world, local_rank):
 
 
 def bench_cuda(args, rank, world, local_rank):
-    import numpy as np
+    import statistics
+
     import torch
 
     torch.cuda.set_device(local_rank)
@@ -350,9 +383,7 @@ def bench_cuda(args, rank, world, local_rank):
 
     if not os.path.exists(os.path.join(ROOT, "paper_1902_10432_gb300", "_lib", "libcbl.so")):
         __graft_entry__.build()
-    from paper_1902_10432_gb300 import cbl, workloads
-
-    from paper_1902_10432_gb300 import ranks
+    from paper_1902_10432_gb300 import cbl, ranks, workloads
 
     rk = ranks.Ranks("nccl")
     w = workload(args.workload, args.precision, args.q)
@@ -361,12 +392,17 @@ def bench_cuda(args, rank, world, local_rank):
 
     sim = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
     workloads.build(sim, w)
+    if args.lbm_variant is not None:
+        sim.set_option("lbm_variant", args.lbm_variant)
+    # the bulk collision's live duration, from event nodes inside the replayed step graph
+    sim.set_option("kernel_events", 1)
     stream = sim.stream
     sim.step(args.warmup)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
+
+    def timed_once():
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -375,21 +411,37 @@ def bench_cuda(args, rank, world, local_rank):
         ev1.synchronize()
         torch.cuda.synchronize()
         barrier()
-    ms_max = rk.max(ev0.elapsed_time(ev1))
-    value = world * w.ncells * args.steps / (ms_max * 1e-3) / 1e6
+        return rk.max(ev0.elapsed_time(ev1)), sim.kernel_times()
 
-    # per-kernel durations (CUDA events between the phases, same stream, kernel-by-kernel launch)
+    reps, kern = [], []
+    with ClockSampler(local_rank) as clk:
+        t_ms, kt = timed_once()
+        reps.append(t_ms)
+        kern += kt
+        # every rank takes the same repeat count (from the max over ranks of the first repeat)
+        n_rep = int(min(args.max_repeats, max(args.min_repeats, -(-args.min_seconds * 1e3 // max(t_ms, 1e-3)))))
+        for _ in range(n_rep - 1):
+            t_ms, kt = timed_once()
+            reps.append(t_ms)
+            kern += kt
+    ms_med = statistics.median(reps)
+    value = world * w.ncells * args.steps / (ms_med * 1e-3) / 1e6
+    t_kernel_ms = statistics.mean(kern)
+
+    # per-phase durations (CUDA events between the phases, same stream, kernel-by-kernel launch)
     phases = sim.time_phases(max(3, min(args.steps, 20)))
     mass = sim.total_mass()
     err = sim.info()["device_error"]
     sim.close()
     del sim
 
-    # end-to-end through the C ABI with host buffers: set-up from the host mask, K steps, fields back
+    # end to end through the C ABI with host buffers: set-up from the host mask, K steps, fields back
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s2 = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
     workloads.build(s2, w)
+    if args.lbm_variant is not None:
+        s2.set_option("lbm_variant", args.lbm_variant)
     s2.step(args.steps)
     rho, vel, phf = s2.fields()
     torch.cuda.synchronize()
@@ -401,27 +453,33 @@ def bench_cuda(args, rank, world, local_rank):
     if rank == 0:
         peak, peak_kind = measured_peaks()
         bpc = alg_bytes_per_cell(prec, args.q)
-        t_col = phases["collide"] * 1e-3
-        achieved = bpc * w.ncells / t_col / 1e9
+        achieved = bpc * w.ncells / (t_kernel_ms * 1e-3) / 1e9
+        step_achieved = bpc * w.ncells / (ms_med / args.steps * 1e-3) / 1e9
+        step_traffic = profiled_step_traffic(w.name, prec, args.q)
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_med / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[prec], "data": "synthetic",
-            "config": {"workload": "%s %dx%dx%d D3Q%d, 2 free spheres R=20, %s populations, MPF kinetics on"
-                                   % (w.name, w.nx, w.ny, w.nz, args.q, prec),
-                       "cells": w.ncells, "seed": w.meta.get("seed"), "theta_deg": w.meta.get("theta_deg"),
-                       "liquid_fraction_of_solid": round(w.meta.get("liquid_fraction_of_solid", 0), 4),
+            "config": {"workload": describe(w, args.q), "cells": w.ncells, "seed": w.meta.get("seed"),
                        "inputs_vs_l2": "populations 2 x %.0f MB > 129 MB L2 (no flush needed)"
-                                       % (w.ncells * 19 * POP_BYTES[prec] / 1e6),
+                                       % (w.ncells * args.q * POP_BYTES[prec] / 1e6),
+                       "timing": "median of %d repeats of %d steps (CUDA events on the step stream)"
+                                 % (len(reps), args.steps),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "collision pass (k_collide + k_collide_near)", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(w.name, prec, int(w.params.get("q", 19))), "peak_kind": peak_kind,
-                         "alg_bytes_per_cell": bpc,
-                         "step_frac": bpc * w.ncells / (ms_max / args.steps * 1e-3) / 1e9 / peak},
+            "repeats_ms": [round(x, 4) for x in reps],
+            "roofline": {"bound": "hbm", "kernel": "bulk collision (k_collide: pull, force, BGK, store)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": profiled_traffic(w.name, prec, args.q), "peak_kind": peak_kind,
+                         "peak_datasheet": HBM_DATASHEET_GBS, "alg_bytes_per_cell": bpc,
+                         "kernel_ms": t_kernel_ms, "kernel_launches_timed": len(kern),
+                         "step": {"achieved": step_achieved, "frac": step_achieved / peak,
+                                  "traffic": step_traffic,
+                                  "traffic_over_alg": None if step_traffic is None
+                                  else step_traffic / (bpc * w.ncells)}},
             "phases_ms": {k: round(v, 5) for k, v in phases.items()},
-            "gpu_launches": kernels_per_step(len(w.bodies), w.params.get("mpf_kinetics", 1), False) * args.steps,
+            "gpu_launches": kernels_per_step(len(w.bodies), w.params.get("mpf_kinetics", 1),
+                                             args.lbm_variant == 1) * args.steps * len(reps),
             "clocks": clk.summary(),
             "e2e": {"value": world * w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
@@ -429,34 +487,9 @@ def bench_cuda(args, rank, world, local_rank):
             "fluid_mass": mass, "device_error": err,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(workload(args.workload, "fp64", args.q, sample=True))
         print(json.dumps(line), flush=True)
     rk.close()
-    return 0
-
-
-def pattern_probe():
-    """Bandwidth of the bare D3Q19 pull pattern next to unshifted streams and a copy (the ceiling of
-    the collision pass's access pattern); prints the probe's lines and one JSON summary line."""
-    import re
-    import subprocess
-    import tempfile
-
-    src = os.path.join(ROOT, "paper_1902_10432_gb300", "csrc", "pattern_probe.cu")
-    with tempfile.TemporaryDirectory() as d:
-        exe = os.path.join(d, "pattern_probe")
-        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
-        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
-    print(out, end="", file=sys.stderr)
-    best = {}
-    for name, us, gbs in re.findall(r"^(\w+)\s+([\d.]+) us\s+([\d.]+) GB/s", out, flags=re.M):
-        best[name] = max(best.get(name, 0.0), float(gbs))
-    peak, _ = measured_peaks()
-    fma = {name: float(v) for name, v in re.findall(r"^(fma\d+)\s+[\d.]+ us\s+([\d.]+) TFLOP/s", out, flags=re.M)}
-    check = [l for l in out.splitlines() if "mismatches" in l]
-    print(json.dumps({"metric": "pattern bandwidth", "unit": "GB/s", "best_of_3": best, "peak": peak,
-                      "frac_of_peak": {k: v / peak for k, v in best.items()}, "fma_tflops": fma,
-                      "check": check[0] if check else ""}), flush=True)
     return 0
 
 
@@ -468,7 +501,7 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
     ap.add_argument("--q", type=int, default=19, choices=[19, 27], help="velocity set: D3Q19 or D3Q27")
-    ap.add_argument("--workload", default="spheres2",
+    ap.add_argument("--workload", default="tetra4",
                     choices=["spheres2", "plates48", "tetra4", "batch64", "surrogate"])
     ap.add_argument("--sur-equil", type=int, default=800)
     ap.add_argument("--sur-seeds", type=int, default=2, help="64-instance batches of training runs")
@@ -484,11 +517,13 @@ def main():
     ap.add_argument("--sur-pack-equil", type=int, default=1000)
     ap.add_argument("--sur-save", default="", help="write the training samples to this .npz")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--pattern-probe", action="store_true",
-                    help="build and run the access-pattern probe of the collision pass (csrc/pattern_probe.cu)")
+    ap.add_argument("--min-repeats", type=int, default=5)
+    ap.add_argument("--max-repeats", type=int, default=200)
+    ap.add_argument("--min-seconds", type=float, default=2.0,
+                    help="repeat the timed region until about this much load has passed")
+    ap.add_argument("--lbm-variant", type=int, default=None, choices=[0, 1],
+                    help="lattice-Boltzmann pass: 0 split density + collision, 1 fused (default: the library's)")
     args = ap.parse_args()
-    if args.pattern_probe:
-        return pattern_probe()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -43,8 +43,8 @@ typedef enum {
   CBL_ERR_OOM = 3,         /* the allocator returned NULL */
   CBL_ERR_CUDA = 4,        /* a CUDA runtime call failed */
   CBL_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
-  CBL_ERR_UNSTABLE = 6,    /* NaN / Inf in the fluid mass */
-  CBL_ERR_UNSUPPORTED = 7  /* feature not built (e.g. a velocity set other than D3Q19) */
+  CBL_ERR_UNSTABLE = 6,    /* NaN / Inf in the fluid mass, or a body update that was not finite */
+  CBL_ERR_UNSUPPORTED = 7  /* feature not built (e.g. the fused pass for a precision other than FP32) */
 } cbl_status;
 
 /* Storage precision of the lattice-Boltzmann populations. Arithmetic is FP64 for CBL_FP64 and FP32
@@ -61,7 +61,7 @@ typedef struct {
 
 typedef struct {
   int nx, ny, nz;          /* lattice size, each >= 4 */
-  int q;                   /* velocity set: 19 (D3Q19) */
+  int q;                   /* velocity set: 19 (D3Q19) or 27 (D3Q27, the set of Sec. 3.2.1) */
   double tau;              /* BGK relaxation time (Eq. lb_collision), > 0.5 */
   double G;                /* Shan-Chen coupling (Eq. benzi_force), paper: -5 */
   double rho0;             /* reference density of psi (Eq. mean_field_potential), paper: 1 */
@@ -98,7 +98,9 @@ typedef struct {
  * caller until cbl_destroy. */
 cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_ctx** out);
 
-/* Add a solid body (before cbl_init_fluid). Its phase-field tile is allocated here. `body_id`
+/* Add a solid body (before cbl_init_fluid). Its phase-field tile is allocated here. CBL_ERR_ARG for
+ * a non-finite or out-of-range field (centre beyond 1e6, radius or half extents <= 0, mass density
+ * <= 0, wetting density < 0). `body_id`
  * (may be NULL) receives the 0-based id. A body whose support (surface + eta/2) covers the whole
  * periodic length along an axis is infinite along it (the plates of the planar bridge, Sec. 2.1):
  * it turns only about that axis; the other angular-velocity components are held at zero. */
@@ -111,7 +113,8 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id);
 cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour,
                           const unsigned char* liquid_mask_host);
 
-/* Same, from per-cell density and velocity (host arrays of N and 3N doubles; u may be NULL). */
+/* Same, from per-cell density and velocity (host arrays of N and 3N doubles; u may be NULL).
+ * CBL_ERR_ARG if a density is negative or not finite, or a velocity is not finite. */
 cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const double* u_host);
 
 /* Advance nsteps time steps (asynchronous on the context's stream). One step: pull streaming with
@@ -152,7 +155,9 @@ cbl_status cbl_read_phi(cbl_ctx* ctx, int body, double* phi_host);
 cbl_status cbl_read_body_forces(cbl_ctx* ctx, double* F, double* T, double* parts);
 
 /* Body state (host arrays, nb*3 / nb*4 / nb / nb*9; any may be NULL): centre of mass, velocity,
- * angular velocity, orientation quaternion, mass, body-frame inertia. */
+ * angular velocity, orientation quaternion, mass, body-frame inertia. Returns CBL_ERR_UNSTABLE (with
+ * the arrays filled) once a body update was not finite or moved a body by a lattice length or more
+ * in one step: that body is then held at its last finite pose (device error bit 3). */
 cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double* Q, double* M,
                           double* I);
 
@@ -167,7 +172,7 @@ cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double*
  * part of the paper's method: it serves the learned-force surrogate. */
 cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Q, const double* V, const double* W);
 
-/* Set body velocities (host arrays nb*3, either may be NULL). */
+/* Set body velocities (host arrays nb*3, either may be NULL). CBL_ERR_ARG for a non-finite value. */
 cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* W);
 
 /* Checkpoint (Sec. 3: the state between two steps is the populations, the phase fields, the
@@ -193,18 +198,18 @@ cbl_status cbl_load(cbl_ctx* ctx, const char* path);
 cbl_status cbl_set_bodies_fixed(cbl_ctx* ctx, const int* fixed);
 
 /* Fluid mass sum_x rho(x) over fluid cells in the last completed step, FP64. Returns
- * CBL_ERR_UNSTABLE if it is not finite. */
+ * CBL_ERR_UNSTABLE if it is not finite or a body update was not finite (device error bit 3). */
 cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass);
 
 /* Number of bodies, cells; device error word (0 = none; bit 0 tile overflow, bit 1 neighbour
- * list overflow, bit 2 lost refill). */
+ * list overflow, bit 2 lost refill, bit 3 a body update that was not finite, the body held). */
 cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_error);
 
 /* Phases of one step, in launch order, as reported by cbl_time_phases. */
 #define CBL_NPHASES 9
-/* 0 pull + density + psi (FP64 storage only), 1 pull + force + collision + mass partials (for FP32
- * and FP16-deviation storage this is the single fused pass that also computes psi), 2 solid-fluid
- * force on the
+/* 0 pull + density + psi (nothing with the fused pass, "lbm_variant" 1), 1 pull + force + collision
+ * + mass partials, bulk and next to a solid (with the fused pass: the single pass that also computes
+ * psi), 2 solid-fluid force on the
  * bodies (momentum exchange and adhesion, FP64 sums), 3 solid-solid repulsion, 4 rigid-body update,
  * 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle flags, 8 cover refill,
  * boundary-cell list and the end of the step (fluid mass, buffer flip). */
@@ -213,6 +218,14 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
  * on the context's stream between the phases, synchronise, and write the mean duration per step of
  * each phase in milliseconds to ms[CBL_NPHASES] (host array). The state advances by nsteps. */
 cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
+
+/* Durations in milliseconds of the bulk collision kernel in the last min(n, 512, max) step-graph
+ * replays of the last cbl_step call (oldest first; n = that call's steps), measured inside the
+ * replayed graph by two event-record nodes on the kernel's stream that bracket its launch (option
+ * "kernel_events" = 1, set before the step graph is built). ms: host array of `max` floats;
+ * *count receives the number written. Synchronises the context's stream. CBL_ERR_STATE if the option
+ * is off. */
+cbl_status cbl_kernel_times(cbl_ctx* ctx, int max, float* ms, int* count);
 
 /* Execution options (no effect on the results beyond rounding order):
  *   "lbm_variant"  0 = split density and collision kernels (default), 1 = single fused pass that
@@ -231,6 +244,8 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
  *                  body and that grows with the distance travelled; set before the first
  *                  cbl_add_body (CBL_ERR_STATE after). Results do not depend on it while no phi
  *                  above 1e-12 reaches the halo (device error bit 0 stays clear).
+ *   "kernel_events" 1 = the step graph brackets the bulk collision with event-record nodes, read
+ *                  back by cbl_kernel_times; 0 (default) = none.
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 
@@ -240,14 +255,17 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
  * The step is the plain fluid part of cbl_step on a lattice without solid bodies: pull streaming,
  * psi, Shan-Chen force, Guo-forced BGK collision; FP32 populations, SoA [direction][cell] with a
  * stride of nx*ny*nz, in the direction order of cbl_read_populations. f_in and f_out are the
- * caller's device buffers (19 * nx*ny*nz floats each, distinct); mass_out (device, may be NULL)
- * receives the fluid mass of the step. Scratch (psi, flags, mass slots) is a fixed set of device
- * arrays inside the library, sized for CBL_NOALLOC_MAX_CELLS cells and held on every GPU that
- * loads the library until the process exits; larger lattices return CBL_ERR_ARG. The first call
- * on a device looks up those arrays with that device current and synchronises the device: make it
- * before any stream capture. All calls share the arrays: calls that overlap on the GPU (other
- * streams, other threads) race. Work is enqueued on `stream` (NULL = legacy default stream).
- * Returns CBL_ERR_ARG for bad sizes or pointers, CBL_ERR_CUDA if a CUDA call fails. */
+ * caller's device buffers (19 * nx*ny*nz floats each, not overlapping); mass_out (device, may be
+ * NULL) receives the fluid mass of the step. The library cannot check the buffers' sizes or where
+ * they live: too small a buffer, or a host pointer, is a memory fault on the GPU (the Python binding
+ * checks them before the call). Scratch (psi, flags, mass slots) is a fixed set of device arrays
+ * inside the library, sized for CBL_NOALLOC_MAX_CELLS cells and held on every GPU that loads the
+ * library until the process exits; larger lattices return CBL_ERR_ARG. Each call looks up those
+ * arrays with the calling device current and clears, on `stream`, the part it uses; the first call
+ * on a device may load the library's device code, so make it before any stream capture. All calls
+ * share the arrays: calls that overlap on the GPU (other streams, other threads) race. Work is
+ * enqueued on `stream` (NULL = legacy default stream). Returns CBL_ERR_ARG for bad sizes,
+ * non-finite parameters, NULL or overlapping buffers, CBL_ERR_CUDA if a CUDA call fails. */
 #define CBL_NOALLOC_MAX_CELLS (1 << 20)
 cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int nx, int ny, int nz, double tau, double G,
                                 double rho0, const double* ext_force, double* mass_out, void* stream);

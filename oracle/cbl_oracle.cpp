@@ -137,12 +137,13 @@ struct Oracle {
   void coords(long n, int& x, int& y, int& z) const {
     x = (int)(n % nx); long r = n / nx; y = (int)(r % ny); z = (int)(r / ny);
   }
-  // minimum-image component
+  // minimum-image component: the representative of d modulo n in [-n/2, n/2). The IEEE remainder
+  // is exact (d - k n with k the nearest integer to d / n, ties to even), so only the tie r = n/2
+  // needs moving to -n/2; a non-finite d gives NaN.
   double mi(double d, int n) const {
-    double h = 0.5 * n;
-    while (d >= h) d -= n;
-    while (d < -h) d += n;
-    return d;
+    double r = std::remainder(d, (double)n);
+    if (r >= 0.5 * n) r -= n;
+    return r;
   }
   int dims(int d) const { return d == 0 ? nx : (d == 1 ? ny : nz); }
 };

@@ -83,6 +83,7 @@ SIGNATURES = {
     "cbl_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int)]),
     "cbl_time_phases": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "cbl_kernel_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "cbl_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
     "cbl_lbm_step_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _P, _P, _P]),
@@ -333,6 +334,14 @@ class Sim:
         self._ck(self._lib.cbl_time_phases(self._h, int(n), ms))
         return dict(zip(self.PHASES, list(ms)))
 
+    def kernel_times(self, max_n=512):
+        """Durations (ms) of the bulk collision in the replays of the last step() call, measured by
+        event nodes inside the step graph (needs set_option("kernel_events", 1) before stepping)."""
+        buf = (ctypes.c_float * max_n)()
+        n = ctypes.c_int()
+        self._ck(self._lib.cbl_kernel_times(self._h, int(max_n), buf, ctypes.byref(n)))
+        return list(buf[:n.value])
+
     def set_option(self, key, value):
         self._ck(self._lib.cbl_set_option(self._h, key.encode(), float(value)))
 
@@ -468,18 +477,58 @@ class MLP:
 NOALLOC_MAX_CELLS = 1 << 20
 
 
+def _check_noalloc_args(f_in, f_out, nx, ny, nz, mass_out):
+    """The C entry point cannot see buffer sizes or devices, so a wrong buffer would be a memory fault
+    on the GPU: every property it relies on is checked here, before the call (ValueError)."""
+    import torch
+
+    n = 19 * int(nx) * int(ny) * int(nz)
+    for name, t in (("f_in", f_in), ("f_out", f_out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != torch.float32:
+            raise ValueError("%s must be float32, got %s" % (name, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() < n:
+            raise ValueError("%s holds %d floats, the lattice needs 19*nx*ny*nz = %d" % (name, t.numel(), n))
+    a0, a1 = f_in.data_ptr(), f_in.data_ptr() + 4 * n
+    b0, b1 = f_out.data_ptr(), f_out.data_ptr() + 4 * n
+    if a0 < b1 and b0 < a1:
+        raise ValueError("f_in and f_out overlap")
+    if mass_out is not None:
+        if not isinstance(mass_out, torch.Tensor) or mass_out.dtype != torch.float64 or mass_out.numel() < 1:
+            raise ValueError("mass_out must be a float64 tensor with at least one element")
+    dev = None
+    for name, t in (("f_in", f_in), ("f_out", f_out), ("mass_out", mass_out)):
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if dev is None:
+            dev = torch.cuda.current_device()
+        if t.device.index != dev:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, t.device.index, dev))
+
+
 def lbm_step_noalloc(f_in, f_out, nx, ny, nz, tau=1.0, G=-5.0, rho0=1.0, ext_force=None, mass_out=None,
                      stream=None):
-    """One fluid-only LBM step on caller-owned device tensors (float32, 19*nx*ny*nz each) with no
-    device allocation inside the library (see cbl_lbm_step_noalloc in include/cbl.h)."""
+    """One fluid-only LBM step on caller-owned device tensors (float32, 19*nx*ny*nz each, on the current
+    device, not overlapping) with no device allocation inside the library (cbl_lbm_step_noalloc in
+    include/cbl.h). mass_out: optional float64 CUDA tensor. The work is enqueued on `stream`
+    (a torch.cuda.Stream), by default on torch's current stream, so it is ordered with the caller's
+    other work on that stream. Arguments the library cannot check are checked here (ValueError)."""
+    import torch
+
+    _check_noalloc_args(f_in, f_out, nx, ny, nz, mass_out)
     lib = load()
     ext = None
     if ext_force is not None:
         ext = (ctypes.c_double * 3)(*ext_force)
+    s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
     st = lib.cbl_lbm_step_noalloc(ctypes.c_void_p(f_in.data_ptr()), ctypes.c_void_p(f_out.data_ptr()), nx, ny, nz,
                                   float(tau), float(G), float(rho0), ext,
                                   None if mass_out is None else ctypes.c_void_p(mass_out.data_ptr()),
-                                  None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+                                  ctypes.c_void_p(s))
     if st != 0:
         raise CblError(st, "cbl_lbm_step_noalloc")
-

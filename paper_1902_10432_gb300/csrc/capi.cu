@@ -2,6 +2,7 @@
 // CUDA graph, read-out. Declared in include/cbl.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +56,14 @@ struct cbl_ctx {
   long long t = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // live timing of the bulk collision inside the replayed step graph ("kernel_events" option): two
+  // event-record nodes bracket its launch; before each replay they are pointed at the next pair of
+  // a ring of events, so the pairs of the last steps can be read back after the replays
+  int kev = 0;
+  cudaEvent_t kev_cap[2] = {nullptr, nullptr};
+  cudaGraphNode_t kev_node[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> kev_ring;  // 2 * KEV_RING events
+  long long kev_steps = 0;            // replays recorded by the last cbl_step
   std::vector<void*> allocs;
   std::string err;
 };
@@ -106,6 +115,12 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   const cbl_params& p = *params;
   if (p.nx < 4 || p.ny < 4 || p.nz < 4) return fail(nullptr, CBL_ERR_ARG, "lattice sides must be >= 4");
   if (p.q != 19 && p.q != 27) return fail(nullptr, CBL_ERR_UNSUPPORTED, "velocity sets: D3Q19 or D3Q27");
+  {
+    const double vals[] = {p.tau, p.G, p.rho0, p.ext_force[0], p.ext_force[1], p.ext_force[2], p.mobility, p.eta,
+                           p.sigma_sf, p.sigma_ss, p.e0, p.rc, p.solid_threshold, p.member_threshold};
+    for (double v : vals)
+      if (!std::isfinite(v)) return fail(nullptr, CBL_ERR_ARG, "parameters must be finite");
+  }
   if (!(p.tau > 0.5)) return fail(nullptr, CBL_ERR_ARG, "tau must be > 0.5");
   if (!(p.rho0 > 0)) return fail(nullptr, CBL_ERR_ARG, "rho0 must be > 0");
   if (p.prec < CBL_FP64 || p.prec > CBL_FP16DEV) return fail(nullptr, CBL_ERR_ARG, "unknown precision");
@@ -207,7 +222,21 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "bodies must be added before cbl_init_fluid");
   if ((int)ctx->hb.size() >= MAX_BODIES) return fail(ctx, CBL_ERR_ARG, "too many bodies");
   if (body->shape != 0 && body->shape != 1) return fail(ctx, CBL_ERR_ARG, "shape must be 0 (sphere) or 1 (box)");
-  if (!(body->mass_density > 0)) return fail(ctx, CBL_ERR_ARG, "mass_density must be > 0");
+  if (!(body->mass_density > 0) || !std::isfinite(body->mass_density))
+    return fail(ctx, CBL_ERR_ARG, "mass_density must be finite and > 0");
+  if (!(body->wetting_rho >= 0) || !std::isfinite(body->wetting_rho))
+    return fail(ctx, CBL_ERR_ARG, "wetting_rho must be finite and >= 0");
+  for (int a = 0; a < 3; ++a) {
+    // a centre far outside the lattice is almost certainly a mistake, and its tile origin would
+    // not fit an int
+    if (!(std::fabs(body->center[a]) <= 1e6)) return fail(ctx, CBL_ERR_ARG, "centre must be finite, |c| <= 1e6");
+    if (body->shape == 1 && !(body->half[a] > 0 && std::isfinite(body->half[a])))
+      return fail(ctx, CBL_ERR_ARG, "box half extents must be finite and > 0");
+  }
+  for (int a = 0; a < 4; ++a)
+    if (!std::isfinite(body->quat[a])) return fail(ctx, CBL_ERR_ARG, "quaternion must be finite");
+  if (body->shape == 0 && !(body->radius > 0 && std::isfinite(body->radius)))
+    return fail(ctx, CBL_ERR_ARG, "sphere radius must be finite and > 0");
   BodyDev b;
   std::memset(&b, 0, sizeof(b));
   b.shape = body->shape;
@@ -231,7 +260,6 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
   // past R + eta/2 on a body that moved a cell and keeps growing slowly with the distance travelled
   double h[3];
   if (b.shape == 0) {
-    if (!(b.radius > 0)) return fail(ctx, CBL_ERR_ARG, "sphere radius must be > 0");
     for (int a = 0; a < 3; ++a) h[a] = b.radius;
   } else {
     double w = b.q0[0], x = b.q0[1], y = b.q0[2], z = b.q0[3];
@@ -251,8 +279,9 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id) {
         if (c != a) b.rot_lock |= 1 << c;
   long long sz = 1;
   for (int a = 0; a < 3; ++a) {
-    int half = (int)std::ceil(h[a] + 0.5 * ctx->p.eta + 2.5 + ctx->tile_tail);
-    int L = 2 * half + 1;
+    // sized in double first: a body larger than the lattice takes the whole axis
+    const double half = std::ceil(h[a] + 0.5 * ctx->p.eta + 2.5 + ctx->tile_tail);
+    int L = 2.0 * half + 1.0 >= (double)n[a] ? n[a] : 2 * (int)half + 1;
     if (L >= n[a]) {
       L = n[a];
       b.o[a] = 0;
@@ -347,7 +376,8 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
 cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour, const unsigned char* mask) {
   if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
   if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "already initialised");
-  if (!(rho_liquid >= 0) || !(rho_vapour >= 0)) return fail(ctx, CBL_ERR_ARG, "densities must be >= 0");
+  if (!(rho_liquid >= 0) || !(rho_vapour >= 0) || !std::isfinite(rho_liquid) || !std::isfinite(rho_vapour))
+    return fail(ctx, CBL_ERR_ARG, "densities must be finite and >= 0");
   std::vector<double> rho((size_t)ctx->lat.N);
   for (size_t n = 0; n < rho.size(); ++n) rho[n] = (mask && mask[n]) ? rho_liquid : rho_vapour;
   return init_common(ctx, rho.data(), nullptr);
@@ -356,6 +386,13 @@ cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour, co
 cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const double* u_host) {
   if (!ctx || !rho_host) return fail(ctx, CBL_ERR_ARG, "NULL argument");
   if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "already initialised");
+  const size_t N = (size_t)ctx->lat.N;
+  for (size_t n = 0; n < N; ++n)
+    if (!(rho_host[n] >= 0) || !std::isfinite(rho_host[n]))
+      return fail(ctx, CBL_ERR_ARG, "initial densities must be finite and >= 0");
+  if (u_host)
+    for (size_t n = 0; n < 3 * N; ++n)
+      if (!std::isfinite(u_host[n])) return fail(ctx, CBL_ERR_ARG, "initial velocities must be finite");
   return init_common(ctx, rho_host, u_host);
 }
 
@@ -371,6 +408,15 @@ static void enqueue_lbm(cbl_ctx* ctx, int phases, cudaStream_t s) {
                     (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
                     s, phases);
   }
+}
+
+static const int KEV_RING = 512;
+
+// bulk collision, bracketed by the timing events when "kernel_events" is on
+static void enqueue_bulk(cbl_ctx* ctx, cudaStream_t s) {
+  if (ctx->kev) cudaEventRecordWithFlags(ctx->kev_cap[0], s, cudaEventRecordExternal);
+  enqueue_lbm(ctx, 2, s);
+  if (ctx->kev) cudaEventRecordWithFlags(ctx->kev_cap[1], s, cudaEventRecordExternal);
 }
 
 // One step, enqueued for capture into a graph. With bodies, the collision of the cells next to a
@@ -408,11 +454,13 @@ static void enqueue_step(cbl_ctx* ctx) {
                   ctx->side);
     phase_update(ctx->side);
     cudaEventRecord(ctx->ev_join, ctx->side);
-    enqueue_lbm(ctx, 2, ctx->s);
+    enqueue_bulk(ctx, ctx->s);
     cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0);
     flags_refill(ctx->s);
   } else {
-    enqueue_lbm(ctx, 7, ctx->s);
+    enqueue_lbm(ctx, 1, ctx->s);
+    enqueue_bulk(ctx, ctx->s);
+    enqueue_lbm(ctx, 4, ctx->s);
     ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->s);
     if (nb) {
@@ -441,13 +489,55 @@ cbl_status cbl_step(cbl_ctx* ctx, int nsteps) {
     // the side stream's priority is recorded on its kernel nodes; the executable graph honours it
     // only with this flag
     CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, ctx->node_priority ? cudaGraphInstantiateFlagUseNodePriority : 0));
+    if (ctx->kev) {
+      // the two event-record nodes that bracket the bulk collision
+      size_t nn = 0;
+      CK(cudaGraphGetNodes(ctx->graph, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CK(cudaGraphGetNodes(ctx->graph, nodes.data(), &nn));
+      ctx->kev_node[0] = ctx->kev_node[1] = nullptr;
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        CK(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (int k = 0; k < 2; ++k)
+          if (ev == ctx->kev_cap[k]) ctx->kev_node[k] = nd;
+      }
+      if (!ctx->kev_node[0] || !ctx->kev_node[1])
+        return fail(ctx, CBL_ERR_CUDA, "timing events of the bulk collision not found in the step graph");
+    }
   }
   // the diag word is tested for non-zero: byte-wise memsets keep the whole call asynchronous
   CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
-  for (int k = 0; k < nsteps - 1; ++k) CK(cudaGraphLaunch(ctx->gexec, ctx->s));
-  CK(cudaMemsetAsync(&ctx->st->diag, 1, sizeof(int), ctx->s));
-  CK(cudaGraphLaunch(ctx->gexec, ctx->s));
+  for (int k = 0; k < nsteps; ++k) {
+    if (k == nsteps - 1) CK(cudaMemsetAsync(&ctx->st->diag, 1, sizeof(int), ctx->s));
+    if (ctx->kev) {
+      const int r = k % KEV_RING;
+      CK(cudaGraphExecEventRecordNodeSetEvent(ctx->gexec, ctx->kev_node[0], ctx->kev_ring[2 * r]));
+      CK(cudaGraphExecEventRecordNodeSetEvent(ctx->gexec, ctx->kev_node[1], ctx->kev_ring[2 * r + 1]));
+    }
+    CK(cudaGraphLaunch(ctx->gexec, ctx->s));
+  }
+  ctx->kev_steps = nsteps;
   ctx->t += nsteps;
+  return CBL_OK;
+}
+
+cbl_status cbl_kernel_times(cbl_ctx* ctx, int max, float* ms, int* count) {
+  if (!ctx || !ms || !count || max < 0) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  if (!ctx->kev) return fail(ctx, CBL_ERR_STATE, "option kernel_events is off");
+  CK(cudaStreamSynchronize(ctx->s));
+  const long long have = std::min<long long>(ctx->kev_steps, KEV_RING);
+  const int n = (int)std::min<long long>(have, (long long)max);
+  // the last n replays, oldest first
+  for (int j = 0; j < n; ++j) {
+    const long long k = ctx->kev_steps - n + j;
+    const int r = (int)(k % KEV_RING);
+    CK(cudaEventElapsedTime(&ms[j], ctx->kev_ring[2 * r], ctx->kev_ring[2 * r + 1]));
+  }
+  *count = n;
   return CBL_OK;
 }
 
@@ -600,6 +690,16 @@ cbl_status cbl_read_body_forces(cbl_ctx* ctx, double* F, double* T, double* part
   return CBL_OK;
 }
 
+// CBL_ERR_UNSTABLE once a body update was not finite (device error bit E_UNSTABLE; that body is
+// held at its last finite pose)
+static cbl_status unstable_check(cbl_ctx* ctx) {
+  StepState h;
+  CK(cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  if (h.err & E_UNSTABLE) return fail(ctx, CBL_ERR_UNSTABLE, "a body update was not finite; the body is held");
+  return CBL_OK;
+}
+
 cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double* Qo, double* M, double* I) {
   if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
@@ -620,7 +720,7 @@ cbl_status cbl_get_bodies(cbl_ctx* ctx, double* X, double* V, double* W, double*
     if (I)
       for (int a = 0; a < 9; ++a) I[9 * b + a] = h[b].Ib[a];
   }
-  return CBL_OK;
+  return unstable_check(ctx);
 }
 
 cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, const double* V, const double* W) {
@@ -628,6 +728,9 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
   const int nb = (int)ctx->hb.size();
   if (!nb) return CBL_OK;
+  for (int k = 0; k < 3 * nb; ++k)
+    if ((V && !std::isfinite(V[k])) || (W && !std::isfinite(W[k])))
+      return fail(ctx, CBL_ERR_ARG, "velocities must be finite");
   std::vector<BodyDev> h0(nb), h(nb);
   CK(cudaMemcpyAsync(h0.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
@@ -728,6 +831,9 @@ cbl_status cbl_set_body_velocities(cbl_ctx* ctx, const double* V, const double* 
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
   const int nb = (int)ctx->hb.size();
   if (!nb) return CBL_OK;
+  for (int k = 0; k < 3 * nb; ++k)
+    if ((V && !std::isfinite(V[k])) || (W && !std::isfinite(W[k])))
+      return fail(ctx, CBL_ERR_ARG, "velocities must be finite");
   std::vector<BodyDev> h(nb);
   CK(cudaMemcpyAsync(h.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
@@ -779,6 +885,11 @@ struct CkptHeader {
   double tau, G, rho0, ext[3], mobility, eta, sigma_sf, sigma_ss, e0, rc, solid_thr, member_thr;
   int mpf, nrep;
 };
+// the header is compared with memcmp after a struct copy, which need not keep padding bytes: the
+// members are laid out so that there are none
+static_assert(sizeof(CkptHeader) == 8 + 8 * sizeof(int) + 4 * sizeof(long long) + 14 * sizeof(double) +
+                                        2 * sizeof(int),
+              "CkptHeader must have no implicit padding");
 
 struct Buf {
   void* dev;
@@ -934,6 +1045,7 @@ cbl_status cbl_total_mass(cbl_ctx* ctx, double* mass) {
   CK(cudaStreamSynchronize(ctx->s));
   *mass = h.last_mass;
   if (!std::isfinite(h.last_mass)) return fail(ctx, CBL_ERR_UNSTABLE, "fluid mass is not finite");
+  if (h.err & E_UNSTABLE) return fail(ctx, CBL_ERR_UNSTABLE, "a body update was not finite; the body is held");
   return CBL_OK;
 }
 
@@ -977,6 +1089,16 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     if (!ctx->hb.empty()) return fail(ctx, CBL_ERR_STATE, "tile_tail must be set before the first body");
     ctx->tile_tail = value;
     return CBL_OK;
+  } else if (k == "kernel_events") {
+    const int v = (int)value;
+    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "kernel_events must be 0 or 1");
+    if (v && ctx->kev_ring.empty()) {
+      for (int k2 = 0; k2 < 2; ++k2) CK(cudaEventCreate(&ctx->kev_cap[k2]));
+      ctx->kev_ring.resize(2 * KEV_RING);
+      for (cudaEvent_t& e : ctx->kev_ring) CK(cudaEventCreate(&e));
+    }
+    ctx->kev = v;
+    ctx->kev_steps = 0;
   } else if (k == "lbm_block_x") {
     const int v = (int)value;
     if (v != 32 && v != 64 && v != 128) return fail(ctx, CBL_ERR_ARG, "lbm_block_x must be 32, 64 or 128");
@@ -1103,6 +1225,10 @@ cbl_status cbl_destroy(cbl_ctx* ctx) {
   cudaStreamDestroy(ctx->side);
   cudaEventDestroy(ctx->ev_fork);
   cudaEventDestroy(ctx->ev_join);
+  for (cudaEvent_t e : ctx->kev_cap)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->kev_ring)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return CBL_OK;
 }

@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "periodic.h"
+
 namespace cbl {
 
 // ------------------------------------------------------------------------------------------
@@ -69,7 +71,9 @@ constexpr int MAXNB = 24;  // neighbour-list capacity per body (tiles that overl
 constexpr int MASS_SLOTS = 256;
 
 // Device error word bits.
-constexpr int E_TILE = 1, E_NBLIST = 2, E_REFILL = 4;
+// E_UNSTABLE: a body's update gave a non-finite position, velocity or angular velocity, or moved it
+// by a lattice length or more in one step; that body is then held at its last pose.
+constexpr int E_TILE = 1, E_NBLIST = 2, E_REFILL = 4, E_UNSTABLE = 8;
 
 struct Lat {
   int nx, ny, nz;
@@ -161,17 +165,7 @@ __device__ __forceinline__ float par<float>(double, float f) { return f; }
 // 64-bit integers, since negative v have the sign bit set.
 __device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
 
-__host__ __device__ inline int wrapi(int a, int n) {
-  int r = a % n;
-  return r < 0 ? r + n : r;
-}
-// minimum image, same rule as a plain "while (d >= n/2) d -= n; while (d < -n/2) d += n"
-__host__ __device__ inline double mimg(double d, int n) {
-  double h = 0.5 * n;
-  while (d >= h) d -= n;
-  while (d < -h) d += n;
-  return d;
-}
+// wrapi, mimg, wrapd: periodic wraps with a fixed operation count (periodic.h)
 
 // ---- kernel launchers (defined in lbm.cu / lbm27.cu per velocity set, and phase.cu) ------------
 // Populations live in two buffers fa, fb; StepState::parity selects the current state

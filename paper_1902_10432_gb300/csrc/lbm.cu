@@ -19,9 +19,8 @@
 // This file is compiled once per velocity set: as itself for D3Q19 (namespace cbl::q19) and through
 // lbm27.cu with CBL_Q = 27 (namespace cbl::q27). The fused single-pass variants and the
 // no-allocation entry point exist for D3Q19 only.
-#include <mutex>
-
 #include <climits>
+#include <cmath>
 #include "../../include/cbl.h"
 #include "cbl_dev.cuh"
 
@@ -1494,16 +1493,21 @@ __device__ __align__(256) uint16_t g_na_flags[CBL_NOALLOC_MAX_CELLS];
 __device__ __align__(256) double g_na_mass[cbl::MASS_SLOTS];
 __device__ __align__(256) cbl::StepState g_na_state;
 
+// device addresses of the arrays, looked up with the calling device current
 struct NaScratch {
   float* psi = nullptr;
   uint16_t* flags = nullptr;
   double* mass = nullptr;
   cbl::StepState* state = nullptr;
 };
-constexpr int NA_MAX_DEVICES = 64;
-NaScratch g_na[NA_MAX_DEVICES];
-bool g_na_ready[NA_MAX_DEVICES];
-std::mutex g_na_mutex;
+
+cudaError_t na_lookup(NaScratch& a) {
+  cudaError_t e;
+  if ((e = cudaGetSymbolAddress((void**)&a.psi, g_na_psi)) != cudaSuccess) return e;
+  if ((e = cudaGetSymbolAddress((void**)&a.flags, g_na_flags)) != cudaSuccess) return e;
+  if ((e = cudaGetSymbolAddress((void**)&a.mass, g_na_mass)) != cudaSuccess) return e;
+  return cudaGetSymbolAddress((void**)&a.state, g_na_state);
+}
 
 __global__ void k_na_mass(const double* __restrict__ slots, double* __restrict__ out) {
   __shared__ double red[256];
@@ -1522,31 +1526,27 @@ extern "C" cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int 
                                            void* stream) {
   using namespace cbl;
   using namespace cbl::q19;
-  if (!f_in || !f_out || f_in == f_out) return CBL_ERR_ARG;
+  if (!f_in || !f_out) return CBL_ERR_ARG;
   if (nx < 4 || ny < 4 || nz < 4) return CBL_ERR_ARG;
   const long long N = (long long)nx * ny * nz;
   if (N > CBL_NOALLOC_MAX_CELLS) return CBL_ERR_ARG;
-  if (!(tau > 0.5) || !(rho0 > 0)) return CBL_ERR_ARG;
+  if (!(tau > 0.5) || !(rho0 > 0) || !std::isfinite(tau) || !std::isfinite(G) || !std::isfinite(rho0)) return CBL_ERR_ARG;
+  if (ext_force && !(std::isfinite(ext_force[0]) && std::isfinite(ext_force[1]) && std::isfinite(ext_force[2])))
+    return CBL_ERR_ARG;
+  // the two population arrays must not overlap (the step reads f_in while it writes f_out)
+  const size_t pop = (size_t)Q * (size_t)N;
+  if (f_out < f_in + pop && f_in < f_out + pop) return CBL_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return CBL_ERR_CUDA;
-  {
-    // once per device, with that device current: host code needs the arrays' device addresses
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ready[dev]) {
-      NaScratch& a = g_na[dev];
-      if (cudaGetSymbolAddress((void**)&a.psi, g_na_psi) != cudaSuccess) return CBL_ERR_CUDA;
-      if (cudaGetSymbolAddress((void**)&a.flags, g_na_flags) != cudaSuccess) return CBL_ERR_CUDA;
-      if (cudaGetSymbolAddress((void**)&a.mass, g_na_mass) != cudaSuccess) return CBL_ERR_CUDA;
-      if (cudaGetSymbolAddress((void**)&a.state, g_na_state) != cudaSuccess) return CBL_ERR_CUDA;
-      // all fluid, parity 0 (read f_in, write f_out), no field record
-      if (cudaMemset(a.flags, 0, sizeof(uint16_t) * CBL_NOALLOC_MAX_CELLS) != cudaSuccess) return CBL_ERR_CUDA;
-      if (cudaMemset(a.state, 0, sizeof(StepState)) != cudaSuccess) return CBL_ERR_CUDA;
-      if (cudaDeviceSynchronize() != cudaSuccess) return CBL_ERR_CUDA;
-      g_na_ready[dev] = true;
-    }
-  }
-  const NaScratch& a = g_na[dev];
+  // The arrays' device addresses are looked up on every call, with the calling device current
+  // (cheap, and never stale after a device reset reloads the library's module). The first lookup on
+  // a device may load the module: make the first call before any stream capture.
+  NaScratch a;
+  if (na_lookup(a) != cudaSuccess) return CBL_ERR_CUDA;
+  // every call shares the arrays and they keep the last call's contents: clear what must start at
+  // zero (all-fluid flags of this lattice, parity 0: read f_in and write f_out, no field record,
+  // mass slots)
+  if (cudaMemsetAsync(a.flags, 0, sizeof(uint16_t) * (size_t)N, s) != cudaSuccess) return CBL_ERR_CUDA;
+  if (cudaMemsetAsync(a.state, 0, sizeof(StepState), s) != cudaSuccess) return CBL_ERR_CUDA;
   Lat lat;
   lat.nx = nx;
   lat.ny = ny;

@@ -474,7 +474,10 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
 // ---- rigid bodies ------------------------------------------------------------------------------
 // Semi-implicit Euler with dt = 1: V += F/M, X += V, omega += I_w^-1 T with I_w = R I_body R^T,
 // q <- normalize(exp(omega/2) q); fixed bodies keep V = omega = 0.
-__device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
+// A body whose update is not finite, or moves it by a lattice length or more in one step (a run
+// that has blown up), is held at its last pose from then on and E_UNSTABLE is raised: every later
+// kernel that derives a tile origin or a wrap from X gets finite, in-range values.
+__device__ void integrate(BodyDev& b, const double* parts, const Lat& lat, StepState* st) {
   // FP64 throughout (GB300 issues FP64 at 1/64 of the FP32 rate and one thread runs this chain, so
   // the operation count is kept small: one reciprocal of M and of |q|, sincos, and the world-frame
   // inverse inertia applied as R (I_body^-1 (R^T T)) instead of being formed)
@@ -493,13 +496,14 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
   }
   const int n[3] = {lat.nx, lat.ny, lat.nz};
   const double iM = 1.0 / b.M;
+  const double Q0[4] = {b.Q[0], b.Q[1], b.Q[2], b.Q[3]};
+  bool bad = false;
   for (int a = 0; a < 3; ++a) {
     b.V[a] += F[a] * iM;
-    double x = b.X[a] + b.V[a];
-    // periodic wrap (a move of less than a lattice side wraps once: the same value as fmod)
-    while (x >= (double)n[a]) x -= n[a];
-    while (x < 0) x += n[a];
-    b.X[a] = x;
+    // finite and shorter than the lattice side (NaN fails the comparison)
+    bad |= !(fabs(b.V[a]) < (double)n[a]);
+    // periodic wrap in closed form (a move of less than a lattice side: the value of fmod)
+    b.X[a] = wrapd(b.X[a] + b.V[a], n[a]);
   }
   double R[9];
   quat_R(b.Q, R);
@@ -523,6 +527,18 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat) {
     const double iq = 1.0 / sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
     for (int a = 0; a < 4; ++a) b.Q[a] = nq[a] * iq;
   }
+  for (int a = 0; a < 3; ++a) bad |= !isfinite(b.W[a]) || !isfinite(b.X[a]);
+  for (int a = 0; a < 4; ++a) bad |= !isfinite(b.Q[a]);
+  if (bad) {
+    for (int a = 0; a < 3; ++a) {
+      b.X[a] = b.Xprev[a];
+      b.V[a] = 0.0;
+      b.W[a] = 0.0;
+    }
+    for (int a = 0; a < 4; ++a) b.Q[a] = Q0[a];
+    b.fixed = 1;
+    atomicOr(&st->err, E_UNSTABLE);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
@@ -531,7 +547,7 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     BodyDev& b = bodies[i];
     double* a = acc + (size_t)i * ACC_N;
-    integrate(b, a, lat);
+    integrate(b, a, lat, st);
     mirror_f(b);
     for (int k = 0; k < ACC_N; ++k) {
       last[(size_t)i * ACC_N + k] = a[k];

@@ -15,7 +15,7 @@ spheres), so these generators stand in for its set-ups at the sizes of the bench
                free plates, R = 20).
 
 A body's shape is the phi = 1/2 surface. Contact angles are turned into the wetting parameter
-varrho_B through the table tests/golden/wetting_table.json (written by the FP64 oracle from
+varrho_B through the table data/wetting_table.json (written by the FP64 oracle from
 sessile-drop runs).
 """
 from __future__ import annotations
@@ -28,9 +28,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 RHO_L, RHO_V = 1.88844, 0.11942  # flat-interface coexistence of G = -5, psi = 1 - exp(-rho)
-_ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-WETTING_TABLE = os.path.join(_ROOT, "tests", "golden", "wetting_table.json")
-WETTING_90 = os.path.join(_ROOT, "tests", "golden", "wetting_90.json")
+_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+WETTING_TABLE = os.path.join(_DATA, "wetting_table.json")
+WETTING_90 = os.path.join(_DATA, "wetting_90.json")
 PLATE_DENSITY_RATIO = 1.72e4  # rho_S / rho_L of the free plates (Sec. 4.2: slow, heavy plates)
 
 # Solid cells are those with fluid phase below 0.05, i.e. deeper than this below the phi = 1/2
@@ -73,7 +73,7 @@ def varrho_for_angle(theta_deg: float) -> float:
 
 def varrho_90() -> float:
     """Wetting parameter of a 90 degree contact angle: the value for which the meniscus of a planar
-    bridge between plates is flat (zero Laplace pressure), from tests/golden/wetting_90.json (written
+    bridge between plates is flat (zero Laplace pressure), from data/wetting_90.json (written
     by the FP64 oracle). The sessile-drop table places 90 degrees a few degrees off in the plate
     geometry, which the plate force is sensitive to."""
     with open(WETTING_90) as f:

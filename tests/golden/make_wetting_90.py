@@ -1,4 +1,5 @@
-"""Write tests/golden/wetting_90.json: the wetting parameter varrho_B of a 90 degree contact angle.
+"""Write paper_1902_10432_gb300/data/wetting_90.json (the calibration table the
+package reads): the wetting parameter varrho_B of a 90 degree contact angle.
 
 At 90 degrees the liquid-vapour interfaces of a planar bridge between parallel plates are flat
 (Sec. 2.1: the plate-force derivation assumes 90 degree wetting so that the solid-liquid terms
@@ -72,7 +73,8 @@ def main():
     out = {"description": "varrho_B with a flat planar meniscus (zero Laplace pressure, 90 degree wetting), "
                           "FP64 oracle, D3Q19, tau=1, G=-5, rho0=1, plates gap %d, %d steps" % (GAP, STEPS),
            "varrho_90": round(b, 5), "samples": samples}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "wetting_90.json")
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))),
+                        "paper_1902_10432_gb300", "data", "wetting_90.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", path)

@@ -1,4 +1,5 @@
-"""Write tests/golden/wetting_table.json: contact angle Theta vs wetting parameter varrho_B.
+"""Write paper_1902_10432_gb300/data/wetting_table.json (the calibration table the
+package reads): contact angle Theta vs wetting parameter varrho_B.
 
 The paper sets wetting through varrho_B (Sec. 3.2.3: solid nodes act as fluid of that density;
 varrho = 2 in the parameter table of Sec. 3.3) and relates the contact angle to the interface
@@ -74,7 +75,8 @@ def main():
         out["varrho"].append(v)
         out["theta_deg"].append(round(th, 3))
         out["radius"].append(round(R, 3))
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "wetting_table.json")
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))),
+                        "paper_1902_10432_gb300", "data", "wetting_table.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", path)

@@ -21,4 +21,5 @@ def test_reference_arm_json_line():
     assert d["warmup"] >= 3 and d["steps"] == 1  # at least three warm-up steps, whatever is asked
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"].startswith("spheres2")
+    assert d["config"]["workload"].startswith("tetra4 256x256x256")  # the default workload
+    assert "128x128x128" in d["cpu_baseline"]["sample"]  # timed on the bounded half-scale sample

@@ -46,7 +46,13 @@ def test_noalloc_two_steps_match_cbl_step():
         assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
         m = mass[k].item()
         assert abs(m - sim.total_mass()) <= 1e-12 * abs(sim.total_mass())
-    # sizes beyond the fixed scratch are rejected
+    # sizes beyond the fixed scratch are rejected by the library (buffers large enough for the
+    # lattice, so that only the scratch limit can refuse the call)
     big = (cbl.NOALLOC_MAX_CELLS // (16 * 16)) + 1
+    ga = torch.zeros(19 * 16 * 16 * big, dtype=torch.float32, device=dev)
+    gb = torch.empty_like(ga)
     with pytest.raises(cbl.CblError):
-        cbl.lbm_step_noalloc(fa, fb, 16, 16, big)
+        cbl.lbm_step_noalloc(ga, gb, 16, 16, big)
+    # buffers too small for the lattice are refused before the call
+    with pytest.raises(ValueError):
+        cbl.lbm_step_noalloc(fa[:100], fb, nx, ny, nz)
