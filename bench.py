@@ -10,8 +10,8 @@ refill. Other workloads: spheres2 (two spheres in 128x128x256), plates48, batch6
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--precision fp32]
 
 The timed region is exactly K steps (one replay of the step graph each), bracketed by a barrier and a
-device synchronisation; it is repeated (at least 5 times, and until about two seconds of load have
-passed, so that the clock sampler sees the GPU busy) and the median repeat is reported.
+device synchronisation; it is repeated (at least 5 times, until about two seconds of load have
+passed or about 600 steps have run, whichever comes first) and the median repeat is reported.
 N > 1 runs under torchrun as independent replicas (one per GPU, no collective: the step does not
 shard across GPUs in this build); value = cells x steps summed over ranks / max time.
 --impl reference times the FP64 CPU oracle (the slow, plain implementation the CUDA path is
@@ -418,8 +418,13 @@ def bench_cuda(args, rank, world, local_rank):
         t_ms, kt = timed_once()
         reps.append(t_ms)
         kern += kt
-        # every rank takes the same repeat count (from the max over ranks of the first repeat)
-        n_rep = int(min(args.max_repeats, max(args.min_repeats, -(-args.min_seconds * 1e3 // max(t_ms, 1e-3)))))
+        # every rank takes the same repeat count (from the max over ranks of the first repeat): at
+        # least min_repeats, about min_seconds of load, and no more than max_steps_total steps in all
+        # (the workloads are dynamic: spheres pulled together by their bridges make contact after
+        # some thousand steps, so the bench times the first few hundred steps)
+        by_time = -(-args.min_seconds * 1e3 // max(t_ms, 1e-3))
+        by_steps = (args.max_steps_total - args.warmup) // args.steps
+        n_rep = int(max(args.min_repeats, min(args.max_repeats, by_time, by_steps)))
         for _ in range(n_rep - 1):
             t_ms, kt = timed_once()
             reps.append(t_ms)
@@ -521,6 +526,8 @@ def main():
     ap.add_argument("--max-repeats", type=int, default=200)
     ap.add_argument("--min-seconds", type=float, default=2.0,
                     help="repeat the timed region until about this much load has passed")
+    ap.add_argument("--max-steps-total", type=int, default=600,
+                    help="cap on warm-up plus timed steps (the workloads evolve with time)")
     ap.add_argument("--lbm-variant", type=int, default=None, choices=[0, 1],
                     help="lattice-Boltzmann pass: 0 split density + collision, 1 fused (default: the library's)")
     args = ap.parse_args()

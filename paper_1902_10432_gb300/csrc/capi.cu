@@ -46,8 +46,9 @@ struct cbl_ctx {
   double* mass_part = nullptr;
   unsigned n_mass_part = 0;
   int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
-  int fused_tz = 0;      // > 0: FP32 / FP16 storage steps with the fused single-pass kernel
+  int fused_tz = 0;      // > 0: the density and the bulk collision run as one fused pass (k_fused)
   int fused_tz_req = 0;  // requested z extent of a fused block (0 = derived)
+  int fused_ty = 8;      // y extent of a fused block's consumer tile (4 or 8; x extent 32)
   int block_x = 32;      // x extent of the split kernels' 128-thread blocks
   double tile_tail = 2.5;  // cells of room for the advection tail in each body tile
   int node_priority = 1;   // 1: the step graph keeps the side stream's priority on its kernels
@@ -396,13 +397,20 @@ cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const dou
   return init_common(ctx, rho_host, u_host);
 }
 
-// phases: 1 density, 2 bulk collision, 4 collision of the cells next to a solid (the fused pass does
-// all of it under 2)
+// phases: 1 density (fused pass: psi over the bodies' tiles only), 2 bulk collision (fused pass:
+// with the density), 4 collision of the cells next to a solid
 static void enqueue_lbm(cbl_ctx* ctx, int phases, cudaStream_t s) {
   if (ctx->fused_tz) {
+    if (phases & 1)
+      ctx->ops.density_tiles(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, (int)ctx->hb.size(),
+                             ctx->max_tile, ctx->psi, ctx->pp, s);
     if (phases & 2)
       ctx->ops.lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
-                       ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->nbuf, s);
+                         ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->fused_ty, s);
+    if (phases & 4)
+      ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+                        (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist, s,
+                        4);
   } else {
     ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
                     (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
@@ -436,16 +444,18 @@ static void enqueue_step(cbl_ctx* ctx) {
     ctx->ops.refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
                   ctx->arena, ctx->p.member_threshold, ctx->mbox, 1, s);
   };
-  if (nb && !ctx->fused_tz && ctx->branches) {
+  if (nb && ctx->branches) {
     // The bulk collision (every cell without a solid neighbour) runs beside the chain that needs only
     // the source populations, psi and the phase fields: collision of the cells next to a solid, force
     // pass, repulsion, body update, advection, kinetics. That chain is the longer path and is made
     // of small latency-bound kernels, so it runs on the high-priority side stream, whose blocks are
     // scheduled ahead of the bulk collision's queued ones. The flag update and the refill rewrite
-    // what the bulk collision reads and writes, so they wait for both.
-    enqueue_lbm(ctx, 1, ctx->s);
+    // what the bulk collision reads and writes, so they wait for both. With the fused pass, psi of the
+    // bodies' tiles (all that the side chain needs) is the side chain's first kernel.
+    if (!ctx->fused_tz) enqueue_lbm(ctx, 1, ctx->s);
     cudaEventRecord(ctx->ev_fork, ctx->s);
     cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    if (ctx->fused_tz) enqueue_lbm(ctx, 1, ctx->side);
     enqueue_lbm(ctx, 4, ctx->side);
     ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->side);
@@ -1062,20 +1072,28 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
   return CBL_OK;
 }
 
+// z extent of the fused pass's blocks: the requested one, or enough blocks for four waves
+static int fused_tz_of(const cbl_ctx* ctx) {
+  return ctx->fused_tz_req > 0 ? ctx->fused_tz_req : ctx->ops.fused_tz(ctx->lat, ctx->prec, ctx->fused_ty, 4);
+}
+
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
   if (!ctx || !key) return fail(ctx, CBL_ERR_ARG, "NULL argument");
   const std::string k(key);
   if (k == "lbm_variant") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "lbm_variant must be 0 or 1");
-    if (v == 1 && ctx->prec != 1) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass stores FP32");
-    if (v == 1 && ctx->ops.q != 19) return fail(ctx, CBL_ERR_UNSUPPORTED, "the fused pass is D3Q19 only");
-    ctx->fused_tz = v ? (ctx->fused_tz_req > 0 ? ctx->fused_tz_req : ctx->ops.fused_tz(ctx->lat, 2)) : 0;
+    ctx->fused_tz = v ? fused_tz_of(ctx) : 0;
   } else if (k == "fused_tz") {
     const int v = (int)value;
     if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
     ctx->fused_tz_req = v;
-    if (ctx->fused_tz) ctx->fused_tz = v > 0 ? v : ctx->ops.fused_tz(ctx->lat, 2);
+    if (ctx->fused_tz) ctx->fused_tz = fused_tz_of(ctx);
+  } else if (k == "fused_ty") {
+    const int v = (int)value;
+    if (v != 4 && v != 8) return fail(ctx, CBL_ERR_ARG, "fused_ty must be 4 or 8");
+    ctx->fused_ty = v;
+    if (ctx->fused_tz) ctx->fused_tz = fused_tz_of(ctx);
   } else if (k == "node_priority") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "node_priority must be 0 or 1");

@@ -172,18 +172,22 @@ __device__ __forceinline__ long long dbits(double v) { return __double_as_longlo
 // (0: fa, 1: fb). The step reads the current buffer, writes the other, and the closing kernel flips
 // the parity, so one captured graph serves every step.
 // launch_lbm_step phases: bit 0 density, bit 1 bulk collision, bit 2 collision of the cells next to
-// a solid. launch_lbm_fused: single-pass step for FP32 and FP16-deviation storage (prec 1, 2;
-// D3Q19 only), tz = z extent of a block (see fused_tz).
+// a solid. launch_lbm_fused: density and bulk collision in one pass (cells next to a solid excluded:
+// launch_density_tiles fills psi over the bodies' tiles for their collision); blocks of 32 x ty
+// consumer columns (ty 4 or 8) and as many producer threads, marching tz planes along z.
 #define CBL_LBM_LAUNCHERS                                                                              \
   void set_fp16_weights(cudaStream_t s);                                                             \
   void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi, \
                        const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st,      \
                        double* diag_rho, double* diag_vel, const PhysParams& pp, void* nbuf,          \
                        const int* blist, cudaStream_t s, int phases);                                 \
-  int fused_tz(const Lat& lat, int blocks_per_sm);                                                   \
+  int fused_tz(const Lat& lat, int prec, int ty, int waves);                                        \
   void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,         \
                         const BodyDev* bodies, double* mass_part, StepState* st, double* diag_rho,   \
-                        double* diag_vel, const PhysParams& pp, int tz, void* nbuf, cudaStream_t s); \
+                        double* diag_vel, const PhysParams& pp, int tz, int ty, cudaStream_t s);     \
+  void launch_density_tiles(int prec, const Lat& lat, const void* fa, const void* fb,                \
+                            const StepState* st, const uint16_t* flags, const BodyDev* bodies, int nb, \
+                            int max_tile, void* psi, const PhysParams& pp, cudaStream_t s);          \
   void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags, \
                        const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st, \
                        const void* nbuf, double G, cudaStream_t s);                                   \
@@ -211,6 +215,7 @@ struct LbmOps {
   decltype(&q19::launch_lbm_step) lbm_step;
   decltype(&q19::fused_tz) fused_tz;
   decltype(&q19::launch_lbm_fused) lbm_fused;
+  decltype(&q19::launch_density_tiles) density_tiles;
   decltype(&q19::launch_boundary) boundary;
   decltype(&q19::launch_read_populations) read_populations;
   decltype(&q19::launch_zero_solid) zero_solid;
@@ -219,7 +224,8 @@ struct LbmOps {
 };
 inline LbmOps lbm_ops(int q) {
 #define CBL_OPS(ns) \
-  LbmOps { q, &ns::set_fp16_weights, &ns::launch_lbm_step, &ns::fused_tz, &ns::launch_lbm_fused, &ns::launch_boundary, \
+  LbmOps { q, &ns::set_fp16_weights, &ns::launch_lbm_step, &ns::fused_tz, &ns::launch_lbm_fused,                   \
+           &ns::launch_density_tiles, &ns::launch_boundary,                                                             \
            &ns::launch_read_populations, &ns::launch_zero_solid, &ns::launch_init_fluid, &ns::launch_refill }
   return q == 27 ? CBL_OPS(q27) : CBL_OPS(q19);
 #undef CBL_OPS

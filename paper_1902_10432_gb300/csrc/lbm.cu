@@ -7,6 +7,9 @@
 //               correction (Eqs. lb_bounce_back_us, lb_bounce_back_mass), Guo-forced BGK
 //               collision (Eqs. lb_collision, distribution_eq, guo_forcing, fluid_velocity),
 //               FP64 fluid-mass partial sums.
+//  k_fused    : the two above in one pass over HBM (psi of each z-plane and a one-cell ring kept in
+//               shared memory, populations pulled again for the collision from the caches); fluid
+//               cells next to a solid are left to k_collide_near, fed by k_density_tiles.
 //  k_boundary : over the list of fluid cells next to a solid: momentum exchange on the bodies
 //               (Eq. solid_liquid_force) and the reaction of the Shan-Chen force (Sec. 3.2.3),
 //               summed in FP64.
@@ -17,8 +20,8 @@
 // Populations are SoA, f[i * N + n], in FP64, FP32 or binary16 deviations from the weights.
 //
 // This file is compiled once per velocity set: as itself for D3Q19 (namespace cbl::q19) and through
-// lbm27.cu with CBL_Q = 27 (namespace cbl::q27). The fused single-pass variants and the
-// no-allocation entry point exist for D3Q19 only.
+// lbm27.cu with CBL_Q = 27 (namespace cbl::q27). The no-allocation entry point exists for D3Q19
+// only.
 #include <climits>
 #include <cmath>
 #include "../../include/cbl.h"
@@ -294,10 +297,11 @@ struct CollideMinBlocks<__half> {
 // sources, wall terms, (rho, psi) for the force pass); without it the pull reads no flags at all, so
 // the bulk kernel carries neither the flag loads (on which the population addresses would depend)
 // nor the registers of the wall terms. Returns rho.
-template <typename S, bool NEAR>
+// psi_at(i): psi at x + c_i (i >= 1) and at x itself (i = 0).
+template <typename S, bool NEAR, typename PsiAt>
 __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__ src, S* __restrict__ dst,
                                                            const uint16_t* __restrict__ flags,
-                                                           const typename St<S>::R* __restrict__ psi,
+                                                           const PsiAt& psi_at,
                                                            const BodyDev* __restrict__ bodies, int diag,
                                                            double* __restrict__ diag_rho,
                                                            double* __restrict__ diag_vel, const Lat& lat,
@@ -310,11 +314,11 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
   {
     // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
     // it needs only psi, so the populations are not yet live
-    const R ps = psi[n];
+    const R ps = psi_at(0);
     R sx = 0, sy = 0, sz = 0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const R wp = (R)w_of(i) * psi[nbr(c, lat, i, +1)];
+      const R wp = (R)w_of(i) * psi_at(i);
       if (cx_of(i)) sx += wp * (R)cx_of(i);
       if (cy_of(i)) sy += wp * (R)cy_of(i);
       if (cz_of(i)) sz += wp * (R)cz_of(i);
@@ -385,10 +389,10 @@ __device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, do
     if (t != 0.0) atomicAdd(mass_part + (slot & (MASS_SLOTS - 1)), t);
   }
 }
-__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, float v, unsigned slot) {
+// the same from a compensated pair (hi, lo) per thread
+__device__ __forceinline__ void add_mass_slot2(double* __restrict__ mass_part, float hi, float lo, unsigned slot) {
   __shared__ float whi[32], wlo[32];
   const int lin = threadIdx.x + blockDim.x * threadIdx.y;
-  float hi = v, lo = 0.0f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -417,6 +421,39 @@ __device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, fl
     if (t != 0.0) atomicAdd(mass_part + (slot & (MASS_SLOTS - 1)), t);
   }
 }
+__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, float v, unsigned slot) {
+  add_mass_slot2(mass_part, v, 0.0f, slot);
+}
+
+// fluid-mass accumulation of one thread over several cells: FP64 as it is, FP32 in a compensated
+// pair (Knuth's TwoSum per add), so a thread's partial sum keeps the precision of a single cell's
+template <typename R>
+struct MassAcc;
+template <>
+struct MassAcc<double> {
+  double v = 0.0;
+  __device__ void add(double x) { v += x; }
+};
+template <>
+struct MassAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+    hi = s;
+  }
+};
+
+__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, const MassAcc<double>& a,
+                                              unsigned slot) {
+  add_mass_slot(mass_part, a.v, slot);
+}
+__device__ __forceinline__ void add_mass_slot(double* __restrict__ mass_part, const MassAcc<float>& a,
+                                              unsigned slot) {
+  add_mass_slot2(mass_part, a.hi, a.lo, slot);
+}
+
 
 // Bulk collision: solid cells store zeros, fluid cells without a solid neighbour collide; fluid cells
 // next to a solid are left to k_collide_near.
@@ -450,7 +487,8 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
       diag_vel[3 * n + 2] = 0.0;
     }
   } else if (valid && !(fl & F_NEAR)) {
-    my_mass = collide_fluid<S, false>(src, dst, flags, psi, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
+    auto psi_at = [&](int i) -> R { return i ? psi[nbr(c, lat, i, +1)] : psi[n]; };
+    my_mass = collide_fluid<S, false>(src, dst, flags, psi_at, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
   }
   add_mass_slot(mass_part, my_mass, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
@@ -475,448 +513,190 @@ __global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __r
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
     const long long n = blist[k];
     const Cell c = cell_of(n, lat);
-    my_mass += collide_fluid<S, true>(src, dst, flags, psi, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
+    auto psi_at = [&](int i) -> R { return i ? psi[nbr(c, lat, i, +1)] : psi[n]; };
+    my_mass += collide_fluid<S, true>(src, dst, flags, psi_at, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
   }
   add_mass_slot(mass_part, my_mass, blockIdx.x * 7u + 3u);
 }
 
-#if CBL_Q == 19
-// ---- fused step: pull + density + psi + Shan-Chen force + collision in one pass ----------------
-// A block owns a TX x TY column of cells and marches along z over [z0, z0 + tz). For every plane it
-// pulls the populations of the plane's cells plus a one-cell ring around them (periodic
-// coordinates), stores psi of that extended plane in a three-plane ring in shared memory and the
-// interior populations in a double buffer; once psi of plane z + 1 exists it collides plane z.
-// Every interior population is read from global memory once; the ring cells are re-reads of cells
-// that neighbouring blocks own (served from L2). Storage float or binary16, arithmetic FP32.
-template <typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) k_lbm_fused(S* __restrict__ fa, S* __restrict__ fb,
-                                                      const uint16_t* __restrict__ flags,
-                                                      const BodyDev* __restrict__ bodies,
-                                                      double* __restrict__ mass_part,
-                                                      const StepState* __restrict__ st,
-                                                      double* __restrict__ diag_rho, double* __restrict__ diag_vel,
-                                                      Lat lat, PhysParams pp, int tz,
-                                                      RhoPsi<float>* __restrict__ nbuf) {
-  using R = typename St<S>::R;
-  constexpr int NT = TX * TY, EX = TX + 2, EY = TY + 2, EP = EX * EY;
-  __shared__ R s_psi[3][EP];
-  __shared__ R s_f[2][Q][NT];
-  __shared__ unsigned s_sl[2][NT];
-  __shared__ double s_red[NT / 32];
+// the cell (gx, gy, gz) lies in the tile of a body with a lower id than `self` (so that a pass over
+// the tiles visits every cell once)
+__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
+                                                 int gz, const Lat& lat) {
+  for (int k = 0; k < b.nnb; ++k) {
+    int o = b.nbl[k];
+    if (o >= self) break;
+    const BodyDev& ob = bodies[o];
+    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
+        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
+      return true;
+  }
+  return false;
+}
 
-  const size_t N = (size_t)lat.Ns;  // population stride
+// ---- fused bulk pass: density, psi, Shan-Chen force and collision in one pass -----------------
+// The Shan-Chen force at x needs psi of the post-streaming density of this step at all neighbours
+// x + c_i (Eq. benzi_force), so every cell's populations are pulled twice per step: once for the
+// density, once for the collision. The split path does that in two kernels, two passes over HBM.
+// Here a block owns a TX x TY column of cells and marches along z over [z0, z0 + tz): for plane
+// z + 1 it pulls the populations of its own cells and of the one-cell ring around them (periodic
+// coordinates) and keeps only psi, in a ring of four planes in shared memory; then it collides plane
+// z, pulling its own cells' populations again. That second pull comes one plane after the first and
+// is served by the L1/L2 caches, and the ring cells are cells that neighbouring blocks own (L2), so
+// HBM sees every population read once per step. Fluid cells next to a solid (F_NEAR) are left to
+// k_collide_near, which reads psi from the lattice array that k_density_tiles fills over the bodies'
+// tiles. The arithmetic is that of k_density + k_collide, term by term in the same order, so both
+// paths give bit-identical results.
+
+// psi of one cell from the current populations: the post-streaming density with half-way
+// bounce-back at solid neighbours (Eq. lb_bounce_back; the g terms cancel in the density because of
+// the mass correction), psi = 1 - exp(-rho / rho0) (Eq. mean_field_potential); a solid cell carries
+// psi of its owner's wetting density (Sec. 3.2.3). The same expression as k_density.
+template <typename S>
+__device__ __forceinline__ typename St<S>::R psi_of_cell(const S* __restrict__ src, const uint16_t* __restrict__ flags,
+                                                         const BodyDev* __restrict__ bodies, const Lat& lat,
+                                                         const Cell& c, double rho0, float rho0_f) {
+  using R = typename St<S>::R;
+  const uint16_t fl = __ldg(flags + c.n);
+  if (fl & F_SOLID) return par<R>(bodies[fl & F_OWNER].psi_wet, bodies[fl & F_OWNER].psi_wet_f);
+  R fi[Q];
+  unsigned sl;
+  pull<S>(src, flags, lat, c, (long long)c.n, fi, sl, fl);
+  R rho = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) rho += fi[i];
+  return (R)1 - exp(-rho / par<R>(rho0, rho0_f));
+}
+
+// Named barriers of the fused pass's producer/consumer hand-off (barrier 0 is __syncthreads).
+// bar.arrive marks the calling warp's arrival and does not wait; bar.sync waits for the barrier's
+// generation to complete; once `count` threads have done either, the generation completes and the
+// arriving threads' earlier shared-memory writes are visible to the waiting ones.
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Block layout: TX x TY consumer threads (warps 0 .. TY*TX/32 - 1), one per column of the tile,
+// collide plane after plane; NPW producer warps behind them compute psi of the extended plane
+// (tile + one-cell ring) up to K - 2 planes ahead, so the HBM latency of the producers' pulls
+// overlaps the consumers' collisions. psi planes live in K shared-memory slots; FULL(s) hands slot
+// s from the producers to the consumers, EMPTY(s) hands it back. Every barrier generation has all
+// NALL threads: each producer thread arrives on FULL(slot of q) for every plane q and waits on
+// EMPTY before overwriting a slot (planes q >= K); each consumer waits on FULL for every plane and
+// releases plane j - 1 after colliding plane j (only while a producer will wait for it).
+template <typename S, int TX, int TY, int NPW, int MINB>
+__global__ void __launch_bounds__(TX * TY + 32 * NPW, MINB) k_fused(S* __restrict__ fa, S* __restrict__ fb,
+                                                                     const uint16_t* __restrict__ flags,
+                                                                     const BodyDev* __restrict__ bodies,
+                                                                     double* __restrict__ mass_part,
+                                                                     const StepState* __restrict__ st,
+                                                                     double* __restrict__ diag_rho,
+                                                                     double* __restrict__ diag_vel, Lat lat,
+                                                                     PhysParams pp, int tz) {
+  using R = typename St<S>::R;
+  constexpr int NC = TX * TY, NP = 32 * NPW, NALL = NC + NP;
+  constexpr int EX = TX + 2, EY = TY + 2, EP = EX * EY, MAXP = (EP + NP - 1) / NP;
+  constexpr int K = 4;
+  static_assert(NC % 32 == 0, "whole consumer warps");
+  __shared__ R s_psi[K][EP];
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
   const int zend = min(z0 + tz, lat.nz);
-  const R rho0 = par<R>(pp.rho0, pp.rho0_f);
-  R my_mass = 0;
-
-  // psi (and, for interior cells of the tile, the pulled populations) of plane z into ring slot
-  // and population buffer `buf` (buf < 0: psi only)
-  auto pull_plane = [&](int z, int buf) {
-    const int zz = z < 0 ? z + lat.nz : (z >= lat.nz ? z - lat.nz : z);
-    const int slot = (z - z0 + 3) % 3;
-    for (int p = tid; p < EP; p += NT) {
-      const int ex = p % EX, ey = p / EX;
-      int x = x0 - 1 + ex, y = y0 - 1 + ey;
-      x = x < 0 ? x + lat.nx : (x >= lat.nx ? x - lat.nx : x);
-      y = y < 0 ? y + lat.ny : (y >= lat.ny ? y - lat.ny : y);
-      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * zz);
-      const uint16_t fl = __ldg(flags + n);
-      const bool interior = buf >= 0 && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
-      const int ii = (ey - 1) * TX + (ex - 1);
-      if (fl & F_SOLID) {
-        s_psi[slot][p] = par<R>(bodies[fl & F_OWNER].psi_wet, bodies[fl & F_OWNER].psi_wet_f);
-        if (interior) s_sl[buf][ii] = 0xFFFFFFFFu;  // marks a solid cell
-        continue;
-      }
-      const Cell c = cell_of(n, lat);
-      R fi[Q];
-      unsigned sl;
-      pull<S>(src, flags, lat, c, n, fi, sl);
-      R rho = 0;
+  const int J = zend - z0 + 1;  // planes z0 - 1 .. zend have indices 0 .. J
+  MassAcc<R> mass;
+  if (tid >= NC) {
+    // producer: psi of extended cells p = ptid + k NP, for planes z0 - 1 .. zend
+    const int ptid = tid - NC;
+    int xs[MAXP], ys[MAXP];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) rho += fi[i];
-      s_psi[slot][p] = (R)1 - exp(-rho / rho0);
-      if (interior) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) s_f[buf][i][ii] = fi[i];
-        s_sl[buf][ii] = sl;
-      }
+    for (int k = 0; k < MAXP; ++k) {
+      const int p = ptid + k * NP;
+      xs[k] = wrapi(x0 - 1 + p % EX, lat.nx);
+      ys[k] = wrapi(y0 - 1 + p / EX, lat.ny);
     }
-  };
-
-  pull_plane(z0 - 1, -1);
-  pull_plane(z0, 0);
-  const int tx = tid % TX, ty = tid / TX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool mine = x < lat.nx && y < lat.ny;
-  for (int z = z0; z < zend; ++z) {
-    const int buf = (z - z0) & 1;
-    pull_plane(z + 1, z + 1 < zend ? buf ^ 1 : -1);
-    __syncthreads();
-    const unsigned sl = s_sl[buf][tid];
-    if (mine && sl != 0xFFFFFFFFu) {
-      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * z);
-      const int sm = (z - 1 - z0 + 3) % 3, s0 = (z - z0 + 3) % 3, sp = (z + 1 - z0 + 3) % 3;
-      const int pc = (ty + 1) * EX + (tx + 1);
-      const R ps = s_psi[s0][pc];
-      R sx = 0, sy = 0, sz = 0;
+    for (int j = 0; j <= J; ++j) {
+      const int sl = j % K;
+      if (j >= K) named_sync(1 + K + sl, NALL);
+      const int zz = wrapi(z0 - 1 + j, lat.nz);
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int slot = cz_of(i) > 0 ? sp : (cz_of(i) < 0 ? sm : s0);
-        const R wp = (R)w_of(i) * s_psi[slot][pc + cy_of(i) * EX + cx_of(i)];
-        if (cx_of(i)) sx += wp * (R)cx_of(i);
-        if (cy_of(i)) sy += wp * (R)cy_of(i);
-        if (cz_of(i)) sz += wp * (R)cz_of(i);
+      for (int k = 0; k < MAXP; ++k) {
+        const int p = ptid + k * NP;
+        if (p < EP)
+          s_psi[sl][p] = psi_of_cell<S>(src, flags, bodies, lat, make_cell(xs[k], ys[k], zz, lat), pp.rho0, pp.rho0_f);
       }
-      const R mG = -par<R>(pp.G, pp.G_f) * ps;
-      const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
-      R fi[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) fi[i] = s_f[buf][i][tid];
-      R rho = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) rho += fi[i];
-      my_mass += rho;
-      if (sl) {
-        nbuf[n] = RhoPsi<R>{rho, ps};
-        const Cell c = make_cell(x, y, z, lat);
-        R drho = 0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          if (!(sl & (1u << i))) continue;
-          const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
-          const R g = wall_term<R>(bodies[B], c, lat, i, rho);
-          fi[i] += g;
-          drho -= g;
-        }
-        fi[0] += drho;
-      }
-      R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (cx_of(i)) mx += (R)cx_of(i) * fi[i];
-        if (cy_of(i)) my += (R)cy_of(i) * fi[i];
-        if (cz_of(i)) mz += (R)cz_of(i) * fi[i];
-      }
-      R vx = 0, vy = 0, vz = 0;
-      if (rho > (R)0) {
-        const R ir = (R)1 / rho;
-        vx = mx * ir;
-        vy = my * ir;
-        vz = mz * ir;
-      }
-      const R itau = (R)1 / par<R>(pp.tau, pp.tau_f);
-      const R pref = (R)1 - (R)0.5 * itau;
-      const R uu = vx * vx + vy * vy + vz * vz;
-      const R vF = vx * Fx + vy * Fy + vz * Fz;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
-        const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
-        const R w = (R)w_of(i);
-        const R feq = rho * w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
-        const R Fi = pref * w * ((R)3 * (cF - vF) + (R)9 * cu * cF);
-        St<S>::st(dst, (size_t)i * N + n, i, fi[i] - (fi[i] - feq) * itau + Fi);
-      }
-      if (diag) {
-        diag_rho[n] = (double)rho;
-        diag_vel[3 * n] = (double)vx;
-        diag_vel[3 * n + 1] = (double)vy;
-        diag_vel[3 * n + 2] = (double)vz;
-      }
-    } else if (mine) {
-      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * z);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
-      if (diag) {
-        diag_rho[n] = 0.0;
-        diag_vel[3 * n] = 0.0;
-        diag_vel[3 * n + 1] = 0.0;
-        diag_vel[3 * n + 2] = 0.0;
-      }
+      named_arrive(1 + sl, NALL);
     }
-    __syncthreads();
-  }
-  double m = warp_mass(my_mass);
-  if ((tid & 31) == 0) s_red[tid >> 5] = m;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < NT / 32; ++w) t += s_red[w];
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (t != 0.0) atomicAdd(mass_part + (b & (MASS_SLOTS - 1)), t);
-  }
-}
-
-// ---- fused step with asynchronous plane prefetch (FP32 storage) -------------------------------
-// Same decomposition as k_lbm_fused, but the populations that the pull of a plane needs are copied
-// into shared memory with cp.async two planes ahead of their use (a three-stage ring), so the
-// global-memory latency of plane z + 2 overlaps the psi pass of plane z + 1 and the collision of
-// plane z. Sources that are solid (bounce-back) are substituted when the plane is consumed, only in
-// cells flagged as next to a solid.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-template <int TX, int TY>
-struct AsyncSmem {
-  static constexpr int EX = TX + 2, EY = TY + 2, EP = EX * EY, NT = TX * TY;
-  float pull[3][Q][EP];
-  float psi[3][EP];
-  unsigned sl[3][NT];
-  double red[NT / 32];
-};
-
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) k_lbm_fused_async(float* __restrict__ fa, float* __restrict__ fb,
-                                                            const uint16_t* __restrict__ flags,
-                                                            const BodyDev* __restrict__ bodies,
-                                                            double* __restrict__ mass_part,
-                                                            const StepState* __restrict__ st,
-                                                            double* __restrict__ diag_rho,
-                                                            double* __restrict__ diag_vel, Lat lat, PhysParams pp,
-                                                            int tz,
-                                                            RhoPsi<float>* __restrict__ nbuf) {
-  using R = float;
-  using SM = AsyncSmem<TX, TY>;
-  constexpr int NT = SM::NT, EX = SM::EX, EP = SM::EP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM& sm = *reinterpret_cast<SM*>(smem_raw);
-
-  const size_t N = (size_t)lat.Ns;  // population stride
-  const int diag = st->diag;
-  const float* __restrict__ src = st->parity ? fb : fa;
-  float* __restrict__ dst = st->parity ? fa : fb;
-  const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
-  const int zend = min(z0 + tz, lat.nz);
-  const R rho0 = par<R>(pp.rho0, pp.rho0_f);
-  R my_mass = 0;
-  auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
-  auto stage = [&](int z) { return (z - z0 + 1) % 3; };
-  const int nx = lat.nx, ny = lat.ny, nz = lat.nz;
-  const unsigned nxy = (unsigned)nx * (unsigned)ny;
-
-  // this thread's extended cells (at most two) and their wrapped x / y offsets for the source
-  // shifts -1, 0, +1 (the y offsets pre-multiplied by nx), computed once per block
-  constexpr int NP = (EP + NT - 1) / NT;
-  static_assert(NP <= 2, "at most two extended cells per thread");
-  int pp_[NP];
-  unsigned xo[NP][3], yo[NP][3];
-  int np = 0;
+  } else {
+    // consumer: the collision of this thread's column
+    const int tx = tid % TX, ty = tid / TX;
+    const bool valid = x0 + tx < lat.nx && y0 + ty < lat.ny;
+    const int p_own = (ty + 1) * EX + tx + 1;
+    const int xo = valid ? x0 + tx : 0, yo = valid ? y0 + ty : 0;
+    named_sync(1 + 0, NALL);  // plane z0 - 1
+    for (int z = z0; z < zend; ++z) {
+      const int j = z - z0 + 1;
+      if (j == 1) named_sync(1 + 1 % K, NALL);  // plane z0
+      named_sync(1 + (j + 1) % K, NALL);        // plane z + 1
+      if (valid) {
+        const Cell c = make_cell(xo, yo, z, lat);
+        const long long n = c.n;
+        const uint16_t fl = flags[n];
+        if (fl & F_SOLID) {
+          const size_t N = (size_t)lat.Ns;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const int p = tid + j * NT;
-    pp_[j] = p;
-    if (p < EP) np = j + 1;
-    const int ex = p % EX, ey = p / EX;
-    const int xe = wrap(x0 - 1 + ex, nx), ye = wrap(y0 - 1 + ey, ny);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      xo[j][k] = (unsigned)wrap(xe + k - 1, nx);
-      yo[j][k] = (unsigned)wrap(ye + k - 1, ny) * (unsigned)nx;
-    }
-  }
-
-  // copy the pull sources of plane z (all 19 directions, the extended plane) into its stage:
-  // source of direction i at cell (x, y, z) is (x - cx, y - cy, z - cz), i.e. shift k = 1 - c
-  auto issue = [&](int z) {
-    const int sg = stage(z);
-    const int zz = wrap(z, nz);
-    size_t zo[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) zo[k] = (size_t)wrap(zz + k - 1, nz) * nxy;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float* base = src + (size_t)i * N + zo[1 - cz_of(i)];
-#pragma unroll
-      for (int j = 0; j < NP; ++j)
-        if (j < np) cp_async4(&sm.pull[sg][i][pp_[j]], base + xo[j][1 - cx_of(i)] + yo[j][1 - cy_of(i)]);
-    }
-  };
-  // psi of plane z (and, for interior cells, the bounce-back substitution kept in the stage)
-  auto consume = [&](int z, bool keep) {
-    const int sg = stage(z), slot = (z - z0 + 3) % 3;
-    const size_t zoff = (size_t)wrap(z, nz) * nxy;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      if (j >= np) break;
-      const int p = pp_[j];
-      const int ex = p % EX, ey = p / EX;
-      const long long n = (long long)(zoff + xo[j][1] + yo[j][1]);
-      const uint16_t fl = __ldg(flags + n);
-      const bool interior = keep && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
-      const int ii = (ey - 1) * TX + (ex - 1);
-      if (fl & F_SOLID) {
-        sm.psi[slot][p] = par<R>(bodies[fl & F_OWNER].psi_wet, bodies[fl & F_OWNER].psi_wet_f);
-        if (interior) sm.sl[sg][ii] = 0xFFFFFFFFu;
-        continue;
-      }
-      unsigned sl = 0;
-      R rho = 0;
-      if (fl & F_NEAR) {
-        const Cell c = cell_of(n, lat);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          R v = sm.pull[sg][i][p];
-          if (i && (__ldg(flags + nbr(c, lat, i, -1)) & F_SOLID)) {
-            sl |= 1u << i;
-            v = __ldg(src + (size_t)opp_of(i) * N + n);
-            sm.pull[sg][i][p] = v;
+          for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
+          if (diag) {
+            diag_rho[n] = 0.0;
+            diag_vel[3 * n] = 0.0;
+            diag_vel[3 * n + 1] = 0.0;
+            diag_vel[3 * n + 2] = 0.0;
           }
-          rho += v;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rho += sm.pull[sg][i][p];
-      }
-      sm.psi[slot][p] = (R)1 - exp(-rho / rho0);
-      if (interior) sm.sl[sg][ii] = sl;
-    }
-  };
-
-  issue(z0 - 1);
-  cp_async_commit();
-  issue(z0);
-  cp_async_commit();
-  if (z0 + 1 <= zend) issue(z0 + 1);
-  cp_async_commit();
-  cp_async_wait<2>();
-  __syncthreads();
-  consume(z0 - 1, false);
-  __syncthreads();
-  if (z0 + 2 <= zend) issue(z0 + 2);
-  cp_async_commit();
-  cp_async_wait<2>();
-  __syncthreads();
-  consume(z0, true);
-
-  const int tx = tid % TX, ty = tid / TX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool mine = x < lat.nx && y < lat.ny;
-  const int pc = (ty + 1) * EX + (tx + 1);
-  for (int z = z0; z < zend; ++z) {
-    cp_async_wait<1>();
-    __syncthreads();
-    consume(z + 1, z + 1 < zend);
-    __syncthreads();
-    const int sg = stage(z);
-    const unsigned sl = sm.sl[sg][tid];
-    if (mine) {
-      const long long n = (long long)x + (long long)lat.nx * ((long long)y + (long long)lat.ny * z);
-      if (sl == 0xFFFFFFFFu) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) dst[(size_t)i * N + n] = 0.f;
-        if (diag) {
-          diag_rho[n] = 0.0;
-          diag_vel[3 * n] = 0.0;
-          diag_vel[3 * n + 1] = 0.0;
-          diag_vel[3 * n + 2] = 0.0;
-        }
-      } else {
-        const int sm_ = (z - 1 - z0 + 3) % 3, s0 = (z - z0 + 3) % 3, sp = (z + 1 - z0 + 3) % 3;
-        const R ps = sm.psi[s0][pc];
-        R sx = 0, sy = 0, sz = 0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const int slot = cz_of(i) > 0 ? sp : (cz_of(i) < 0 ? sm_ : s0);
-          const R wp = (R)w_of(i) * sm.psi[slot][pc + cy_of(i) * EX + cx_of(i)];
-          if (cx_of(i)) sx += wp * (R)cx_of(i);
-          if (cy_of(i)) sy += wp * (R)cy_of(i);
-          if (cz_of(i)) sz += wp * (R)cz_of(i);
-        }
-        const R mG = -par<R>(pp.G, pp.G_f) * ps;
-        const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
-        R fi[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fi[i] = sm.pull[sg][i][pc];
-        R rho = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rho += fi[i];
-        my_mass += rho;
-        if (sl) {
-          nbuf[n] = RhoPsi<R>{rho, ps};
-          const Cell c = make_cell(x, y, z, lat);
-          R drho = 0;
-#pragma unroll
-          for (int i = 1; i < Q; ++i) {
-            if (!(sl & (1u << i))) continue;
-            const int B = __ldg(flags + nbr(c, lat, i, -1)) & F_OWNER;
-            const R g = wall_term<R>(bodies[B], c, lat, i, rho);
-            fi[i] += g;
-            drho -= g;
-          }
-          fi[0] += drho;
-        }
-        R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          if (cx_of(i)) mx += (R)cx_of(i) * fi[i];
-          if (cy_of(i)) my += (R)cy_of(i) * fi[i];
-          if (cz_of(i)) mz += (R)cz_of(i) * fi[i];
-        }
-        R vx = 0, vy = 0, vz = 0;
-        if (rho > (R)0) {
-          const R ir = (R)1 / rho;
-          vx = mx * ir;
-          vy = my * ir;
-          vz = mz * ir;
-        }
-        const R itau = (R)1 / par<R>(pp.tau, pp.tau_f);
-        const R pref = (R)1 - (R)0.5 * itau;
-        const R uu = vx * vx + vy * vy + vz * vz;
-        const R vF = vx * Fx + vy * Fy + vz * Fz;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
-          const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
-          const R w = (R)w_of(i);
-          const R feq = rho * w * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
-          const R Fi = pref * w * ((R)3 * (cF - vF) + (R)9 * cu * cF);
-          dst[(size_t)i * N + n] = fi[i] - (fi[i] - feq) * itau + Fi;
-        }
-        if (diag) {
-          diag_rho[n] = (double)rho;
-          diag_vel[3 * n] = (double)vx;
-          diag_vel[3 * n + 1] = (double)vy;
-          diag_vel[3 * n + 2] = (double)vz;
+        } else if (!(fl & F_NEAR)) {
+          const int s0 = j % K, sm = (j - 1) % K, sp = (j + 1) % K;
+          auto psi_at = [&](int i) -> R {
+            if (i == 0) return s_psi[s0][p_own];
+            const int sl = cz_of(i) > 0 ? sp : (cz_of(i) < 0 ? sm : s0);
+            return s_psi[sl][p_own + cy_of(i) * EX + cx_of(i)];
+          };
+          mass.add(collide_fluid<S, false>(src, dst, flags, psi_at, bodies, diag, diag_rho, diag_vel, lat, pp,
+                                           nullptr, c, n));
         }
       }
+      // plane j - 1 is no longer read; hand it back if a producer will reuse its slot
+      if (j - 1 <= J - K) named_arrive(1 + K + (j - 1) % K, NALL);
     }
-    __syncthreads();
-    if (z + 3 <= zend) issue(z + 3);
-    cp_async_commit();
   }
-  cp_async_wait<0>();
-  double m = warp_mass(my_mass);
-  if ((tid & 31) == 0) sm.red[tid >> 5] = m;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < NT / 32; ++w) t += sm.red[w];
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (t != 0.0) atomicAdd(mass_part + (b & (MASS_SLOTS - 1)), t);
-  }
+  add_mass_slot(mass_part, mass, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
-// ---- solid-fluid force on the bodies ---------------------------------------------------------
-// For each listed fluid cell x: for a solid upstream neighbour s = x - c_i (owner B), momentum
-// exchange -c_i (2 f*_opp(i)(x) + g_i) with the arm at the link midpoint (Eq. solid_liquid_force);
-// for a solid downstream neighbour x + c_i (owner B), the reaction of the Shan-Chen force,
-// +G psi(x) w_i psi(x + c_i) c_i, arm x + c_i - X_B (Sec. 3.2.3). It reads the same source
-// populations and psi as the collision, so g_i and rho are bit-identical to the ones it used.
-#endif  // CBL_Q == 19 (fused variants)
+// psi of every cell of the bodies' tiles (each cell once: the lowest-id tile that covers it), for
+// the collision of the cells next to a solid on the side branch of the fused step
+template <typename S>
+__global__ void __launch_bounds__(256) k_density_tiles(const S* __restrict__ fa, const S* __restrict__ fb,
+                                                       const StepState* __restrict__ st,
+                                                       const uint16_t* __restrict__ flags,
+                                                       const BodyDev* __restrict__ bodies,
+                                                       typename St<S>::R* __restrict__ psi, Lat lat, double rho0,
+                                                       float rho0_f) {
+  const S* __restrict__ f = st->parity ? fb : fa;
+  const int self = blockIdx.y;
+  const BodyDev& b = bodies[self];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.sz) return;
+  const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];  // tiles hold < 2^31 cells
+  const unsigned r = u / L0;
+  const int gx = wrapi(b.o[0] + (int)(u - r * L0), lat.nx), gy = wrapi(b.o[1] + (int)(r % L1), lat.ny),
+            gz = wrapi(b.o[2] + (int)(r / L1), lat.nz);
+  if (b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat)) return;
+  const Cell c = make_cell(gx, gy, gz, lat);
+  psi[c.n] = psi_of_cell<S>(f, flags, bodies, lat, c, rho0, rho0_f);
+}
 
 // compensated float sum (Knuth's TwoSum): hi + lo carries the exact sum of the added values to about
 // 2^-48 relative, so the per-body sums keep FP64-level accuracy while only the last step per block
@@ -958,6 +738,12 @@ struct LinkSum<double> {
   __device__ double value() const { return v; }
 };
 
+// ---- solid-fluid force on the bodies ---------------------------------------------------------
+// For each listed fluid cell x: for a solid upstream neighbour s = x - c_i (owner B), momentum
+// exchange -c_i (2 f*_opp(i)(x) + g_i) with the arm at the link midpoint (Eq. solid_liquid_force);
+// for a solid downstream neighbour x + c_i (owner B), the reaction of the Shan-Chen force,
+// +G psi(x) w_i psi(x + c_i) c_i, arm x + c_i - X_B (Sec. 3.2.3). It reads the same source
+// populations and psi as the collision, so g_i and rho are bit-identical to the ones it used.
 // One thread per (list cell, direction): ~18x the parallelism of a thread per cell, which matters
 // because the list is short (the fluid cells next to a solid) and each link's work is a chain of
 // dependent loads (flags -> population or body). The 12 sums per body (momentum exchange F, T;
@@ -1108,18 +894,6 @@ __global__ void k_init_fluid(S* __restrict__ f, const uint16_t* __restrict__ fla
   }
 }
 
-__device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const BodyDev& b, int self, int gx, int gy,
-                                                 int gz, const Lat& lat) {
-  for (int k = 0; k < b.nnb; ++k) {
-    int o = b.nbl[k];
-    if (o >= self) break;
-    const BodyDev& ob = bodies[o];
-    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
-        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
-      return true;
-  }
-  return false;
-}
 
 // ---- cover refill and boundary list ------------------------------------------------------------
 // Over the body tiles (each cell once: the lowest-id tile that covers it), after the new flags.
@@ -1348,53 +1122,63 @@ unsigned lbm_blocks(const Lat& lat) {
   return (unsigned)(need < cap ? need : cap);
 }
 
-#if CBL_Q == 19
-constexpr int FTX = 32, FTY = 8;
+// Fused bulk pass: blocks of 32 x ty consumer columns (ty = 4 or 8) and as many producer threads,
+// marching tz planes along z.
+static int fused_min_blocks(int prec, int ty) {
+  // resident blocks per SM asked of the compiler: 64 registers per thread for FP32 / binary16
+  // storage, 128 for FP64
+  const int thr = 2 * 32 * ty;
+  return (prec == 0 ? 32768 : 65536) / (64 * thr);
+}
 
-// z extent of a fused block: as long as possible while the grid still fills the GPU
-// (blocks_per_sm resident blocks per SM)
-int fused_tz(const Lat& lat, int blocks_per_sm) {
-  const long long cols = (long long)((lat.nx + FTX - 1) / FTX) * ((lat.ny + FTY - 1) / FTY);
-  const long long slots = (long long)blocks_per_sm * sm_count();
-  long long nzc = slots / cols;
+// z extent of a fused block: enough blocks for `waves` full waves of resident blocks
+int fused_tz(const Lat& lat, int prec, int ty, int waves) {
+  const long long cols = (long long)((lat.nx + 31) / 32) * ((lat.ny + ty - 1) / ty);
+  const long long slots = (long long)fused_min_blocks(prec, ty) * sm_count() * waves;
+  long long nzc = (slots + cols - 1) / cols;
   if (nzc < 1) nzc = 1;
   if (nzc > lat.nz) nzc = lat.nz;
   return (int)((lat.nz + nzc - 1) / nzc);
 }
 
-template <typename S>
-static void fused_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, const BodyDev* bodies, double* mass_part,
-                    StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp, int tz, void* nbuf,
-                    cudaStream_t s) {
-  dim3 grid((lat.nx + FTX - 1) / FTX, (lat.ny + FTY - 1) / FTY, (lat.nz + tz - 1) / tz);
-  k_lbm_fused<S, FTX, FTY><<<grid, FTX * FTY, 0, s>>>(fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, lat,
-                                                      pp, tz, (RhoPsi<float>*)nbuf);
+template <typename S, int TY, int MINB>
+static void fused_t(const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
+                    double* mass_part, const StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
+                    int tz, cudaStream_t s) {
+  const dim3 grid((lat.nx + 31) / 32, (lat.ny + TY - 1) / TY, (lat.nz + tz - 1) / tz);
+  k_fused<S, 32, TY, TY, MINB><<<grid, 2 * 32 * TY, 0, s>>>((S*)fa, (S*)fb, flags, bodies, mass_part, st, diag_rho,
+                                                           diag_vel, lat, pp, tz);
 }
-
-size_t fused_async_smem() { return sizeof(AsyncSmem<FTX, FTY>); }
 
 void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, const BodyDev* bodies,
                       double* mass_part, StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,
-                      int tz, void* nbuf, cudaStream_t s) {
-  if (prec == 1) {
-    static bool attr = false;
-    const size_t bytes = fused_async_smem();
-    if (!attr) {
-      cudaFuncSetAttribute(k_lbm_fused_async<FTX, FTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      attr = true;
-    }
-    dim3 grid((lat.nx + FTX - 1) / FTX, (lat.ny + FTY - 1) / FTY, (lat.nz + tz - 1) / tz);
-    k_lbm_fused_async<FTX, FTY><<<grid, FTX * FTY, bytes, s>>>((float*)fa, (float*)fb, flags, bodies, mass_part, st,
-                                                               diag_rho, diag_vel, lat, pp, tz, (RhoPsi<float>*)nbuf);
-  } else if (prec == 2)
-    fused_t<__half>(lat, (__half*)fa, (__half*)fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, nbuf, s);
+                      int tz, int ty, cudaStream_t s) {
+  if (ty == 4) {
+    if (prec == 0) fused_t<double, 4, 2>(lat, fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+    else if (prec == 1) fused_t<float, 4, 4>(lat, fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+    else fused_t<__half, 4, 4>(lat, fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+  } else {
+    if (prec == 0) fused_t<double, 8, 1>(lat, fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+    else if (prec == 1) fused_t<float, 8, 2>(lat, fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+    else fused_t<__half, 8, 2>(lat, fa, fb, flags, bodies, mass_part, st, diag_rho, diag_vel, pp, tz, s);
+  }
 }
-#else
-// D3Q27: no fused variant (the context refuses lbm_variant 1)
-int fused_tz(const Lat&, int) { return 0; }
-void launch_lbm_fused(int, const Lat&, void*, void*, const uint16_t*, const BodyDev*, double*, StepState*, double*,
-                      double*, const PhysParams&, int, void*, cudaStream_t) {}
-#endif
+
+void launch_density_tiles(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
+                          const uint16_t* flags, const BodyDev* bodies, int nb, int max_tile, void* psi,
+                          const PhysParams& pp, cudaStream_t s) {
+  if (!nb) return;
+  const dim3 grid((unsigned)((max_tile + 255) / 256), (unsigned)nb);
+  if (prec == 0)
+    k_density_tiles<double><<<grid, 256, 0, s>>>((const double*)fa, (const double*)fb, st, flags, bodies,
+                                                 (double*)psi, lat, pp.rho0, pp.rho0_f);
+  else if (prec == 1)
+    k_density_tiles<float><<<grid, 256, 0, s>>>((const float*)fa, (const float*)fb, st, flags, bodies, (float*)psi,
+                                                lat, pp.rho0, pp.rho0_f);
+  else
+    k_density_tiles<__half><<<grid, 256, 0, s>>>((const __half*)fa, (const __half*)fb, st, flags, bodies,
+                                                 (float*)psi, lat, pp.rho0, pp.rho0_f);
+}
 
 template <typename S>
 static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,

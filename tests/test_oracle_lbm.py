@@ -210,3 +210,113 @@ def test_momentum_conservation_fluid_plus_bodies():
         pf, pb = o.total_momentum()
         assert np.abs(pf + pb - p0).max() < 1e-11, (pf + pb - p0)
     assert np.abs(pb - pb0).max() > 1e-4  # the body did exchange momentum
+
+
+def test_couette_moving_wall_closed_form():
+    # Moving-wall bounce-back (Sec. 3.2.2 Eqs. lb_bounce_back, lb_bounce_back_us): planar Couette
+    # flow between a held plate and a plate sliding tangentially at U (very heavy, so its velocity
+    # stays U). For BGK with half-way bounce-back the steady profile is exactly linear between the
+    # half-way wall positions, u_x = U (z - z_wall)/H, for any tau (the linear profile satisfies the
+    # lattice equations with the Chapman-Enskog non-equilibrium part, and the moving-wall term gives
+    # the wall velocity at the link midpoint). A wrong factor or sign in g, or a wall term applied
+    # to the wrong population, changes the slope or the wall value. Two channels: the gap between
+    # the plates, and the gap that closes through the periodic boundary.
+    U, nz = 0.02, 24
+    o = oracle.Oracle(4, 4, nz, G=0.0, tau=0.8, e0=0.0)
+    o.add_body("box", (1.5, 1.5, 3.0), half=(50.0, 50.0, 3.3), wetting_rho=1.0, fixed=True)
+    o.add_body("box", (1.5, 1.5, 15.0), half=(50.0, 50.0, 3.3), wetting_rho=1.0, mass_density=1e16)
+    o.init_fluid(1.0, 1.0)
+    o.set_body_velocity(1, V=(U, 0.0, 0.0))
+    solid, owner = o.flags()
+    col = solid[:, 0, 0]
+    held = np.nonzero(owner[:, 0, 0] == 0)[0]
+    moving = np.nonzero(owner[:, 0, 0] == 1)[0]
+    assert list(held) == [2, 3, 4] and list(moving) == [14, 15, 16]
+    o.step(3000)  # slowest mode decays as exp(-nu (pi/H)^2 t): 1e-16 by then
+    r, v, _ = o.fields()
+    ux = v[:, :, :, 0]
+    exp = np.zeros(nz)
+    H = 9.0
+    for z in range(5, 14):  # held wall at 4.5, moving wall at 13.5
+        exp[z] = U * (z - 4.5) / H
+    for z in list(range(17, 24)) + [0, 1]:  # moving wall at 16.5, held wall at 1.5 + nz
+        exp[z] = U * ((1.5 + nz - z) % nz) / H
+    fluid = col == 0
+    for y in range(4):
+        for x in range(4):
+            assert np.abs(ux[fluid, y, x] - exp[fluid]).max() < 1e-12 * U, (y, x)
+    assert np.abs(v[fluid][..., 1:]).max() < 1e-14
+    assert np.abs(r[fluid] - 1.0).max() < 1e-12
+
+
+def test_one_step_brute_force_moving_body():
+    # One step with a translating and rotating body, computed by hand: half-way bounce-back with the
+    # moving-wall term g_i = 2 rho w_i c_i.u_B / c_s^2, u_B = V + omega x (x_mid - X_B) at the link
+    # midpoint x_mid = x - c_i/2 (Eq. lb_bounce_back_us, Eq. solid_velocity), rho the density of the
+    # pulled populations, the mass correction delta rho = -sum g_i on the rest population
+    # (Eq. lb_bounce_back_mass), BGK; the momentum exchange -c_i (2 f*_opp + g_i) and its torque
+    # about X_B with the arm at the link midpoint (Eq. solid_liquid_force).
+    tau = 0.9
+    o = oracle.Oracle(4, 4, 4, G=0.0, tau=tau)
+    o.add_body("sphere", (1.0, 2.0, 1.0), radius=2.0, wetting_rho=1.0)
+    o.init_fluid(1.0, 1.0)
+    V = np.array([0.011, -0.023, 0.017])
+    W = np.array([0.021, -0.013, 0.031])
+    o.set_body_velocity(0, V=V, W=W)
+    solid, _ = o.flags()
+    assert solid.sum() == 1 and solid[1, 2, 1] == 1
+    X = o.bodies()["X"][0].copy()
+    c, w = o.velocity_set()
+    Q = len(w)
+    rest = int(np.where((c == 0).all(1))[0][0])
+    opp = [int(np.where((c == -c[i]).all(1))[0][0]) for i in range(Q)]
+    rng = np.random.default_rng(1)
+    f = 0.02 + 0.05 * rng.random((Q, 4, 4, 4))
+    f[:, 1, 2, 1] = 0.0
+    o.set_populations(f)
+
+    def mi(d):
+        return (d + 2.0) % 4.0 - 2.0
+
+    exp = np.zeros_like(f)
+    F = np.zeros(3)
+    T = np.zeros(3)
+    for z in range(4):
+        for y in range(4):
+            for x in range(4):
+                if solid[z, y, x]:
+                    continue
+                fi = np.zeros(Q)
+                links = []
+                for i in range(Q):
+                    sx, sy, sz = (x - c[i, 0]) % 4, (y - c[i, 1]) % 4, (z - c[i, 2]) % 4
+                    if i != rest and solid[sz, sy, sx]:
+                        fi[i] = f[opp[i], z, y, x]
+                        links.append(i)
+                    else:
+                        fi[i] = f[i, sz, sy, sx]
+                rho = fi.sum()
+                drho = 0.0
+                for i in links:
+                    mid = np.array([x, y, z], float) - 0.5 * c[i]
+                    arm = mi(mid - X)
+                    uB = V + np.cross(W, arm)
+                    g = 2.0 * rho * w[i] * (c[i] @ uB) * 3.0
+                    dP = -c[i] * (2.0 * f[opp[i], z, y, x] + g)
+                    F += dP
+                    T += np.cross(arm, dP)
+                    fi[i] += g
+                    drho -= g
+                fi[rest] += drho
+                u = (c.T @ fi) / rho
+                cu = c @ u
+                feq = rho * w * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * u @ u)
+                exp[:, z, y, x] = fi - (fi - feq) / tau
+    o.step(1)
+    s1, _ = o.flags()
+    assert np.array_equal(s1, solid)  # no cover event: the populations are the collision's
+    got = o.populations()
+    assert np.abs(got - exp).max() < 1e-15
+    _, _, parts = o.body_forces()
+    assert np.allclose(parts[0, 0, :3], F, rtol=1e-12, atol=1e-16)
+    assert np.allclose(parts[0, 0, 3:], T, rtol=1e-11, atol=1e-16)

@@ -188,3 +188,69 @@ def test_repulsion_single_pair_closed_form(d):
     assert np.allclose(FA, exp_A, rtol=1e-12, atol=1e-18)
     assert np.allclose(FB, -exp_A, rtol=1e-12, atol=1e-18)
     assert np.abs(parts[:, 2, 3:]).max() < 1e-18  # arm = 0 for a one-point body at its centre
+
+
+def _plate_x(r, u, eta_cells=5.0, nx_per_r=64, h_per_r=6.0, c_per_r=20.0):
+    # a plate spanning y and z (its phase field varies only along x): the 1D profile
+    # 1/2 - 1/2 sin(pi d / eta) across both faces, advected at the uniform velocity (u, 0, 0)
+    o = oracle.Oracle(int(nx_per_r * r), 4, 4, eta=eta_cells * r)
+    o.add_body("box", (c_per_r * r, 1.5, 1.5), half=(h_per_r * r, 50.0, 50.0), wetting_rho=1.0, mass_density=1.0)
+    o.init_fluid(1.0, 1.0)
+    o.set_body_velocity(0, V=(u, 0.0, 0.0))
+    return o
+
+
+@pytest.mark.parametrize("u", [0.3, -0.3])
+def test_muscl_sweep_one_step_by_hand(u):
+    # One directional sweep (Eq. phase_advection, split form, Sec. 3.3) computed here on the 1D
+    # profile: MC-limited slope minmod(2 dm, (dm + dp)/2, 2 dp) (van Leer), upwind face value
+    # phi_i + (1 - |u|)/2 slope_i (u > 0) or phi_{i+1} - (1 - |u|)/2 slope_{i+1} (u < 0), conservative
+    # update phi_i - (F_{i+1/2} - F_{i-1/2}); the y and z sweeps carry no flux.
+    o = _plate_x(1, u)
+    p0 = o.phi(0)[0, 0, :].copy()
+    o.phase_only(kinetics=False)
+    got = o.phi(0)
+
+    def mc(dm, dp):
+        s = np.minimum(np.minimum(2 * np.abs(dm), 0.5 * np.abs(dm + dp)), 2 * np.abs(dp))
+        return np.where(dm * dp > 0, np.sign(dm) * s, 0.0)
+
+    pm1, p1, p2 = np.roll(p0, 1), np.roll(p0, -1), np.roll(p0, -2)
+    if u >= 0:
+        face = p0 + 0.5 * (1 - u) * mc(p0 - pm1, p1 - p0)
+    else:
+        face = p1 - 0.5 * (1 + u) * mc(p1 - p0, p2 - p1)
+    flux = u * face
+    exp = p0 - (flux - np.roll(flux, 1))
+    exp = np.clip(exp, 0.0, 1.0)
+    exp[exp < 1e-12] = 0.0
+    exp[exp > 1 - 1e-12] = 1.0
+    assert (np.abs(np.diff(p0)) > 0.05).sum() >= 6  # non-trivial slopes across both faces
+    for y in range(4):
+        for z in range(4):
+            assert np.abs(got[z, y, :] - exp).max() < 1e-15
+
+
+@pytest.mark.parametrize("u", [0.3, -0.3])
+def test_muscl_second_order_convergence(u):
+    # The split MUSCL scheme with the MC limiter is second order on smooth data: advecting the
+    # interface profile over a fixed distance (12 cells at resolution 1, at fixed Courant number
+    # |u| = 0.3), refining the grid by 2 (interface width eta = 5 r, plate and lattice scaled with
+    # it) cuts the L1 error against the exactly translated profile by about 4 (the profile is only
+    # C^1 at |d| = eta/2 and the limiter flattens its plateaus, so the measured factor is 3.2-3.5).
+    # Dropping the (1 - |u|) time correction, doubling the slope term or using the minmod limiter
+    # leaves a first-order error: factor <= 2.3 and errors 7-40 times larger at r = 4.
+    errs = {}
+    for r in (2, 4):
+        o = _plate_x(r, u)
+        n = int(round(12.0 * r / abs(u)))
+        for _ in range(n):
+            o.phase_only(kinetics=False)
+        phi = o.phi(0)[0, 0, :]
+        x = np.arange(phi.size)
+        d = np.abs(x - (20.0 * r + u * n)) - 6.0 * r
+        eta = 5.0 * r
+        exact = np.where(d <= -eta / 2, 1.0, np.where(d >= eta / 2, 0.0, 0.5 - 0.5 * np.sin(np.pi * d / eta)))
+        errs[r] = np.abs(phi - exact).sum() / r
+    assert errs[2] / errs[4] > 2.8, errs
+    assert errs[4] < 0.04, errs
