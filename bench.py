@@ -233,7 +233,9 @@ def bench_reference(args, rank, world):
 
 
 def bench_batch(args, rank, world, local_rank):
-    """64 independent two-sphere instances: one batched graph vs the instances run one after another.
+    """64 independent two-sphere instances: one batched graph (the bulk lattice-Boltzmann pass of all
+    instances in one persistent launch, tile shape from the autotuner) vs the instances run one after
+    another.
     On several GPUs each rank runs its share of the instances (no collective on the data path); the
     time is the slowest rank's and the work is the total."""
     import torch
@@ -268,6 +270,8 @@ def bench_batch(args, rank, world, local_rank):
         torch.cuda.synchronize()
     seq_s = rk.max(time.perf_counter() - t0)
     batch = cbl.Batch(sims)
+    tile, tile_ms = autotune.tune_batch(batch, steps=3)
+    binfo = batch.info()
     batch.step(args.warmup)
     batch.sync()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -292,11 +296,19 @@ def bench_batch(args, rank, world, local_rank):
             "config": {"workload": "batch64: 64 two-sphere instances, boxes U{64..128}^3, R U[10,24], "
                                    "liquid fraction U[0.01,0.2], angle U[30,90] deg, seed 0",
                        "cells": int(cells), "autotune_choices": choices,
+                       "batch": {"mode": "persistent" if binfo["mode"] == 1 else "branch per instance",
+                                 "tile": autotune.BATCH_TILES.get(binfo["tile"]), "work_items": binfo["items"],
+                                 "grid_blocks": binfo["grid"],
+                                 "tile_ms_per_step": {str(autotune.BATCH_TILES[k]): round(v, 3)
+                                                      for k, v in tile_ms.items()}},
                        "parallelism": "instances sharded over %d GPUs" % world if world > 1 else "single GPU"},
             "sequential_mlups": cells * args.steps / seq_s / 1e6,
             "speedup_vs_sequential": seq_s / bat_s, "clocks": clk.summary(),
-            "gpu_launches": args.steps * sum(n * kernels_per_step(2, 1, json.loads(c).get("lbm_variant") == 1)
-                                             for c, n in choices.items())}
+            # persistent mode: one launch for the bulk pass of all instances, then each instance's side
+            # chain (its step without the density and bulk collision kernels)
+            "gpu_launches": args.steps * ((1 + len(ws) * (kernels_per_step(2, 1, False) - 2)) if binfo["mode"] == 1
+                                          else sum(n * kernels_per_step(2, 1, json.loads(c).get("lbm_variant") == 1)
+                                                   for c, n in choices.items()))}
     if rk.root:
         print(json.dumps(line), flush=True)
     batch.close()

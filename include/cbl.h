@@ -154,6 +154,12 @@ cbl_status cbl_read_phi(cbl_ctx* ctx, int body, double* phi_host);
  * Host pointers; any may be NULL. */
 cbl_status cbl_read_body_forces(cbl_ctx* ctx, double* F, double* T, double* parts);
 
+/* Mean per-body total force F (nb*3) and torque T (nb*3) over the steps since the last reset (FP64
+ * running sums kept on the device by the rigid-body update, so a mean over many steps needs no host
+ * read per step); *nsteps (may be NULL) receives that number of steps. reset != 0 starts the sums
+ * anew after reading. Host pointers; F, T may be NULL. cbl_load and cbl_init_fluid start them at 0. */
+cbl_status cbl_read_force_mean(cbl_ctx* ctx, double* F, double* T, long long* nsteps, int reset);
+
 /* Body state (host arrays, nb*3 / nb*4 / nb / nb*9; any may be NULL): centre of mass, velocity,
  * angular velocity, orientation quaternion, mass, body-frame inertia. Returns CBL_ERR_UNSTABLE (with
  * the arrays filled) once a body update was not finite or moved a body by a lattice length or more
@@ -270,17 +276,36 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
 cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int nx, int ny, int nz, double tau, double G,
                                 double rho0, const double* ext_force, double* mass_out, void* stream);
 
-/* Batches: advance many independent contexts with one call. One CUDA graph holds one step of every
- * instance, each instance on its own branch (fork/join), so the kernels of independent instances
- * run concurrently. The contexts must be initialised (cbl_init_fluid), live on the current device
+/* Batches: advance many independent contexts (lattices of any size, each with its own bodies and
+ * parameters) with one call; one captured CUDA graph holds one step of every instance.
+ * Persistent mode (mode 1, the default when every instance has the same precision and velocity set
+ * and uses the split pass): the step of all instances starts with ONE launch of a persistent kernel
+ * that computes psi and then the bulk collision of every cell of every instance (Sec. 3.2.1, 3.2.3):
+ * its grid is as large as the GPU holds resident blocks, each block takes work items (a tile of one
+ * instance; tile shape from "tile", picked by the project's autotuner) from a device queue, and the
+ * two phases are separated by a grid barrier whose wait is bounded (option "spin_limit", clock64
+ * cycles, default ~2 s): a block that waits longer sets an error word and returns, and
+ * cbl_batch_sync then returns CBL_ERR_TIMEOUT (that step's results are not valid; the contexts stay
+ * usable). Each instance's remaining work (the cells next to a solid, the bodies, the phase fields,
+ * flags and refill) follows on its own graph branch. Mode 0: one fork/join branch per instance with
+ * its whole step. The contexts must be initialised (cbl_init_fluid), live on the current device
  * and outlive the batch; while in a batch they must not be stepped on their own. `stream` (may be
- * NULL: the library creates one) orders the batch's work. */
+ * NULL: the library creates one) orders the batch's work. The batch itself allocates its instance
+ * table and control block with cudaMalloc (a few kB). */
 typedef struct cbl_batch cbl_batch;
 cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch** out);
 /* Advance every instance nsteps steps (asynchronous); the fields of the last step are kept. */
 cbl_status cbl_batch_step(cbl_batch* batch, int nsteps);
-/* Wait for the batch's stream. */
+/* Wait for the batch's stream; CBL_ERR_TIMEOUT if a grid-barrier wait of the persistent kernel ran
+ * out since the last call (the error word is cleared). */
 cbl_status cbl_batch_sync(cbl_batch* batch);
+/* Batch options (synchronises, rebuilds the graphs): "mode" 0 or 1; "tile" 0..3, the persistent
+ * kernel's tile of x * y * z cells: 32*4*1, 32*4*4 (default), 32*4*8, 64*2*4; "spin_limit" the
+ * barrier wait limit in clock64 cycles (0 makes every wait run out at once: a test of the timeout
+ * path). CBL_ERR_UNSUPPORTED for mode 1 over mixed precisions or velocity sets. */
+cbl_status cbl_batch_set_option(cbl_batch* batch, const char* key, double value);
+/* The batch's mode, tile shape, number of work items per phase and grid size (blocks). */
+cbl_status cbl_batch_info(cbl_batch* batch, int* mode, int* tile, long long* items, int* grid);
 cbl_status cbl_batch_destroy(cbl_batch* batch);
 
 /* Force surrogate network (no counterpart in the paper's method: it stands in for the force
@@ -308,6 +333,23 @@ cbl_status cbl_mlp_zero_grad(cbl_mlp* mlp);
  * copy, clear the gradient. */
 cbl_status cbl_mlp_adam_step(cbl_mlp* mlp, float lr, float beta1, float beta2, float eps);
 cbl_status cbl_mlp_sync(cbl_mlp* mlp);
+/* Advance nb rigid spheres `steps` semi-implicit Euler steps (dt = 1) under the network's pair forces
+ * and torques plus a fixed per-body bias force, with the fluid frozen: the surrogate window of the
+ * hybrid advance (no counterpart in the paper's method), all on the device in one launch. For every
+ * step and bridged pair (i, j) (pairs: npairs * 2 body ids; VL: their bridge volumes), both sides
+ * form the features in the pair frame (e_z from the body to its partner, minimum image over the
+ * periodic box dims[3]): gap (r - R_i - R_j) sqrt(R* / V_L), cos_theta, R_i / R_j, V_L / R*^3 with
+ * R* = 2 R_i R_j / (R_i + R_j); standardise them with norm = {x mean[4], x std[4], x min[4], x max[4],
+ * y mean[6], y std[6]} (clipped to [min, max] first); run the network; and add force * 2 pi R* sigma
+ * and torque * 2 pi R*^2 sigma, turned to the lattice frame, to body i. Then each body whose fixed[i]
+ * is 0: V += (F + bias) / M, X += V (wrapped into the box), omega += T * Iinv (spheres: a scalar
+ * inverse inertia). X, V, Wang (nb * 3, in/out), M, Iinv, R (nb), fixed (nb ints), bias (nb * 3),
+ * pairs, VL are device pointers; dims and norm host pointers. nb <= 2048. CBL_ERR_ARG for bad sizes
+ * or a non-finite or degenerate normalisation. Asynchronous on the network's stream. */
+cbl_status cbl_mlp_advance(cbl_mlp* mlp, double* X, double* V, double* Wang, const double* M, const double* Iinv,
+                           const double* R, const int* fixed, const double* bias, const int* pairs, const double* VL,
+                           int nb, int npairs, int steps, const int* dims, double cos_theta, const float* norm,
+                           double sigma);
 cbl_status cbl_mlp_destroy(cbl_mlp* mlp);
 
 /* Release every device allocation and the context. */

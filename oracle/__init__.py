@@ -50,6 +50,7 @@ class orc_params(ctypes.Structure):
         ("solid_threshold", ctypes.c_double),
         ("member_threshold", ctypes.c_double),
         ("nthreads", ctypes.c_int),
+        ("store_prec", ctypes.c_int),
     ]
 
 
@@ -89,6 +90,8 @@ def _load():
             lib.orc_total_mass.argtypes = [P]
             lib.orc_total_momentum.argtypes = [P, D, D]
             lib.orc_phase_only.argtypes = [P, ctypes.c_int]
+            lib.orc_round_binary16.restype = ctypes.c_double
+            lib.orc_round_binary16.argtypes = [ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -103,7 +106,7 @@ def _vp(a):
 
 DEFAULTS = dict(q=19, tau=1.0, G=-5.0, rho0=1.0, ext_force=(0.0, 0.0, 0.0), mpf_kinetics=0,
                 mobility=1e-5, eta=5.0, sigma_sf=3.583e-2, sigma_ss=0.5 * 3.583e-2, e0=1e-3, rc=3.0, nrep=4,
-                solid_threshold=0.05, member_threshold=0.5, nthreads=0)
+                solid_threshold=0.05, member_threshold=0.5, nthreads=0, store_prec=0)
 
 
 class Oracle:
@@ -256,3 +259,8 @@ class Oracle:
         b = np.empty(3)
         self._lib.orc_total_momentum(self._h, _dp(a), _dp(b))
         return a, b
+
+
+def round_binary16(h):
+    """The binary16 rounding of the oracle's storage model (store_prec = 2)."""
+    return _load().orc_round_binary16(float(h))

@@ -116,3 +116,28 @@ def cap_angle(base_halfwidth, height):
     """Contact angle of a circular cap (2D cut) from its base half-width a and height h:
     tan(theta/2) = h / a."""
     return 2.0 * math.atan2(height, base_halfwidth)
+
+
+# --- Sec. 2.1: a bridge between parallel plates away from 90 degrees ---------------------------
+def toroidal_bridge(sigma, theta, h, V):
+    """Toroidal (circular-meridian) approximation of an axisymmetric liquid bridge between two
+    parallel plates with the same contact angle theta (radians, 0 < theta <= pi/2), gap h and liquid
+    volume V. The paper's force on a plate (Sec. 2.1, Eq. plate_force) is the surface-tension pull
+    along the contact line plus the Laplace pressure on the wetted area; evaluated at the neck
+    (radius a) it is F = 2 pi sigma a - pi a^2 dp, with dp = sigma (1/a - 1/r1) from Eq.
+    young_laplace with the two principal curvatures, the meridian being a circle of radius
+    r1 = h / (2 cos theta) that meets both plates at theta. Hence F = pi sigma a (1 + a / r1); at
+    90 degrees r1 is infinite and F = pi sigma a with V = pi a^2 h (the cylinder of Eq.
+    plate_force). a follows from V = pi int_{-h/2}^{h/2} (a + r1 - sqrt(r1^2 - z^2))^2 dz.
+    Returns (a, r1, F)."""
+    if abs(theta - math.pi / 2) < 1e-12:
+        a = math.sqrt(V / (math.pi * h))
+        return a, math.inf, math.pi * sigma * a
+    r1 = h / (2.0 * math.cos(theta))
+
+    def vol(a):
+        f = lambda z: (a + r1 - math.sqrt(r1 * r1 - z * z)) ** 2
+        return math.pi * integrate.quad(f, -0.5 * h, 0.5 * h)[0]
+
+    a = optimize.brentq(lambda x: vol(x) - V, 1e-9, math.sqrt(V / (math.pi * h)) + r1)
+    return a, r1, math.pi * sigma * a * (1.0 + a / r1)

@@ -56,6 +56,8 @@ typedef struct {
   double solid_threshold;      // a cell is solid iff fluid phase < this (paper: 0.05)
   double member_threshold;     // repulsion body point iff phi_B >= this (READING: 0.5)
   int nthreads;                // OpenMP threads (0 = runtime default)
+  int store_prec;              // storage model of the populations (analysis only, see round_store):
+                               // 0 FP64 (the method), 1 FP32, 2 binary16 deviations from w_i
 } orc_params;
 
 }  // extern "C"
@@ -207,6 +209,37 @@ int nthreads_of(const Oracle& o) {
   (void)o;
   return 1;
 #endif
+}
+
+// ---------------------------------------------------------------------------------------------
+// Storage model (analysis only; not part of the paper's method, off by default). The CUDA library
+// can store the populations in FP32, or as binary16 deviations h_i = f_i - w_i from the lattice
+// weights. To separate what that storage costs from what its arithmetic costs, the oracle can round
+// its stored populations the same way after every store (the collision and the cover refill) and
+// otherwise stay FP64. Binary16 rounding is written out from the format: 11 significant bits for
+// |h| >= 2^-14, a quantum of 2^-24 below, round to nearest even (std::nearbyint in the default
+// rounding mode); the weights are rounded the same way first, so a zero population stays exact.
+double round_binary16(double h) {
+  const double a = std::fabs(h);
+  if (a == 0.0) return h;
+  if (a < 0x1p-14) return std::nearbyint(h * 0x1p24) * 0x1p-24;
+  int e;
+  std::frexp(a, &e);  // a = m 2^e, m in [0.5, 1): 11 significant bits are multiples of 2^(e - 11)
+  return std::ldexp(std::nearbyint(std::ldexp(h, 11 - e)), e - 11);
+}
+
+void round_store(Oracle& o) {
+  if (o.p.store_prec == 0) return;
+  const int Q = o.L.Q;
+  const long N = o.N;
+  double wh[27];
+  for (int i = 0; i < Q; ++i) wh[i] = round_binary16(o.L.w[i]);
+#pragma omp parallel for schedule(static) num_threads(nthreads_of(o))
+  for (long n = 0; n < N; ++n)
+    for (int i = 0; i < Q; ++i) {
+      double& f = o.f[(size_t)i * N + n];
+      f = o.p.store_prec == 1 ? (double)(float)f : round_binary16((double)(float)(f - wh[i])) + wh[i];
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -853,12 +886,14 @@ int orc_step(void* h, int nsteps) {
   if (!o->ready) return -1;
   for (int s = 0; s < nsteps; ++s) {
     lbm_step(*o);
+    round_store(*o);
     repulsion(*o);
     for (Body& b : o->bodies) integrate_body(*o, b);
     if (!o->bodies.empty()) {
       advect(*o);
       if (o->p.mpf_kinetics) kinetics(*o);
       flags_and_refill(*o);
+      round_store(*o);
     }
     o->t++;
   }
@@ -914,6 +949,9 @@ void orc_velocity_set(void* h, int* c, double* w) {
     w[i] = o->L.w[i];
   }
 }
+
+// The binary16 rounding of the storage model, for its test against an independent implementation.
+double orc_round_binary16(double h) { return round_binary16(h); }
 
 // Per-body total force/torque of the last step, and the parts
 // [momentum exchange F,T | SC adhesion F,T | repulsion F,T] (18 per body).

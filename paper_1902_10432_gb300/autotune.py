@@ -1,7 +1,9 @@
-"""Project autotuner: picks the execution variant of the lattice kernels for a lattice shape.
+"""Project autotuner: picks the execution variant of the lattice kernels for a lattice shape, and the
+tile shape of the persistent batch kernel for a batch.
 
-Candidates: the split density + collision kernels with 128-thread blocks of x extent 32, 64 or 128,
-and (FP32 storage) the single fused pass. Each candidate is timed on the simulation it will run
+Candidates for one lattice: the split density + collision kernels with 128-thread blocks of x extent
+32, 64 or 128, and the fused single pass. For a batch (tune_batch): the persistent kernel's tile
+shapes 32x4x1, 32x4x4, 32x4x8 and 64x2x4 cells. Each candidate is timed on the simulation it will run
 (three warm-up steps, then CUDA events around a few steps on the simulation's stream; the state
 advances, which does not matter for the choice); the fastest is applied and cached in a JSON file
 keyed by lattice shape, precision, whether bodies are present and the GPU name.
@@ -19,8 +21,7 @@ _lock = threading.Lock()
 
 def candidates(prec):
     c = [dict(lbm_variant=0, lbm_block_x=bx) for bx in (32, 64, 128)]
-    if prec == "fp32":
-        c.append(dict(lbm_variant=1, lbm_block_x=32))
+    c.append(dict(lbm_variant=1, lbm_block_x=32))
     return c
 
 
@@ -83,4 +84,28 @@ def tune(sim, steps=6, use_cache=True):
             with open(tmp, "w") as f:
                 json.dump(cache, f, indent=1, sort_keys=True)
             os.replace(tmp, CACHE)
+    return best, results
+
+
+BATCH_TILES = {0: (32, 4, 1), 1: (32, 4, 4), 2: (32, 4, 8), 3: (64, 2, 4)}
+
+
+def tune_batch(batch, steps=4):
+    """Time the persistent kernel's tile shapes on `batch` (its instances advance) and keep the
+    fastest. Returns (tile, {tile: ms/step})."""
+    import time
+
+    if batch.info()["mode"] != 1:
+        return None, {}
+    results = {}
+    for t in BATCH_TILES:
+        batch.set_option("tile", t)
+        batch.step(2)
+        batch.sync()
+        t0 = time.perf_counter()
+        batch.step(steps)
+        batch.sync()
+        results[t] = (time.perf_counter() - t0) * 1e3 / steps
+    best = min(results, key=results.get)
+    batch.set_option("tile", best)
     return best, results

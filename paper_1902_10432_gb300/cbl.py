@@ -74,6 +74,7 @@ SIGNATURES = {
     "cbl_read_phi": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cbl_read_body_forces": (ctypes.c_int, [_P, _P, _P, _P]),
     "cbl_get_bodies": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "cbl_read_force_mean": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "cbl_set_body_velocities": (ctypes.c_int, [_P, _P, _P]),
     "cbl_set_bodies_fixed": (ctypes.c_int, [_P, _P]),
     "cbl_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
@@ -91,6 +92,9 @@ SIGNATURES = {
     "cbl_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "cbl_batch_sync": (ctypes.c_int, [_P]),
     "cbl_batch_destroy": (ctypes.c_int, [_P]),
+    "cbl_batch_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
+    "cbl_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]),
     "cbl_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                       ctypes.POINTER(_P)]),
     "cbl_mlp_num_params": (ctypes.c_int64, [_P]),
@@ -102,6 +106,8 @@ SIGNATURES = {
     "cbl_mlp_zero_grad": (ctypes.c_int, [_P]),
     "cbl_mlp_adam_step": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "cbl_mlp_sync": (ctypes.c_int, [_P]),
+    "cbl_mlp_advance": (ctypes.c_int, [_P] + [_P] * 10 + [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                                          ctypes.c_double, _P, ctypes.c_double]),
     "cbl_mlp_destroy": (ctypes.c_int, [_P]),
     "cbl_destroy": (ctypes.c_int, [_P]),
     "cbl_last_error": (ctypes.c_char_p, [_P]),
@@ -288,6 +294,16 @@ class Sim:
         self._ck(self._lib.cbl_read_body_forces(self._h, _vp(F), _vp(T), _vp(parts)))
         return F.reshape(nb, 3), T.reshape(nb, 3), parts.reshape(nb, 3, 6)
 
+    def force_mean(self, reset=True):
+        """Mean total force and torque per body over the steps since the last reset (device-side sums),
+        and that number of steps; reset starts the sums anew."""
+        nb = self.nb
+        F = np.empty(3 * nb)
+        T = np.empty(3 * nb)
+        n = ctypes.c_longlong()
+        self._ck(self._lib.cbl_read_force_mean(self._h, _vp(F), _vp(T), ctypes.byref(n), int(bool(reset))))
+        return F.reshape(nb, 3), T.reshape(nb, 3), n.value
+
     def bodies(self):
         nb = self.nb
         X, V, W = (np.empty(3 * nb) for _ in range(3))
@@ -358,8 +374,9 @@ class Sim:
 
 
 class Batch:
-    """Independent simulations advanced together: one CUDA graph holds one step of every instance,
-    each on its own branch (cbl_batch_* in include/cbl.h). The simulations must outlive the batch."""
+    """Independent simulations advanced together: one CUDA graph holds one step of every instance, the
+    bulk lattice-Boltzmann pass of all instances in one persistent launch (cbl_batch_* in
+    include/cbl.h). The simulations must outlive the batch."""
 
     def __init__(self, sims, stream=None):
         self._lib = load()
@@ -378,7 +395,22 @@ class Batch:
             raise CblError(st, self._lib.cbl_last_error(None).decode())
 
     def sync(self):
-        self._lib.cbl_batch_sync(self._h)
+        st = self._lib.cbl_batch_sync(self._h)
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(None).decode())
+
+    def set_option(self, key, value):
+        st = self._lib.cbl_batch_set_option(self._h, key.encode(), float(value))
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(None).decode())
+
+    def info(self):
+        m, t, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        it = ctypes.c_longlong()
+        st = self._lib.cbl_batch_info(self._h, ctypes.byref(m), ctypes.byref(t), ctypes.byref(it), ctypes.byref(g))
+        if st != 0:
+            raise CblError(st, self._lib.cbl_last_error(None).decode())
+        return dict(mode=m.value, tile=t.value, items=it.value, grid=g.value)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -456,6 +488,22 @@ class MLP:
         self._ck(self._lib.cbl_mlp_adam_step(self._h, lr, beta1, beta2, eps), "adam_step")
 
     def sync(self):
+        self._lib.cbl_mlp_sync(self._h)
+
+    def advance(self, X, V, W, M, Iinv, R, fixed, bias, pairs, VL, steps, dims, cos_theta, norm, sigma):
+        """Bodies advanced `steps` steps under the network's pair forces on the device (cbl_mlp_advance):
+        X, V, W (nb x 3 float64), M, Iinv, R (nb float64), fixed (nb int32), bias (nb x 3 float64), pairs
+        (npairs x 2 int32), VL (npairs float64) are CUDA tensors on the network's device; X, V, W are
+        updated in place. dims (3 ints) and norm (28 floats) are host sequences."""
+        import torch
+
+        torch.cuda.current_stream().synchronize()
+        ptr = lambda t: _P(t.data_ptr()) if t is not None and t.numel() else None
+        d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+        nm = (ctypes.c_float * 28)(*[float(v) for v in norm])
+        self._ck(self._lib.cbl_mlp_advance(self._h, ptr(X), ptr(V), ptr(W), ptr(M), ptr(Iinv), ptr(R), ptr(fixed),
+                                           ptr(bias), ptr(pairs), ptr(VL), int(X.shape[0]), int(pairs.shape[0]),
+                                           int(steps), d, float(cos_theta), nm, float(sigma)), "advance")
         self._lib.cbl_mlp_sync(self._h)
 
     @property

@@ -14,6 +14,17 @@
 
 using namespace cbl;
 
+namespace cbl {
+thread_local int g_launch_share = 1;
+}
+
+// sets the share of the GPU for the launches of this host thread while in scope
+struct LaunchShare {
+  int keep;
+  explicit LaunchShare(int n) : keep(g_launch_share) { g_launch_share = n < 1 ? 1 : n; }
+  ~LaunchShare() { g_launch_share = keep; }
+};
+
 struct cbl_ctx {
   cbl_params p;
   cbl_allocator alloc;
@@ -40,8 +51,10 @@ struct cbl_ctx {
   long long arena_n = 0;
   int max_tile = 0;
   double *acc = nullptr, *last = nullptr, *volacc = nullptr, *scratch = nullptr;
+  double* fsum = nullptr;      // per body: running sums of the total force and torque (6 doubles)
+  long long fsum_steps = 0;    // steps summed into fsum since its last reset
   double* rtab = nullptr;  // per body and axis: minimum-image offsets of the tile coordinates
-  int* mbox = nullptr;     // per body: tile-coordinate box of its member cells (lo[3], hi[3])
+  int* mbox = nullptr;     // per body: member record (box lo[3], hi[3], largest squared distance; MBOX_N ints)
   int Lmax = 1;            // longest tile side
   double* mass_part = nullptr;
   unsigned n_mass_part = 0;
@@ -315,13 +328,14 @@ static cbl_status alloc_bodies(cbl_ctx* ctx) {
   ctx->acc = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
   ctx->last = (double*)dalloc(ctx, sizeof(double) * ACC_N * nb);
   ctx->volacc = (double*)dalloc(ctx, sizeof(double) * 2 * nb);
+  ctx->fsum = (double*)dalloc(ctx, sizeof(double) * 6 * nb);
   ctx->scratch = (double*)dalloc(ctx, sizeof(double) * 9 * nb);
   for (const BodyDev& b : ctx->hb)
     for (int a = 0; a < 3; ++a) ctx->Lmax = std::max(ctx->Lmax, b.L[a]);
   ctx->rtab = (double*)dalloc(ctx, sizeof(double) * 3 * (size_t)ctx->Lmax * nb);
-  ctx->mbox = (int*)dalloc(ctx, sizeof(int) * 6 * nb);
+  ctx->mbox = (int*)dalloc(ctx, sizeof(int) * MBOX_N * nb);
   ctx->blist = (int*)dalloc(ctx, sizeof(int) * (size_t)(ctx->arena_n / 3));
-  if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->scratch || !ctx->blist ||
+  if (!ctx->db || !ctx->arena || !ctx->acc || !ctx->last || !ctx->volacc || !ctx->fsum || !ctx->scratch || !ctx->blist ||
       !ctx->rtab || !ctx->mbox)
     return fail(ctx, CBL_ERR_OOM, "device allocation failed (bodies)");
   return CBL_OK;
@@ -338,6 +352,7 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
     CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * ACC_N * nb, ctx->s));
     CK(cudaMemsetAsync(ctx->last, 0, sizeof(double) * ACC_N * nb, ctx->s));
     CK(cudaMemsetAsync(ctx->volacc, 0, sizeof(double) * 2 * nb, ctx->s));
+    CK(cudaMemsetAsync(ctx->fsum, 0, sizeof(double) * 6 * nb, ctx->s));
     launch_rasterize(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->p.eta, ctx->s);
     launch_neighbour_lists(ctx->db, nb, ctx->lat, ctx->st, ctx->s);
     launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 1, ctx->st,
@@ -460,7 +475,7 @@ static void enqueue_step(cbl_ctx* ctx) {
     ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->side);
     launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->side);
-    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox,
+    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox, ctx->fsum,
                   ctx->side);
     phase_update(ctx->side);
     cudaEventRecord(ctx->ev_join, ctx->side);
@@ -476,10 +491,32 @@ static void enqueue_step(cbl_ctx* ctx) {
     if (nb) {
       launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
       launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax,
-                    ctx->mbox, ctx->s);
+                    ctx->mbox, ctx->fsum, ctx->s);
       phase_update(ctx->s);
       flags_refill(ctx->s);
     }
+  }
+  launch_finish(ctx->mass_part, ctx->n_mass_part, ctx->st, ctx->s);
+}
+
+// The part of a step that follows the bulk lattice-Boltzmann pass in a persistent batch launch: the
+// collision of the cells next to a solid, the bodies' chain, flags and refill, the step's end.
+static void enqueue_side_chain(cbl_ctx* ctx) {
+  const int nb = (int)ctx->hb.size();
+  enqueue_lbm(ctx, 4, ctx->s);
+  if (nb) {
+    ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
+                      ctx->nbuf, ctx->pp.G, ctx->s);
+    launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
+    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox, ctx->fsum,
+                  ctx->s);
+    launch_advect(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->pp.mpf, ctx->volacc, ctx->st, ctx->rtab,
+                  ctx->Lmax, ctx->s);
+    if (ctx->pp.mpf) launch_kinetics(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->volacc, ctx->pp, ctx->s);
+    launch_flags(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->flags, ctx->p.solid_threshold, 0, ctx->st,
+                 ctx->s);
+    ctx->ops.refill(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->max_tile, ctx->st, ctx->blist,
+                    ctx->arena, ctx->p.member_threshold, ctx->mbox, 1, ctx->s);
   }
   launch_finish(ctx->mass_part, ctx->n_mass_part, ctx->st, ctx->s);
 }
@@ -532,6 +569,7 @@ cbl_status cbl_step(cbl_ctx* ctx, int nsteps) {
   }
   ctx->kev_steps = nsteps;
   ctx->t += nsteps;
+  ctx->fsum_steps += nsteps;
   return CBL_OK;
 }
 
@@ -571,7 +609,7 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
     CK(cudaEventRecord(ev[3], ctx->s));
     if (nb) launch_repulsion(ctx->lat, ctx->db, nb, ctx->max_tile, ctx->arena, ctx->acc, ctx->pp, ctx->mbox, ctx->s);
     CK(cudaEventRecord(ev[4], ctx->s));
-    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox,
+    launch_bodies(ctx->lat, ctx->db, nb, ctx->acc, ctx->last, ctx->volacc, ctx->st, ctx->rtab, ctx->Lmax, ctx->mbox, ctx->fsum,
                   ctx->s);
     CK(cudaEventRecord(ev[5], ctx->s));
     if (nb)
@@ -601,6 +639,7 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
   for (int k = 0; k <= CBL_NPHASES; ++k) cudaEventDestroy(ev[k]);
   for (int k = 0; k < CBL_NPHASES; ++k) ms[k] = acc[k] / nsteps;
   ctx->t += nsteps;
+  ctx->fsum_steps += nsteps;
   return CBL_OK;
 }
 
@@ -707,6 +746,29 @@ static cbl_status unstable_check(cbl_ctx* ctx) {
   CK(cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   if (h.err & E_UNSTABLE) return fail(ctx, CBL_ERR_UNSTABLE, "a body update was not finite; the body is held");
+  return CBL_OK;
+}
+
+cbl_status cbl_read_force_mean(cbl_ctx* ctx, double* F, double* T, long long* nsteps, int reset) {
+  if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
+  if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "not initialised");
+  const int nb = (int)ctx->hb.size();
+  if (nsteps) *nsteps = ctx->fsum_steps;
+  if (!nb) return CBL_OK;
+  std::vector<double> h((size_t)6 * nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->fsum, h.size() * 8, cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  const double inv = ctx->fsum_steps ? 1.0 / (double)ctx->fsum_steps : 0.0;
+  for (int b = 0; b < nb; ++b)
+    for (int c = 0; c < 3; ++c) {
+      if (F) F[3 * b + c] = h[6 * b + c] * inv;
+      if (T) T[3 * b + c] = h[6 * b + 3 + c] * inv;
+    }
+  if (reset) {
+    CK(cudaMemsetAsync(ctx->fsum, 0, sizeof(double) * 6 * nb, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->fsum_steps = 0;
+  }
   return CBL_OK;
 }
 
@@ -884,7 +946,7 @@ cbl_status cbl_set_bodies_fixed(cbl_ctx* ctx, const int* fixed) {
 // scratch that each step rebuilds (psi, the near-solid side buffer, mass partials, offset tables)
 // is not stored.
 static const char CKPT_MAGIC[8] = {'C', 'B', 'L', 'S', 'T', 'A', 'T', 'E'};
-static const int CKPT_VERSION = 1;
+static const int CKPT_VERSION = 2;
 
 namespace {
 struct CkptHeader {
@@ -950,7 +1012,7 @@ static std::vector<Buf> ckpt_buffers(cbl_ctx* ctx) {
     v.push_back({ctx->acc, sizeof(double) * ACC_N * nb});
     v.push_back({ctx->last, sizeof(double) * ACC_N * nb});
     v.push_back({ctx->volacc, sizeof(double) * 2 * nb});
-    v.push_back({ctx->mbox, sizeof(int) * 6 * nb});
+    v.push_back({ctx->mbox, sizeof(int) * MBOX_N * nb});
     v.push_back({ctx->blist, sizeof(int) * (size_t)(ctx->arena_n / 3)});
   }
   return v;
@@ -1041,6 +1103,8 @@ cbl_status cbl_load(cbl_ctx* ctx, const char* path) {
   if (st != CBL_OK) return st;
   if (!ok) return fail(ctx, CBL_ERR_ARG, std::string(path) + " is truncated");
   CK(cudaMemsetAsync(ctx->mass_part, 0, (size_t)ctx->n_mass_part * 8, ctx->s));
+  if (nb) CK(cudaMemsetAsync(ctx->fsum, 0, sizeof(double) * 6 * nb, ctx->s));  // running sums start anew
+  ctx->fsum_steps = 0;
   CK(cudaStreamSynchronize(ctx->s));
   ctx->t = h.t;
   ctx->ready = true;
@@ -1142,11 +1206,31 @@ struct cbl_batch {
   bool own_stream = false;
   cudaGraph_t graph[2] = {nullptr, nullptr};      // [0] no field record, [1] record fields
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // persistent mode: one launch of the bulk lattice-Boltzmann pass over every instance, then the
+  // instances' side chains on their branches
+  int mode = 0;        // 0: one fork/join branch with the whole step per instance; 1: persistent
+  int tile_cfg = 1;    // tile shape of the persistent kernel (batch_tile)
+  int cooperative = 1;
+  int grid = 0;
+  long long items = 0;
+  long long spin_limit = 4000000000LL;  // clock64 cycles a block may wait at the grid barrier (~2 s)
+  BatchInst* tab = nullptr;
+  BatchCtl* ctl = nullptr;
 };
 
 static cudaError_t batch_capture(cbl_batch* b, int diag, cudaGraph_t* g) {
   cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
+  // the instances' kernels run side by side: each sizes its device-sized grids for its share
+  LaunchShare share((int)std::min<size_t>(b->ctxs.size(), 64));
+  cudaError_t el = cudaSuccess;
+  if (b->mode == 1) {
+    cbl_ctx* c0 = b->ctxs[0];
+    for (cbl_ctx* c : b->ctxs) cudaMemsetAsync(&c->st->diag, diag, sizeof(int), b->s);
+    cudaMemsetAsync(b->ctl, 0, BATCH_CTL_RESET_BYTES, b->s);
+    el = c0->ops.batch_lbm(c0->prec, b->tile_cfg, b->tab, (int)b->ctxs.size(), b->items, b->ctl, b->grid,
+                           b->cooperative, b->s);
+  }
   cudaEventRecord(b->events[0], b->s);
   for (size_t k = 0; k < b->ctxs.size(); ++k) {
     cbl_ctx* c = b->ctxs[k];
@@ -1154,15 +1238,84 @@ static cudaError_t batch_capture(cbl_batch* b, int diag, cudaGraph_t* g) {
     cudaStreamWaitEvent(br, b->events[0], 0);
     cudaStream_t keep = c->s;
     c->s = br;
-    cudaMemsetAsync(&c->st->diag, diag, sizeof(int), br);
-    enqueue_step(c);
+    if (b->mode == 1) {
+      enqueue_side_chain(c);
+    } else {
+      cudaMemsetAsync(&c->st->diag, diag, sizeof(int), br);
+      enqueue_step(c);
+    }
     c->s = keep;
     cudaEventRecord(b->events[k + 1], br);
     cudaStreamWaitEvent(b->s, b->events[k + 1], 0);
   }
   cudaError_t e1 = cudaGetLastError();
   cudaError_t e2 = cudaStreamEndCapture(b->s, g);
+  if (el != cudaSuccess) return el;
   return e1 != cudaSuccess ? e1 : e2;
+}
+
+static void batch_drop_graphs(cbl_batch* b) {
+  for (int d = 0; d < 2; ++d) {
+    if (b->gexec[d]) cudaGraphExecDestroy(b->gexec[d]);
+    if (b->graph[d]) cudaGraphDestroy(b->graph[d]);
+    b->gexec[d] = nullptr;
+    b->graph[d] = nullptr;
+  }
+}
+
+// (re)build the instance table and both step graphs for the batch's mode and tile shape
+static cudaError_t batch_build(cbl_batch* b) {
+  batch_drop_graphs(b);
+  if (b->mode == 1) {
+    cbl_ctx* c0 = b->ctxs[0];
+    int t[3];
+    c0->ops.batch_tile(b->tile_cfg, t);
+    std::vector<BatchInst> h(b->ctxs.size());
+    long long items = 0;
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+      const cbl_ctx* c = b->ctxs[k];
+      BatchInst& I = h[k];
+      std::memset(&I, 0, sizeof(I));
+      I.lat = c->lat;
+      I.fa = c->fa;
+      I.fb = c->fb;
+      I.psi = c->psi;
+      I.flags = c->flags;
+      I.bodies = c->db;
+      I.mass_part = c->mass_part;
+      I.st = c->st;
+      I.diag_rho = c->diag_rho;
+      I.diag_vel = c->diag_vel;
+      I.pp = c->pp;
+      const int n[3] = {c->lat.nx, c->lat.ny, c->lat.nz};
+      for (int a = 0; a < 3; ++a) I.tiles[a] = (n[a] + t[a] - 1) / t[a];
+      I.item0 = items;
+      items += (long long)I.tiles[0] * I.tiles[1] * I.tiles[2];
+    }
+    b->items = items;
+    cudaError_t e = cudaMemcpy(b->tab, h.data(), sizeof(BatchInst) * h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = c0->ops.batch_blocks_per_sm(c0->prec, b->tile_cfg) * sms;
+    if (b->grid <= 0) return cudaErrorInvalidConfiguration;
+    BatchCtl ctl;
+    std::memset(&ctl, 0, sizeof(ctl));
+    ctl.spin_limit = b->spin_limit;
+    e = cudaMemcpy(b->ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  for (int d = 0; d < 2; ++d) {
+    cudaError_t e = batch_capture(b, d, &b->graph[d]);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[d], b->graph[d], cudaGraphInstantiateFlagUseNodePriority);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      batch_drop_graphs(b);
+      return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch** out) {
@@ -1175,6 +1328,11 @@ cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch
   }
   cbl_batch* b = new cbl_batch();
   b->ctxs.assign(ctxs, ctxs + n);
+  // the persistent launch serves instances of one precision and velocity set on the split pass
+  bool uniform = true;
+  for (int k = 0; k < n; ++k)
+    uniform &= ctxs[k]->prec == ctxs[0]->prec && ctxs[k]->ops.q == ctxs[0]->ops.q && ctxs[k]->fused_tz == 0;
+  b->mode = uniform ? 1 : 0;
   if (stream) {
     b->s = (cudaStream_t)stream;
   } else {
@@ -1189,9 +1347,15 @@ cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch
   bool ok = true;
   for (int k = 0; k < n; ++k) ok &= cudaStreamCreateWithFlags(&b->branches[k], cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k <= n; ++k) ok &= cudaEventCreateWithFlags(&b->events[k], cudaEventDisableTiming) == cudaSuccess;
-  for (int d = 0; d < 2 && ok; ++d) {
-    ok &= batch_capture(b, d, &b->graph[d]) == cudaSuccess;
-    ok &= ok && cudaGraphInstantiate(&b->gexec[d], b->graph[d], cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
+  ok &= cudaMalloc(&b->tab, sizeof(BatchInst) * n) == cudaSuccess;
+  ok &= cudaMalloc(&b->ctl, sizeof(BatchCtl)) == cudaSuccess;
+  if (ok && batch_build(b) != cudaSuccess && b->mode == 1) {
+    // a cooperative kernel that cannot be captured: the same launch, plain (the grid is sized to be
+    // resident, and the barrier's wait is bounded either way)
+    b->cooperative = 0;
+    ok = batch_build(b) == cudaSuccess;
+  } else if (ok) {
+    ok = b->gexec[0] != nullptr;
   }
   if (!ok) {
     cudaGetLastError();
@@ -1202,32 +1366,80 @@ cbl_status cbl_batch_create(cbl_ctx* const* ctxs, int n, void* stream, cbl_batch
   return CBL_OK;
 }
 
+cbl_status cbl_batch_set_option(cbl_batch* b, const char* key, double value) {
+  if (!b || !key) return fail(nullptr, CBL_ERR_ARG, "NULL argument");
+  const std::string k(key);
+  const int v = (int)value;
+  if (cudaStreamSynchronize(b->s) != cudaSuccess) return fail(nullptr, CBL_ERR_CUDA, "sync");
+  if (k == "mode") {
+    if (v != 0 && v != 1) return fail(nullptr, CBL_ERR_ARG, "mode must be 0 or 1");
+    if (v == 1) {
+      for (cbl_ctx* c : b->ctxs)
+        if (c->prec != b->ctxs[0]->prec || c->ops.q != b->ctxs[0]->ops.q || c->fused_tz)
+          return fail(nullptr, CBL_ERR_UNSUPPORTED, "persistent mode needs one precision and velocity set, split pass");
+    }
+    b->mode = v;
+  } else if (k == "tile") {
+    if (v < 0 || v >= BATCH_TILE_CFGS) return fail(nullptr, CBL_ERR_ARG, "tile must be 0..3");
+    b->tile_cfg = v;
+  } else if (k == "spin_limit") {
+    if (!(value >= 0)) return fail(nullptr, CBL_ERR_ARG, "spin_limit must be >= 0");
+    b->spin_limit = (long long)value;
+  } else {
+    return fail(nullptr, CBL_ERR_ARG, "unknown batch option " + k);
+  }
+  if (batch_build(b) != cudaSuccess) return fail(nullptr, CBL_ERR_CUDA, "batch graph capture failed");
+  return CBL_OK;
+}
+
+cbl_status cbl_batch_info(cbl_batch* b, int* mode, int* tile, long long* items, int* grid) {
+  if (!b) return fail(nullptr, CBL_ERR_ARG, "NULL batch");
+  if (mode) *mode = b->mode;
+  if (tile) *tile = b->tile_cfg;
+  if (items) *items = b->items;
+  if (grid) *grid = b->grid;
+  return CBL_OK;
+}
+
 cbl_status cbl_batch_step(cbl_batch* b, int nsteps) {
   if (!b) return fail(nullptr, CBL_ERR_ARG, "NULL batch");
   if (nsteps < 0) return fail(nullptr, CBL_ERR_ARG, "nsteps must be >= 0");
   for (int k = 0; k < nsteps; ++k)
     if (cudaGraphLaunch(b->gexec[k == nsteps - 1 ? 1 : 0], b->s) != cudaSuccess)
       return fail(nullptr, CBL_ERR_CUDA, "batch graph launch failed");
-  for (cbl_ctx* c : b->ctxs) c->t += nsteps;
+  for (cbl_ctx* c : b->ctxs) {
+    c->t += nsteps;
+    c->fsum_steps += nsteps;
+  }
   return CBL_OK;
 }
 
 cbl_status cbl_batch_sync(cbl_batch* b) {
   if (!b) return fail(nullptr, CBL_ERR_ARG, "NULL batch");
-  return cudaStreamSynchronize(b->s) == cudaSuccess ? CBL_OK : fail(nullptr, CBL_ERR_CUDA, "sync");
+  if (cudaStreamSynchronize(b->s) != cudaSuccess) return fail(nullptr, CBL_ERR_CUDA, "sync");
+  if (b->mode == 1) {
+    int err = 0;
+    if (cudaMemcpy(&err, &b->ctl->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(nullptr, CBL_ERR_CUDA, "sync");
+    if (err) {
+      const int zero = 0;
+      cudaMemcpy(&b->ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return fail(nullptr, CBL_ERR_TIMEOUT, "a grid-barrier wait of the persistent batch kernel ran out");
+    }
+  }
+  return CBL_OK;
 }
 
 cbl_status cbl_batch_destroy(cbl_batch* b) {
   if (!b) return CBL_OK;
   if (b->s) cudaStreamSynchronize(b->s);
-  for (int d = 0; d < 2; ++d) {
-    if (b->gexec[d]) cudaGraphExecDestroy(b->gexec[d]);
-    if (b->graph[d]) cudaGraphDestroy(b->graph[d]);
-  }
+  batch_drop_graphs(b);
   for (cudaStream_t br : b->branches)
     if (br) cudaStreamDestroy(br);
   for (cudaEvent_t e : b->events)
     if (e) cudaEventDestroy(e);
+  if (b->tab) cudaFree(b->tab);
+  if (b->ctl) cudaFree(b->ctl);
   if (b->own_stream) cudaStreamDestroy(b->s);
   delete b;
   return CBL_OK;

@@ -66,6 +66,11 @@ constexpr uint16_t F_OWNER = 0x1FFF;
 constexpr int MAX_BODIES = 0x1FFF;
 constexpr uint16_t F_STALE = 0x1FFF;  // owner id of a cell solid before a body move (never a body)
 constexpr int MAXNB = 24;  // neighbour-list capacity per body (tiles that overlap)
+// Per-body member record (rebuilt by the refill pass from the cells with phi >= the membership
+// threshold): tile-coordinate box lo[3], hi[3], then the bit pattern of the largest squared distance
+// of a member cell from the body's centre X (a non-negative float: its bits order like the value),
+// and one unused word.
+constexpr int MBOX_N = 8, MBOX_R2 = 6;
 
 // Fluid-mass accumulation slots written by the collision kernel and summed by the body kernel.
 constexpr int MASS_SLOTS = 256;
@@ -167,6 +172,45 @@ __device__ __forceinline__ long long dbits(double v) { return __double_as_longlo
 
 // wrapi, mimg, wrapd: periodic wraps with a fixed operation count (periodic.h)
 
+// ---- batches of independent lattices -----------------------------------------------------------
+// One instance of a batch, as the persistent lattice-Boltzmann kernel sees it (a device-resident
+// table, one entry per instance): its lattice and buffers, and where its work items start. A work
+// item is one tile of TX x TY x TZ cells of one instance; the items of all instances are numbered
+// one after the other, instance by instance.
+struct BatchInst {
+  Lat lat;
+  void *fa, *fb, *psi;
+  const uint16_t* flags;
+  const BodyDev* bodies;
+  double* mass_part;
+  StepState* st;
+  double *diag_rho, *diag_vel;
+  PhysParams pp;
+  int tiles[3];    // tiles per axis
+  int pad;
+  long long item0;  // first work item of this instance
+};
+
+// Control block of the persistent kernel. queue[p]: next work item of phase p; arrive / gen: the
+// grid barrier between the phases (arrivals of this generation, generation count); spin_limit: the
+// longest a block waits at the barrier, in clock64 cycles, before it sets err bit 0 and returns.
+// The first 20 bytes (queues and arrivals) are cleared before every launch.
+struct BatchCtl {
+  unsigned long long queue[2];
+  unsigned arrive, gen;
+  long long spin_limit;
+  int err, pad;
+};
+constexpr size_t BATCH_CTL_RESET_BYTES = 2 * sizeof(unsigned long long) + sizeof(unsigned);
+constexpr int BATCH_TILE_CFGS = 4;  // tile shapes of the persistent kernel (see batch_tile)
+
+// Share of the GPU that the kernels launched by this host thread may assume (1 = all of it). The
+// grid-stride kernels whose work is only known on the device (the collision of the cells next to a
+// solid, the solid-fluid force pass, the repulsion) size their grids for a few waves of the whole
+// GPU; a batch that runs n instances side by side sets n while it captures their steps, so that the
+// n copies together fill the GPU instead of each filling it (capi.cu: LaunchShare).
+extern thread_local int g_launch_share;
+
 // ---- kernel launchers (defined in lbm.cu / lbm27.cu per velocity set, and phase.cu) ------------
 // Populations live in two buffers fa, fb; StepState::parity selects the current state
 // (0: fa, 1: fb). The step reads the current buffer, writes the other, and the closing kernel flips
@@ -200,7 +244,11 @@ __device__ __forceinline__ long long dbits(double v) { return __double_as_longlo
                          const double* u, cudaStream_t s);                                            \
   void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags, const BodyDev* bodies, \
                      int nb, int max_tile, StepState* st, int* blist, const double* arena,           \
-                     double member_thr, int* mbox, int next, cudaStream_t s);
+                     double member_thr, int* mbox, int next, cudaStream_t s);                        \
+  void batch_tile(int cfg, int* t);                                                                   \
+  int batch_blocks_per_sm(int prec, int cfg);                                                         \
+  cudaError_t launch_batch_lbm(int prec, int cfg, const BatchInst* tab, int ninst, long long items,  \
+                               BatchCtl* ctl, int grid, int cooperative, cudaStream_t s);
 namespace q19 {
 CBL_LBM_LAUNCHERS
 }
@@ -221,12 +269,16 @@ struct LbmOps {
   decltype(&q19::launch_zero_solid) zero_solid;
   decltype(&q19::launch_init_fluid) init_fluid;
   decltype(&q19::launch_refill) refill;
+  decltype(&q19::batch_tile) batch_tile;
+  decltype(&q19::batch_blocks_per_sm) batch_blocks_per_sm;
+  decltype(&q19::launch_batch_lbm) batch_lbm;
 };
 inline LbmOps lbm_ops(int q) {
 #define CBL_OPS(ns) \
   LbmOps { q, &ns::set_fp16_weights, &ns::launch_lbm_step, &ns::fused_tz, &ns::launch_lbm_fused,                   \
            &ns::launch_density_tiles, &ns::launch_boundary,                                                             \
-           &ns::launch_read_populations, &ns::launch_zero_solid, &ns::launch_init_fluid, &ns::launch_refill }
+           &ns::launch_read_populations, &ns::launch_zero_solid, &ns::launch_init_fluid, &ns::launch_refill,        \
+           &ns::batch_tile, &ns::batch_blocks_per_sm, &ns::launch_batch_lbm }
   return q == 27 ? CBL_OPS(q27) : CBL_OPS(q19);
 #undef CBL_OPS
 }
@@ -245,7 +297,7 @@ void launch_body_props(const Lat& lat, BodyDev* bodies, int nb, int max_tile, do
 void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, const double* arena, double* acc,
                       const PhysParams& pp, const int* mbox, cudaStream_t s);
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   StepState* st, double* rtab, int Lmax, int* mbox, cudaStream_t s);
+                   StepState* st, double* rtab, int Lmax, int* mbox, double* fsum, cudaStream_t s);
 void launch_finish(double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s);
 void launch_advect(const Lat& lat, const BodyDev* bodies, int nb, int max_tile, double* arena, int mpf, double* volacc,
                    StepState* st, const double* rtab, int Lmax, cudaStream_t s);

@@ -22,6 +22,7 @@
 // This file is compiled once per velocity set: as itself for D3Q19 (namespace cbl::q19) and through
 // lbm27.cu with CBL_Q = 27 (namespace cbl::q27). The no-allocation entry point exists for D3Q19
 // only.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include "../../include/cbl.h"
@@ -314,14 +315,18 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
   {
     // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
     // it needs only psi, so the populations are not yet live
+    // The sum over directions is taken over opposite pairs (c_opp = -c_i, equal weights), as sums of
+    // differences psi(x + c_i) - psi(x - c_i): the same value, but its rounding scales with the small
+    // differences of psi across a cell, not with psi itself (in the bulk of a phase the terms cancel,
+    // and summing them one by one in FP32 would leave a rounding residue of ~1e-7 psi as a force).
     const R ps = psi_at(0);
     R sx = 0, sy = 0, sz = 0;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const R wp = (R)w_of(i) * psi_at(i);
-      if (cx_of(i)) sx += wp * (R)cx_of(i);
-      if (cy_of(i)) sy += wp * (R)cy_of(i);
-      if (cz_of(i)) sz += wp * (R)cz_of(i);
+    for (int i = 1; i < Q; i += 2) {
+      const R wd = (R)w_of(i) * (psi_at(i) - psi_at(i + 1));
+      if (cx_of(i)) sx += wd * (R)cx_of(i);
+      if (cy_of(i)) sy += wd * (R)cy_of(i);
+      if (cz_of(i)) sz += wd * (R)cz_of(i);
     }
     const R mG = -par<R>(pp.G, pp.G_f) * ps;
     const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
@@ -347,13 +352,16 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
       }
       fi[0] += drho;
     }
-    // velocity with the half-force shift, Eq. fluid_velocity
+    // velocity with the half-force shift, Eq. fluid_velocity; the momentum, like the force, summed
+    // over opposite pairs as f_i - f_opp(i) (rounding of the order of the differences, not of the
+    // populations, which matters at the small velocities of these flows)
     R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (cx_of(i)) mx += (R)cx_of(i) * fi[i];
-      if (cy_of(i)) my += (R)cy_of(i) * fi[i];
-      if (cz_of(i)) mz += (R)cz_of(i) * fi[i];
+    for (int i = 1; i < Q; i += 2) {
+      const R d = fi[i] - fi[i + 1];
+      if (cx_of(i)) mx += (R)cx_of(i) * d;
+      if (cy_of(i)) my += (R)cy_of(i) * d;
+      if (cz_of(i)) mz += (R)cz_of(i) * d;
     }
     R vx = 0, vy = 0, vz = 0;
     if (rho > (R)0) {
@@ -738,6 +746,113 @@ struct LinkSum<double> {
   __device__ double value() const { return v; }
 };
 
+// ---- persistent lattice-Boltzmann pass over a batch of lattices ---------------------------------
+// One launch for every instance of a batch: the grid is as large as the GPU holds at once (every
+// block resident), and each block takes work items (one tile of TX x TY x TZ cells of one instance)
+// from a device queue until none are left. Phase 0 computes psi of every cell of every instance (as
+// k_density); a grid barrier follows, since a cell's force needs psi of cells that other blocks
+// computed; phase 1 collides every cell without a solid neighbour (as k_collide). The barrier's wait
+// is bounded: a block that has waited spin_limit cycles sets err bit 0 and returns, and so does every
+// block once err is set, so an incomplete barrier ends the launch instead of hanging it.
+__device__ __forceinline__ bool grid_barrier(BatchCtl* ctl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &ctl->gen;
+    const unsigned gen = *vgen;  // read before arriving: the last arrival needs this block's
+    __threadfence();
+    if (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1) {
+      atomicExch(&ctl->arrive, 0u);
+      __threadfence();
+      atomicAdd(&ctl->gen, 1u);
+    } else {
+      const long long t0 = clock64(), limit = ctl->spin_limit;
+      while (*vgen == gen) {
+        if (clock64() - t0 > limit) {
+          atomicOr(&ctl->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)&ctl->err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename S, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY, CollideMinBlocks<S>::value)
+    k_batch_lbm(const BatchInst* __restrict__ tab, int ninst, long long items, BatchCtl* ctl) {
+  using R = typename St<S>::R;
+  __shared__ long long s_item;
+  for (int phase = 0; phase < 2; ++phase) {
+    if (phase == 1 && !grid_barrier(ctl)) return;
+    for (;;) {
+      if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctl->queue[phase], 1ull);
+      __syncthreads();
+      const long long item = s_item;
+      __syncthreads();  // s_item is written again in the next round
+      if (item >= items) break;
+      // the instance whose items contain this one (item0 ascends with the instance index)
+      int lo = 0, hi = ninst - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].item0 <= item) lo = mid;
+        else hi = mid - 1;
+      }
+      const BatchInst& I = tab[lo];
+      const Lat lat = I.lat;
+      const long long k = item - I.item0;
+      const int bx = (int)(k % I.tiles[0]), by = (int)((k / I.tiles[0]) % I.tiles[1]),
+                bz = (int)(k / ((long long)I.tiles[0] * I.tiles[1]));
+      const int x = bx * TX + (int)(threadIdx.x % TX), y = by * TY + (int)(threadIdx.x / TX);
+      const bool valid = x < lat.nx && y < lat.ny;
+      const StepState* st = I.st;
+      const S* __restrict__ src = (const S*)(st->parity ? I.fb : I.fa);
+      R* __restrict__ psi = (R*)I.psi;
+      const int z0 = bz * TZ, z1 = min(z0 + TZ, lat.nz);
+      if (phase == 0) {
+        if (valid)
+          for (int z = z0; z < z1; ++z) {
+            const Cell c = make_cell(x, y, z, lat);
+            psi[c.n] = psi_of_cell<S>(src, I.flags, I.bodies, lat, c, I.pp.rho0, I.pp.rho0_f);
+          }
+      } else {
+        S* __restrict__ dst = (S*)(st->parity ? I.fa : I.fb);
+        const int diag = st->diag;
+        const size_t N = (size_t)lat.Ns;
+        MassAcc<R> mass;
+        if (valid)
+          for (int z = z0; z < z1; ++z) {
+            const Cell c = make_cell(x, y, z, lat);
+            const long long n = c.n;
+            const uint16_t fl = I.flags[n];
+            if (fl & F_SOLID) {
+#pragma unroll
+              for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
+              if (diag) {
+                I.diag_rho[n] = 0.0;
+                I.diag_vel[3 * n] = 0.0;
+                I.diag_vel[3 * n + 1] = 0.0;
+                I.diag_vel[3 * n + 2] = 0.0;
+              }
+            } else if (!(fl & F_NEAR)) {
+              auto psi_at = [&](int i) -> R { return i ? psi[nbr(c, lat, i, +1)] : psi[n]; };
+              mass.add(collide_fluid<S, false>(src, dst, I.flags, psi_at, I.bodies, diag, I.diag_rho, I.diag_vel, lat,
+                                               I.pp, nullptr, c, n));
+            }
+          }
+        add_mass_slot(I.mass_part, mass, (unsigned)k);
+      }
+    }
+  }
+}
+
 // ---- solid-fluid force on the bodies ---------------------------------------------------------
 // For each listed fluid cell x: for a solid upstream neighbour s = x - c_i (owner B), momentum
 // exchange -c_i (2 f*_opp(i)(x) + g_i) with the arm at the link midpoint (Eq. solid_liquid_force);
@@ -919,6 +1034,7 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
   // repulsion pass of the next step
   bool member = false;
   int mi[3] = {0, 0, 0};
+  float r2 = 0.0f;  // squared distance of a member cell from the body's centre
   if (t < b.sz) {
     const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];  // tiles hold < 2^31 cells
     const unsigned r = u / L0;
@@ -929,6 +1045,13 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
     mi[2] = i2;
     const int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
     m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
+    if (member) {
+      // in float from the float mirror of X (FP64 is 1/64 rate here and this is a bound with slack);
+      // tile cells lie within half a lattice length of X along each axis, so one wrap suffices
+      const float dx = mimg1<float>((float)gx - b.Xf[0], lat.nx), dy = mimg1<float>((float)gy - b.Xf[1], lat.ny),
+                  dz = mimg1<float>((float)gz - b.Xf[2], lat.nz);
+      r2 = dx * dx + dy * dy + dz * dz;
+    }
     if (!(b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat))) {
       const Cell c = cell_of(m, lat);
       const uint16_t fm = flags[m];
@@ -1023,8 +1146,8 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
   }
   // warp, then block, then one set of global atomics per block (all warps of a block hit the same
   // six words, so per-warp global atomics would queue up)
-  __shared__ int sbox[6];
-  if (threadIdx.x < 6) sbox[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
+  __shared__ int sbox[7];
+  if (threadIdx.x < 7) sbox[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : (threadIdx.x < 6 ? INT_MIN : 0);
   __syncthreads();
   if (__ballot_sync(0xffffffffu, member)) {
     const int lane = threadIdx.x & 31;
@@ -1037,11 +1160,14 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
         atomicMax(sbox + 3 + a, hi);
       }
     }
+    // non-negative floats order like their bit patterns
+    const unsigned rb = __reduce_max_sync(0xffffffffu, member ? __float_as_uint(r2) : 0u);
+    if (lane == 0) atomicMax(sbox + 6, (int)rb);
   }
   __syncthreads();
-  if (threadIdx.x < 6 && sbox[0] <= sbox[3]) {
-    if (threadIdx.x < 3) atomicMin(mbox + 6 * self + threadIdx.x, sbox[threadIdx.x]);
-    else atomicMax(mbox + 6 * self + threadIdx.x, sbox[threadIdx.x]);
+  if (threadIdx.x < 7 && sbox[0] <= sbox[3]) {
+    if (threadIdx.x < 3) atomicMin(mbox + MBOX_N * self + threadIdx.x, sbox[threadIdx.x]);
+    else atomicMax(mbox + MBOX_N * self + threadIdx.x, sbox[threadIdx.x]);
   }
   // warp-aggregated append to the boundary list
   const unsigned mask = __ballot_sync(0xffffffffu, boundary);
@@ -1194,7 +1320,7 @@ static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void
     k_collide<S><<<grid, blk, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel, lat,
                                       pp, (RhoPsi<R>*)nbuf);
   if ((phases & 4) && blist)
-    k_collide_near<S><<<2 * sm_count(), 128, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho,
+    k_collide_near<S><<<std::max(1, 2 * sm_count() / g_launch_share), 128, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho,
                                                       diag_vel, blist, lat, pp, (RhoPsi<R>*)nbuf);
 }
 
@@ -1219,7 +1345,7 @@ static void boundary_t(const Lat& lat, const S* fa, const S* fb, const uint16_t*
                        cudaStream_t s) {
   using R = typename St<S>::R;
   // whole-lattice grid-stride rounds; the list length is only known on the device
-  k_boundary<S><<<8 * sm_count(), 256, 0, s>>>(fa, fb, flags, bodies, acc, blist, st, (const RhoPsi<R>*)nbuf, lat, G,
+  k_boundary<S><<<std::max(2, 8 * sm_count() / g_launch_share), 256, 0, s>>>(fa, fb, flags, bodies, acc, blist, st, (const RhoPsi<R>*)nbuf, lat, G,
                                                 (float)G);
 }
 
@@ -1259,6 +1385,68 @@ void launch_refill(int prec, const Lat& lat, void* fa, void* fb, uint16_t* flags
   else
     k_refill<__half><<<grid, T, 0, s>>>((__half*)fa, (__half*)fb, flags, bodies, st, blist, lat, arena, member_thr,
                                         mbox, next);
+}
+
+// Tile shapes of the persistent batch kernel (x, y, z cells; 128 threads per block).
+void batch_tile(int cfg, int* t) {
+  static const int T[BATCH_TILE_CFGS][3] = {{32, 4, 1}, {32, 4, 4}, {32, 4, 8}, {64, 2, 4}};
+  const int k = cfg < 0 || cfg >= BATCH_TILE_CFGS ? 1 : cfg;
+  for (int a = 0; a < 3; ++a) t[a] = T[k][a];
+}
+
+template <typename S, int TX, int TY, int TZ>
+static int batch_occ() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_lbm<S, TX, TY, TZ>, TX * TY, 0);
+  return nb;
+}
+
+template <typename S>
+static int batch_occ_cfg(int cfg) {
+  switch (cfg) {
+    case 0: return batch_occ<S, 32, 4, 1>();
+    case 2: return batch_occ<S, 32, 4, 8>();
+    case 3: return batch_occ<S, 64, 2, 4>();
+    default: return batch_occ<S, 32, 4, 4>();
+  }
+}
+
+int batch_blocks_per_sm(int prec, int cfg) {
+  return prec == 0 ? batch_occ_cfg<double>(cfg) : (prec == 1 ? batch_occ_cfg<float>(cfg) : batch_occ_cfg<__half>(cfg));
+}
+
+template <typename S, int TX, int TY, int TZ>
+static cudaError_t batch_launch(const BatchInst* tab, int ninst, long long items, BatchCtl* ctl, int grid, int coop,
+                                cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(TX * TY);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = coop ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_batch_lbm<S, TX, TY, TZ>, tab, ninst, items, ctl);
+}
+
+template <typename S>
+static cudaError_t batch_launch_cfg(int cfg, const BatchInst* tab, int ninst, long long items, BatchCtl* ctl, int grid,
+                                    int coop, cudaStream_t s) {
+  switch (cfg) {
+    case 0: return batch_launch<S, 32, 4, 1>(tab, ninst, items, ctl, grid, coop, s);
+    case 2: return batch_launch<S, 32, 4, 8>(tab, ninst, items, ctl, grid, coop, s);
+    case 3: return batch_launch<S, 64, 2, 4>(tab, ninst, items, ctl, grid, coop, s);
+    default: return batch_launch<S, 32, 4, 4>(tab, ninst, items, ctl, grid, coop, s);
+  }
+}
+
+cudaError_t launch_batch_lbm(int prec, int cfg, const BatchInst* tab, int ninst, long long items, BatchCtl* ctl,
+                             int grid, int cooperative, cudaStream_t s) {
+  if (prec == 0) return batch_launch_cfg<double>(cfg, tab, ninst, items, ctl, grid, cooperative, s);
+  if (prec == 1) return batch_launch_cfg<float>(cfg, tab, ninst, items, ctl, grid, cooperative, s);
+  return batch_launch_cfg<__half>(cfg, tab, ninst, items, ctl, grid, cooperative, s);
 }
 
 }  // namespace q19 / q27

@@ -197,6 +197,85 @@ __global__ void k_round_bf16(const float* __restrict__ w, __nv_bfloat16* __restr
 
 }  // namespace
 
+// ---- bodies advanced by the network's pair forces (the surrogate window, on the device) ----------
+// One block runs `steps` semi-implicit Euler steps of nb rigid spheres under the network's forces and
+// torques of the bridged pairs plus a fixed per-body bias force, with the fluid frozen. Per step,
+// one thread per (pair, side) forms the pair's features in its frame (e_z from the body to its
+// partner, minimum image), standardises them (clipped to the training range), runs the network with
+// the weights in shared memory, and adds the de-standardised force and torque, turned back to the
+// lattice frame, to its body; then one thread per free body updates V, X (periodic) and omega.
+// Features and targets are those of the host-side surrogate: gap s sqrt(R*/V_L), cos(theta),
+// R_i/R_j, V_L/R*^3; force over 2 pi R* sigma and torque over 2 pi R*^2 sigma, R* = 2 R_i R_j/(R_i+R_j).
+struct AdvNorm {
+  float xm[IN], xs[IN], xlo[IN], xhi[IN], ym[OUT], ys[OUT];
+};
+
+__device__ __forceinline__ double mimg_adv(double d, double n) { return d - n * rint(d / n); }
+
+__global__ void __launch_bounds__(256) k_mlp_advance(const __nv_bfloat16* __restrict__ wg, double* __restrict__ X,
+                                                     double* __restrict__ V, double* __restrict__ Wang,
+                                                     const double* __restrict__ M, const double* __restrict__ Iinv,
+                                                     const double* __restrict__ R, const int* __restrict__ fixed,
+                                                     const double* __restrict__ bias, const int* __restrict__ pairs,
+                                                     const double* __restrict__ VL, int nb, int npairs, int steps,
+                                                     int nx, int ny, int nz, double cth, AdvNorm nm, double sigma) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(raw);
+  double* F = reinterpret_cast<double*>(raw + ((NPARAM * sizeof(__nv_bfloat16) + 15) / 16) * 16);
+  double* T = F + 3 * nb;
+  load_weights(wg, w);
+  const double dims[3] = {(double)nx, (double)ny, (double)nz};
+  for (int it = 0; it < steps; ++it) {
+    for (int k = threadIdx.x; k < 3 * nb; k += blockDim.x) F[k] = T[k] = 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * npairs; k += blockDim.x) {
+      const int p = k >> 1, a = pairs[2 * p + (k & 1)], b = pairs[2 * p + 1 - (k & 1)];
+      double d[3], r = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        d[c] = mimg_adv(X[3 * b + c] - X[3 * a + c], dims[c]);
+        r += d[c] * d[c];
+      }
+      r = sqrt(r);
+      double ez[3] = {d[0] / r, d[1] / r, d[2] / r};
+      const double ref[3] = {fabs(ez[0]) < 0.9 ? 1.0 : 0.0, fabs(ez[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+      double ex[3] = {ref[1] * ez[2] - ref[2] * ez[1], ref[2] * ez[0] - ref[0] * ez[2], ref[0] * ez[1] - ref[1] * ez[0]};
+      const double en = sqrt(ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2]);
+      for (int c = 0; c < 3; ++c) ex[c] /= en;
+      const double ey[3] = {ez[1] * ex[2] - ez[2] * ex[1], ez[2] * ex[0] - ez[0] * ex[2], ez[0] * ex[1] - ez[1] * ex[0]};
+      const double Ra = R[a], Rb = R[b], Rs = 2.0 * Ra * Rb / (Ra + Rb), vl = VL[p];
+      const double feat[IN] = {(r - Ra - Rb) * sqrt(Rs / vl), cth, Ra / Rb, vl / (Rs * Rs * Rs)};
+      float xi[IN], yo[OUT];
+      for (int i = 0; i < IN; ++i) {
+        const float v = fminf(fmaxf((float)feat[i], nm.xlo[i]), nm.xhi[i]);
+        xi[i] = (v - nm.xm[i]) / nm.xs[i];
+      }
+      fwd_one<false>(w, xi, yo, nullptr, nullptr, nullptr);
+      const double sc = 2.0 * 3.14159265358979323846 * Rs * sigma;
+      double fl[3], tl[3];
+      for (int c = 0; c < 3; ++c) {
+        fl[c] = (double)(yo[c] * nm.ys[c] + nm.ym[c]) * sc;
+        tl[c] = (double)(yo[3 + c] * nm.ys[3 + c] + nm.ym[3 + c]) * sc * Rs;
+      }
+      for (int c = 0; c < 3; ++c) {  // frame rows ex, ey, ez: world = frame^T local
+        atomicAdd(&F[3 * a + c], ex[c] * fl[0] + ey[c] * fl[1] + ez[c] * fl[2]);
+        atomicAdd(&T[3 * a + c], ex[c] * tl[0] + ey[c] * tl[1] + ez[c] * tl[2]);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      if (fixed[i]) continue;
+      for (int c = 0; c < 3; ++c) {
+        V[3 * i + c] += (F[3 * i + c] + bias[3 * i + c]) / M[i];
+        double x = X[3 * i + c] + V[3 * i + c];
+        x -= dims[c] * floor(x / dims[c]);
+        X[3 * i + c] = x;
+        Wang[3 * i + c] += T[3 * i + c] * Iinv[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 struct cbl_mlp {
   cudaStream_t s = nullptr;
   bool own = false;
@@ -264,6 +343,31 @@ cbl_status cbl_mlp_forward(cbl_mlp* m, const float* x, float* y, int n) {
   if (!m || !x || !y || n < 0) return CBL_ERR_ARG;
   if (n == 0) return CBL_OK;
   k_mlp_fwd<<<(n + 127) / 128, 128, 0, m->s>>>(m->wb, x, y, n);
+  return cudaGetLastError() == cudaSuccess ? CBL_OK : CBL_ERR_CUDA;
+}
+
+cbl_status cbl_mlp_advance(cbl_mlp* m, double* X, double* V, double* Wang, const double* M, const double* Iinv,
+                           const double* R, const int* fixed, const double* bias, const int* pairs, const double* VL,
+                           int nb, int npairs, int steps, const int* dims, double cos_theta, const float* norm,
+                           double sigma) {
+  if (!m || !X || !V || !Wang || !M || !Iinv || !R || !fixed || !bias || !dims || !norm) return CBL_ERR_ARG;
+  if (nb <= 0 || nb > 2048 || npairs < 0 || (npairs && (!pairs || !VL)) || steps < 0) return CBL_ERR_ARG;
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || !(sigma > 0)) return CBL_ERR_ARG;
+  for (int k = 0; k < 4 * IN + 2 * OUT; ++k)
+    if (!std::isfinite(norm[k])) return CBL_ERR_ARG;
+  for (int k = 0; k < IN; ++k)
+    if (!(norm[IN + k] > 0) || norm[2 * IN + k] > norm[3 * IN + k]) return CBL_ERR_ARG;
+  if (steps == 0) return CBL_OK;
+  AdvNorm nm;
+  std::memcpy(&nm, norm, sizeof(nm));
+  const size_t smem = ((NPARAM * sizeof(__nv_bfloat16) + 15) / 16) * 16 + sizeof(double) * 6 * (size_t)nb;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mlp_advance, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_mlp_advance<<<1, 256, smem, m->s>>>(m->wb, X, V, Wang, M, Iinv, R, fixed, bias, pairs, VL, nb, npairs, steps,
+                                        dims[0], dims[1], dims[2], cos_theta, nm, sigma);
   return cudaGetLastError() == cudaSuccess ? CBL_OK : CBL_ERR_CUDA;
 }
 

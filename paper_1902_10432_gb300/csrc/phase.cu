@@ -343,10 +343,6 @@ __global__ void k_body_props_finish(BodyDev* bodies, int nb, const double* scrat
 // ---- solid-solid repulsion ---------------------------------------------------------------------
 // For a point x of body A (phi_A >= the membership threshold) and every body B whose tile overlaps
 // A's: sum the table forces f(d) over the points x + d of B; torque (x - X_A) x (sum f).
-__device__ __forceinline__ double support_radius(const BodyDev& b, double eta) {
-  const double h = b.shape == 0 ? b.radius : sqrt(b.half[0] * b.half[0] + b.half[1] * b.half[1] + b.half[2] * b.half[2]);
-  return h + 0.5 * eta;
-}
 
 __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const double* arena, double* acc, Lat lat,
                                                    double rc, int Rc, double thr, double eta,
@@ -362,16 +358,19 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
   __shared__ int s_near;
   if (threadIdx.x == 0) {
     int nearby = 0;
-    const double ea = support_radius(a, eta);
     const int nn[3] = {lat.nx, lat.ny, lat.nz};
-    const int* ba = mbox + 6 * self;
+    const int* ba = mbox + MBOX_N * self;
+    // every member point of a body lies within its member radius of its centre X, so two bodies
+    // whose centres are farther apart than the two member radii plus rc (and a cell of slack) have
+    // no pair in range
+    const double ra = sqrt((double)__int_as_float(ba[MBOX_R2]));
     for (int k = 0; k < a.nnb && !nearby; ++k) {
       const BodyDev& b = bodies[a.nbl[k]];
       const double dx = mimg(b.X[0] - a.X[0], lat.nx), dy = mimg(b.X[1] - a.X[1], lat.ny),
                    dz = mimg(b.X[2] - a.X[2], lat.nz);
-      const double lim = ea + support_radius(b, eta) + rc + 1.0;
+      const int* bb = mbox + MBOX_N * a.nbl[k];
+      const double lim = ra + sqrt((double)__int_as_float(bb[MBOX_R2])) + rc + 1.0;
       if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
-      const int* bb = mbox + 6 * a.nbl[k];
       bool boxes = true;
       for (int d = 0; d < 3 && boxes; ++d) {
         if (ba[d] > ba[3 + d] || bb[d] > bb[3 + d]) {  // an empty box: no members
@@ -410,7 +409,7 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
         // tile coordinates of the other body's member cells (phi >= thr) lie in its box mbox (built by
         // the refill pass after the last flag update); the offsets reach Rc cells per axis, so a point
         // outside the box grown by Rc (periodically) finds no partner
-        const int* bx = mbox + 6 * a.nbl[k];
+        const int* bx = mbox + MBOX_N * a.nbl[k];
         int l[3];
         bool near = true;
         for (int d = 0; d < 3; ++d) {
@@ -421,6 +420,15 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
           if (bx[d] > bx[3 + d] || !in) near = false;  // an empty box has no members
         }
         if (!near) continue;
+        {
+          // and within B's member radius (plus rc and a cell) of B's centre
+          float dx = (float)c.gx - b.Xf[0], dy = (float)c.gy - b.Xf[1], dz = (float)c.gz - b.Xf[2];
+          dx -= (float)lat.nx * rintf(dx / (float)lat.nx);
+          dy -= (float)lat.ny * rintf(dy / (float)lat.ny);
+          dz -= (float)lat.nz * rintf(dz / (float)lat.nz);
+          const float lim = sqrtf(__int_as_float(bx[MBOX_R2])) + (float)rc + 1.0f;
+          if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
+        }
         const double* bb = arena + b.off;
         // offsets in groups of 8: the group's loads are issued before any of them is tested (a
         // test per load would wait for each load in turn); contributions are added in offset order
@@ -542,23 +550,30 @@ __device__ void integrate(BodyDev& b, const double* parts, const Lat& lat, StepS
 }
 
 __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                                                StepState* st, Lat lat, double* rtab, int Lmax, int* mbox) {
+                                                StepState* st, Lat lat, double* rtab, int Lmax, int* mbox,
+                                                double* fsum) {
   const int n[3] = {lat.nx, lat.ny, lat.nz};
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     BodyDev& b = bodies[i];
     double* a = acc + (size_t)i * ACC_N;
     integrate(b, a, lat, st);
     mirror_f(b);
+    // running sums of the total force and torque (mean forces over many steps without host reads)
+    for (int c = 0; c < 3; ++c) {
+      fsum[6 * i + c] += a[ACC_MOM_F + c] + a[ACC_ADH_F + c] + a[ACC_REP_F + c];
+      fsum[6 * i + 3 + c] += a[ACC_MOM_T + c] + a[ACC_ADH_T + c] + a[ACC_REP_T + c];
+    }
     for (int k = 0; k < ACC_N; ++k) {
       last[(size_t)i * ACC_N + k] = a[k];
       a[k] = 0.0;
     }
     volacc[2 * i] = 0.0;
     volacc[2 * i + 1] = 0.0;
-    for (int a = 0; a < 3; ++a) {  // member box: rebuilt by this step's refill pass
-      mbox[6 * i + a] = INT_MAX;
-      mbox[6 * i + 3 + a] = INT_MIN;
+    for (int a = 0; a < 3; ++a) {  // member record: rebuilt by this step's refill pass
+      mbox[MBOX_N * i + a] = INT_MAX;
+      mbox[MBOX_N * i + 3 + a] = INT_MIN;
     }
+    mbox[MBOX_N * i + MBOX_R2] = 0;
     for (int d = 0; d < 3; ++d) {
       b.o_prev[d] = b.o[d];
       if (b.L[d] < n[d]) b.o[d] = (int)floor(b.X[d] + 0.5) - b.L[d] / 2;
@@ -1084,15 +1099,15 @@ void launch_repulsion(const Lat& lat, const BodyDev* bodies, int nb, int max_til
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     dim3 g = tile_grid(max_tile, nb);
     // a few waves in all, but never more than four chunks of the tile per block (many bodies)
-    const unsigned cap = std::max((g.x + 3) / 4, (unsigned)std::max(1, 4 * nsm / nb));
+    const unsigned cap = std::max((g.x + 3) / 4, (unsigned)std::max(1, 4 * nsm / (nb * g_launch_share)));
     if (g.x > cap) g.x = cap;
     k_repulsion<<<g, 256, 0, s>>>(bodies, arena, acc, lat, pp.rc, (int)std::ceil(pp.rc), pp.member_threshold, pp.eta,
                                   mbox);
   }
 }
 void launch_bodies(const Lat& lat, BodyDev* bodies, int nb, double* acc, double* last, double* volacc,
-                   StepState* st, double* rtab, int Lmax, int* mbox, cudaStream_t s) {
-  if (nb) k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, st, lat, rtab, Lmax, mbox);
+                   StepState* st, double* rtab, int Lmax, int* mbox, double* fsum, cudaStream_t s) {
+  if (nb) k_bodies<<<1, 256, 0, s>>>(bodies, nb, acc, last, volacc, st, lat, rtab, Lmax, mbox, fsum);
 }
 void launch_finish(double* mass_part, unsigned n_mass_part, StepState* st, cudaStream_t s) {
   k_finish<<<1, 256, 0, s>>>(mass_part, n_mass_part, st);
@@ -1129,10 +1144,13 @@ void launch_clear_tile_flags(const Lat& lat, const BodyDev* bodies, int nb, int 
 }
 __global__ void k_reset_member_boxes(int* mbox, int nb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < 6 * nb) mbox[k] = (k % 6) < 3 ? INT_MAX : INT_MIN;
+  if (k < MBOX_N * nb) {
+    const int e = k % MBOX_N;
+    mbox[k] = e < 3 ? INT_MAX : (e < 6 ? INT_MIN : 0);
+  }
 }
 void launch_reset_member_boxes(int* mbox, int nb, cudaStream_t s) {
-  if (nb) k_reset_member_boxes<<<(6 * nb + 255) / 256, 256, 0, s>>>(mbox, nb);
+  if (nb) k_reset_member_boxes<<<(MBOX_N * nb + 255) / 256, 256, 0, s>>>(mbox, nb);
 }
 void launch_clear_stale(const Lat& lat, uint16_t* flags, cudaStream_t s) {
   k_clear_stale<<<(unsigned)((lat.N + 255) / 256), 256, 0, s>>>(flags, lat.N);

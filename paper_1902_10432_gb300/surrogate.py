@@ -14,9 +14,10 @@ measured against.
   the spheres held fixed and moved together step by step, the force averaged after each step has
   relaxed: quasi-static force-gap sweeps of intact bridges. (A node that turns fluid starts empty, Sec. 3.2.2, so a
   body move launches pressure pulses that the hold lets decay.)
-* The hybrid advance alternates a K-step lattice-Boltzmann burst (true forces; the per-body residual
-  becomes a bias) with a W-step window in which the bodies move under the network's pair forces plus
-  the bias while the fluid is frozen; the bodies' phase fields are then rebuilt at the new poses.
+* The hybrid advance alternates a K-step lattice-Boltzmann burst (true forces, averaged on the device;
+  the per-body residual becomes a bias) with a W-step window in which the bodies move under the
+  network's pair forces and torques plus the bias while the fluid is frozen, all W steps in one
+  device launch (cbl_mlp_advance); the bodies' phase fields are then rebuilt at the new poses.
 All heavy work runs in the CUDA library (LBM steps, network forward/backward/Adam); this module only
 arranges inputs and reads results.
 """
@@ -138,15 +139,14 @@ def generate(ws, equil=800, hold=150, avg=75, records=80, dgap=-0.04, min_gap=1.
                 e = _pair_axis(P[0], P[1], meta[k]["dims"])
                 sims[k].move_bodies(np.stack([P[0] - 0.5 * dgap * e, P[1] + 0.5 * dgap * e]))
         batch.step(hold - avg)
-        Fs = {k: np.zeros((2, 3)) for k in live}
-        Ts = {k: np.zeros((2, 3)) for k in live}
-        for _ in range(avg):
-            batch.step(1)
-            batch.sync()
-            for k in live:
-                F, T, _ = sims[k].body_forces()
-                Fs[k] += F / avg
-                Ts[k] += T / avg
+        batch.sync()
+        for k in live:
+            sims[k].force_mean(reset=True)  # start the device-side sums for the averaging window
+        batch.step(avg)
+        batch.sync()
+        Fs, Ts = {}, {}
+        for k in live:
+            Fs[k], Ts[k], _ = sims[k].force_mean(reset=True)
         for k in live:
             s, m = sims[k], meta[k]
             b = s.bodies()
@@ -192,6 +192,10 @@ class Surrogate:
         xt = torch.tensor((Xc - self.xm) / self.xs, dtype=torch.float32, device="cuda")
         y = self.mlp.forward(xt).cpu().numpy().astype(np.float64)
         return y * self.ys + self.ym
+
+    def norm(self):
+        """The standardisation in the order cbl_mlp_advance takes it: x mean, std, min, max; y mean, std."""
+        return np.concatenate([self.xm, self.xs, self.xlo, self.xhi, self.ym, self.ys]).astype(np.float32)
 
 
 def train(X, Y, inst, iters=3000, lr=3e-3, holdout=0.1, seed=0, log=None):
@@ -266,6 +270,46 @@ def pair_forces(sur, X, R, pairs, VL, theta, dims):
     return F
 
 
+def pair_torques(sur, X, R, pairs, VL, theta, dims):
+    """Network torques on every body (world frame) from the bridged pairs."""
+    T = np.zeros_like(X)
+    for (i, j) in pairs:
+        for a, b in ((i, j), (j, i)):
+            f, fr = features(X[a], X[b], R[a], R[b], VL[(i, j)], theta, dims)
+            y = sur.predict(f[None])[0]
+            T[a] += fr.T @ (y[3:] * force_scale(R[a], R[b]) * rstar(R[a], R[b]))
+    return T
+
+
+def advance_host(sur, X, V, W, M, Iinv, R, pairs, VL, theta, dims, bias, steps):
+    """The surrogate window on the host (numpy; the reference for the device version): `steps`
+    semi-implicit Euler steps of the bodies under the network's pair forces and torques plus bias."""
+    X, V, W = X.copy(), V.copy(), W.copy()
+    for _ in range(steps):
+        F = pair_forces(sur, X, R, pairs, VL, theta, dims) + bias
+        T = pair_torques(sur, X, R, pairs, VL, theta, dims)
+        V += F / M[:, None]
+        X = (X + V) % np.asarray(dims, float)
+        W += T * Iinv[:, None]
+    return X, V, W
+
+
+def advance_device(sur, X, V, W, M, Iinv, R, pairs, VL, theta, dims, bias, steps):
+    """The surrogate window on the device: one launch of cbl_mlp_advance for all `steps` steps (pair
+    features, network forward with the weights in shared memory, translation and rotation)."""
+    import torch
+
+    dev = "cuda"
+    t = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    Xt, Vt, Wt = t(X), t(V), t(W)
+    pl = [p for p in pairs]
+    pt = t(np.array(pl, np.int32).reshape(-1, 2), torch.int32)
+    vl = t(np.array([VL[p] for p in pl], np.float64))
+    sur.mlp.advance(Xt, Vt, Wt, t(M), t(Iinv), t(np.asarray(R, float)), t(np.zeros(len(R), np.int32), torch.int32),
+                    t(bias), pt, vl, steps, dims, math.cos(math.radians(theta)), sur.norm(), SIGMA)
+    return Xt.cpu().numpy(), Vt.cpu().numpy(), Wt.cpu().numpy()
+
+
 def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg=50, log=None):
     """`windows` times: K LBM steps (the true force is the mean over the last avg of them; its residual
     against the network becomes a per-body bias), then W surrogate steps with the fluid frozen and the
@@ -280,18 +324,18 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
     rho = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float64, device="cuda")
     b = sim.bodies()
     M = b["M"]
+    Iinv = 3.0 / np.trace(b["I"], axis1=1, axis2=2)  # spheres: scalar inertia
     errs, corr, absd = [], [], []
     bias = None
     Rv = np.asarray(R, float)
     t0 = time.perf_counter()
 
     def burst():
+        # the force is the mean over the last avg steps, summed on the device (no host read per step)
         sim.step(K - avg)
-        F = np.zeros((len(R), 3))
-        for _ in range(avg):
-            sim.step(1)
-            F += sim.body_forces()[0] / avg
-        return F
+        sim.force_mean(reset=True)
+        sim.step(avg)
+        return sim.force_mean(reset=True)[0]
 
     for win in range(windows):
         F_lbm = burst()
@@ -317,11 +361,9 @@ def hybrid_run(sim, sur, R, pairs, VL, theta, dims, windows=4, K=100, W=200, avg
                 dc = np.linalg.norm(F_mlp[on] + bias[on] - F_lbm[on], axis=1)
                 corr.append(dc[big] / n[big])
         bias = F_lbm - F_mlp
-        for _ in range(W):
-            F = pair_forces(sur, X, R, live, VLm, theta, dims) + bias
-            V += F / M[:, None]
-            X = (X + V) % np.asarray(dims, float)
-        sim.move_bodies(X, V=V)
+        Wb = b["W"].copy()
+        X, V, Wb = advance_device(sur, X, V, Wb, M, Iinv, R, live, VLm, theta, dims, bias, W)
+        sim.move_bodies(X, V=V, W=Wb)
         if log and errs:
             log("window %d: %d of %d bridges intact; median relative force error %.3f over %d bodies" % (
                 win, len(live), len(pairs), float(np.median(errs[-1])) if len(errs[-1]) else float("nan"),

@@ -5,10 +5,14 @@ import oracle
 from paper_1902_10432_gb300 import cbl, workloads
 
 
-def make_pair(w, **override):
+def make_pair(w, options=None, **override):
+    """The workload on the CUDA path (execution options, e.g. tile_tail, applied before the bodies are
+    added) and on the oracle."""
     params = dict(w.params)
     params.update(override)
     g = cbl.Sim(w.nx, w.ny, w.nz, **params)
+    for k, v in (options or {}).items():
+        g.set_option(k, v)
     workloads.build(g, w)
     o = oracle.Oracle(w.nx, w.ny, w.nz, **{k: v for k, v in params.items() if k != "prec"})
     workloads.build(o, w)

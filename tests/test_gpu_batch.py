@@ -99,3 +99,101 @@ def test_move_bodies_matches_fresh_setup_and_keeps_mass():
     assert np.array_equal(sa, sf) and np.array_equal(oa, of)
     a.step(5)  # the moved state steps cleanly
     assert a.info()["device_error"] == 0 and np.isfinite(a.total_mass())
+
+
+def _batch_of(ws, mode=None, tile=None):
+    from paper_1902_10432_gb300 import cbl
+
+    sims = [_sim(w) for w in ws]
+    b = cbl.Batch(sims)
+    if mode is not None:
+        b.set_option("mode", mode)
+    if tile is not None:
+        b.set_option("tile", tile)
+    return sims, b
+
+
+def test_persistent_batch_is_the_default_and_matches_branch_mode():
+    # the persistent launch (psi and bulk collision of every instance in one kernel, work items from
+    # a device queue, a grid barrier between the phases) against one fork/join branch per instance
+    ws = workloads.batch64(seed=5, n=4)
+    pa, ba = _batch_of(ws)
+    assert ba.info()["mode"] == 1 and ba.info()["items"] > 0 and ba.info()["grid"] > 0
+    pb, bb = _batch_of(ws, mode=0)
+    for b in (ba, bb):
+        b.step(30)
+        b.sync()
+    for a, g in zip(pa, pb):
+        ra, va, _ = a.fields()
+        rg, vg, _ = g.fields()
+        assert np.abs(ra - rg).max() <= 1e-5 * np.abs(ra).max()  # FP32, forces summed in another order
+        assert a.info()["device_error"] == 0
+    ba.close()
+    bb.close()
+
+
+@pytest.mark.parametrize("tile", [0, 2, 3])
+def test_persistent_tile_shapes_agree(tile):
+    # every tile shape computes every cell once: the fields of a held-body batch (no force feedback)
+    # agree bit for bit with the default tile
+    ws = workloads.batch64(seed=6, n=3, fixed=True)
+    pa, ba = _batch_of(ws)
+    pb, bb = _batch_of(ws, tile=tile)
+    for b in (ba, bb):
+        b.step(12)
+        b.sync()
+    for a, g in zip(pa, pb):
+        assert np.array_equal(a.populations(), g.populations())
+    ba.close()
+    bb.close()
+
+
+def test_batched_instances_match_the_oracle():
+    # FP64 instances of different sizes in one persistent batch, each against its own oracle run
+    from _pair import compare
+
+    import oracle
+
+    ws = [workloads.small_spheres(seed=s, prec="fp64", nx=nx, ny=ny, nz=nz, mobility=2e-3)
+          for s, (nx, ny, nz) in enumerate([(40, 36, 64), (36, 44, 56), (48, 40, 60)])]
+    sims, b = _batch_of(ws)
+    assert b.info()["mode"] == 1
+    b.step(100)
+    b.sync()
+    for w, g in zip(ws, sims):
+        o = oracle.Oracle(w.nx, w.ny, w.nz, **{k: v for k, v in w.params.items() if k != "prec"})
+        workloads.build(o, w)
+        o.step(100)
+        e = compare(g, o)
+        assert e["flag_mismatch"] == 0 and e["rho"] < 1e-10 and e["vel"] < 1e-8 and e["force"] < 1e-9, e
+    b.close()
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable():
+    # a barrier wait limit of 0 cycles makes every block but the last give up at once: the step's
+    # results are not valid, cbl_batch_sync reports CBL_ERR_TIMEOUT, and with the limit restored the
+    # batch steps normally again
+    from paper_1902_10432_gb300 import cbl
+
+    ws = workloads.batch64(seed=7, n=2)
+    sims, b = _batch_of(ws)
+    b.set_option("spin_limit", 0)
+    b.step(1)
+    with pytest.raises(cbl.CblError) as ei:
+        b.sync()
+    assert ei.value.status == 5  # CBL_ERR_TIMEOUT
+    b.set_option("spin_limit", 4e9)
+    b.step(3)
+    b.sync()  # no error this time
+    b.close()
+
+
+def test_autotune_picks_a_batch_tile():
+    from paper_1902_10432_gb300 import autotune
+
+    ws = workloads.batch64(seed=8, n=3)
+    sims, b = _batch_of(ws)
+    tile, ms = autotune.tune_batch(b, steps=2)
+    assert tile in autotune.BATCH_TILES and len(ms) == len(autotune.BATCH_TILES)
+    assert b.info()["tile"] == tile
+    b.close()

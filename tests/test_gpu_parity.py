@@ -59,29 +59,35 @@ def test_plates48_fp16dev_error_reported():
     e = compare(g, o)
     print("FP16-deviation storage vs FP64 oracle after 500 steps:", e)
     assert e["flag_mismatch"] == 0
-    assert e["rho"] < 0.1 and e["force"] < 0.5  # a sanity bound: this error is reported, not bounded
+    # binary16 deviations from the weights (storage only, FP32 arithmetic): this error is reported, not
+    # bounded by the contract; measured rho 0.045, force 0.13 (the bound is a sanity check at about
+    # twice that)
+    assert e["rho"] < 0.1 and e["force"] < 0.3
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
 def test_moving_spheres(prec, tol):
-    # light spheres: they move, cells are covered and uncovered, tiles recentre, kinetics on
+    # light spheres: they move, cells are covered and uncovered, tiles recentre, kinetics on; 500
+    # steps, density and velocity within tol, per-body force within 10 tol (FP32: the contract's
+    # 1e-4 and 1e-3). These light spheres travel far enough that their advection tails reach the halo
+    # of the default tiles within 500 steps; with 30 cells of room (tile_tail) every tile spans the
+    # whole 40 x 36 x 64 lattice, so the tiled phase field equals the oracle's dense one (device error
+    # bit 0 stays clear). Tiles narrower than the lattice are covered by the cluster and plate tests.
     w = workloads.small_spheres(prec=prec, mobility=2e-3)
-    g, o = make_pair(w)
+    g, o = make_pair(w, options=dict(tile_tail=30.0))
     s0, _ = o.flags()
-    for k in range(2):
+    for k in range(5):
         g.step(100)
         o.step(100)
         e = compare(g, o)
-        print(prec, o.t, e)
-        if prec == "fp64":
-            assert e["flag_mismatch"] == 0
-        assert e["flag_mismatch"] <= 4
-        assert e["rho"] < tol and e["vel"] < 10 * tol
+        print(prec, o.t, e, "device error", g.info()["device_error"])
+        assert g.info()["device_error"] == 0
+        assert e["flag_mismatch"] == 0
+        assert e["rho"] < tol and e["vel"] < tol
         assert e["force"] < 10 * tol and e["X"] < 1e-3
         assert e["phi_fluid"] < (1e-9 if prec == "fp64" else 1e-3)
     s1, _ = o.flags()
     assert (s0 != s1).sum() > 10  # bodies actually moved
-    assert g.info()["device_error"] == 0
 
 
 def test_mass_conservation_moving_fp64():
@@ -151,7 +157,7 @@ def test_spheres2_full_size_fp32_500_steps():
     e = compare(g, o)
     print("spheres2 full size:", w.meta, e)
     assert e["flag_mismatch"] <= 8
-    assert e["rho"] < 1e-4 and e["vel"] < 1e-3
+    assert e["rho"] < 1e-4 and e["vel"] < 1e-4
     assert e["force"] < 1e-3
 
 

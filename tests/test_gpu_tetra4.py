@@ -1,14 +1,29 @@
-"""Four-sphere cluster. The multi-body path against the FP64 oracle at round-off (FP64 on both sides),
-and the 256^3 crop errors of FP32 and binary16-deviation storage after 500 steps.
+"""Four-sphere cluster (Sec. 4.3.2 set-up): the CUDA path against the FP64 oracle.
 
-In this configuration the FP32 and binary16 differences from FP64 grow with time (measured: FP32
-about 1e-6 at step 50, 2e-5 at 150, 1e-3 to 1e-2 at 500, while FP64 on the GPU stays at 1e-15 of the
-oracle): the flow amplifies rounding, most where cells are nearly empty (a node that turns fluid
-starts with density zero, Sec. 3.2.2) and the velocity m / rho is ill-conditioned. The crop test
-states the errors; the FP64 test pins the implementation."""
+At half scale (128^3, R = 12, surface gap 4), in the driver's GPU suite: one oracle run, and the
+CUDA path with FP64, FP32 and binary16-deviation storage, compared at steps 150, 300 and 500 on the
+central 64^3 crop and on the whole lattice.
+
+* FP64 on the GPU stays at round-off of the oracle (the multi-body path: shared tiles, neighbour
+  lists, repulsion culling) to step 500.
+* Binary16-deviation storage: its error is the storage's. The oracle's storage model (the FP64 method
+  with its stored populations rounded to binary16 deviations after every store;
+  tests/golden/tetra4_half_storage.json, written by tests/golden/make_tetra4_storage.py from the
+  oracle alone) deviates from the FP64 oracle by what the GPU path does, within a factor of 2 at
+  every step: the kernels add nothing measurable to it.
+* FP32: the same storage model in FP32 stays within ~3e-7 of FP64 up to step 300, so FP32 storage is
+  not what limits the FP32 path; its FP32 arithmetic is. The FP32 path is within the contract's
+  tolerances (1e-4 on density and velocity, 1e-3 on force) at step 150, and its error then grows with
+  the four bodies' coupled motion (measured on the crop: density 5.9e-5 and velocity 4.4e-4 at step
+  300, 1.7e-3 and 1.8e-2 at 500); those values, with a margin of 3, are the stated bounds here.
+
+The full-size comparison (256^3, the oracle on the whole lattice for 500 steps, ~8 minutes on 16
+cores) is kept as a long test (CBL_LONG_TESTS=1).
+"""
 import json
 import os
 
+import numpy as np
 import pytest
 
 from paper_1902_10432_gb300 import workloads
@@ -16,19 +31,11 @@ from _pair import compare, make_pair, rel_linf
 
 pytestmark = pytest.mark.gpu
 
-
-@pytest.mark.slow
-def test_tetra4_small_fp64_matches_oracle():
-    # the cluster at half scale (128^3, R = 12, surface gap 4): four free bodies with shared tiles,
-    # neighbour lists and repulsion culling, 300 steps
-    w = workloads.tetra4(seed=0, prec="fp64", n=128, R=12.0, surface_gap=4.0)
-    g, o = make_pair(w)
-    g.step(300)
-    o.step(300)
-    e = compare(g, o)
-    assert e["flag_mismatch"] == 0
-    assert e["rho"] < 1e-12 and e["vel"] < 1e-12 and e["phi_fluid"] < 1e-12
-    assert e["force"] < 1e-10 and e["X"] < 1e-10
+N_HALF = 128
+STEPS_HALF = (150, 300, 500)
+STORAGE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tetra4_half_storage.json")
+# stated FP32 bounds on the crop (measured x 3) after the contract's step-150 check
+FP32_BOUNDS = {300: dict(rho=2e-4, vel=1.5e-3, force=5e-3), 500: dict(rho=5e-3, vel=6e-2, force=0.12)}
 
 
 def _crop_errors(g, o, n, h=32):
@@ -48,6 +55,70 @@ def _crop_errors(g, o, n, h=32):
                 crop_fluid_cells=int(fluid.sum()))
 
 
+@pytest.fixture(scope="module")
+def half_scale():
+    import __graft_entry__
+    import oracle
+    from paper_1902_10432_gb300 import cbl
+
+    __graft_entry__.build()
+    w = workloads.tetra4(seed=0, prec="fp64", n=N_HALF, R=12.0, surface_gap=4.0)
+    o = oracle.Oracle(w.nx, w.ny, w.nz, **{k: v for k, v in w.params.items() if k != "prec"})
+    workloads.build(o, w)
+    gpu = {}
+    for prec in ("fp64", "fp32", "fp16dev"):
+        g = cbl.Sim(w.nx, w.ny, w.nz, **dict(w.params, prec=prec))
+        workloads.build(g, w)
+        gpu[prec] = g
+    out = {}
+    done = 0
+    for s in STEPS_HALF:
+        o.step(s - done)
+        for g in gpu.values():
+            g.step(s - done)
+        done = s
+        out[s] = {p: dict(crop=_crop_errors(g, o, N_HALF), full=compare(g, o), device_error=g.info()["device_error"])
+                  for p, g in gpu.items()}
+    print("tetra4 half scale, errors against the FP64 oracle:", json.dumps(out, default=float))
+    return out
+
+
+def test_tetra4_half_fp64_matches_oracle(half_scale):
+    for s in STEPS_HALF:
+        e = half_scale[s]["fp64"]
+        assert e["device_error"] == 0
+        f = e["full"]
+        assert f["flag_mismatch"] == 0, s
+        assert f["rho"] < 1e-12 and f["vel"] < 1e-12 and f["phi_fluid"] < 1e-12, (s, f)
+        assert f["force"] < 1e-10 and f["X"] < 1e-10, (s, f)
+
+
+def test_tetra4_half_fp32_within_contract_then_stated_bounds(half_scale):
+    e150 = half_scale[150]["fp32"]
+    assert e150["device_error"] == 0
+    f = e150["full"]
+    assert f["flag_mismatch"] == 0 and f["rho"] < 1e-4 and f["vel"] < 1e-4 and f["force"] < 1e-3, f
+    for s in (300, 500):
+        e = half_scale[s]["fp32"]
+        assert e["device_error"] == 0 and e["crop"]["flag_mismatch"] == 0
+        b = FP32_BOUNDS[s]
+        assert e["crop"]["rho"] < b["rho"] and e["crop"]["vel"] < b["vel"], (s, e["crop"])
+        assert e["full"]["force"] < b["force"], (s, e["full"])
+
+
+def test_tetra4_half_fp16dev_error_is_the_storage(half_scale):
+    with open(STORAGE) as fh:
+        model = json.load(fh)["errors_vs_fp64"]
+    for s in STEPS_HALF:
+        e = half_scale[s]["fp16dev"]
+        m = model[str(s)]["fp16dev"]
+        assert e["device_error"] == 0
+        for k, km in (("rho", "rho_crop"), ("vel", "vel_crop")):
+            assert 0.5 < e["crop"][k] / m[km] < 2.0, (s, k, e["crop"][k], m[km])
+        # FP32 storage alone is far below the FP32 path's error: the FP32 path is limited by arithmetic
+        assert model[str(s)]["fp32"]["rho_crop"] < 1e-5
+
+
 @pytest.mark.slow
 @pytest.mark.skipif(os.environ.get("CBL_LONG_TESTS") != "1",
                     reason="the oracle runs 256^3 for 500 steps (~8 minutes): set CBL_LONG_TESTS=1")
@@ -65,7 +136,6 @@ def test_tetra4_crop_fp32_and_fp16_against_oracle():
     e32 = _crop_errors(g32, o, w32.nx)
     e16 = _crop_errors(g16, o, w16.nx)
     print("tetra4 crop errors after 500 steps:", json.dumps({"fp32": e32, "fp16dev": e16}))
-    # stated errors (see the module docstring), bounded at a few times the measured values
     assert e32["flag_mismatch"] == 0
     assert e32["rho"] < 1e-3 and e32["force"] < 5e-2
     assert e16["rho"] < 1.0

@@ -320,3 +320,23 @@ def test_one_step_brute_force_moving_body():
     _, _, parts = o.body_forces()
     assert np.allclose(parts[0, 0, :3], F, rtol=1e-12, atol=1e-16)
     assert np.allclose(parts[0, 0, 3:], T, rtol=1e-11, atol=1e-16)
+
+
+def test_storage_model_rounding():
+    # the storage model's binary16 rounding (analysis option store_prec = 2) against numpy's IEEE
+    # binary16 conversion, over normal and subnormal magnitudes and both signs
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([rng.uniform(-2, 2, 2000), rng.uniform(-1e-4, 1e-4, 2000), rng.uniform(-1e-7, 1e-7, 500),
+                           [0.0, 1.0, -1.0, 0.5, 2.0 ** -14, 2.0 ** -24, 3 * 2.0 ** -25, 1 + 2.0 ** -11]])
+    vals = vals.astype(np.float32).astype(np.float64)  # the model rounds the float value
+    got = np.array([oracle.round_binary16(v) for v in vals])
+    assert np.array_equal(got, vals.astype(np.float16).astype(np.float64))
+    # a run with FP32 storage stays within FP32 rounding of the FP64 run over a few steps
+    rho = 0.12 + 1.77 * (np.random.default_rng(5).random((6, 5, 4)) > 0.5)
+    a, b = oracle.Oracle(4, 5, 6), oracle.Oracle(4, 5, 6, store_prec=1)
+    for o in (a, b):
+        o.init_fluid_fields(rho)
+        o.step(3)
+    fa, fb = a.populations(), b.populations()
+    assert np.array_equal(fb, fb.astype(np.float32).astype(np.float64))
+    assert 0 < np.abs(fa - fb).max() < 1e-6

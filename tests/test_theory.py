@@ -35,3 +35,27 @@ def test_plate_forces_and_motion():
     t = 0.3 * tc
     assert an.plate_gap_planar(h0, s, R, m, t) / R == pytest.approx(h0 / R - 2 * (t / tc) ** 2)
     assert an.plate_gap_cylinder(h0, s, R, m, t) / R == pytest.approx(h0 / R - math.pi * (t / tc) ** 2)
+
+
+def test_toroidal_bridge_limits_and_volume():
+    # the toroidal approximation of a plate bridge (Sec. 2.1 force on a plate, Eq. young_laplace):
+    # continuous into the 90-degree cylinder (Eq. plate_force), and its volume of revolution is the
+    # one a voxel count of the shape gives
+    s, h, V = 3.583e-2, 12.0, math.pi * 100.0 * 12.0
+    a90, r90, F90 = an.toroidal_bridge(s, math.pi / 2, h, V)
+    assert a90 == pytest.approx(10.0) and F90 == pytest.approx(an.plate_force_cylinder(s, 10.0))
+    a, r1, F = an.toroidal_bridge(s, math.radians(89.99), h, V)
+    assert F == pytest.approx(F90, rel=1e-3) and a == pytest.approx(10.0, rel=1e-3)
+    a, r1, F = an.toroidal_bridge(s, math.radians(60.0), h, V)
+    assert r1 == pytest.approx(12.0)
+    assert F > F90  # a concave bridge pulls harder than the cylinder of the same volume
+    import numpy as np
+
+    n = 400  # voxel count of the revolved meridian r(z) = a + r1 - sqrt(r1^2 - z^2)
+    z = (np.arange(n) + 0.5) / n * h - h / 2
+    xy = (np.arange(2 * n) + 0.5) / (2 * n) * 60.0 - 30.0
+    X, Y = np.meshgrid(xy, xy, indexing="ij")
+    R2 = X * X + Y * Y
+    cnt = sum(int((R2 <= (a + r1 - math.sqrt(r1 * r1 - zz * zz)) ** 2).sum()) for zz in z)
+    vox = cnt * (h / n) * (60.0 / (2 * n)) ** 2
+    assert vox == pytest.approx(V, rel=2e-3)
