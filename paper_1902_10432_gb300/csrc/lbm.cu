@@ -535,8 +535,8 @@ __device__ __forceinline__ bool covered_by_lower(const BodyDev* bodies, const Bo
     int o = b.nbl[k];
     if (o >= self) break;
     const BodyDev& ob = bodies[o];
-    if (wrapi(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi(gy - ob.o[1], lat.ny) < ob.L[1] &&
-        wrapi(gz - ob.o[2], lat.nz) < ob.L[2])
+    if (wrapi_near(gx - ob.o[0], lat.nx) < ob.L[0] && wrapi_near(gy - ob.o[1], lat.ny) < ob.L[1] &&
+        wrapi_near(gz - ob.o[2], lat.nz) < ob.L[2])
       return true;
   }
   return false;
@@ -699,8 +699,8 @@ __global__ void __launch_bounds__(256) k_density_tiles(const S* __restrict__ fa,
   if (t >= b.sz) return;
   const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];  // tiles hold < 2^31 cells
   const unsigned r = u / L0;
-  const int gx = wrapi(b.o[0] + (int)(u - r * L0), lat.nx), gy = wrapi(b.o[1] + (int)(r % L1), lat.ny),
-            gz = wrapi(b.o[2] + (int)(r / L1), lat.nz);
+  const int gx = wrapi_near(b.o[0] + (int)(u - r * L0), lat.nx), gy = wrapi_near(b.o[1] + (int)(r % L1), lat.ny),
+            gz = wrapi_near(b.o[2] + (int)(r / L1), lat.nz);
   if (b.nnb && covered_by_lower(bodies, b, self, gx, gy, gz, lat)) return;
   const Cell c = make_cell(gx, gy, gz, lat);
   psi[c.n] = psi_of_cell<S>(f, flags, bodies, lat, c, rho0, rho0_f);
@@ -1043,7 +1043,8 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
     mi[0] = i0;
     mi[1] = i1;
     mi[2] = i2;
-    const int gx = wrapi(b.o[0] + i0, lat.nx), gy = wrapi(b.o[1] + i1, lat.ny), gz = wrapi(b.o[2] + i2, lat.nz);
+    const int gx = wrapi_near(b.o[0] + i0, lat.nx), gy = wrapi_near(b.o[1] + i1, lat.ny),
+              gz = wrapi_near(b.o[2] + i2, lat.nz);
     m = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
     if (member) {
       // in float from the float mirror of X (FP64 is 1/64 rate here and this is a bound with slack);
@@ -1058,7 +1059,8 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
       const bool events = st->ncover != 0;
       const size_t N = (size_t)lat.Ns;  // population stride
       auto at = [&](int x, int y, int z) {
-        return (long long)wrapi(x, lat.nx) + (long long)lat.nx * (wrapi(y, lat.ny) + (long long)lat.ny * wrapi(z, lat.nz));
+        return (long long)wrapi_near(x, lat.nx) +
+               (long long)lat.nx * (wrapi_near(y, lat.ny) + (long long)lat.ny * wrapi_near(z, lat.nz));
       };
       auto fluid_count = [&](int x, int y, int z, bool faces_only) {
         int cnt = 0;
@@ -1216,8 +1218,8 @@ __global__ void k_zero_solid(S* __restrict__ fa, S* __restrict__ fb, const StepS
   if (t >= b.sz) return;
   const unsigned u = (unsigned)t, L0 = (unsigned)b.L[0], L1 = (unsigned)b.L[1];
   const unsigned r = u / L0;
-  const int gx = wrapi(b.o[0] + (int)(u - r * L0), lat.nx), gy = wrapi(b.o[1] + (int)(r % L1), lat.ny),
-            gz = wrapi(b.o[2] + (int)(r / L1), lat.nz);
+  const int gx = wrapi_near(b.o[0] + (int)(u - r * L0), lat.nx), gy = wrapi_near(b.o[1] + (int)(r % L1), lat.ny),
+            gz = wrapi_near(b.o[2] + (int)(r / L1), lat.nz);
   const long long n = gx + (long long)lat.nx * (gy + (long long)lat.ny * gz);
   if (!(flags[n] & F_SOLID)) return;
   S* f = st->parity ? fb : fa;

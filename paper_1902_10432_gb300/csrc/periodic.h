@@ -26,6 +26,18 @@ CBL_HD inline int wrapi(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
+// a mod n for a in [-2n, 3n), without a division (an integer division by a value known only at run
+// time costs some twenty instructions): tile coordinates, whose origins lie within about half a
+// lattice length outside [0, n) and whose offsets are below n, stay in that range. Equal to wrapi
+// there.
+CBL_HD inline int wrapi_near(int a, int n) {
+  if (a < 0) a += n;
+  if (a < 0) a += n;
+  if (a >= n) a -= n;
+  if (a >= n) a -= n;
+  return a;
+}
+
 // Minimum image of a coordinate difference: the representative of d modulo n in [-n/2, n/2).
 // |d| <= 2n: at most two exact shifts by n. Larger |d|: one closed-form reduction first.
 // NaN stays NaN, +-Inf becomes NaN.

@@ -69,15 +69,15 @@ __device__ __forceinline__ TileCell tile_cell(const BodyDev& b, long long t, con
   c.i0 = (int)(u - r * L0);
   c.i1 = (int)(r % L1);
   c.i2 = (int)(r / L1);
-  c.gx = wrapi(b.o[0] + c.i0, lat.nx);
-  c.gy = wrapi(b.o[1] + c.i1, lat.ny);
-  c.gz = wrapi(b.o[2] + c.i2, lat.nz);
+  c.gx = wrapi_near(b.o[0] + c.i0, lat.nx);
+  c.gy = wrapi_near(b.o[1] + c.i1, lat.ny);
+  c.gz = wrapi_near(b.o[2] + c.i2, lat.nz);
   return c;
 }
 
 // local index of global cell g in a tile with origin o, or -1 if outside
 __device__ __forceinline__ long long tile_index(const int o[3], const int L[3], int gx, int gy, int gz, const Lat& lat) {
-  int a = wrapi(gx - o[0], lat.nx), b = wrapi(gy - o[1], lat.ny), c = wrapi(gz - o[2], lat.nz);
+  int a = wrapi_near(gx - o[0], lat.nx), b = wrapi_near(gy - o[1], lat.ny), c = wrapi_near(gz - o[2], lat.nz);
   if (a >= L[0] || b >= L[1] || c >= L[2]) return -1;
   return (long long)a + (long long)L[0] * ((long long)b + (long long)L[1] * c);
 }
@@ -150,7 +150,7 @@ __global__ void k_rasterize(BodyDev* bodies, double* arena, Lat lat, double eta)
 __device__ bool tiles_overlap(const BodyDev& a, const BodyDev& b, const Lat& lat) {
   const int n[3] = {lat.nx, lat.ny, lat.nz};
   for (int d = 0; d < 3; ++d) {
-    bool ov = wrapi(b.o[d] - a.o[d], n[d]) < a.L[d] || wrapi(a.o[d] - b.o[d], n[d]) < b.L[d];
+    bool ov = wrapi_near(b.o[d] - a.o[d], n[d]) < a.L[d] || wrapi_near(a.o[d] - b.o[d], n[d]) < b.L[d];
     if (!ov) return false;
   }
   return true;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_repulsion(const BodyDev* bodies, const 
         int l[3];
         bool near = true;
         for (int d = 0; d < 3; ++d) {
-          l[d] = wrapi(g[d] - b.o[d], nn[d]);
+          l[d] = wrapi_near(g[d] - b.o[d], nn[d]);
           const int lo = bx[d] - Rc, hi = bx[3 + d] + Rc;
           const bool in = (l[d] >= lo && l[d] <= hi) || (l[d] - nn[d] >= lo && l[d] - nn[d] <= hi) ||
                           (l[d] + nn[d] >= lo && l[d] + nn[d] <= hi);
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(256) k_bodies(BodyDev* bodies, int nb, double*
   for (int k = threadIdx.x; k < nb * 3 * Lmax; k += blockDim.x) {
     const int i = k / (3 * Lmax), a = (k / Lmax) % 3, l = k % Lmax;
     const BodyDev& b = bodies[i];
-    if (l < b.L[a]) rtab[k] = mimg(wrapi(b.o[a] + l, n[a]) - b.Xprev[a], n[a]);
+    if (l < b.L[a]) rtab[k] = mimg(wrapi_near(b.o[a] + l, n[a]) - b.Xprev[a], n[a]);
   }
   build_lists(bodies, nb, lat, st);
   if (threadIdx.x == 0) {
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(256) k_sweep(const BodyDev* bodies, double* ar
       // origins are unwrapped integers: take the shift as the minimum image of their difference
       int shift = 0;
       if (use_prev && b.L[a] < nn[a]) {
-        shift = wrapi(b.o[a] - b.o_prev[a], nn[a]);
+        shift = wrapi_near(b.o[a] - b.o_prev[a], nn[a]);
         if (shift > nn[a] / 2) shift -= nn[a];
       }
       li[a] = in_local(ii[a], shift, b.L[a], nn[a]);
@@ -884,7 +884,8 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     out[t] = pa[0];
     return;
   }
-  const int g[3] = {wrapi(b.o[0] + ii[0], nn[0]), wrapi(b.o[1] + ii[1], nn[1]), wrapi(b.o[2] + ii[2], nn[2])};
+  const int g[3] = {wrapi_near(b.o[0] + ii[0], nn[0]), wrapi_near(b.o[1] + ii[1], nn[1]),
+                    wrapi_near(b.o[2] + ii[2], nn[2])};
   // is any other body present in this cell's 7-point stencil?
   bool others = false;
   for (int k = 0; k < b.nnb && !others; ++k) {
@@ -892,7 +893,7 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     int lo[3];
     bool near = true;
     for (int a = 0; a < 3; ++a) {
-      lo[a] = wrapi(g[a] - o.o[a], nn[a]);
+      lo[a] = wrapi_near(g[a] - o.o[a], nn[a]);
       if (o.L[a] < nn[a]) {
         if (lo[a] > nn[a] - 2) lo[a] -= nn[a];
         if (lo[a] < -1 || lo[a] > o.L[a]) near = false;
@@ -955,7 +956,7 @@ __global__ void __launch_bounds__(256) k_kinetics(const BodyDev* bodies, double*
     int lo[3];
     bool near = true;
     for (int a = 0; a < 3; ++a) {
-      lo[a] = wrapi(g[a] - o.o[a], nn[a]);
+      lo[a] = wrapi_near(g[a] - o.o[a], nn[a]);
       if (o.L[a] < nn[a]) {
         if (lo[a] > nn[a] - 2) lo[a] -= nn[a];  // just below the tile: keep the +1 neighbour reachable
         if (lo[a] < -1 || lo[a] > o.L[a]) near = false;

@@ -29,7 +29,9 @@ int main(int argc, char** argv) {
     double v;
     static_assert(sizeof(v) == sizeof(bits), "");
     __builtin_memcpy(&v, &bits, 8);
-    double r = kind[0] == 'm' ? cbl::mimg(v, n) : (kind[0] == 'w' ? cbl::wrapd(v, n) : (double)cbl::wrapi((int)v, n));
+    double r = kind[0] == 'm' ? cbl::mimg(v, n)
+               : kind[0] == 'w' ? cbl::wrapd(v, n)
+               : kind[0] == 'n' ? (double)cbl::wrapi_near((int)v, n) : (double)cbl::wrapi((int)v, n);
     __builtin_memcpy(&bits, &r, 8);
     std::printf("%016llx\n", bits);
   }
@@ -125,5 +127,12 @@ def test_non_finite_and_huge_arguments_return(run):
 
 def test_integer_wrap(run):
     cases = [("i", n, a) for n in (4, 5, 256) for a in range(-3 * n, 3 * n)]
+    for (k, n, a), g in zip(cases, run(cases)):
+        assert g == a % n
+
+
+def test_division_free_wrap_over_its_range(run):
+    # wrapi_near (tile coordinates) equals the modulo over [-2n, 3n)
+    cases = [("n", n, a) for n in (4, 5, 37, 256) for a in range(-2 * n, 3 * n)]
     for (k, n, a), g in zip(cases, run(cases)):
         assert g == a % n
