@@ -34,14 +34,15 @@ sys.path.insert(0, ROOT)
 POP_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 
 
-def kernels_per_step(nb, mpf, fused):
-    """Kernel launches of one step of the library's graph: density + bulk collision + near-solid
-    collision (or the single fused pass), with bodies the force pass, repulsion (two or more bodies),
-    body update, three advection sweeps, kinetics (MPF on), flags and refill, and the closing kernel
-    (fluid mass, buffer flip)."""
-    k = (1 if fused else 2) + 1
+def kernels_per_step(nb, mpf, variant):
+    """Kernel launches of one step of the library's graph: density + bulk collision (variant 0), the
+    fused pass (1), or the edge fix-up + accumulating collision (2); the closing kernel (fluid mass,
+    buffer flip); with bodies the tile pass of psi (variants 1 and 2), the collision of the cells
+    next to a solid, the force pass, repulsion (two or more bodies), body update, three advection
+    sweeps, kinetics (MPF on), flags and refill."""
+    k = (1 if variant == 1 else 2) + 1
     if nb:
-        k += (0 if fused else 1) + 1 + (1 if nb > 1 else 0) + 1 + 3 + (1 if mpf else 0) + 2
+        k += (1 if variant in (1, 2) else 0) + 1 + 1 + (1 if nb > 1 else 0) + 1 + 3 + (1 if mpf else 0) + 2
     return k
 
 
@@ -307,7 +308,7 @@ def bench_batch(args, rank, world, local_rank):
             # persistent mode: one launch for the bulk pass of all instances, then each instance's side
             # chain (its step without the density and bulk collision kernels)
             "gpu_launches": args.steps * ((1 + len(ws) * (kernels_per_step(2, 1, False) - 2)) if binfo["mode"] == 1
-                                          else sum(n * kernels_per_step(2, 1, json.loads(c).get("lbm_variant") == 1)
+                                          else sum(n * kernels_per_step(2, 1, 1 if json.loads(c).get("lbm_variant") == 1 else 0)
                                                    for c, n in choices.items()))}
     if rk.root:
         print(json.dumps(line), flush=True)
@@ -406,6 +407,7 @@ def bench_cuda(args, rank, world, local_rank):
     workloads.build(sim, w)
     if args.lbm_variant is not None:
         sim.set_option("lbm_variant", args.lbm_variant)
+    variant = int(sim.get_option("lbm_variant"))
     # the bulk collision's live duration, from event nodes inside the replayed step graph
     sim.set_option("kernel_events", 1)
     stream = sim.stream
@@ -496,7 +498,7 @@ def bench_cuda(args, rank, world, local_rank):
                                   else step_traffic / (bpc * w.ncells)}},
             "phases_ms": {k: round(v, 5) for k, v in phases.items()},
             "gpu_launches": kernels_per_step(len(w.bodies), w.params.get("mpf_kinetics", 1),
-                                             args.lbm_variant == 1) * args.steps * len(reps),
+                                             variant) * args.steps * len(reps),
             "clocks": clk.summary(),
             "e2e": {"value": world * w.ncells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
@@ -540,8 +542,9 @@ def main():
                     help="repeat the timed region until about this much load has passed")
     ap.add_argument("--max-steps-total", type=int, default=600,
                     help="cap on warm-up plus timed steps (the workloads evolve with time)")
-    ap.add_argument("--lbm-variant", type=int, default=None, choices=[0, 1],
-                    help="lattice-Boltzmann pass: 0 split density + collision, 1 fused (default: the library's)")
+    ap.add_argument("--lbm-variant", type=int, default=None, choices=[0, 1, 2],
+                    help="lattice-Boltzmann pass: 0 split density + collision, 1 fused, 2 accumulating "
+                         "(default: the library's)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -234,10 +234,23 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms);
 cbl_status cbl_kernel_times(cbl_ctx* ctx, int max, float* ms, int* count);
 
 /* Execution options (no effect on the results beyond rounding order):
- *   "lbm_variant"  0 = split density and collision kernels (default), 1 = single fused pass that
- *                  marches along z with prefetch into shared memory (FP32 storage only;
- *                  CBL_ERR_UNSUPPORTED otherwise);
+ *   "lbm_variant"  how each step computes the density and psi that the Shan-Chen force needs
+ *                  (Sec. 3.2.3: psi of the post-streaming density at every neighbour):
+ *                  0 = split pass: a density kernel pulls every cell, then the collision kernel
+ *                  pulls it again (default);
+ *                  1 = fused pass: one kernel marches along z, producer warps compute psi of the
+ *                  plane ahead into shared memory, consumer warps collide;
+ *                  2 = accumulating pass: the collision kernel also sums the next step's density
+ *                  from the post-collision values it stores (shared-memory exchange within regions
+ *                  of 32 x acc_ty columns x acc_sz planes); the next step completes psi of the
+ *                  regions' edge cells from the populations of their outside sources and of the
+ *                  bodies' tiles from the populations. Each step pulls the populations once. A
+ *                  batch (cbl_batch_*) runs its instances with the split pass;
+ *   "fused_ty"     y extent of a fused block's consumer tile: 4 or 8 (default);
  *   "fused_tz"     z extent of a fused block (0 = derived from the SM count);
+ *   "acc_ty"       y extent of an accumulating region: 8 (default) or 16;
+ *   "acc_sz"       z extent of an accumulating region (0 = derived from the SM count: the fewest
+ *                  planes that give two waves of resident blocks);
  *   "lbm_block_x"  x extent of the 128-thread blocks of the split kernels: 32 (default), 64, 128;
  *   "graph_branches" 1 (default) = with bodies, the collision of the fluid cells next to a solid,
  *                  the solid-fluid force pass and the solid-solid repulsion run on a second branch
@@ -254,6 +267,11 @@ cbl_status cbl_kernel_times(cbl_ctx* ctx, int max, float* ms, int* count);
  *                  back by cbl_kernel_times; 0 (default) = none.
  * Unknown keys return CBL_ERR_ARG. The captured step graph is rebuilt at the next cbl_step. */
 cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value);
+
+/* The value in use of an execution option (keys as for cbl_set_option; "acc_sz" and "fused_tz"
+ * report the derived extent when none was requested). CBL_ERR_ARG for an unknown key or a NULL
+ * argument. */
+cbl_status cbl_get_option(cbl_ctx* ctx, const char* key, double* value);
 
 /* One lattice-Boltzmann time step that allocates nothing, for callers that cannot allocate device
  * memory (their memory belongs to another framework's pool, or their process must not call

@@ -2,7 +2,7 @@
 tile shape of the persistent batch kernel for a batch.
 
 Candidates for one lattice: the split density + collision kernels with 128-thread blocks of x extent
-32, 64 or 128, and the fused single pass. For a batch (tune_batch): the persistent kernel's tile
+32, 64 or 128, the fused single pass, and the accumulating pass with regions 8 or 16 rows deep. For a batch (tune_batch): the persistent kernel's tile
 shapes 32x4x1, 32x4x4, 32x4x8 and 64x2x4 cells. Each candidate is timed on the simulation it will run
 (three warm-up steps, then CUDA events around a few steps on the simulation's stream; the state
 advances, which does not matter for the choice); the fastest is applied and cached in a JSON file
@@ -22,6 +22,7 @@ _lock = threading.Lock()
 def candidates(prec):
     c = [dict(lbm_variant=0, lbm_block_x=bx) for bx in (32, 64, 128)]
     c.append(dict(lbm_variant=1, lbm_block_x=32))
+    c += [dict(lbm_variant=2, lbm_block_x=32, acc_ty=ty) for ty in (8, 16)]
     return c
 
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "cbl_time_phases": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "cbl_kernel_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "cbl_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
+    "cbl_get_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]),
     "cbl_lbm_step_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "cbl_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_P)]),
@@ -360,6 +361,11 @@ class Sim:
 
     def set_option(self, key, value):
         self._ck(self._lib.cbl_set_option(self._h, key.encode(), float(value)))
+
+    def get_option(self, key):
+        v = ctypes.c_double()
+        self._ck(self._lib.cbl_get_option(self._h, key.encode(), ctypes.byref(v)))
+        return v.value
 
     @property
     def stream(self):

@@ -59,6 +59,14 @@ struct cbl_ctx {
   double* mass_part = nullptr;
   unsigned n_mass_part = 0;
   int* blist = nullptr;  // fluid cells next to a solid (capacity: the sum of the tile sizes)
+  // accumulating pass (lbm_variant 2): the bulk collision also sums the next step's density; psi
+  // alternates between psi and psi2 with the parity, rhop holds the regions' edge partial sums
+  int acc_pass = 0;
+  int acc_ty = 8;          // y extent of its regions (8 or 16; x extent 32)
+  int acc_sz_req = 0;      // requested z extent of a region (0 = derived)
+  int acc_sz = 0;          // z extent in use
+  void *psi2 = nullptr, *rhop = nullptr;
+  bool psi_valid = false;  // psi of the current step is in place (else a whole-lattice density pass first)
   int fused_tz = 0;      // > 0: the density and the bulk collision run as one fused pass (k_fused)
   int fused_tz_req = 0;  // requested z extent of a fused block (0 = derived)
   int fused_ty = 8;      // y extent of a fused block's consumer tile (4 or 8; x extent 32)
@@ -385,6 +393,7 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
       }
   }
   ctx->ready = true;
+  ctx->psi_valid = false;
   ctx->t = 0;
   return CBL_OK;
 }
@@ -415,19 +424,37 @@ cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const dou
 // phases: 1 density (fused pass: psi over the bodies' tiles only), 2 bulk collision (fused pass:
 // with the density), 4 collision of the cells next to a solid
 static void enqueue_lbm(cbl_ctx* ctx, int phases, cudaStream_t s) {
+  if (ctx->acc_pass) {
+    // accumulating pass: phase 1 completes psi of this step (the regions' edge cells, then the bodies'
+    // tiles from the populations), phase 2 collides and sums the next step's density
+    if (phases & 1) {
+      ctx->ops.psi_fixup(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->psi, ctx->psi2, ctx->rhop, ctx->st, ctx->pp,
+                         ctx->acc_ty, ctx->acc_sz, s);
+      ctx->ops.density_tiles(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, (int)ctx->hb.size(),
+                             ctx->max_tile, ctx->psi, ctx->psi2, ctx->pp, s);
+    }
+    if (phases & 2)
+      ctx->ops.lbm_acc(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->rhop, ctx->db,
+                       ctx->mass_part, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->acc_ty, ctx->acc_sz, s);
+    if (phases & 4)
+      ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->db,
+                        ctx->mass_part, (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp,
+                        ctx->nbuf, ctx->blist, s, 4);
+    return;
+  }
   if (ctx->fused_tz) {
     if (phases & 1)
       ctx->ops.density_tiles(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, (int)ctx->hb.size(),
-                             ctx->max_tile, ctx->psi, ctx->pp, s);
+                             ctx->max_tile, ctx->psi, nullptr, ctx->pp, s);
     if (phases & 2)
       ctx->ops.lbm_fused(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, ctx->mass_part, ctx->st,
                          ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->fused_tz, ctx->fused_ty, s);
     if (phases & 4)
-      ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
-                        (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist, s,
-                        4);
+      ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, nullptr, ctx->db,
+                        ctx->mass_part, (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp,
+                        ctx->nbuf, ctx->blist, s, 4);
   } else {
-    ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->db, ctx->mass_part,
+    ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, nullptr, ctx->db, ctx->mass_part,
                     (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
                     s, phases);
   }
@@ -521,11 +548,42 @@ static void enqueue_side_chain(cbl_ctx* ctx) {
   launch_finish(ctx->mass_part, ctx->n_mass_part, ctx->st, ctx->s);
 }
 
+// Accumulating pass: its buffers, its kernel's shared-memory limit, its region depth, and psi of
+// the current step. psi is not in place after initialisation, a checkpoint load, a move of the
+// bodies, an option change or a batch step: then a whole-lattice density pass computes it, and
+// StepState::psi_skip tells the fix-up and the tile pass of the next step to leave it as it is.
+static cbl_status acc_prepare(cbl_ctx* ctx) {
+  if (!ctx->acc_pass) return CBL_OK;
+  const size_t N = (size_t)ctx->lat.N, el = ctx->prec == 0 ? 8 : 4;
+  if (!ctx->psi2) ctx->psi2 = dalloc(ctx, N * el);
+  if (!ctx->rhop) ctx->rhop = dalloc(ctx, N * el);
+  if (!ctx->psi2 || !ctx->rhop) return fail(ctx, CBL_ERR_OOM, "device allocation failed (accumulating pass)");
+  ctx->acc_sz = ctx->acc_sz_req > 0 ? ctx->acc_sz_req : ctx->ops.acc_sz(ctx->lat, ctx->prec, ctx->acc_ty, 2);
+  // a zero-plane call outside any capture sets the kernel's dynamic shared-memory limit
+  Lat none = ctx->lat;
+  none.nz = 0;
+  CK(ctx->ops.lbm_acc(ctx->prec, none, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->rhop, ctx->db,
+                      ctx->mass_part, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->acc_ty, 1, ctx->s));
+  if (!ctx->psi_valid) {
+    ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->db, ctx->mass_part,
+                      (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
+                      ctx->s, 1);
+    CK(cudaMemsetAsync(&ctx->st->psi_skip, 1, 1, ctx->s));
+    CK(cudaGetLastError());
+    ctx->psi_valid = true;
+  }
+  return CBL_OK;
+}
+
 cbl_status cbl_step(cbl_ctx* ctx, int nsteps) {
   if (!ctx) return fail(ctx, CBL_ERR_ARG, "NULL context");
   if (!ctx->ready) return fail(ctx, CBL_ERR_STATE, "cbl_step before cbl_init_fluid");
   if (nsteps < 0) return fail(ctx, CBL_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return CBL_OK;
+  {
+    const cbl_status sa = acc_prepare(ctx);
+    if (sa != CBL_OK) return sa;
+  }
   if (!ctx->gexec) {
     CK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
     enqueue_step(ctx);
@@ -597,6 +655,10 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
   cudaEvent_t ev[CBL_NPHASES + 1];
   for (int k = 0; k <= CBL_NPHASES; ++k) CK(cudaEventCreate(&ev[k]));
   double acc[CBL_NPHASES] = {0};
+  {
+    const cbl_status sa = acc_prepare(ctx);
+    if (sa != CBL_OK) return sa;
+  }
   CK(cudaMemsetAsync(&ctx->st->diag, 0, sizeof(int), ctx->s));
   for (int it = 0; it < nsteps; ++it) {
     CK(cudaEventRecord(ev[0], ctx->s));
@@ -803,6 +865,7 @@ cbl_status cbl_move_bodies(cbl_ctx* ctx, const double* X, const double* Qn, cons
   for (int k = 0; k < 3 * nb; ++k)
     if ((V && !std::isfinite(V[k])) || (W && !std::isfinite(W[k])))
       return fail(ctx, CBL_ERR_ARG, "velocities must be finite");
+  ctx->psi_valid = false;  // flags and populations change
   std::vector<BodyDev> h0(nb), h(nb);
   CK(cudaMemcpyAsync(h0.data(), ctx->db, sizeof(BodyDev) * nb, cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
@@ -1108,6 +1171,7 @@ cbl_status cbl_load(cbl_ctx* ctx, const char* path) {
   CK(cudaStreamSynchronize(ctx->s));
   ctx->t = h.t;
   ctx->ready = true;
+  ctx->psi_valid = false;
   return CBL_OK;
 }
 
@@ -1136,6 +1200,23 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
   return CBL_OK;
 }
 
+cbl_status cbl_get_option(cbl_ctx* ctx, const char* key, double* value) {
+  if (!ctx || !key || !value) return fail(ctx, CBL_ERR_ARG, "NULL argument");
+  const std::string k(key);
+  if (k == "lbm_variant") *value = ctx->acc_pass ? 2 : (ctx->fused_tz ? 1 : 0);
+  else if (k == "acc_ty") *value = ctx->acc_ty;
+  else if (k == "acc_sz") *value = ctx->acc_sz_req > 0 ? ctx->acc_sz_req : ctx->ops.acc_sz(ctx->lat, ctx->prec, ctx->acc_ty, 2);
+  else if (k == "fused_ty") *value = ctx->fused_ty;
+  else if (k == "fused_tz") *value = ctx->fused_tz;
+  else if (k == "lbm_block_x") *value = ctx->block_x;
+  else if (k == "node_priority") *value = ctx->node_priority;
+  else if (k == "graph_branches") *value = ctx->branches;
+  else if (k == "tile_tail") *value = ctx->tile_tail;
+  else if (k == "kernel_events") *value = ctx->kev;
+  else return fail(ctx, CBL_ERR_ARG, "unknown option " + k);
+  return CBL_OK;
+}
+
 // z extent of the fused pass's blocks: the requested one, or enough blocks for four waves
 static int fused_tz_of(const cbl_ctx* ctx) {
   return ctx->fused_tz_req > 0 ? ctx->fused_tz_req : ctx->ops.fused_tz(ctx->lat, ctx->prec, ctx->fused_ty, 4);
@@ -1146,8 +1227,17 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
   const std::string k(key);
   if (k == "lbm_variant") {
     const int v = (int)value;
-    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "lbm_variant must be 0 or 1");
-    ctx->fused_tz = v ? fused_tz_of(ctx) : 0;
+    if (v != 0 && v != 1 && v != 2) return fail(ctx, CBL_ERR_ARG, "lbm_variant must be 0, 1 or 2");
+    ctx->fused_tz = v == 1 ? fused_tz_of(ctx) : 0;
+    ctx->acc_pass = v == 2;
+  } else if (k == "acc_ty") {
+    const int v = (int)value;
+    if (v != 8 && v != 16) return fail(ctx, CBL_ERR_ARG, "acc_ty must be 8 or 16");
+    ctx->acc_ty = v;
+  } else if (k == "acc_sz") {
+    const int v = (int)value;
+    if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "acc_sz out of range");
+    ctx->acc_sz_req = v;
   } else if (k == "fused_tz") {
     const int v = (int)value;
     if (v < 0 || v > ctx->p.nz) return fail(ctx, CBL_ERR_ARG, "fused_tz out of range");
@@ -1188,6 +1278,7 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
   } else {
     return fail(ctx, CBL_ERR_ARG, "unknown option " + k);
   }
+  ctx->psi_valid = false;
   if (ctx->gexec) {
     cudaStreamSynchronize(ctx->s);
     cudaGraphExecDestroy(ctx->gexec);
@@ -1237,7 +1328,9 @@ static cudaError_t batch_capture(cbl_batch* b, int diag, cudaGraph_t* g) {
     cudaStream_t br = b->branches[k];
     cudaStreamWaitEvent(br, b->events[0], 0);
     cudaStream_t keep = c->s;
+    const int keep_acc = c->acc_pass;
     c->s = br;
+    c->acc_pass = 0;  // a batch runs its instances with the split or fused pass (one psi buffer)
     if (b->mode == 1) {
       enqueue_side_chain(c);
     } else {
@@ -1245,6 +1338,7 @@ static cudaError_t batch_capture(cbl_batch* b, int diag, cudaGraph_t* g) {
       enqueue_step(c);
     }
     c->s = keep;
+    c->acc_pass = keep_acc;
     cudaEventRecord(b->events[k + 1], br);
     cudaStreamWaitEvent(b->s, b->events[k + 1], 0);
   }
@@ -1410,6 +1504,7 @@ cbl_status cbl_batch_step(cbl_batch* b, int nsteps) {
   for (cbl_ctx* c : b->ctxs) {
     c->t += nsteps;
     c->fsum_steps += nsteps;
+    c->psi_valid = false;
   }
   return CBL_OK;
 }

@@ -129,7 +129,7 @@ struct StepState {
   int parity;   // which population buffer is the source this step
   int diag;     // 1: the collision writes rho and v
   int err;      // error word
-  int pad;
+  int psi_skip;  // accumulating pass: psi of this step came from a whole-lattice density pass
   double mass;       // fluid mass of the current step (accumulating)
   double last_mass;  // fluid mass of the last completed step
   unsigned long long lost_refills;
@@ -222,16 +222,25 @@ extern thread_local int g_launch_share;
 #define CBL_LBM_LAUNCHERS                                                                              \
   void set_fp16_weights(cudaStream_t s);                                                             \
   void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi, \
-                       const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st,      \
-                       double* diag_rho, double* diag_vel, const PhysParams& pp, void* nbuf,          \
-                       const int* blist, cudaStream_t s, int phases);                                 \
+                       void* psi_b, const BodyDev* bodies, double* mass_part, unsigned blocks,        \
+                       StepState* st, double* diag_rho, double* diag_vel, const PhysParams& pp,       \
+                       void* nbuf, const int* blist, cudaStream_t s, int phases);                     \
+  int acc_sz(const Lat& lat, int prec, int ty, int waves);                                          \
+  cudaError_t launch_lbm_acc(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,    \
+                             void* psi_a, void* psi_b, void* rhop, const BodyDev* bodies,           \
+                             double* mass_part, StepState* st, double* diag_rho, double* diag_vel,  \
+                             const PhysParams& pp, int ty, int sz, cudaStream_t s);                 \
+  void launch_psi_fixup(int prec, const Lat& lat, const void* fa, const void* fb, void* psi_a,       \
+                        void* psi_b, const void* rhop, const StepState* st, const PhysParams& pp,    \
+                        int ty, int sz, cudaStream_t s);                                             \
   int fused_tz(const Lat& lat, int prec, int ty, int waves);                                        \
   void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags,         \
                         const BodyDev* bodies, double* mass_part, StepState* st, double* diag_rho,   \
                         double* diag_vel, const PhysParams& pp, int tz, int ty, cudaStream_t s);     \
   void launch_density_tiles(int prec, const Lat& lat, const void* fa, const void* fb,                \
                             const StepState* st, const uint16_t* flags, const BodyDev* bodies, int nb, \
-                            int max_tile, void* psi, const PhysParams& pp, cudaStream_t s);          \
+                            int max_tile, void* psi, void* psi_b, const PhysParams& pp,              \
+                            cudaStream_t s);                                                         \
   void launch_boundary(int prec, const Lat& lat, const void* fa, const void* fb, const uint16_t* flags, \
                        const BodyDev* bodies, int nb, double* acc, const int* blist, const StepState* st, \
                        const void* nbuf, double G, cudaStream_t s);                                   \
@@ -261,6 +270,9 @@ struct LbmOps {
   int q;
   decltype(&q19::set_fp16_weights) set_fp16_weights;
   decltype(&q19::launch_lbm_step) lbm_step;
+  decltype(&q19::acc_sz) acc_sz;
+  decltype(&q19::launch_lbm_acc) lbm_acc;
+  decltype(&q19::launch_psi_fixup) psi_fixup;
   decltype(&q19::fused_tz) fused_tz;
   decltype(&q19::launch_lbm_fused) lbm_fused;
   decltype(&q19::launch_density_tiles) density_tiles;
@@ -275,7 +287,8 @@ struct LbmOps {
 };
 inline LbmOps lbm_ops(int q) {
 #define CBL_OPS(ns) \
-  LbmOps { q, &ns::set_fp16_weights, &ns::launch_lbm_step, &ns::fused_tz, &ns::launch_lbm_fused,                   \
+  LbmOps { q, &ns::set_fp16_weights, &ns::launch_lbm_step, &ns::acc_sz, &ns::launch_lbm_acc,                     \
+           &ns::launch_psi_fixup, &ns::fused_tz, &ns::launch_lbm_fused,                                             \
            &ns::launch_density_tiles, &ns::launch_boundary,                                                             \
            &ns::launch_read_populations, &ns::launch_zero_solid, &ns::launch_init_fluid, &ns::launch_refill,        \
            &ns::batch_tile, &ns::batch_blocks_per_sm, &ns::launch_batch_lbm }

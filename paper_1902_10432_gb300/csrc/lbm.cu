@@ -56,12 +56,14 @@ struct St<double> {
   using R = double;
   __device__ static R ld(const double* p, size_t k, int) { return __ldg(p + k); }
   __device__ static void st(double* p, size_t k, int, R v) { p[k] = v; }
+  __device__ static R rt(R v, int) { return v; }
 };
 template <>
 struct St<float> {
   using R = float;
   __device__ static R ld(const float* p, size_t k, int) { return __ldg(p + k); }
   __device__ static void st(float* p, size_t k, int, R v) { p[k] = v; }
+  __device__ static R rt(R v, int) { return v; }
 };
 template <>
 struct St<__half> {
@@ -70,6 +72,8 @@ struct St<__half> {
   __device__ static R ld(const __half* p, size_t k, int i) { return __half2float(__ldg(p + k)) + c_wh[i]; }
   __device__ static R from_raw(unsigned short h, int i) { return __half2float(__ushort_as_half(h)) + c_wh[i]; }
   __device__ static void st(__half* p, size_t k, int i, R v) { p[k] = __float2half_rn(v - c_wh[i]); }
+  // the value a later load of the stored population returns
+  __device__ static R rt(R v, int i) { return __half2float(__float2half_rn(v - c_wh[i])) + c_wh[i]; }
 };
 
 // Density and pseudo-potential of a fluid cell next to a solid, as its collision used them; the
@@ -161,12 +165,14 @@ __device__ __forceinline__ void pull(const S* __restrict__ f, const uint16_t* __
 // f*_i = (1 - 1/tau) f_i + S_i + A_i, f*_opp = (1 - 1/tau) f_opp + S_i - A_i with
 // S_i = (rho w_i / tau)(1 + 4.5 (c.v)^2 - 1.5 v.v) + (1 - 1/2tau) w_i (9 (c.v)(c.F) - 3 v.F),
 // A_i = 3 w_i ((rho / tau) c.v + (1 - 1/2tau) c.F).
-template <typename S>
+// OUT: fo receives the stored values as a later load returns them (the accumulating pass sums them
+// into the next step's density).
+template <typename S, bool OUT = false>
 __device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, long long n,
                                               const typename St<S>::R fi[Q], typename St<S>::R rho,
                                               typename St<S>::R vx, typename St<S>::R vy, typename St<S>::R vz,
                                               typename St<S>::R Fx, typename St<S>::R Fy, typename St<S>::R Fz,
-                                              typename St<S>::R tau) {
+                                              typename St<S>::R tau, typename St<S>::R* fo = nullptr) {
   using R = typename St<S>::R;
   const R itau = (R)1 / tau;
   const R keep = (R)1 - itau;
@@ -178,7 +184,9 @@ __device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, lon
   const R fv = -(R)3 * pref * vF;       // even forcing part without (c.v)(c.F)
   {
     const R w = (R)w_of(0);
-    St<S>::st(dst, (size_t)n, 0, keep * fi[0] + w * (ro * base + fv));
+    const R v0 = keep * fi[0] + w * (ro * base + fv);
+    St<S>::st(dst, (size_t)n, 0, v0);
+    if constexpr (OUT) fo[0] = St<S>::rt(v0, 0);
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -187,8 +195,13 @@ __device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, lon
     const R w = (R)w_of(i);
     const R sym = w * (ro * (base + (R)4.5 * cu * cu) + fv + (R)9 * pref * cu * cF);
     const R anti = (R)3 * w * (ro * cu + pref * cF);
-    St<S>::st(dst, (size_t)i * N + n, i, keep * fi[i] + sym + anti);
-    St<S>::st(dst, (size_t)(i + 1) * N + n, i + 1, keep * fi[i + 1] + sym - anti);
+    const R vp = keep * fi[i] + sym + anti, vm = keep * fi[i + 1] + sym - anti;
+    St<S>::st(dst, (size_t)i * N + n, i, vp);
+    St<S>::st(dst, (size_t)(i + 1) * N + n, i + 1, vm);
+    if constexpr (OUT) {
+      fo[i] = St<S>::rt(vp, i);
+      fo[i + 1] = St<S>::rt(vm, i + 1);
+    }
   }
 }
 
@@ -197,10 +210,13 @@ __global__ void __launch_bounds__(128) k_density(const S* __restrict__ fa, const
                                                  const StepState* __restrict__ st,
                                                  const uint16_t* __restrict__ flags,
                                                  const BodyDev* __restrict__ bodies,
-                                                 typename St<S>::R* __restrict__ psi, Lat lat, double rho0,
+                                                 typename St<S>::R* __restrict__ psi_a,
+                                                 typename St<S>::R* __restrict__ psi_b, Lat lat, double rho0,
                                                  float rho0_f) {
   using R = typename St<S>::R;
   const S* __restrict__ f = st->parity ? fb : fa;
+  // two psi buffers (accumulating pass): the current step's is the one the parity names
+  R* __restrict__ psi = (psi_b && st->parity) ? psi_b : psi_a;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
   if (x >= lat.nx || y >= lat.ny) return;
   const Cell c = make_cell(x, y, z, lat);
@@ -299,7 +315,7 @@ struct CollideMinBlocks<__half> {
 // the bulk kernel carries neither the flag loads (on which the population addresses would depend)
 // nor the registers of the wall terms. Returns rho.
 // psi_at(i): psi at x + c_i (i >= 1) and at x itself (i = 0).
-template <typename S, bool NEAR, typename PsiAt>
+template <typename S, bool NEAR, typename PsiAt, bool OUT = false>
 __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__ src, S* __restrict__ dst,
                                                            const uint16_t* __restrict__ flags,
                                                            const PsiAt& psi_at,
@@ -308,7 +324,8 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
                                                            double* __restrict__ diag_vel, const Lat& lat,
                                                            const PhysParams& pp,
                                                            RhoPsi<typename St<S>::R>* __restrict__ nbuf,
-                                                           const Cell& c, long long n) {
+                                                           const Cell& c, long long n,
+                                                           typename St<S>::R* fo = nullptr) {
   using R = typename St<S>::R;
   const size_t N = (size_t)lat.Ns;  // population stride
   R my_mass = 0;
@@ -370,7 +387,7 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
       vy = my * ir;
       vz = mz * ir;
     }
-    collide_store<S>(dst, N, n, fi, rho, vx, vy, vz, Fx, Fy, Fz, par<R>(pp.tau, pp.tau_f));
+    collide_store<S, OUT>(dst, N, n, fi, rho, vx, vy, vz, Fx, Fy, Fz, par<R>(pp.tau, pp.tau_f), fo);
     if (diag) {
       diag_rho[n] = (double)rho;
       diag_vel[3 * n] = (double)vx;
@@ -505,7 +522,8 @@ __global__ void __launch_bounds__(128, CollideMinBlocks<S>::value) k_collide(S* 
 template <typename S>
 __global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __restrict__ fb,
                                                       const uint16_t* __restrict__ flags,
-                                                      const typename St<S>::R* __restrict__ psi,
+                                                      const typename St<S>::R* __restrict__ psi_a,
+                                                      const typename St<S>::R* __restrict__ psi_b,
                                                       const BodyDev* __restrict__ bodies,
                                                       double* __restrict__ mass_part,
                                                       const StepState* __restrict__ st,
@@ -513,6 +531,7 @@ __global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __r
                                                       const int* __restrict__ blist, Lat lat, PhysParams pp,
                                                       RhoPsi<typename St<S>::R>* __restrict__ nbuf) {
   using R = typename St<S>::R;
+  const R* __restrict__ psi = (psi_b && st->parity) ? psi_b : psi_a;
   const int diag = st->diag;
   const S* __restrict__ src = st->parity ? fb : fa;
   S* __restrict__ dst = st->parity ? fa : fb;
@@ -525,6 +544,207 @@ __global__ void __launch_bounds__(128) k_collide_near(S* __restrict__ fa, S* __r
     my_mass += collide_fluid<S, true>(src, dst, flags, psi_at, bodies, diag, diag_rho, diag_vel, lat, pp, nbuf, c, n);
   }
   add_mass_slot(mass_part, my_mass, blockIdx.x * 7u + 3u);
+}
+
+// ---- accumulating pass (lbm_variant 2) ---------------------------------------------------------
+// The force of step t needs psi of the post-streaming density at every neighbour (Sec. 3.2.3,
+// Eq. mean_field_potential), so the split pass pulls every cell's populations twice per step: once
+// for rho and psi, once for the collision. This pass computes the next step's density while it
+// collides: rho_{t+1}(x) = sum_i f*_i(x - c_i) is the pull of the populations it stores.
+//
+// A block owns a region of 32 x TY columns and marches through sz planes along z. After colliding a
+// plane it puts the stored post-collision values in shared memory; each thread then adds, for its
+// own column, the values whose source lies in the region, into the targets one plane below, in and
+// above (three running sums, one barrier per plane). A cell's sum is complete when all its sources
+// lie in the region: the region's interior cells, whose psi_{t+1} = 1 - exp(-rho / rho0) this pass
+// stores into the other psi buffer (read by no other block: a block's gather reaches one cell into
+// its neighbours, which are edge cells there). The edge cells (first or last column, row or plane
+// of the region) store the partial sum instead; the fix-up pass of the next step adds the sources
+// outside the region. Cells whose sources include a cell next to a solid (collided on the side
+// branch, not here) or a solid lie in a body's tile, and the tile pass of the next step recomputes
+// their psi from the populations, as the split pass does.
+
+// Sources of cell (x, y, z) that lie in its region: the test that splits the sum between this pass
+// and the fix-up (no periodic wrap: a wrapped source counts as outside even in a one-region axis).
+__device__ __forceinline__ bool acc_source_inside(int sx, int sy, int sz_, int x0, int y0, int zb, int nvx, int nvy,
+                                                  int ze) {
+  return sx >= x0 && sx < x0 + nvx && sy >= y0 && sy < y0 + nvy && sz_ >= zb && sz_ < ze;
+}
+
+template <typename S, int TY, int MINB>
+__global__ void __launch_bounds__(32 * TY, MINB) k_collide_acc(S* __restrict__ fa, S* __restrict__ fb,
+                                                                const uint16_t* __restrict__ flags,
+                                                                typename St<S>::R* __restrict__ psi_a,
+                                                                typename St<S>::R* __restrict__ psi_b,
+                                                                typename St<S>::R* __restrict__ rhop,
+                                                                const BodyDev* __restrict__ bodies,
+                                                                double* __restrict__ mass_part,
+                                                                const StepState* __restrict__ st,
+                                                                double* __restrict__ diag_rho,
+                                                                double* __restrict__ diag_vel, Lat lat,
+                                                                PhysParams pp, int sz) {
+  using R = typename St<S>::R;
+  constexpr int NT = 32 * TY;
+  extern __shared__ __align__(16) unsigned char acc_smem[];
+  R* sf = reinterpret_cast<R*>(acc_smem);  // [2][Q - 1][NT]: stored values of the plane, by direction
+  const size_t N = (size_t)lat.Ns;
+  const int diag = st->diag;
+  const int parity = st->parity;
+  const S* __restrict__ src = parity ? fb : fa;
+  S* __restrict__ dst = parity ? fa : fb;
+  const R* __restrict__ psi = parity ? psi_b : psi_a;
+  R* __restrict__ psi_next = parity ? psi_a : psi_b;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY, zb = blockIdx.z * sz;
+  const int ze = min(zb + sz, lat.nz);
+  const int nvx = min(32, lat.nx - x0), nvy = min(TY, lat.ny - y0);
+  const bool valid = tx < nvx && ty < nvy;
+  const int x = valid ? x0 + tx : x0, y = valid ? y0 + ty : y0;
+  const bool edge = tx == 0 || tx == nvx - 1 || ty == 0 || ty == nvy - 1;
+  const size_t col = (size_t)x + (size_t)lat.nx * (size_t)y, plane = (size_t)lat.nx * (size_t)lat.ny;
+  R am = 0, a0 = 0, ap = 0;  // running sums of the targets one plane below, in and above
+  MassAcc<R> mass;
+  for (int z = zb; z < ze; ++z) {
+    R fo[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fo[i] = (R)0;
+    if (valid) {
+      const Cell c = make_cell(x, y, z, lat);
+      const long long n = c.n;
+      const uint16_t fl = flags[n];
+      if (fl & F_SOLID) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) St<S>::st(dst, (size_t)i * N + n, i, (R)0);
+        if (diag) {
+          diag_rho[n] = 0.0;
+          diag_vel[3 * n] = 0.0;
+          diag_vel[3 * n + 1] = 0.0;
+          diag_vel[3 * n + 2] = 0.0;
+        }
+      } else if (!(fl & F_NEAR)) {
+        auto psi_at = [&](int i) -> R { return i ? psi[nbr(c, lat, i, +1)] : psi[n]; };
+        mass.add(collide_fluid<S, false, decltype(psi_at), true>(src, dst, flags, psi_at, bodies, diag, diag_rho,
+                                                                 diag_vel, lat, pp, nullptr, c, n, fo));
+      }
+    }
+    R* buf = sf + (size_t)(z & 1) * (Q - 1) * NT;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) buf[(i - 1) * NT + threadIdx.x] = fo[i];
+    // one barrier per plane: the buffers alternate, and a thread writes a buffer again only after
+    // the next plane's barrier, which every reader of this plane has passed
+    __syncthreads();
+    a0 += fo[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int sx = tx - cx_of(i), sy = ty - cy_of(i);
+      if (sx >= 0 && sx < nvx && sy >= 0 && sy < nvy) {
+        const R v = buf[(i - 1) * NT + sy * 32 + sx];
+        if (cz_of(i) > 0) ap += v;
+        else if (cz_of(i) < 0) am += v;
+        else a0 += v;
+      }
+    }
+    if (z > zb && valid) {
+      const size_t n = col + plane * (size_t)(z - 1);
+      if (edge || z - 1 == zb) rhop[n] = am;
+      else psi_next[n] = (R)1 - exp(-am / par<R>(pp.rho0, pp.rho0_f));
+    }
+    am = a0;
+    a0 = ap;
+    ap = (R)0;
+  }
+  if (valid) rhop[col + plane * (size_t)(ze - 1)] = am;  // the last plane: an edge plane
+  add_mass_slot(mass_part, mass, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+}
+
+// Fix-up of the accumulating pass, at the start of the next step: psi of the regions' edge cells
+// from the partial sum and the populations of the sources outside the region (Eq. lb_streaming
+// pulled from the stored buffer). The cells next to a solid and their neighbours are left to the
+// tile pass that follows. One thread per edge cell, in three ranges: the regions' first and last
+// planes (whole rows), the first and last rows of the other planes (whole rows), the first and last
+// columns of the remaining rows.
+struct AccGeom {
+  int ty, sz, nxr, nyr, nzr;  // region extents in y and z; regions per axis
+  long long n1, n2, n3;       // edge cells of the three ranges
+};
+
+inline AccGeom acc_geom(const Lat& lat, int ty, int sz) {
+  AccGeom g;
+  g.ty = ty;
+  g.sz = sz;
+  g.nxr = (lat.nx + 31) / 32;
+  g.nyr = (lat.ny + ty - 1) / ty;
+  g.nzr = (lat.nz + sz - 1) / sz;
+  g.n1 = 2LL * g.nzr * lat.ny * lat.nx;
+  g.n2 = 2LL * g.nyr * lat.nz * lat.nx;
+  g.n3 = 2LL * g.nxr * lat.ny * lat.nz;
+  return g;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_psi_fixup(const S* __restrict__ fa, const S* __restrict__ fb,
+                                                   typename St<S>::R* __restrict__ psi_a,
+                                                   typename St<S>::R* __restrict__ psi_b,
+                                                   const typename St<S>::R* __restrict__ rhop,
+                                                   const StepState* __restrict__ st, Lat lat, double rho0,
+                                                   float rho0_f, AccGeom g) {
+  using R = typename St<S>::R;
+  if (st->psi_skip) return;
+  const S* __restrict__ f = st->parity ? fb : fa;
+  R* __restrict__ psi = st->parity ? psi_b : psi_a;
+  const size_t N = (size_t)lat.Ns;
+  const long long total = g.n1 + g.n2 + g.n3;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    if (k < g.n1) {
+      // first (side 0) or last (side 1) plane of a region, whole plane
+      const long long r = k / lat.nx;
+      x = (int)(k - r * lat.nx);
+      const long long q = r / lat.ny;
+      y = (int)(r - q * lat.ny);
+      const int zr = (int)(q >> 1), side = (int)(q & 1);
+      const int zb = zr * g.sz, ze = min(zb + g.sz, lat.nz);
+      if (side && ze - 1 == zb) continue;
+      z = side ? ze - 1 : zb;
+    } else if (k < g.n1 + g.n2) {
+      // first or last row of a region, planes that are not a region's first or last
+      const long long kk = k - g.n1;
+      const long long r = kk / lat.nx;
+      x = (int)(kk - r * lat.nx);
+      const long long q = r / lat.nz;
+      z = (int)(r - q * lat.nz);
+      const int yr = (int)(q >> 1), side = (int)(q & 1);
+      const int y0 = yr * g.ty, y1 = min(y0 + g.ty, lat.ny) - 1;
+      if (side && y1 == y0) continue;
+      y = side ? y1 : y0;
+      const int zb = (z / g.sz) * g.sz, ze = min(zb + g.sz, lat.nz);
+      if (z == zb || z == ze - 1) continue;
+    } else {
+      // first or last column of a region, rows and planes that are not a region's first or last
+      const long long kk = k - g.n1 - g.n2;
+      const int e = (int)(kk % (2 * g.nxr));
+      const long long r = kk / (2 * g.nxr);
+      y = (int)(r % lat.ny);
+      z = (int)(r / lat.ny);
+      const int x0 = (e >> 1) * 32, x1 = min(x0 + 32, lat.nx) - 1;
+      if ((e & 1) && x1 == x0) continue;
+      x = (e & 1) ? x1 : x0;
+      const int zb = (z / g.sz) * g.sz, ze = min(zb + g.sz, lat.nz);
+      if (z == zb || z == ze - 1) continue;
+      const int y0 = (y / g.ty) * g.ty, y1 = min(y0 + g.ty, lat.ny) - 1;
+      if (y == y0 || y == y1) continue;
+    }
+    const int x0 = x & ~31, y0 = (y / g.ty) * g.ty, zb = (z / g.sz) * g.sz;
+    const int nvx = min(32, lat.nx - x0), nvy = min(g.ty, lat.ny - y0), ze = min(zb + g.sz, lat.nz);
+    const Cell c = make_cell(x, y, z, lat);
+    R rho = rhop[c.n];
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (!acc_source_inside(x - cx_of(i), y - cy_of(i), z - cz_of(i), x0, y0, zb, nvx, nvy, ze))
+        rho += St<S>::ld(f, (size_t)i * N + (size_t)nbr(c, lat, i, -1), i);
+    psi[c.n] = (R)1 - exp(-rho / par<R>(rho0, rho0_f));
+  }
 }
 
 // the cell (gx, gy, gz) lies in the tile of a body with a lower id than `self` (so that a pass over
@@ -690,9 +910,13 @@ __global__ void __launch_bounds__(256) k_density_tiles(const S* __restrict__ fa,
                                                        const StepState* __restrict__ st,
                                                        const uint16_t* __restrict__ flags,
                                                        const BodyDev* __restrict__ bodies,
-                                                       typename St<S>::R* __restrict__ psi, Lat lat, double rho0,
-                                                       float rho0_f) {
+                                                       typename St<S>::R* __restrict__ psi_a,
+                                                       typename St<S>::R* __restrict__ psi_b, Lat lat,
+                                                       double rho0, float rho0_f) {
+  // accumulating pass: nothing to do in a step whose psi a whole-lattice density pass computed
+  if (psi_b && st->psi_skip) return;
   const S* __restrict__ f = st->parity ? fb : fa;
+  typename St<S>::R* __restrict__ psi = (psi_b && st->parity) ? psi_b : psi_a;
   const int self = blockIdx.y;
   const BodyDev& b = bodies[self];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1294,51 +1518,139 @@ void launch_lbm_fused(int prec, const Lat& lat, void* fa, void* fb, const uint16
 
 void launch_density_tiles(int prec, const Lat& lat, const void* fa, const void* fb, const StepState* st,
                           const uint16_t* flags, const BodyDev* bodies, int nb, int max_tile, void* psi,
-                          const PhysParams& pp, cudaStream_t s) {
+                          void* psi_b, const PhysParams& pp, cudaStream_t s) {
   if (!nb) return;
   const dim3 grid((unsigned)((max_tile + 255) / 256), (unsigned)nb);
   if (prec == 0)
     k_density_tiles<double><<<grid, 256, 0, s>>>((const double*)fa, (const double*)fb, st, flags, bodies,
-                                                 (double*)psi, lat, pp.rho0, pp.rho0_f);
+                                                 (double*)psi, (double*)psi_b, lat, pp.rho0, pp.rho0_f);
   else if (prec == 1)
     k_density_tiles<float><<<grid, 256, 0, s>>>((const float*)fa, (const float*)fb, st, flags, bodies, (float*)psi,
-                                                lat, pp.rho0, pp.rho0_f);
+                                                (float*)psi_b, lat, pp.rho0, pp.rho0_f);
   else
     k_density_tiles<__half><<<grid, 256, 0, s>>>((const __half*)fa, (const __half*)fb, st, flags, bodies,
-                                                 (float*)psi, lat, pp.rho0, pp.rho0_f);
+                                                 (float*)psi, (float*)psi_b, lat, pp.rho0, pp.rho0_f);
 }
 
 template <typename S>
-static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, const BodyDev* bodies,
-                       double* mass_part, unsigned blocks, StepState* st, double* diag_rho, double* diag_vel,
-                       const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s, int phases) {
+static void lbm_step_t(const Lat& lat, S* fa, S* fb, const uint16_t* flags, void* psi, void* psi_b,
+                       const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
+                       double* diag_vel, const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s,
+                       int phases) {
   using R = typename St<S>::R;
   // `blocks` carries the x extent of the 128-thread blocks (32, 64 or 128)
   const int bx = blocks == 64 || blocks == 128 ? (int)blocks : 32, by = 128 / bx;
   const dim3 blk(bx, by, 1);
   const dim3 grid((lat.nx + bx - 1) / bx, (lat.ny + by - 1) / by, lat.nz);
-  if (phases & 1) k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, lat, pp.rho0, pp.rho0_f);
+  if (phases & 1)
+    k_density<S><<<grid, blk, 0, s>>>(fa, fb, st, flags, bodies, (R*)psi, (R*)psi_b, lat, pp.rho0, pp.rho0_f);
   if (phases & 2)
     k_collide<S><<<grid, blk, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho, diag_vel, lat,
                                       pp, (RhoPsi<R>*)nbuf);
   if ((phases & 4) && blist)
-    k_collide_near<S><<<std::max(1, 2 * sm_count() / g_launch_share), 128, 0, s>>>(fa, fb, flags, (const R*)psi, bodies, mass_part, st, diag_rho,
-                                                      diag_vel, blist, lat, pp, (RhoPsi<R>*)nbuf);
+    k_collide_near<S><<<std::max(1, 2 * sm_count() / g_launch_share), 128, 0, s>>>(
+        fa, fb, flags, (const R*)psi, (const R*)psi_b, bodies, mass_part, st, diag_rho, diag_vel, blist, lat, pp,
+        (RhoPsi<R>*)nbuf);
 }
 
-void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi,
+void launch_lbm_step(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi, void* psi_b,
                      const BodyDev* bodies, double* mass_part, unsigned blocks, StepState* st, double* diag_rho,
                      double* diag_vel, const PhysParams& pp, void* nbuf, const int* blist, cudaStream_t s,
                      int phases) {
   if (prec == 0)
-    lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                       pp, nbuf, blist, s, phases);
+    lbm_step_t<double>(lat, (double*)fa, (double*)fb, flags, psi, psi_b, bodies, mass_part, blocks, st, diag_rho,
+                       diag_vel, pp, nbuf, blist, s, phases);
   else if (prec == 1)
-    lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                      pp, nbuf, blist, s, phases);
+    lbm_step_t<float>(lat, (float*)fa, (float*)fb, flags, psi, psi_b, bodies, mass_part, blocks, st, diag_rho,
+                      diag_vel, pp, nbuf, blist, s, phases);
   else
-    lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, bodies, mass_part, blocks, st, diag_rho, diag_vel,
-                       pp, nbuf, blist, s, phases);
+    lbm_step_t<__half>(lat, (__half*)fa, (__half*)fb, flags, psi, psi_b, bodies, mass_part, blocks, st, diag_rho,
+                       diag_vel, pp, nbuf, blist, s, phases);
+}
+
+// Accumulating pass: blocks of 32 x ty threads (ty = 8 or 16) marching sz planes. Resident blocks
+// per SM asked of the compiler: 64 registers per thread for FP32 storage, 80 for binary16, 128 for
+// FP64.
+static int acc_min_blocks(int prec, int ty) {
+  const int regs = prec == 0 ? 128 : (prec == 1 ? 64 : 80);
+  return std::max(1, 65536 / (regs * 32 * ty));
+}
+
+template <typename S, int TY>
+static size_t acc_smem() {
+  return (size_t)2 * (Q - 1) * 32 * TY * sizeof(typename St<S>::R);
+}
+
+// z extent of the accumulating pass's regions. A block marches its whole region, so the pass takes
+// (waves of resident blocks) x (planes per region); the regions' edge planes add fix-up work. The
+// extent minimises waves x planes + EDGE x (edge planes per resident block), over at most `waves`
+// x 4 waves (EDGE: a fix-up plane costs about a fifth of a marched plane).
+int acc_sz(const Lat& lat, int prec, int ty, int waves) {
+  const long long cols = (long long)((lat.nx + 31) / 32) * ((lat.ny + ty - 1) / ty);
+  const long long slots = (long long)acc_min_blocks(prec, ty) * sm_count();
+  const double EDGE = 0.2;
+  int best = lat.nz;
+  double best_cost = 1e300;
+  for (int sz = 1; sz <= lat.nz; ++sz) {
+    const long long nzc = (lat.nz + sz - 1) / sz;
+    if (sz < lat.nz && nzc * cols > slots * waves * 4) continue;
+    const long long w = (nzc * cols + slots - 1) / slots;
+    const double cost = (double)(w * sz) + EDGE * 2.0 * (double)(nzc * cols) / (double)slots;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = sz;
+    }
+  }
+  return best;
+}
+
+template <typename S, int TY, int MINB>
+static cudaError_t acc_t(const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi_a, void* psi_b,
+                         void* rhop, const BodyDev* bodies, double* mass_part, StepState* st, double* diag_rho,
+                         double* diag_vel, const PhysParams& pp, int sz, cudaStream_t s) {
+  using R = typename St<S>::R;
+  const size_t smem = acc_smem<S, TY>();
+  // nz = 0: set the kernel's dynamic shared-memory limit (outside any stream capture) and return
+  if (lat.nz <= 0)
+    return cudaFuncSetAttribute(k_collide_acc<S, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const dim3 grid((lat.nx + 31) / 32, (lat.ny + TY - 1) / TY, (lat.nz + sz - 1) / sz);
+  k_collide_acc<S, TY, MINB><<<grid, 32 * TY, smem, s>>>((S*)fa, (S*)fb, flags, (R*)psi_a, (R*)psi_b, (R*)rhop,
+                                                         bodies, mass_part, st, diag_rho, diag_vel, lat, pp, sz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_acc(int prec, const Lat& lat, void* fa, void* fb, const uint16_t* flags, void* psi_a,
+                           void* psi_b, void* rhop, const BodyDev* bodies, double* mass_part, StepState* st,
+                           double* diag_rho, double* diag_vel, const PhysParams& pp, int ty, int sz,
+                           cudaStream_t s) {
+#define CBL_ACC(S, TY, MINB) \
+  acc_t<S, TY, MINB>(lat, fa, fb, flags, psi_a, psi_b, rhop, bodies, mass_part, st, diag_rho, diag_vel, pp, sz, s)
+  if (ty == 16) {
+    if (prec == 0) return CBL_ACC(double, 16, 1);
+    if (prec == 1) return CBL_ACC(float, 16, 2);
+    return CBL_ACC(__half, 16, 1);
+  }
+  if (prec == 0) return CBL_ACC(double, 8, 2);
+  if (prec == 1) return CBL_ACC(float, 8, 4);
+  return CBL_ACC(__half, 8, 3);
+#undef CBL_ACC
+}
+
+void launch_psi_fixup(int prec, const Lat& lat, const void* fa, const void* fb, void* psi_a, void* psi_b,
+                      const void* rhop, const StepState* st, const PhysParams& pp, int ty, int sz, cudaStream_t s) {
+  const AccGeom g = acc_geom(lat, ty, sz);
+  const long long total = g.n1 + g.n2 + g.n3;
+  const long long need = (total + 255) / 256, cap = 16LL * sm_count();
+  const unsigned grid = (unsigned)std::max(1LL, std::min(need, cap));
+  if (prec == 0)
+    k_psi_fixup<double><<<grid, 256, 0, s>>>((const double*)fa, (const double*)fb, (double*)psi_a, (double*)psi_b,
+                                             (const double*)rhop, st, lat, pp.rho0, pp.rho0_f, g);
+  else if (prec == 1)
+    k_psi_fixup<float><<<grid, 256, 0, s>>>((const float*)fa, (const float*)fb, (float*)psi_a, (float*)psi_b,
+                                            (const float*)rhop, st, lat, pp.rho0, pp.rho0_f, g);
+  else
+    k_psi_fixup<__half><<<grid, 256, 0, s>>>((const __half*)fa, (const __half*)fb, (float*)psi_a, (float*)psi_b,
+                                             (const float*)rhop, st, lat, pp.rho0, pp.rho0_f, g);
 }
 
 template <typename S>
@@ -1537,7 +1849,7 @@ extern "C" cbl_status cbl_lbm_step_noalloc(const float* f_in, float* f_out, int 
   if (cudaMemsetAsync(a.mass, 0, sizeof(double) * MASS_SLOTS, s) != cudaSuccess) return CBL_ERR_CUDA;
   const dim3 blk(32, 4, 1);
   const dim3 grid((nx + 31) / 32, (ny + 3) / 4, nz);
-  k_density<float><<<grid, blk, 0, s>>>(f_in, f_in, a.state, a.flags, nullptr, a.psi, lat, rho0, (float)rho0);
+  k_density<float><<<grid, blk, 0, s>>>(f_in, f_in, a.state, a.flags, nullptr, a.psi, nullptr, lat, rho0, (float)rho0);
   k_collide<float><<<grid, blk, 0, s>>>(const_cast<float*>(f_in), f_out, a.flags, a.psi, nullptr, a.mass, a.state,
                                         nullptr, nullptr, lat, pp, nullptr);
   if (mass_out) k_na_mass<<<1, 256, 0, s>>>(a.mass, mass_out);

@@ -613,6 +613,7 @@ __global__ void __launch_bounds__(256) k_finish(double* mass_part, unsigned n_ma
   if (threadIdx.x == 0) {
     st->last_mass = red[0];
     st->parity ^= 1;
+    st->psi_skip = 0;
   }
 }
 
