@@ -165,6 +165,31 @@ __device__ __forceinline__ void pull(const S* __restrict__ f, const uint16_t* __
 // f*_i = (1 - 1/tau) f_i + S_i + A_i, f*_opp = (1 - 1/tau) f_opp + S_i - A_i with
 // S_i = (rho w_i / tau)(1 + 4.5 (c.v)^2 - 1.5 v.v) + (1 - 1/2tau) w_i (9 (c.v)(c.F) - 3 v.F),
 // A_i = 3 w_i ((rho / tau) c.v + (1 - 1/2tau) c.F).
+// Post-collision values of one cell, handed to sink(i, v) in direction order.
+template <typename R, typename Sink>
+__device__ __forceinline__ void bgk_values(const R fi[Q], R rho, R vx, R vy, R vz, R Fx, R Fy, R Fz, R tau,
+                                           const Sink& sink) {
+  const R itau = (R)1 / tau;
+  const R keep = (R)1 - itau;
+  const R pref = (R)1 - (R)0.5 * itau;
+  const R ro = rho * itau;
+  const R uu = vx * vx + vy * vy + vz * vz;
+  const R vF = vx * Fx + vy * Fy + vz * Fz;
+  const R base = (R)1 - (R)1.5 * uu;   // even part without (c.v)^2
+  const R fv = -(R)3 * pref * vF;       // even forcing part without (c.v)(c.F)
+  sink(0, keep * fi[0] + (R)w_of(0) * (ro * base + fv));
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
+    const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
+    const R w = (R)w_of(i);
+    const R sym = w * (ro * (base + (R)4.5 * cu * cu) + fv + (R)9 * pref * cu * cF);
+    const R anti = (R)3 * w * (ro * cu + pref * cF);
+    sink(i, keep * fi[i] + sym + anti);
+    sink(i + 1, keep * fi[i + 1] + sym - anti);
+  }
+}
+
 // OUT: fo receives the stored values as a later load returns them (the accumulating pass sums them
 // into the next step's density).
 template <typename S, bool OUT = false>
@@ -174,35 +199,10 @@ __device__ __forceinline__ void collide_store(S* __restrict__ dst, size_t N, lon
                                               typename St<S>::R Fx, typename St<S>::R Fy, typename St<S>::R Fz,
                                               typename St<S>::R tau, typename St<S>::R* fo = nullptr) {
   using R = typename St<S>::R;
-  const R itau = (R)1 / tau;
-  const R keep = (R)1 - itau;
-  const R pref = (R)1 - (R)0.5 * itau;
-  const R ro = rho * itau;
-  const R uu = vx * vx + vy * vy + vz * vz;
-  const R vF = vx * Fx + vy * Fy + vz * Fz;
-  const R base = (R)1 - (R)1.5 * uu;   // even part without (c.v)^2
-  const R fv = -(R)3 * pref * vF;       // even forcing part without (c.v)(c.F)
-  {
-    const R w = (R)w_of(0);
-    const R v0 = keep * fi[0] + w * (ro * base + fv);
-    St<S>::st(dst, (size_t)n, 0, v0);
-    if constexpr (OUT) fo[0] = St<S>::rt(v0, 0);
-  }
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
-    const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
-    const R w = (R)w_of(i);
-    const R sym = w * (ro * (base + (R)4.5 * cu * cu) + fv + (R)9 * pref * cu * cF);
-    const R anti = (R)3 * w * (ro * cu + pref * cF);
-    const R vp = keep * fi[i] + sym + anti, vm = keep * fi[i + 1] + sym - anti;
-    St<S>::st(dst, (size_t)i * N + n, i, vp);
-    St<S>::st(dst, (size_t)(i + 1) * N + n, i + 1, vm);
-    if constexpr (OUT) {
-      fo[i] = St<S>::rt(vp, i);
-      fo[i + 1] = St<S>::rt(vm, i + 1);
-    }
-  }
+  bgk_values<R>(fi, rho, vx, vy, vz, Fx, Fy, Fz, tau, [&](int i, R v) {
+    St<S>::st(dst, (size_t)i * N + (size_t)n, i, v);
+    if constexpr (OUT) fo[i] = St<S>::rt(v, i);
+  });
 }
 
 template <typename S>
@@ -315,6 +315,51 @@ struct CollideMinBlocks<__half> {
 // the bulk kernel carries neither the flag loads (on which the population addresses would depend)
 // nor the registers of the wall terms. Returns rho.
 // psi_at(i): psi at x + c_i (i >= 1) and at x itself (i = 0).
+// Shan-Chen force with wetting (Eq. shan_chen_force; solid neighbours carry psi of their wetting
+// density) plus the external force. psi_at(i): psi at x + c_i (i >= 1) and at x (i = 0).
+// The sum over directions is taken over opposite pairs (c_opp = -c_i, equal weights), as sums of
+// differences psi(x + c_i) - psi(x - c_i): the same value, but its rounding scales with the small
+// differences of psi across a cell, not with psi itself (in the bulk of a phase the terms cancel, and
+// summing them one by one in FP32 would leave a rounding residue of ~1e-7 psi as a force).
+template <typename R, typename PsiAt>
+__device__ __forceinline__ void sc_force(const PsiAt& psi_at, const PhysParams& pp, R& ps, R& Fx, R& Fy, R& Fz) {
+  ps = psi_at(0);
+  R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const R wd = (R)w_of(i) * (psi_at(i) - psi_at(i + 1));
+    if (cx_of(i)) sx += wd * (R)cx_of(i);
+    if (cy_of(i)) sy += wd * (R)cy_of(i);
+    if (cz_of(i)) sz += wd * (R)cz_of(i);
+  }
+  const R mG = -par<R>(pp.G, pp.G_f) * ps;
+  Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]);
+  Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]);
+  Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
+}
+
+// Velocity with the half-force shift (Eq. fluid_velocity); the momentum, like the force, summed over
+// opposite pairs as f_i - f_opp(i) (rounding of the order of the differences, not of the
+// populations, which matters at the small velocities of these flows).
+template <typename R>
+__device__ __forceinline__ void fluid_velocity(const R fi[Q], R rho, R Fx, R Fy, R Fz, R& vx, R& vy, R& vz) {
+  R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const R d = fi[i] - fi[i + 1];
+    if (cx_of(i)) mx += (R)cx_of(i) * d;
+    if (cy_of(i)) my += (R)cy_of(i) * d;
+    if (cz_of(i)) mz += (R)cz_of(i) * d;
+  }
+  vx = vy = vz = (R)0;
+  if (rho > (R)0) {
+    const R ir = (R)1 / rho;
+    vx = mx * ir;
+    vy = my * ir;
+    vz = mz * ir;
+  }
+}
+
 template <typename S, bool NEAR, typename PsiAt, bool OUT = false>
 __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__ src, S* __restrict__ dst,
                                                            const uint16_t* __restrict__ flags,
@@ -330,23 +375,9 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
   const size_t N = (size_t)lat.Ns;  // population stride
   R my_mass = 0;
   {
-    // Shan-Chen force with wetting first (solid neighbours carry psi of their wetting density):
-    // it needs only psi, so the populations are not yet live
-    // The sum over directions is taken over opposite pairs (c_opp = -c_i, equal weights), as sums of
-    // differences psi(x + c_i) - psi(x - c_i): the same value, but its rounding scales with the small
-    // differences of psi across a cell, not with psi itself (in the bulk of a phase the terms cancel,
-    // and summing them one by one in FP32 would leave a rounding residue of ~1e-7 psi as a force).
-    const R ps = psi_at(0);
-    R sx = 0, sy = 0, sz = 0;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      const R wd = (R)w_of(i) * (psi_at(i) - psi_at(i + 1));
-      if (cx_of(i)) sx += wd * (R)cx_of(i);
-      if (cy_of(i)) sy += wd * (R)cy_of(i);
-      if (cz_of(i)) sz += wd * (R)cz_of(i);
-    }
-    const R mG = -par<R>(pp.G, pp.G_f) * ps;
-    const R Fx = mG * sx + par<R>(pp.ext[0], pp.ext_f[0]), Fy = mG * sy + par<R>(pp.ext[1], pp.ext_f[1]), Fz = mG * sz + par<R>(pp.ext[2], pp.ext_f[2]);
+    // the force first: it needs only psi, so the populations are not yet live
+    R ps, Fx, Fy, Fz;
+    sc_force<R>(psi_at, pp, ps, Fx, Fy, Fz);
     R fi[Q];
     unsigned sl;
     pull<S>(src, flags, lat, c, n, fi, sl, NEAR ? F_NEAR : (uint16_t)0);
@@ -369,24 +400,8 @@ __device__ __forceinline__ typename St<S>::R collide_fluid(const S* __restrict__
       }
       fi[0] += drho;
     }
-    // velocity with the half-force shift, Eq. fluid_velocity; the momentum, like the force, summed
-    // over opposite pairs as f_i - f_opp(i) (rounding of the order of the differences, not of the
-    // populations, which matters at the small velocities of these flows)
-    R mx = (R)0.5 * Fx, my = (R)0.5 * Fy, mz = (R)0.5 * Fz;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      const R d = fi[i] - fi[i + 1];
-      if (cx_of(i)) mx += (R)cx_of(i) * d;
-      if (cy_of(i)) my += (R)cy_of(i) * d;
-      if (cz_of(i)) mz += (R)cz_of(i) * d;
-    }
-    R vx = 0, vy = 0, vz = 0;
-    if (rho > (R)0) {
-      const R ir = (R)1 / rho;
-      vx = mx * ir;
-      vy = my * ir;
-      vz = mz * ir;
-    }
+    R vx, vy, vz;
+    fluid_velocity<R>(fi, rho, Fx, Fy, Fz, vx, vy, vz);
     collide_store<S, OUT>(dst, N, n, fi, rho, vx, vy, vz, Fx, Fy, Fz, par<R>(pp.tau, pp.tau_f), fo);
     if (diag) {
       diag_rho[n] = (double)rho;
