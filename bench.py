@@ -407,6 +407,9 @@ def bench_cuda(args, rank, world, local_rank):
     workloads.build(sim, w)
     if args.lbm_variant is not None:
         sim.set_option("lbm_variant", args.lbm_variant)
+    for kv in args.option:
+        k, v = kv.split("=")
+        sim.set_option(k, float(v))
     variant = int(sim.get_option("lbm_variant"))
     # the bulk collision's live duration, from event nodes inside the replayed step graph
     sim.set_option("kernel_events", 1)
@@ -487,7 +490,10 @@ def bench_cuda(args, rank, world, local_rank):
                                  % (len(reps), args.steps),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "repeats_ms": [round(x, 4) for x in reps],
-            "roofline": {"bound": "hbm", "kernel": "bulk collision (k_collide: pull, force, BGK, store)",
+            "roofline": {"bound": "hbm", "kernel": {0: "bulk collision (k_collide: pull, force, BGK, store)",
+                                                    1: "fused pass (k_fused: psi of the plane ahead, collision)",
+                                                    2: "accumulating collision (k_collide_acc: collision and "
+                                                       "next step's density)"}[variant],
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": profiled_traffic(w.name, prec, args.q), "peak_kind": peak_kind,
                          "peak_datasheet": HBM_DATASHEET_GBS, "alg_bytes_per_cell": bpc,
@@ -542,6 +548,8 @@ def main():
                     help="repeat the timed region until about this much load has passed")
     ap.add_argument("--max-steps-total", type=int, default=600,
                     help="cap on warm-up plus timed steps (the workloads evolve with time)")
+    ap.add_argument("--option", action="append", default=[],
+                    help="execution option key=value for the timed simulation (cbl_set_option), repeatable")
     ap.add_argument("--lbm-variant", type=int, default=None, choices=[0, 1, 2],
                     help="lattice-Boltzmann pass: 0 split density + collision, 1 fused, 2 accumulating "
                          "(default: the library's)")

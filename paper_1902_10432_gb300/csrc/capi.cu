@@ -73,6 +73,7 @@ struct cbl_ctx {
   int block_x = 32;      // x extent of the split kernels' 128-thread blocks
   double tile_tail = 2.5;  // cells of room for the advection tail in each body tile
   int node_priority = 1;   // 1: the step graph keeps the side stream's priority on its kernels
+  int side_first = 0;      // 1 (split pass, bodies): the side chain starts beside the density pass
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -203,8 +204,7 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
   const size_t N = (size_t)ctx->lat.N;
   ctx->fa = dalloc(ctx, (size_t)ctx->lat.Ns * ctx->ops.q * ctx->elem);
   ctx->fb = dalloc(ctx, (size_t)ctx->lat.Ns * ctx->ops.q * ctx->elem);
-  // the split density + collision pair is the default; the fused single-pass variant is chosen
-  // per lattice by cbl_tune (it needs no psi array but holds fewer threads per SM)
+  // psi of the split and fused passes (the accumulating pass adds a second buffer when chosen)
   ctx->psi = dalloc(ctx, N * (ctx->prec == 0 ? 8 : 4));
   ctx->nbuf = dalloc(ctx, N * 2 * (ctx->prec == 0 ? 8 : 4));
   ctx->flags = (uint16_t*)dalloc(ctx, N * 2);
@@ -494,10 +494,17 @@ static void enqueue_step(cbl_ctx* ctx) {
     // scheduled ahead of the bulk collision's queued ones. The flag update and the refill rewrite
     // what the bulk collision reads and writes, so they wait for both. With the fused pass, psi of the
     // bodies' tiles (all that the side chain needs) is the side chain's first kernel.
-    if (!ctx->fused_tz) enqueue_lbm(ctx, 1, ctx->s);
+    // side_first (split pass): the side chain starts at the top of the step with psi of the bodies'
+    // tiles (all it reads), beside the whole-lattice density pass and the bulk collision on the main
+    // branch; both passes write the same psi values into the tiles' cells.
+    const bool early = ctx->side_first && !ctx->fused_tz && !ctx->acc_pass;
+    if (!ctx->fused_tz && !early) enqueue_lbm(ctx, 1, ctx->s);
     cudaEventRecord(ctx->ev_fork, ctx->s);
     cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     if (ctx->fused_tz) enqueue_lbm(ctx, 1, ctx->side);
+    if (early)
+      ctx->ops.density_tiles(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile,
+                             ctx->psi, nullptr, ctx->pp, ctx->side);
     enqueue_lbm(ctx, 4, ctx->side);
     ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->side);
@@ -506,6 +513,7 @@ static void enqueue_step(cbl_ctx* ctx) {
                   ctx->side);
     phase_update(ctx->side);
     cudaEventRecord(ctx->ev_join, ctx->side);
+    if (early) enqueue_lbm(ctx, 1, ctx->s);
     enqueue_bulk(ctx, ctx->s);
     cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0);
     flags_refill(ctx->s);
@@ -1211,6 +1219,7 @@ cbl_status cbl_get_option(cbl_ctx* ctx, const char* key, double* value) {
   else if (k == "lbm_block_x") *value = ctx->block_x;
   else if (k == "node_priority") *value = ctx->node_priority;
   else if (k == "graph_branches") *value = ctx->branches;
+  else if (k == "side_first") *value = ctx->side_first;
   else if (k == "tile_tail") *value = ctx->tile_tail;
   else if (k == "kernel_events") *value = ctx->kev;
   else return fail(ctx, CBL_ERR_ARG, "unknown option " + k);
@@ -1252,6 +1261,10 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "node_priority must be 0 or 1");
     ctx->node_priority = v;
+  } else if (k == "side_first") {
+    const int v = (int)value;
+    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "side_first must be 0 or 1");
+    ctx->side_first = v;
   } else if (k == "graph_branches") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "graph_branches must be 0 or 1");
