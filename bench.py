@@ -49,8 +49,13 @@ def kernels_per_step(nb, mpf, variant):
 # DRAM bytes per launch of the bulk collision, and per step of the whole step graph, from one-pass
 # ncu captures (gpu__time_duration, dram__bytes_read/write only), valid only for the source they were
 # taken on (source_hash of the lattice-Boltzmann sources); None otherwise
-PROFILED = {}
-PROFILED_STEP = {}
+PROFILED = {
+    ("tetra4", "fp32", 19, "69eafe2e841d"): 2721.9e6,      # k_collide<float>, mean of 15 launches
+    ("tetra4", "fp16dev", 19, "69eafe2e841d"): 1452.5e6,   # k_collide<__half>, mean of 10 launches
+}
+PROFILED_STEP = {
+    ("tetra4", "fp32", 19, "69eafe2e841d"): 4199.5e6,      # every kernel of one step
+}
 
 
 def source_hash():

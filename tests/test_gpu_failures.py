@@ -81,7 +81,8 @@ def test_init_with_failing_allocator_after_create():
     b = cbl.cbl_body()
     b.shape, b.center[:], b.radius, b.mass_density, b.wetting_rho = 0, (12.0, 12.0, 12.0), 4.0, 4.0, 1.0
     b.quat[:] = (1.0, 0.0, 0.0, 0.0)
-    st = lib.cbl_add_body(h, ctypes.byref(b))
+    bid = ctypes.c_int()
+    st = lib.cbl_add_body(h, ctypes.byref(b), ctypes.byref(bid))
     if st == 0:
         st = lib.cbl_init_fluid(h, 1.9, 0.12, None)
     assert st == 3, st
