@@ -213,12 +213,13 @@ cbl_status cbl_info(cbl_ctx* ctx, int* nbodies, int64_t* ncells, int* device_err
 
 /* Phases of one step, in launch order, as reported by cbl_time_phases. */
 #define CBL_NPHASES 9
-/* 0 pull + density + psi (nothing with the fused pass, "lbm_variant" 1), 1 pull + force + collision
- * + mass partials, bulk and next to a solid (with the fused pass: the single pass that also computes
- * psi), 2 solid-fluid force on the
- * bodies (momentum exchange and adhesion, FP64 sums), 3 solid-solid repulsion, 4 rigid-body update,
- * 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle flags, 8 cover refill,
- * boundary-cell list and the end of the step (fluid mass, buffer flip). */
+/* 0 psi of the step: pull + density + psi (split pass), psi of the bodies' tiles (fused pass,
+ * "lbm_variant" 1), the regions' edge cells and the tiles (accumulating pass, 2); 1 collision:
+ * pull + force + collision + mass partials, bulk and next to a solid (the fused pass also computes
+ * psi, the accumulating pass the next step's density); 2 solid-fluid force on the bodies (momentum
+ * exchange and adhesion reaction, compensated sums into FP64 accumulators); 3 solid-solid repulsion,
+ * 4 rigid-body update, 5 phase-field advection (three sweeps), 6 phase-field kinetics, 7 obstacle
+ * flags, 8 cover refill, boundary-cell list and the end of the step (fluid mass, buffer flip). */
 
 /* Run nsteps time steps launched kernel by kernel (not through the graph) with CUDA events recorded
  * on the context's stream between the phases, synchronise, and write the mean duration per step of
