@@ -10,9 +10,14 @@
 //  k_fused    : the two above in one pass over HBM (psi of each z-plane and a one-cell ring kept in
 //               shared memory, populations pulled again for the collision from the caches); fluid
 //               cells next to a solid are left to k_collide_near, fed by k_density_tiles.
-//  k_boundary : over the list of fluid cells next to a solid: momentum exchange on the bodies
-//               (Eq. solid_liquid_force) and the reaction of the Shan-Chen force (Sec. 3.2.3),
-//               summed in FP64.
+//  k_collide_acc, k_psi_fixup : the collision that also sums the next step's density from the
+//               values it stores (regions marched along z, shared-memory exchange), and the
+//               completion of psi at the regions' edges at the start of the next step.
+//  k_collide_near : the collision of the fluid cells next to a solid (the boundary-cell list).
+//  k_boundary : over the same list: momentum exchange on the bodies (Eq. solid_liquid_force) and
+//               the reaction of the Shan-Chen force (Sec. 3.2.3), summed in FP64.
+//  k_batch_lbm : the density and bulk collision of every instance of a batch in one persistent
+//               launch (work queue, bounded grid barrier).
 //  k_refill   : cover refill of nodes that became solid (Sec. 3.2.2), as a gather over each
 //               fluid node's 26 neighbours so that no two threads write the same populations; the
 //               same scan rebuilds the boundary-cell list for the next step.
