@@ -109,7 +109,7 @@ cbl_status cbl_add_body(cbl_ctx* ctx, const cbl_body* body, int* body_id);
 /* Initialise the phase fields, obstacle flags (Sec. 3.2.2: solid iff fluid phase < threshold),
  * body mass, centre of mass and inertia, and the fluid: f = f_eq(rho, 0) with rho = rho_liquid
  * where liquid_mask_host[n] != 0 and rho_vapour elsewhere (mask may be NULL: all vapour).
- * The mask is a host array of nx*ny*nz bytes. */
+ * The mask is a host array of nx*ny*nz bytes; it is copied to the device and expanded there. */
 cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour,
                           const unsigned char* liquid_mask_host);
 

@@ -349,7 +349,17 @@ static cbl_status alloc_bodies(cbl_ctx* ctx) {
   return CBL_OK;
 }
 
-static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double* u_host) {
+// initial density from a liquid mask on the device (NULL mask: vapour everywhere)
+__global__ void k_rho_from_mask(double* __restrict__ rho, const unsigned char* __restrict__ mask, long long N,
+                                double rho_l, double rho_v) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) rho[n] = (mask && mask[n]) ? rho_l : rho_v;
+}
+
+// rho_host: the initial density field; or, with rho_host NULL, the liquid mask (host, may be NULL)
+// and the two densities, expanded on the device
+static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double* u_host,
+                              const unsigned char* mask = nullptr, double rho_l = 0.0, double rho_v = 0.0) {
   const size_t N = (size_t)ctx->lat.N;
   const int nb = (int)ctx->hb.size();
   if (nb) {
@@ -369,8 +379,15 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
   }
   double* drho = (double*)dalloc(ctx, N * 8);
   double* du = u_host ? (double*)dalloc(ctx, N * 24) : nullptr;
-  if (!drho || (u_host && !du)) return fail(ctx, CBL_ERR_OOM, "device allocation failed (initial fields)");
-  CK(cudaMemcpyAsync(drho, rho_host, N * 8, cudaMemcpyHostToDevice, ctx->s));
+  unsigned char* dmask = (!rho_host && mask) ? (unsigned char*)dalloc(ctx, N) : nullptr;
+  if (!drho || (u_host && !du) || (!rho_host && mask && !dmask))
+    return fail(ctx, CBL_ERR_OOM, "device allocation failed (initial fields)");
+  if (rho_host) {
+    CK(cudaMemcpyAsync(drho, rho_host, N * 8, cudaMemcpyHostToDevice, ctx->s));
+  } else {
+    if (dmask) CK(cudaMemcpyAsync(dmask, mask, N, cudaMemcpyHostToDevice, ctx->s));
+    k_rho_from_mask<<<(unsigned)((N + 255) / 256), 256, 0, ctx->s>>>(drho, dmask, (long long)N, rho_l, rho_v);
+  }
   if (du) CK(cudaMemcpyAsync(du, u_host, N * 24, cudaMemcpyHostToDevice, ctx->s));
   ctx->ops.init_fluid(ctx->prec, ctx->lat, ctx->fa, ctx->flags, drho, du, ctx->s);
   // first boundary-cell list (no cover events yet, so the pass only scans) and member boxes
@@ -382,7 +399,7 @@ static cbl_status init_common(cbl_ctx* ctx, const double* rho_host, const double
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->s));
   // the initial-field buffers are released right away
-  for (void* q : {(void*)drho, (void*)du}) {
+  for (void* q : {(void*)drho, (void*)du, (void*)dmask}) {
     if (!q) continue;
     for (size_t k = 0; k < ctx->allocs.size(); ++k)
       if (ctx->allocs[k] == q) {
@@ -403,9 +420,7 @@ cbl_status cbl_init_fluid(cbl_ctx* ctx, double rho_liquid, double rho_vapour, co
   if (ctx->ready) return fail(ctx, CBL_ERR_STATE, "already initialised");
   if (!(rho_liquid >= 0) || !(rho_vapour >= 0) || !std::isfinite(rho_liquid) || !std::isfinite(rho_vapour))
     return fail(ctx, CBL_ERR_ARG, "densities must be finite and >= 0");
-  std::vector<double> rho((size_t)ctx->lat.N);
-  for (size_t n = 0; n < rho.size(); ++n) rho[n] = (mask && mask[n]) ? rho_liquid : rho_vapour;
-  return init_common(ctx, rho.data(), nullptr);
+  return init_common(ctx, nullptr, nullptr, mask, rho_liquid, rho_vapour);
 }
 
 cbl_status cbl_init_fluid_fields(cbl_ctx* ctx, const double* rho_host, const double* u_host) {

@@ -1244,7 +1244,13 @@ __global__ void k_init_fluid(S* __restrict__ f, const uint16_t* __restrict__ fla
     return;
   }
   double r = rho[n];
-  double ux = u ? u[3 * n] : 0.0, uy = u ? u[3 * n + 1] : 0.0, uz = u ? u[3 * n + 2] : 0.0;
+  if (!u) {
+    // at rest: f_eq = rho w_i exactly (the bracket below is exactly 1), without its FP64 arithmetic
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St<S>::st(f, (size_t)i * N + n, i, (R)(r * w_of(i)));
+    return;
+  }
+  double ux = u[3 * n], uy = u[3 * n + 1], uz = u[3 * n + 2];
   double uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
