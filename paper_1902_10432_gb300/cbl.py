@@ -249,10 +249,17 @@ class Sim:
     def step(self, n=1):
         self._ck(self._lib.cbl_step(self._h, int(n)))
 
-    def fields(self):
-        rho = np.empty(self.N)
-        vel = np.empty(3 * self.N)
-        phf = np.empty(self.N)
+    def fields(self, out=None):
+        """Density, velocity and fluid phase field of the last step, float64 numpy arrays. out: three
+        float64 C-contiguous host arrays of N, 3N and N values to read into (e.g. views of pinned
+        memory, which the copies use directly); new arrays otherwise."""
+        if out is None:
+            rho, vel, phf = np.empty(self.N), np.empty(3 * self.N), np.empty(self.N)
+        else:
+            rho, vel, phf = out
+            for a, n in ((rho, self.N), (vel, 3 * self.N), (phf, self.N)):
+                if a.dtype != np.float64 or a.size != n or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("out: float64 C-contiguous arrays of N, 3N and N values")
         self._ck(self._lib.cbl_read_fields(self._h, _vp(rho), _vp(vel), _vp(phf), 0))
         return rho.reshape(self.shape), vel.reshape(self.shape + (3,)), phf.reshape(self.shape)
 
