@@ -73,7 +73,6 @@ struct cbl_ctx {
   int block_x = 32;      // x extent of the split kernels' 128-thread blocks
   double tile_tail = 2.5;  // cells of room for the advection tail in each body tile
   int node_priority = 1;   // 1: the step graph keeps the side stream's priority on its kernels
-  int side_first = 0;      // 1 (split pass, bodies): the side chain starts beside the density pass
   StepState* st = nullptr;
   bool ready = false;
   long long t = 0;
@@ -174,6 +173,9 @@ cbl_status cbl_create(const cbl_params* params, const cbl_allocator* alloc, cbl_
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->s);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_join})
+      if (e) cudaEventDestroy(e);
     delete ctx;
     return fail(nullptr, CBL_ERR_CUDA, "stream or event creation failed");
   }
@@ -509,17 +511,10 @@ static void enqueue_step(cbl_ctx* ctx) {
     // scheduled ahead of the bulk collision's queued ones. The flag update and the refill rewrite
     // what the bulk collision reads and writes, so they wait for both. With the fused pass, psi of the
     // bodies' tiles (all that the side chain needs) is the side chain's first kernel.
-    // side_first (split pass): the side chain starts at the top of the step with psi of the bodies'
-    // tiles (all it reads), beside the whole-lattice density pass and the bulk collision on the main
-    // branch; both passes write the same psi values into the tiles' cells.
-    const bool early = ctx->side_first && !ctx->fused_tz && !ctx->acc_pass;
-    if (!ctx->fused_tz && !early) enqueue_lbm(ctx, 1, ctx->s);
+    if (!ctx->fused_tz) enqueue_lbm(ctx, 1, ctx->s);
     cudaEventRecord(ctx->ev_fork, ctx->s);
     cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     if (ctx->fused_tz) enqueue_lbm(ctx, 1, ctx->side);
-    if (early)
-      ctx->ops.density_tiles(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->st, ctx->flags, ctx->db, nb, ctx->max_tile,
-                             ctx->psi, nullptr, ctx->pp, ctx->side);
     enqueue_lbm(ctx, 4, ctx->side);
     ctx->ops.boundary(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->db, nb, ctx->acc, ctx->blist, ctx->st,
                     ctx->nbuf, ctx->pp.G, ctx->side);
@@ -528,7 +523,6 @@ static void enqueue_step(cbl_ctx* ctx) {
                   ctx->side);
     phase_update(ctx->side);
     cudaEventRecord(ctx->ev_join, ctx->side);
-    if (early) enqueue_lbm(ctx, 1, ctx->s);
     enqueue_bulk(ctx, ctx->s);
     cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0);
     flags_refill(ctx->s);
@@ -572,9 +566,10 @@ static void enqueue_side_chain(cbl_ctx* ctx) {
 }
 
 // Accumulating pass: its buffers, its kernel's shared-memory limit, its region depth, and psi of
-// the current step. psi is not in place after initialisation, a checkpoint load, a move of the
-// bodies, an option change or a batch step: then a whole-lattice density pass computes it, and
-// StepState::psi_skip tells the fix-up and the tile pass of the next step to leave it as it is.
+// the current step, which the pass computes in the step before. psi is not in place after
+// initialisation, a checkpoint load, a move of the bodies, an option change, kernel-by-kernel timing
+// or a batch step: then a whole-lattice density pass computes it, and StepState::psi_skip tells the
+// fix-up and the tile pass of the next step to leave it as it is.
 static cbl_status acc_prepare(cbl_ctx* ctx) {
   if (!ctx->acc_pass) return CBL_OK;
   const size_t N = (size_t)ctx->lat.N, el = ctx->prec == 0 ? 8 : 4;
@@ -723,6 +718,7 @@ cbl_status cbl_time_phases(cbl_ctx* ctx, int nsteps, double* ms) {
   }
   for (int k = 0; k <= CBL_NPHASES; ++k) cudaEventDestroy(ev[k]);
   for (int k = 0; k < CBL_NPHASES; ++k) ms[k] = acc[k] / nsteps;
+  ctx->psi_valid = false;  // these steps computed psi at their start, not for the step after
   ctx->t += nsteps;
   ctx->fsum_steps += nsteps;
   return CBL_OK;
@@ -1234,7 +1230,6 @@ cbl_status cbl_get_option(cbl_ctx* ctx, const char* key, double* value) {
   else if (k == "lbm_block_x") *value = ctx->block_x;
   else if (k == "node_priority") *value = ctx->node_priority;
   else if (k == "graph_branches") *value = ctx->branches;
-  else if (k == "side_first") *value = ctx->side_first;
   else if (k == "tile_tail") *value = ctx->tile_tail;
   else if (k == "kernel_events") *value = ctx->kev;
   else return fail(ctx, CBL_ERR_ARG, "unknown option " + k);
@@ -1276,10 +1271,7 @@ cbl_status cbl_set_option(cbl_ctx* ctx, const char* key, double value) {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "node_priority must be 0 or 1");
     ctx->node_priority = v;
-  } else if (k == "side_first") {
-    const int v = (int)value;
-    if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "side_first must be 0 or 1");
-    ctx->side_first = v;
+
   } else if (k == "graph_branches") {
     const int v = (int)value;
     if (v != 0 && v != 1) return fail(ctx, CBL_ERR_ARG, "graph_branches must be 0 or 1");

@@ -95,35 +95,3 @@ def test_free_spheres_match(prec, tol):
     Xa, Xb = a.bodies()["X"], b.bodies()["X"]
     assert np.abs(Xa - Xb).max() < 1e-6
     assert a.info()["device_error"] == 0 and b.info()["device_error"] == 0
-
-
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16dev"])
-def test_side_first_held_plates_bitwise(prec):
-    # option side_first: the side chain starts beside the density pass, with psi of the tiles from
-    # the tile pass; the values are the density pass's own, so held bodies give the same populations
-    w = workloads.plates48(prec=prec)
-    sims = []
-    for v in (0, 1):
-        s = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
-        s.set_option("side_first", v)
-        workloads.build(s, w)
-        s.step(40)
-        sims.append(s)
-    a, b = sims
-    assert np.array_equal(a.populations(), b.populations())
-
-
-def test_side_first_free_spheres_fp64():
-    w = workloads.small_spheres(prec="fp64", mobility=2e-3)
-    sims = []
-    for v in (0, 1):
-        s = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
-        s.set_option("side_first", v)
-        workloads.build(s, w)
-        s.step(100)
-        sims.append(s)
-    a, b = sims
-    ra, va, _ = a.fields()
-    rb, vb, _ = b.fields()
-    assert np.abs(ra - rb).max() <= 1e-12 * np.abs(ra).max()
-    assert np.abs(a.bodies()["X"] - b.bodies()["X"]).max() < 1e-10
