@@ -74,3 +74,51 @@ def test_tetra4_full_size_one_step_from_gpu_state():
     assert err_vel < 1e-3, err_vel
     assert err_F < 1e-3, err_F
     assert g.info()["device_error"] == 0
+
+
+def test_tetra4_full_size_one_step_binary16_against_storage_model():
+    """The same check for binary16 deviation storage (the four-sphere cluster's second precision):
+    the oracle with its binary16 storage model (store_prec 2: every stored population rounded to a
+    binary16 deviation from the binary16-rounded weight, the representation the CUDA path stores)
+    takes one step from the GPU's stored state. The CUDA path computes the step in FP32, the oracle
+    in FP64, and both round to binary16 on the store: a population agrees exactly unless the two
+    roundings of the arithmetic fall on different sides of a binary16 rounding boundary, and then by
+    one binary16 unit of its deviation."""
+    import oracle
+
+    w = workloads.tetra4(seed=0, prec="fp16dev")
+    params = dict(w.params, mpf_kinetics=0)
+    g = cbl.Sim(w.nx, w.ny, w.nz, **params)
+    workloads.build(g, w)
+    g.set_fixed([True] * len(w.bodies))
+    g.step(60)
+    f_gpu = g.populations()
+
+    o = oracle.Oracle(w.nx, w.ny, w.nz, store_prec=2, **{k: v for k, v in params.items() if k != "prec"})
+    workloads.build(o, w)
+    o.set_fixed([True] * len(w.bodies))
+    cg, wg = g.velocity_set()
+    co, _ = o.velocity_set()
+    perm = [int(np.flatnonzero((co == cg[i]).all(axis=1))[0]) for i in range(len(cg))]
+    f_o = np.empty_like(f_gpu)
+    f_o[perm] = f_gpu
+    o.set_populations(f_o)
+    del f_o
+    g.step(1)
+    o.step(1)
+    fg = g.populations()
+    fo = o.populations()[perm]
+    sg, _ = g.flags()
+    fluid = sg == 0
+    what = (np.asarray(wg, np.float16).astype(np.float64))[:, None, None, None]  # binary16-rounded weights
+    hg, ho = fg - what, fo - what
+    mag = np.maximum(np.abs(hg), np.abs(ho))
+    ulp = np.maximum(2.0 ** (np.floor(np.log2(np.maximum(mag, 2.0 ** -14))) - 10), 2.0 ** -24)
+    diff = np.abs(fg - fo)[:, fluid]
+    ulp = ulp[:, fluid]
+    frac = float((diff > 0).mean())
+    worst = float((diff / ulp).max())
+    print("256^3 binary16, one step from the GPU state: %.2e of the populations differ, by at most %.3f "
+          "binary16 units of their deviation" % (frac, worst))
+    assert worst <= 1.0 + 1e-9, worst
+    assert frac < 1e-2, frac
