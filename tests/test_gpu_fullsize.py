@@ -122,3 +122,55 @@ def test_tetra4_full_size_one_step_binary16_against_storage_model():
           "binary16 units of their deviation" % (frac, worst))
     assert worst <= 1.0 + 1e-9, worst
     assert frac < 1e-2, frac
+
+
+def test_batch64_one_step_of_sampled_instances():
+    """The 64-instance batch of the bench (boxes U{64..128}^3, FP32, the persistent launch with its
+    default tile shape), bodies held and kinetics off: after 40 steps three instances (the smallest,
+    the median and the largest box) are written into oracles with the same set-up, and the batch and
+    the oracles take one step; every cell of those instances is compared."""
+    import oracle
+
+    ws = workloads.batch64(seed=0, prec="fp32")
+    sims = []
+    for w in ws:
+        s = cbl.Sim(w.nx, w.ny, w.nz, **dict(w.params, mpf_kinetics=0))
+        workloads.build(s, w)
+        s.set_fixed([True] * len(w.bodies))
+        sims.append(s)
+    b = cbl.Batch(sims)
+    assert b.info()["mode"] == 1  # the persistent launch
+    b.step(40)
+    b.sync()
+    order = np.argsort([w.ncells for w in ws])
+    pick = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    oracles = {}
+    for k in pick:
+        w = ws[k]
+        o = oracle.Oracle(w.nx, w.ny, w.nz, **{kk: v for kk, v in dict(w.params, mpf_kinetics=0).items()
+                                                 if kk != "prec"})
+        workloads.build(o, w)
+        o.set_fixed([True] * len(w.bodies))
+        cg, _ = sims[k].velocity_set()
+        co, _ = o.velocity_set()
+        perm = [int(np.flatnonzero((co == cg[i]).all(axis=1))[0]) for i in range(len(cg))]
+        f = sims[k].populations()
+        fo = np.empty_like(f)
+        fo[perm] = f
+        o.set_populations(fo)
+        oracles[k] = (o, perm)
+    b.step(1)
+    b.sync()
+    for k, (o, perm) in oracles.items():
+        o.step(1)
+        g = sims[k]
+        fg = g.populations()
+        fo = o.populations()[perm]
+        err_f = float(np.abs(fg - fo).max() / np.abs(fo).max())
+        Fg, _, _ = g.body_forces()
+        Fo, _, _ = o.body_forces()
+        err_F = float(np.abs(Fg - Fo).max() / np.abs(Fo).max())
+        print("batch instance %d (%d^3 cells): populations %.2e, force %.2e" % (k, round(ws[k].ncells ** (1 / 3)), err_f, err_F))
+        assert err_f < 1e-5 and err_F < 1e-3, (k, err_f, err_F)
+        assert g.info()["device_error"] == 0
+    b.close()
