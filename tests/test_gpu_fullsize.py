@@ -174,3 +174,51 @@ def test_batch64_one_step_of_sampled_instances():
         assert err_f < 1e-5 and err_F < 1e-3, (k, err_f, err_F)
         assert g.info()["device_error"] == 0
     b.close()
+
+
+def test_tetra4_full_size_release_three_steps_from_gpu_state():
+    """The moving-body path at full size: after 60 held steps (kinetics off, so the phase fields are
+    the set-up's on both sides) the GPU's populations go into the oracle, both release the four
+    bodies from rest and take three steps (forces, rigid-body update, advection of the phase fields
+    with the new velocities, flags), compared at every cell."""
+    import oracle
+
+    w = workloads.tetra4(seed=0, prec="fp32")
+    params = dict(w.params, mpf_kinetics=0)
+    nb = len(w.bodies)
+    g = cbl.Sim(w.nx, w.ny, w.nz, **params)
+    workloads.build(g, w)
+    g.set_fixed([True] * nb)
+    g.step(60)
+    o = oracle.Oracle(w.nx, w.ny, w.nz, **{k: v for k, v in params.items() if k != "prec"})
+    workloads.build(o, w)
+    cg, _ = g.velocity_set()
+    co, _ = o.velocity_set()
+    perm = [int(np.flatnonzero((co == cg[i]).all(axis=1))[0]) for i in range(len(cg))]
+    f = g.populations()
+    fo = np.empty_like(f)
+    fo[perm] = f
+    o.set_populations(fo)
+    del f, fo
+    g.set_fixed([False] * nb)
+    g.step(3)
+    o.step(3)
+    sg, _ = g.flags()
+    so, _ = o.flags()
+    assert (sg != so).sum() == 0
+    fg = g.populations()
+    fo = o.populations()[perm]
+    err_f = float(np.abs(fg - fo).max() / np.abs(fo).max())
+    Fg, _, _ = g.body_forces()
+    Fo, _, _ = o.body_forces()
+    err_F = float(np.abs(Fg - Fo).max() / np.abs(Fo).max())
+    bg, bo = g.bodies(), o.bodies()
+    dX = float(np.abs(bg["X"] - bo["X"]).max())
+    dV = float(np.abs(bg["V"] - bo["V"]).max() / max(np.abs(bo["V"]).max(), 1e-300))
+    moved = float(np.abs(bo["X"] - np.array([b["center"] for b in w.bodies])).max())
+    print("256^3, released, three steps from the GPU state: populations %.2e, force %.2e, V %.2e, "
+          "X %.2e (bodies moved %.2e)" % (err_f, err_F, dV, dX, moved))
+    assert moved > 0.0
+    assert err_f < 1e-5 and err_F < 1e-3 and dV < 1e-3, (err_f, err_F, dV)
+    assert dX < 1e-3 * moved + 1e-12, (dX, moved)
+    assert g.info()["device_error"] == 0
