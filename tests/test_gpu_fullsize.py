@@ -222,3 +222,38 @@ def test_tetra4_full_size_release_three_steps_from_gpu_state():
     assert err_f < 1e-5 and err_F < 1e-3 and dV < 1e-3, (err_f, err_F, dV)
     assert dX < 1e-3 * moved + 1e-12, (dX, moved)
     assert g.info()["device_error"] == 0
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_spheres2_full_size_one_step_from_gpu_state(q):
+    """The two-sphere workload at full size (128 x 128 x 256, FP32) with D3Q19 and with the paper's
+    D3Q27 (Sec. 3.2.1), held bodies, kinetics off: one step from the GPU's state against the oracle."""
+    import oracle
+
+    w = workloads.spheres2(seed=0, prec="fp32")
+    params = dict(w.params, mpf_kinetics=0, q=q)
+    g = cbl.Sim(w.nx, w.ny, w.nz, **params)
+    workloads.build(g, w)
+    g.set_fixed([True] * len(w.bodies))
+    g.step(60)
+    o = oracle.Oracle(w.nx, w.ny, w.nz, **{k: v for k, v in params.items() if k != "prec"})
+    workloads.build(o, w)
+    o.set_fixed([True] * len(w.bodies))
+    cg, _ = g.velocity_set()
+    co, _ = o.velocity_set()
+    assert len(cg) == q
+    perm = [int(np.flatnonzero((co == cg[i]).all(axis=1))[0]) for i in range(len(cg))]
+    f = g.populations()
+    fo = np.empty_like(f)
+    fo[perm] = f
+    o.set_populations(fo)
+    g.step(1)
+    o.step(1)
+    fg = g.populations()
+    fo = o.populations()[perm]
+    err_f = float(np.abs(fg - fo).max() / np.abs(fo).max())
+    Fg, _, _ = g.body_forces()
+    Fo, _, _ = o.body_forces()
+    err_F = float(np.abs(Fg - Fo).max() / np.abs(Fo).max())
+    print("two spheres D3Q%d, one step from the GPU state: populations %.2e, force %.2e" % (q, err_f, err_F))
+    assert err_f < 1e-5 and err_F < 1e-3, (err_f, err_F)
