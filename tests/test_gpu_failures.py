@@ -9,6 +9,8 @@
   loop depends on a value).
 * More overlapping body tiles than a neighbour list holds: device error bit 1 is set, read by
   cbl_info.
+* A covered node whose mass has no fluid receiver (two plates closing on a liquid layer): device
+  error bit 2.
 """
 import ctypes
 import math
@@ -139,3 +141,22 @@ def test_neighbour_list_overflow_sets_device_error():
     s = cbl.Sim(w.nx, w.ny, w.nz, **w.params)
     workloads.build(s, w)
     assert s.info()["device_error"] & 2
+
+
+def test_lost_refill_sets_device_error():
+    # two plates spanning x and y with a liquid-filled gap of 8 cells; moving one onto the other
+    # covers the gap's last fluid layer with no fluid node within sqrt(3) of it: its mass cannot be
+    # handed on (Sec. 3.2.2), which device error bit 2 records
+    n, nz = 32, 48
+    s = cbl.Sim(n, n, nz, prec="fp64")
+    half = (n / 2.0 + 2.0, n / 2.0 + 2.0, 1.5)
+    c = (n - 1) / 2.0
+    s.add_body("box", center=(c, c, 12.0), half=half, mass_density=4.0, wetting_rho=1.0, fixed=True)
+    s.add_body("box", center=(c, c, 23.0), half=half, mass_density=4.0, wetting_rho=1.0, fixed=True)
+    s.init_fluid(1.9, 0.12, np.ones((nz, n, n), np.uint8))
+    s.step(2)
+    assert s.info()["device_error"] == 0
+    X = s.bodies()["X"].copy()
+    X[1, 2] -= 8.0
+    s.move_bodies(X)
+    assert s.info()["device_error"] & 4
