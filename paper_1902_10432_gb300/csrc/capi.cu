@@ -65,6 +65,7 @@ struct cbl_ctx {
   int acc_ty = 8;          // y extent of its regions (8 or 16; x extent 32)
   int acc_sz_req = 0;      // requested z extent of a region (0 = derived)
   int acc_sz = 0;          // z extent in use
+  int acc_attr_ty = 0;     // region depth whose kernel has its shared-memory limit set
   void *psi2 = nullptr, *rhop = nullptr;
   bool psi_valid = false;  // psi of the current step is in place (else a whole-lattice density pass first)
   int fused_tz = 0;      // > 0: the density and the bulk collision run as one fused pass (k_fused)
@@ -577,11 +578,14 @@ static cbl_status acc_prepare(cbl_ctx* ctx) {
   if (!ctx->rhop) ctx->rhop = dalloc(ctx, N * el);
   if (!ctx->psi2 || !ctx->rhop) return fail(ctx, CBL_ERR_OOM, "device allocation failed (accumulating pass)");
   ctx->acc_sz = ctx->acc_sz_req > 0 ? ctx->acc_sz_req : ctx->ops.acc_sz(ctx->lat, ctx->prec, ctx->acc_ty, 2);
-  // a zero-plane call outside any capture sets the kernel's dynamic shared-memory limit
-  Lat none = ctx->lat;
-  none.nz = 0;
-  CK(ctx->ops.lbm_acc(ctx->prec, none, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->rhop, ctx->db,
-                      ctx->mass_part, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->acc_ty, 1, ctx->s));
+  if (ctx->acc_attr_ty != ctx->acc_ty) {
+    // a zero-plane call outside any capture sets the kernel's dynamic shared-memory limit
+    Lat none = ctx->lat;
+    none.nz = 0;
+    CK(ctx->ops.lbm_acc(ctx->prec, none, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->rhop, ctx->db,
+                        ctx->mass_part, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->acc_ty, 1, ctx->s));
+    ctx->acc_attr_ty = ctx->acc_ty;
+  }
   if (!ctx->psi_valid) {
     ctx->ops.lbm_step(ctx->prec, ctx->lat, ctx->fa, ctx->fb, ctx->flags, ctx->psi, ctx->psi2, ctx->db, ctx->mass_part,
                       (unsigned)ctx->block_x, ctx->st, ctx->diag_rho, ctx->diag_vel, ctx->pp, ctx->nbuf, ctx->blist,
