@@ -28,13 +28,17 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def test_tetra4_full_size_one_step_from_gpu_state():
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_tetra4_full_size_one_step_from_gpu_state(variant):
+    # variant: the lattice-Boltzmann pass (0 split, the default and the bench's; 1 fused; 2
+    # accumulating), all three against the same oracle step
     import oracle
 
     w = workloads.tetra4(seed=0, prec="fp32")
     assert (w.nx, w.ny, w.nz) == (256, 256, 256)
     params = dict(w.params, mpf_kinetics=0)
     g = cbl.Sim(w.nx, w.ny, w.nz, **params)
+    g.set_option("lbm_variant", variant)
     workloads.build(g, w)
     g.set_fixed([True] * len(w.bodies))
     g.step(60)
@@ -68,8 +72,8 @@ def test_tetra4_full_size_one_step_from_gpu_state():
     Fg, _, _ = g.body_forces()
     Fo, _, _ = o.body_forces()
     err_F = float(np.abs(Fg - Fo).max() / np.abs(Fo).max())
-    print("256^3 one step from the GPU state: populations %.2e, density %.2e, velocity %.2e, force %.2e"
-          % (err_f, err_rho, err_vel, err_F))
+    print("256^3 one step from the GPU state (pass %d): populations %.2e, density %.2e, velocity %.2e, "
+          "force %.2e" % (variant, err_f, err_rho, err_vel, err_F))
     assert err_f < 1e-5 and err_rho < 1e-5, (err_f, err_rho)
     assert err_vel < 1e-3, err_vel
     assert err_F < 1e-3, err_F
