@@ -63,7 +63,7 @@ def source_hash():
     import hashlib
 
     h = hashlib.sha1()
-    for name in ("lbm.cu", "cbl_dev.cuh", "periodic.h"):
+    for name in ("lbm.cu", "cbl_dev.cuh", "periodic.h", "weights.h"):
         with open(os.path.join(ROOT, "paper_1902_10432_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "periodic.h"
+#include "weights.h"
 
 namespace cbl {
 

@@ -171,6 +171,17 @@ __device__ __forceinline__ void pull(const S* __restrict__ f, const uint16_t* __
 // S_i = (rho w_i / tau)(1 + 4.5 (c.v)^2 - 1.5 v.v) + (1 - 1/2tau) w_i (9 (c.v)(c.F) - 3 v.F),
 // A_i = 3 w_i ((rho / tau) c.v + (1 - 1/2tau) c.F).
 // Post-collision values of one cell, handed to sink(i, v) in direction order.
+// Weight w_i in the arithmetic type of a kernel: the FP32 set whose values sum to exactly 1 (so the
+// equilibria of an FP32 collision add no mass, weights.h), or the FP64 value.
+template <typename R>
+__device__ __forceinline__ R wgt(int i) {
+  if constexpr (sizeof(R) == 8) {
+    return (R)w_of(i);
+  } else {
+    return wf_of(i);
+  }
+}
+
 template <typename R, typename Sink>
 __device__ __forceinline__ void bgk_values(const R fi[Q], R rho, R vx, R vy, R vz, R Fx, R Fy, R Fz, R tau,
                                            const Sink& sink) {
@@ -182,12 +193,12 @@ __device__ __forceinline__ void bgk_values(const R fi[Q], R rho, R vx, R vy, R v
   const R vF = vx * Fx + vy * Fy + vz * Fz;
   const R base = (R)1 - (R)1.5 * uu;   // even part without (c.v)^2
   const R fv = -(R)3 * pref * vF;       // even forcing part without (c.v)(c.F)
-  sink(0, keep * fi[0] + (R)w_of(0) * (ro * base + fv));
+  sink(0, keep * fi[0] + wgt<R>(0) * (ro * base + fv));
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const R cu = (R)cx_of(i) * vx + (R)cy_of(i) * vy + (R)cz_of(i) * vz;
     const R cF = (R)cx_of(i) * Fx + (R)cy_of(i) * Fy + (R)cz_of(i) * Fz;
-    const R w = (R)w_of(i);
+    const R w = wgt<R>(i);
     const R sym = w * (ro * (base + (R)4.5 * cu * cu) + fv + (R)9 * pref * cu * cF);
     const R anti = (R)3 * w * (ro * cu + pref * cF);
     sink(i, keep * fi[i] + sym + anti);
@@ -1383,7 +1394,7 @@ __global__ void __launch_bounds__(256) k_refill(S* __restrict__ fa, S* __restric
 #pragma unroll
                   for (int i = 0; i < Q; ++i) {
                     const R cu = (R)cx_of(i) * ux + (R)cy_of(i) * uy + (R)cz_of(i) * uz;
-                    add[i] += rho * (R)w_of(i) * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu) * inv;
+                    add[i] += rho * wgt<R>(i) * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu) * inv;
                   }
                 }
 #pragma unroll
