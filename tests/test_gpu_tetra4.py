@@ -11,13 +11,18 @@ central 64^3 crop and on the whole lattice.
   tests/golden/tetra4_half_storage.json, written by tests/golden/make_tetra4_storage.py from the
   oracle alone) deviates from the FP64 oracle by what the GPU path does, within a factor of 2 at
   every step: the kernels add nothing measurable to it.
-* FP32: the same storage model in FP32 stays within ~3e-7 of FP64 up to step 300, so FP32 storage is
-  not what limits the FP32 path; its FP32 arithmetic is. The FP32 path is within the contract's
-  tolerances (1e-4 on density and velocity, 1e-3 on force) at step 150, and its error then grows with
-  the four bodies' coupled motion (measured on the crop: density 5.9e-5 and velocity 4.4e-4 at step
-  300, 1.7e-3 and 1.8e-2 at 500); those values, with a margin of 3, are the stated bounds here.
+* FP32: within the contract's tolerances (1e-4 on density and velocity, 1e-3 on force) at steps 150
+  and 300 (measured 2e-6 and 8e-6 on density). The free bodies' positions then differ from the
+  oracle's by ~3e-6 lattice units, and a cell whose fluid phase crosses the obstacle threshold
+  (Sec. 3.2.2) changes its flag one step earlier or later than in the oracle: the cover or uncover
+  event and its refill are a step apart, and the fields differ locally by O(1) for a few tens of
+  steps (measured: one flag apart at step 319, velocity error 1.0 at step 320, 7e-3 at step 340).
+  The FP64 method does the same: the GPU's FP64 path with the body centres moved by 3e-6 at the start
+  departs from its unmoved run by more than the FP32 path does at step 500 (the test measures both;
+  moved by 1e-9 it stays at 1e-11). So after step 300 the FP32 comparison is bounded by that spread
+  of the method itself, and by its measured values with a margin of 3.
 
-The full-size comparison (256^3, the oracle on the whole lattice for 500 steps, ~8 minutes on 16
+The full-size comparison (256^3, the oracle on the whole lattice for 500 steps, ~15 minutes on 16
 cores) is kept as a long test (CBL_LONG_TESTS=1).
 """
 import json
@@ -34,8 +39,10 @@ pytestmark = pytest.mark.gpu
 N_HALF = 128
 STEPS_HALF = (150, 300, 500)
 STORAGE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tetra4_half_storage.json")
-# stated FP32 bounds on the crop (measured x 3) after the contract's step-150 check
-FP32_BOUNDS = {300: dict(rho=2e-4, vel=1.5e-3, force=5e-3), 500: dict(rho=5e-3, vel=6e-2, force=0.12)}
+# stated FP32 bounds at step 500 on the crop (measured 2.1e-4, 8.1e-3, 8.1e-3, x 3)
+FP32_BOUNDS_500 = dict(rho=6e-4, vel=2.5e-2, force=2.5e-2)
+# body-centre offset of the FP64 spread run: the FP32 path's position difference near step 300
+DX_SPREAD = 3e-6
 
 
 def _crop_errors(g, o, n, h=32):
@@ -66,9 +73,11 @@ def half_scale():
     o = oracle.Oracle(w.nx, w.ny, w.nz, **{k: v for k, v in w.params.items() if k != "prec"})
     workloads.build(o, w)
     gpu = {}
-    for prec in ("fp64", "fp32", "fp16dev"):
-        g = cbl.Sim(w.nx, w.ny, w.nz, **dict(w.params, prec=prec))
+    for prec in ("fp64", "fp32", "fp16dev", "fp64_moved"):
+        g = cbl.Sim(w.nx, w.ny, w.nz, **dict(w.params, prec=prec.split("_")[0]))
         workloads.build(g, w)
+        if prec == "fp64_moved":
+            g.move_bodies(g.bodies()["X"] + DX_SPREAD)
         gpu[prec] = g
     out = {}
     done = 0
@@ -94,16 +103,21 @@ def test_tetra4_half_fp64_matches_oracle(half_scale):
 
 
 def test_tetra4_half_fp32_within_contract_then_stated_bounds(half_scale):
-    e150 = half_scale[150]["fp32"]
-    assert e150["device_error"] == 0
-    f = e150["full"]
-    assert f["flag_mismatch"] == 0 and f["rho"] < 1e-4 and f["vel"] < 1e-4 and f["force"] < 1e-3, f
-    for s in (300, 500):
+    for s in (150, 300):
         e = half_scale[s]["fp32"]
-        assert e["device_error"] == 0 and e["crop"]["flag_mismatch"] == 0
-        b = FP32_BOUNDS[s]
-        assert e["crop"]["rho"] < b["rho"] and e["crop"]["vel"] < b["vel"], (s, e["crop"])
-        assert e["full"]["force"] < b["force"], (s, e["full"])
+        assert e["device_error"] == 0
+        f = e["full"]
+        assert f["flag_mismatch"] == 0 and f["rho"] < 1e-4 and f["vel"] < 1e-4 and f["force"] < 1e-3, (s, f)
+    e = half_scale[500]["fp32"]
+    m = half_scale[500]["fp64_moved"]
+    assert e["device_error"] == 0 and e["crop"]["flag_mismatch"] == 0
+    b = FP32_BOUNDS_500
+    assert e["crop"]["rho"] < b["rho"] and e["crop"]["vel"] < b["vel"], e["crop"]
+    assert e["full"]["force"] < b["force"], e["full"]
+    # the spread of the FP64 method under a 3e-6 shift of the body centres bounds the FP32 path
+    # (whole lattice: the flag events need not fall inside the crop)
+    for k in ("rho", "vel", "force"):
+        assert e["full"][k] <= m["full"][k], (k, e["full"][k], m["full"][k])
 
 
 def test_tetra4_half_fp16dev_error_is_the_storage(half_scale):
