@@ -48,9 +48,10 @@ typedef enum {
 } cbl_status;
 
 /* Storage precision of the lattice-Boltzmann populations. Arithmetic is FP64 for CBL_FP64 and FP32
- * otherwise. CBL_FP16DEV stores h_i = f_i - w_i in binary16 (w_i rounded to binary16), halving
- * the population bytes. Phase fields, body reductions and the rigid-body integrator are FP64 in
- * every mode. */
+ * otherwise; the FP32 collision uses FP32 weights whose sum is exactly 1 (each within 2 ulp of w_i),
+ * so that its equilibria add no mass (Sec. 3.2.1). CBL_FP16DEV stores h_i = f_i - w_i in binary16
+ * (w_i rounded to binary16), halving the population bytes. Phase fields, body reductions and the
+ * rigid-body integrator are FP64 in every mode. */
 typedef enum { CBL_FP64 = 0, CBL_FP32 = 1, CBL_FP16DEV = 2 } cbl_prec;
 
 typedef struct {
