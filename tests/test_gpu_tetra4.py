@@ -1,6 +1,6 @@
 """Four-sphere cluster (Sec. 4.3.2 set-up): the CUDA path against the FP64 oracle.
 
-At half scale (128^3, R = 12, surface gap 4), in the driver's GPU suite: one oracle run, and the
+At half scale (128^3, R = 12, surface gap 4), in the default GPU suite: one oracle run, and the
 CUDA path with FP64, FP32 and binary16-deviation storage, compared at steps 150, 300 and 500 on the
 central 64^3 crop and on the whole lattice.
 
