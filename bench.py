@@ -231,8 +231,8 @@ def bench_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": describe(full, args.q), "cells": full.ncells, "inputs_vs_l2": "CPU run"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-                             "sample": "%s: %d time steps after %d warm-up steps" % (describe(w, args.q), args.steps,
-                                                                                  args.warmup)},
+                             "sample": "%s: %d time steps of the FP64 oracle (arithmetic and storage FP64) "
+                                       "after %d warm-up steps" % (describe(w, args.q), args.steps, args.warmup)},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
